@@ -1,0 +1,143 @@
+"""The benchmark workloads as seeded problem + solver settings.
+
+Each Workload bundles one Helmholtz problem (grid, omega, kappa, gamma,
+sources) with the solver settings both the oracle and the CUDA path are run
+with (levels, shift alpha, patch type, intergrid scheme, tolerance).  The
+damping per level is NOT part of a workload: each implementation carries its
+own copy of the paper's damping table.
+
+  config1  2D homogeneous 129^2, ABC, centre source, plain FP64, tol 1e-7
+  config2  2D layered 1025^2 (seed 0), 20-cell absorbing layer, tol 1e-6
+  config3  3D geophysical 257^3 (seed 0), 16-cell layer, surface source
+  config4  2D homogeneous 513^2, 64 seeded sources x 3 frequencies (seed 1)
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field, replace
+
+import numpy as np
+
+from . import media
+
+
+@dataclass
+class Workload:
+    name: str
+    dim: int
+    n: int                      # nodes per axis; h = 1/(n-1)
+    omega: float
+    kappa: np.ndarray           # slowness per node, float64, shape (n,)*dim
+    gamma: np.ndarray           # attenuation per node, float64
+    sources: list               # node coordinates (x, y[, z]) of unit point sources
+    levels: int
+    alpha: float                # complex shift parameter
+    patch: str                  # 'plus' | 'element' | 'rb' | 'full' | 'jacobi'
+    intergrid: str              # 'leveldep' | 'cubic' | 'mixed' | 'linear'
+    tol: float
+    precision: str = "mixed"    # 'fp64' | 'mixed'
+    patch_coarse: str | None = None   # patch on levels >= 2 (None: same as fine)
+    restart: int = 5
+    nu1: int = 1
+    nu2: int = 1
+    max_iter: int = 2000
+    layer_cells: int = 0
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def h(self) -> float:
+        return 1.0 / (self.n - 1)
+
+    @property
+    def shape(self):
+        return (self.n,) * self.dim
+
+    @property
+    def nodes(self) -> int:
+        return self.n ** self.dim
+
+    def rhs(self, k: int = 0) -> np.ndarray:
+        """Point source k as a flattened complex128 vector (unscaled q)."""
+        return media.point_source(self.shape, self.sources[k], self.h).ravel()
+
+    def rhs_block(self) -> np.ndarray:
+        """All sources as an [nodes, nsrc] complex128 array (source innermost)."""
+        return np.stack([self.rhs(k) for k in range(len(self.sources))], axis=1)
+
+
+def _centre(n, dim):
+    return tuple([(n - 1) // 2] * dim)
+
+
+def config1(n: int = 129, levels: int = 4, **kw) -> Workload:
+    """2D homogeneous, kappa = 1, 10 points per wavelength, gamma/omega = 0.01,
+    first-order ABC on all sides (no layer), centre source, plain FP64, tol 1e-7."""
+    h = 1.0 / (n - 1)
+    omega = media.omega_for_ppw(10.0, h, v_min=1.0)
+    kappa = media.homogeneous_kappa(n, 2, 1.0)
+    gamma = media.absorbing_gamma(kappa.shape, omega, 0.01, 0)
+    w = Workload(name=f"2d-homogeneous-{n}", dim=2, n=n, omega=omega, kappa=kappa,
+                 gamma=gamma, sources=[_centre(n, 2)], levels=levels, alpha=0.25,
+                 patch="plus", intergrid="leveldep", tol=1e-7, precision="fp64")
+    return replace(w, **kw)
+
+
+def config2(n: int = 1025, levels: int = 6, seed: int = 0, layer_cells: int = 20, **kw) -> Workload:
+    """2D layered medium (seeded), 10 ppw at v_min = 1.5, gamma/omega = 0.01,
+    absorbing layer + ABC, centre source, tol 1e-6."""
+    h = 1.0 / (n - 1)
+    omega = media.omega_for_ppw(10.0, h, v_min=1.5)
+    kappa = media.layered_kappa_2d(n, seed)
+    gamma = media.absorbing_gamma(kappa.shape, omega, 0.01, layer_cells)
+    w = Workload(name=f"2d-layered-{n}", dim=2, n=n, omega=omega, kappa=kappa, gamma=gamma,
+                 sources=[_centre(n, 2)], levels=levels, alpha=0.25, patch="plus",
+                 intergrid="leveldep", tol=1e-6, precision="mixed", layer_cells=layer_cells,
+                 meta={"seed": seed})
+    return replace(w, **kw)
+
+
+def config3(n: int = 257, levels: int = 5, seed: int = 0, layer_cells: int = 16, **kw) -> Workload:
+    """3D geophysical-like medium (seeded), 8 ppw at v_min = 1.5,
+    gamma/omega = 0.01, absorbing layer + ABC, source just below the top layer."""
+    h = 1.0 / (n - 1)
+    omega = media.omega_for_ppw(8.0, h, v_min=1.5)
+    kappa = media.geophysical_kappa_3d(n, seed)
+    gamma = media.absorbing_gamma(kappa.shape, omega, 0.01, layer_cells)
+    c = (n - 1) // 2
+    src = (c, c, min(layer_cells + 1, n - 1))
+    w = Workload(name=f"3d-geophysical-{n}", dim=3, n=n, omega=omega, kappa=kappa, gamma=gamma,
+                 sources=[src], levels=levels, alpha=0.5, patch="element",
+                 intergrid="linear", tol=1e-6, precision="mixed", layer_cells=layer_cells,
+                 meta={"seed": seed})
+    return replace(w, **kw)
+
+
+def config4(n: int = 513, levels: int = 5, nsrc: int = 64, seed: int = 1,
+            ppws=(8.0, 10.0, 12.0), **kw) -> list:
+    """Batched multi-RHS: config 1's medium at n^2, `nsrc` seeded interior
+    sources, one Workload per frequency (8, 10, 12 points per wavelength)."""
+    h = 1.0 / (n - 1)
+    kappa = media.homogeneous_kappa(n, 2, 1.0)
+    srcs = media.random_interior_nodes(n, 2, nsrc, seed)
+    out = []
+    for ppw in ppws:
+        omega = media.omega_for_ppw(ppw, h, v_min=1.0)
+        gamma = media.absorbing_gamma(kappa.shape, omega, 0.01, 0)
+        w = Workload(name=f"2d-homogeneous-{n}-ppw{ppw:g}", dim=2, n=n, omega=omega,
+                     kappa=kappa, gamma=gamma, sources=list(srcs), levels=levels, alpha=0.25,
+                     patch="plus", intergrid="leveldep", tol=1e-6, precision="mixed",
+                     meta={"seed": seed, "ppw": ppw})
+        out.append(replace(w, **kw))
+    return out
+
+
+def small_variant(which: str, n: int, levels: int, **kw) -> Workload:
+    """A scaled-down instance of a config's generator (same recipe, smaller grid)."""
+    if which == "config1":
+        return config1(n=n, levels=levels, **kw)
+    if which == "config2":
+        layer = kw.pop("layer_cells", max(4, (20 * (n - 1)) // 1024))
+        return config2(n=n, levels=levels, layer_cells=layer, **kw)
+    if which == "config3":
+        layer = kw.pop("layer_cells", max(3, (16 * (n - 1)) // 256))
+        return config3(n=n, levels=levels, layer_cells=layer, **kw)
+    raise ValueError(which)
