@@ -1,0 +1,305 @@
+#!/usr/bin/env python
+"""Benchmark: FGMRES(5) + Vanka-smoothed shifted-Laplacian V(1,1) solves/s.
+
+Workload (default): the 2D layered medium, 1025 x 1025 nodes (h = 1/1024),
+seeded (seed 0), 10 points per wavelength at v_min = 1.5, gamma/omega =
+0.01, 20-cell absorbing layer + first-order ABC, centre point source,
+6-level V(1,1) with RB-patch additive Vanka (level-dependent intergrid,
+shift alpha = 0.1), complex-FP32 V-cycle inside FP64 FGMRES(5), tol 1e-6.
+
+One step = one complete solve (zero initial guess to relative residual
+1e-6) through the C ABI on device-resident inputs; the hierarchy is set up
+once before timing (the paper times the Krylov iterations only).  The
+working set per solve (~0.5 GB) exceeds the 129 MB L2, so no flush is
+needed between steps.  e2e repeats the step with the source in pinned host
+memory and the solution returned to host memory (copies inside the timed
+region).  The plain FP64 GPU path is timed beside it, and the FP64 CPU
+oracle on a bounded sample of the same solve (cpu_baseline).
+
+Multi-GPU: independent replicas (one solve stream per rank, no data-path
+collective); value = all ranks' solves / max-over-ranks time.
+`--impl reference` times the FP64 CPU oracle instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "solves/s @ rel-res 1e-6 (mixed vs plain FP64); Vanka DOF/s; p50/p99 latency"
+UNIT = "solves/s"
+
+
+def _env_rank():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    except Exception:  # noqa: BLE001
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:  # noqa: BLE001
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=2)
+            except Exception:  # noqa: BLE001
+                self.proc.kill()
+
+    def summary(self):
+        import statistics
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_solver(w, precision, stream=None):
+    from paper_2511_16808_gb300.solver import HelmholtzSolver
+    return HelmholtzSolver(w.dim, [w.n] * w.dim, w.kappa.ravel(), w.omega, w.gamma.ravel(), w.alpha,
+                           w.levels, patch=w.patch, intergrid=w.intergrid, precision=precision,
+                           tol=w.tol, restart=w.restart, nu1=w.nu1, nu2=w.nu2, max_iter=w.max_iter,
+                           patch_coarse=w.patch_coarse, stream=stream)
+
+
+def time_solves(torch, solver, q, p, steps, stream):
+    """Device time (ms) of `steps` consecutive solves with CUDA events on the launching stream."""
+    from paper_2511_16808_gb300 import hz
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    start.record(stream)
+    infos = []
+    for _ in range(steps):
+        ok, inf = hz.hz_solve(solver.ctx, q, p, 1, stream)
+        infos.append(inf[0])
+    end.record(stream)
+    end.synchronize()
+    return start.elapsed_time(end), infos
+
+
+def cpu_baseline_sample(workload: str, iters: int, ref_iters: int):
+    """Run the oracle in a fresh single-threaded process on a bounded sample
+    (setup, then `iters` FGMRES iterations of the same solve)."""
+    code = f"""
+import os, sys, time, json
+sys.path.insert(0, {ROOT!r})
+import workloads
+from oracle import solver, fgmres
+w = getattr(workloads, {workload!r})()
+pr = solver.from_workload(w)
+q = pr.rhs(w.rhs(0))
+t = time.perf_counter()
+x, info = fgmres.fgmres(pr.A, q, pr.precond, m=w.restart, tol=w.tol, max_iter={iters})
+dt = time.perf_counter() - t
+print(json.dumps({{"s_per_iter": dt / info.iters, "iters": info.iters}}))
+"""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+    if r.returncode != 0:
+        return None
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    s_per_solve = d["s_per_iter"] * ref_iters
+    return {"value": 1.0 / s_per_solve, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{workload}: setup untimed, then {d['iters']} FGMRES iterations of the same "
+                      f"solve timed ({d['s_per_iter'] * 1e3:.1f} ms/iteration) and scaled by the "
+                      f"{ref_iters} iterations a full solve takes"}
+
+
+def run_ours(args):
+    import torch
+    import workloads
+
+    rank, world, local = _env_rank()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    w = getattr(workloads, args.config)()
+    stream = torch.cuda.current_stream()
+    solver = make_solver(w, "mixed", stream)
+    q = torch.tensor(w.rhs(0), device="cuda")
+    p = torch.empty_like(q)
+    for _ in range(args.warmup):
+        solver.solve(q, p)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    with ClockSampler(local) as clk:
+        ms, infos = time_solves(torch, solver, q, p, args.steps, stream)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    iters = infos[-1].iters
+    value = world * args.steps / (ms / 1e3)
+
+    # e2e through the C ABI with host buffers (pinned source, host solution)
+    from paper_2511_16808_gb300 import hz
+    qh = torch.tensor(w.rhs(0)).pin_memory()
+    ph = torch.empty_like(qh).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    hz.hz_solve(solver.ctx, qh, ph, 1, stream)
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(e2e_steps):
+        hz.hz_solve(solver.ctx, qh, ph, 1, stream)
+    t1.record(stream)
+    t1.synchronize()
+    e2e_ms = t0.elapsed_time(t1)
+
+    out = None
+    if rank == 0:
+        # plain FP64 GPU path on the same workload
+        fp64 = None
+        if not args.no_fp64:
+            s64 = make_solver(w, "fp64", stream)
+            s64.solve(q, p)
+            ms64, inf64 = time_solves(torch, s64, q, p, max(1, min(args.steps, 2)), stream)
+            fp64 = {"value": max(1, min(args.steps, 2)) / (ms64 / 1e3), "unit": UNIT,
+                    "iters": inf64[-1].iters, "relres_true": inf64[-1].relres_true,
+                    "ms_per_solve": ms64 / max(1, min(args.steps, 2))}
+            s64.close()
+        vdofs = None
+        cpu = None
+        if not args.no_cpu_baseline:
+            cpu = cpu_baseline_sample(args.config, args.cpu_iters, iters)
+        peak, src = _peaks()
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c64 V-cycle / c128 FGMRES",
+            "data": "synthetic (seeded layered medium)",
+            "config": {"workload": w.name, "nodes": w.nodes, "levels": w.levels, "patch": w.patch,
+                       "intergrid": w.intergrid, "alpha": w.alpha, "tol": w.tol, "restart": w.restart,
+                       "omega": w.omega, "layer_cells": w.layer_cells,
+                       "l2": "working set per solve > 129 MB L2 (no flush)",
+                       "parallelism": f"replicas x{world}"},
+            "iters": iters, "relres_true": infos[-1].relres_true,
+            "unknowns_vcycles_per_s": value * w.nodes * iters,
+            "e2e": {"value": e2e_steps / (e2e_ms / 1e3), "unit": UNIT,
+                    "h2d_bytes_per_step": 16 * w.nodes, "d2h_bytes_per_step": 16 * w.nodes},
+            "plain_fp64": fp64,
+            "clocks": clk.summary(),
+            "roofline": None,
+            "cpu_baseline": cpu,
+            "gpu_launches": None,
+            "peak_source": src,
+            "vanka_dof_per_s": vdofs,
+        }
+    solver.close()
+    if dist:
+        dist.destroy_process_group()
+    return out
+
+
+def run_reference(args):
+    rank, world, local = _env_rank()
+    if rank != 0:
+        return None
+    import workloads
+    from oracle import fgmres, solver
+    w = getattr(workloads, args.config)()
+    gold = os.path.join(ROOT, "tests", "golden", f"oracle_{args.config}.json")
+    with open(gold) as f:
+        ref_iters = json.load(f)["iters"]
+    pr = solver.from_workload(w)
+    q = pr.rhs(w.rhs(0))
+    per_step = args.ref_iters_per_step
+    times = []
+    for k in range(args.warmup + args.steps):
+        t = time.perf_counter()
+        fgmres.fgmres(pr.A, q, pr.precond, m=w.restart, tol=w.tol, max_iter=per_step)
+        if k >= args.warmup:
+            times.append(time.perf_counter() - t)
+    s_per_iter = sum(times) / (len(times) * per_step)
+    value = 1.0 / (s_per_iter * ref_iters)
+    sample = (f"{w.name}: each step = {per_step} FGMRES iterations of the oracle solve "
+              f"(setup untimed), scaled by the {ref_iters} iterations of a full oracle solve")
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * s_per_iter * ref_iters,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+            "data": "synthetic (seeded layered medium)",
+            "config": {"workload": w.name, "nodes": w.nodes, "levels": w.levels},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="config2")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-iters", type=int, default=25)
+    ap.add_argument("--ref-iters-per-step", type=int, default=5)
+    args = ap.parse_args()
+    out = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if out is not None:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,209 @@
+/*
+ * hz.h — C ABI of the GB300 (sm_103a) Vanka-smoothed shifted-Laplacian
+ * multigrid / FGMRES solver for the finite-difference Helmholtz equation.
+ *
+ * Method: Yovel, He & Treister, "Vanka-smoothed Shifted Laplacian multigrid
+ * preconditioners for the Helmholtz equations" (arXiv 2511.16808).
+ *
+ *   Eq. (1)        -Lap p - omega^2 kappa^2 (1 - i gamma/omega) p = q
+ *   Eq. (shift)    H_s = H + i alpha omega^2 M   (shift adds damping)
+ *   Section 3.1    Galerkin coarse operators R H P, level-dependent intergrid
+ *   Section 3.2/3  additive Vanka smoother, Eq. (smoother), boundary patches
+ *   Algorithm 1    two-grid cycle, applied recursively as a V-cycle
+ *   Section 2.3    flexible GMRES(m) with the cycle as right preconditioner
+ *
+ * Discretisation (Section 2.1, second-order variant): 5-point (2D) or
+ * 7-point (3D) stencil on a nodal grid with spacing h; boundary nodes carry
+ * the first-order absorbing condition dp/dn = -i omega kappa p through a
+ * ghost point, and every boundary row is halved once per boundary axis, so
+ * the matrix is complex symmetric.  The right-hand side is scaled the same
+ * way (q_hat = prod_a w_a * q, w_a = 1/2 on the two end nodes of axis a).
+ *
+ * Conventions for every entry point
+ *  - Fields are interleaved complex (re, im) arrays, node-major with x
+ *    fastest: node index (k*n_y + j)*n_x + i.  With nrhs > 1 the right-hand
+ *    side index is innermost: element (node*nrhs + r).
+ *  - "c128" fields are double pairs, "c64" fields float pairs.
+ *  - Pointers documented "host or device" may be either; the library finds
+ *    out with cudaPointerGetAttributes and stages host data itself.  All other
+ *    field pointers are device pointers.
+ *  - The caller owns every buffer it passes.  hz_setup copies kappa and gamma;
+ *    the context owns the hierarchy and the Krylov workspace.
+ *  - Every call returns an hz_status; no C++ exception crosses the ABI and
+ *    nothing aborts.  hz_last_error() gives the last message of this thread.
+ *  - One context per stream: a context used concurrently from two host threads
+ *    returns HZ_ERR_BUSY to the second.
+ *  - Inputs are never modified.
+ */
+#ifndef HZ_H
+#define HZ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HZ_ABI_VERSION 1
+#define HZ_MAX_LEVELS 10
+#define HZ_MAX_STENCIL 343   /* 7^3: cubic Galerkin stencils in 3D */
+
+typedef enum {
+  HZ_OK = 0,
+  HZ_ERR_INVALID_ARG = 1,
+  HZ_ERR_OOM = 2,
+  HZ_ERR_CUDA = 3,
+  HZ_ERR_NOT_CONVERGED = 4,   /* max_iter reached; info and the last iterate are filled */
+  HZ_ERR_BREAKDOWN = 5,       /* FGMRES breakdown with a non-converged residual */
+  HZ_ERR_TIMEOUT = 6,         /* a bounded device-side wait gave up */
+  HZ_ERR_BUSY = 7,            /* context in use by another host thread */
+  HZ_ERR_NO_DEVICE = 8        /* no CUDA device or no sm_103 device */
+} hz_status;
+
+/* Vanka patches, Section 3.2 (HZ_PATCH_JACOBI: a 1x1 patch = damped Jacobi). */
+typedef enum {
+  HZ_PATCH_JACOBI = 0,
+  HZ_PATCH_ELEMENT = 1,  /* 2^d vertices of a cell                        */
+  HZ_PATCH_PLUS = 2,     /* node + 2d nearest neighbours                  */
+  HZ_PATCH_RB = 3,       /* node + same red-black colour in the 3^d box   */
+  HZ_PATCH_FULL = 4      /* the 3^d box                                    */
+} hz_patch;
+
+/* Intergrid schemes, Section 3.1 (Eqs. biliniearIntergrid, bicubicIntergrid,
+ * level1Intergrid, levelDepIntergrid; trilinear/tricubic in 3D). */
+typedef enum {
+  HZ_IG_LINEAR = 0,      /* linear R and P on every level                 */
+  HZ_IG_CUBIC = 1,       /* cubic R and P on every level                  */
+  HZ_IG_MIXED = 2,       /* linear R, cubic P on every level              */
+  HZ_IG_LEVELDEP = 3     /* cubic/cubic for 1->2, linear R / cubic P below */
+} hz_intergrid;
+
+typedef enum {
+  HZ_PREC_FP64 = 0,      /* V-cycle in complex FP64                        */
+  HZ_PREC_MIXED = 1      /* V-cycle in complex FP32 inside FP64 FGMRES     */
+} hz_precision;
+
+typedef struct {
+  int dim;               /* 2 or 3                                        */
+  int n[3];              /* nodes per axis (x, y, z); n[2] = 1 in 2D       */
+  double h;              /* uniform grid spacing                           */
+} hz_grid;
+
+typedef struct {
+  int levels;                        /* multigrid levels, 1..HZ_MAX_LEVELS;
+                                        (n[a]-1) divisible by 2^(levels-1) */
+  hz_patch patch[HZ_MAX_LEVELS];     /* smoother per level, [0] = finest   */
+  double damping[HZ_MAX_LEVELS];     /* damping w per level                */
+  int nu1, nu2;                      /* pre- / post-relaxations            */
+  hz_intergrid intergrid;
+  hz_precision precision;
+  int restart_m;                     /* FGMRES restart length, 1..16       */
+  double tol;                        /* relative residual ||q_hat - A p|| / ||q_hat|| */
+  int max_iter;                      /* max preconditioner applications    */
+  int nrhs_max;                      /* largest nrhs any call will pass    */
+} hz_opts;
+
+typedef struct hz_ctx hz_ctx;        /* opaque, owned by the library */
+
+typedef struct {
+  int iters;                         /* preconditioner applications        */
+  int converged;                     /* 1 if relres_true < tol             */
+  double relres_est;                 /* last Arnoldi residual estimate     */
+  double relres_true;                /* ||q_hat - A p|| / ||q_hat||, FP64  */
+} hz_info;
+
+/* Per-level description (component entry points below). */
+typedef struct {
+  int n[3];                          /* nodes per axis                     */
+  int64_t nodes;
+  int stencil_size;                  /* entries of the level's shifted operator */
+  int stencil_off[HZ_MAX_STENCIL][3];
+  int smoother_size;                 /* entries of the assembled Vanka sum */
+  int smoother_off[HZ_MAX_STENCIL][3];
+  hz_patch patch;
+  double damping;
+  int is_coarsest;
+} hz_level_desc;
+
+/* ---- library ---------------------------------------------------------- */
+
+int hz_abi_version(void);
+const char* hz_status_string(hz_status s);
+/* Message of the last failing call on this host thread ("" if none). */
+const char* hz_last_error(void);
+
+/* Defaults for dim = 2 or 3: levels 4, RB patch (2D) / element patch (3D)
+ * on every level with the damping of Table relaxParam (levels beyond the
+ * table reuse its last row), V(1,1), level-dependent intergrid (2D) /
+ * linear (3D), mixed precision, GMRES(5) (Section 5.2), tol 1e-6,
+ * max_iter 2000, nrhs_max 1. */
+hz_status hz_opts_default(int dim, hz_opts* out);
+
+/* Damping of Table relaxParam for a patch on a level (0 = finest); levels
+ * beyond the table reuse its last row, patches without a column (2D full,
+ * 3D RB and full) use the plus-patch column.  Returns NaN for a bad dim. */
+double hz_default_damping(int dim, hz_patch patch, int level);
+
+/* Device bytes a context for this grid and options will hold (for admission
+ * by an HBM budget).  Does not touch the GPU. */
+hz_status hz_setup_bytes(const hz_grid* g, const hz_opts* opts, size_t* bytes);
+
+/* Build the hierarchy (Sections 3.1-3.3) for A_s = A + i alpha omega^2 M.
+ *   kappa  slowness per node, double, host or device, n_x*n_y*n_z values
+ *   gamma  attenuation per node, double, host or device; NULL = gamma0 everywhere
+ *   omega  angular frequency (> 0); shift_alpha >= 0
+ * Errors: HZ_ERR_INVALID_ARG for bad sizes / non-finite or non-positive kappa,
+ * HZ_ERR_OOM when device memory runs out (nothing is leaked), HZ_ERR_CUDA.
+ * Work is queued on cuda_stream (a cudaStream_t, NULL = default stream); the
+ * call returns after setup has finished on the device. */
+hz_status hz_setup(const hz_grid* g, const double* kappa, double omega, const double* gamma,
+                   double gamma0, double shift_alpha, const hz_opts* opts, void* cuda_stream,
+                   hz_ctx** out);
+
+hz_status hz_destroy(hz_ctx* ctx);
+
+/* Solve A p = q_hat with FGMRES(m) preconditioned by one V(nu1,nu2)-cycle
+ * (zero initial guess, Section 5).  q: unscaled source, c128, host or device,
+ * nodes*nrhs values; p: c128 output, host or device; info: nrhs entries
+ * (host).  Returns HZ_ERR_NOT_CONVERGED (with p and info filled) when any
+ * right-hand side misses tol within max_iter. */
+hz_status hz_solve(hz_ctx* ctx, const void* q, void* p, int nrhs, hz_info* info, void* cuda_stream);
+
+/* z = V-cycle(r) with zero initial guess (Algorithm 1, recursive).
+ * r, z: c128 device arrays of nodes*nrhs values (r in the row-scaled space). */
+hz_status hz_precond_apply(hz_ctx* ctx, const void* r, void* z, int nrhs, void* cuda_stream);
+
+/* w = A v (shifted = 0) or w = A_s v (shifted = 1), FP64; c128 device arrays. */
+hz_status hz_apply_operator(hz_ctx* ctx, const void* v, void* w, int nrhs, int shifted,
+                            void* cuda_stream);
+
+/* ---- component entry points (one row of the method each) ---------------
+ * Level fields are device arrays in the context's V-cycle precision (c128
+ * for HZ_PREC_FP64, c64 for HZ_PREC_MIXED) of the level's node count. */
+
+hz_status hz_level_count(const hz_ctx* ctx, int* levels);
+hz_status hz_level_describe(const hz_ctx* ctx, int level, hz_level_desc* out);
+
+/* Copy a level's stencil planes to host as c128 [size][nodes] (plane-major):
+ * what = 0: shifted Galerkin operator A_s^level (Section 3.1); what = 1: the
+ * assembled Vanka sum sum_i V_i^T W_i H_i^{-1} V_i (Eq. smoother, no damping).
+ * The FP64 values computed at setup are returned for both precisions. */
+hz_status hz_level_export(const hz_ctx* ctx, int level, int what, void* host_out);
+
+/* r = f - A_s^level u. */
+hz_status hz_level_residual(hz_ctx* ctx, int level, const void* u, const void* f, void* r,
+                            void* cuda_stream);
+/* One additive Vanka relaxation (Eq. smoother): u += w M (f - A_s u). */
+hz_status hz_level_smooth(hz_ctx* ctx, int level, void* u, const void* f, void* cuda_stream);
+/* fc = R_level r (to level+1). */
+hz_status hz_level_restrict(hz_ctx* ctx, int level, const void* r, void* fc, void* cuda_stream);
+/* u += P_level ec (from level+1). */
+hz_status hz_level_prolong_add(hz_ctx* ctx, int level, const void* ec, void* u, void* cuda_stream);
+/* u = (A_s^L)^{-1} f on the coarsest level L (dense inverse from setup). */
+hz_status hz_coarse_solve(hz_ctx* ctx, const void* f, void* u, void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HZ_H */

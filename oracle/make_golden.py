@@ -1,0 +1,61 @@
+"""Write the oracle's full-size reference results (test infrastructure only).
+
+Runs the FP64 oracle (and nothing else) on a workload from `workloads` and
+stores, in tests/golden/oracle_<name>.json: the FGMRES iteration count and
+true relative residual at the workload's tolerance, the oracle's seconds per
+iteration on this host, and the solution of a tighter solve (tol 1e-10) at
+seeded sampled nodes, so that the full-size CUDA result can be checked one
+sampled output at a time.  Usage: python -m oracle.make_golden config2
+"""
+from __future__ import annotations
+
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+from oracle import solver  # noqa: E402
+
+SAMPLES = 4096
+
+
+def run(name: str, out_dir: str = os.path.join(ROOT, "tests", "golden")) -> dict:
+    w = getattr(workloads, name)()
+    t0 = time.time()
+    pr = solver.from_workload(w)
+    t_setup = time.time() - t0
+    q = w.rhs(0)
+    t0 = time.time()
+    p, info = pr.solve(q, tol=w.tol, m=w.restart, max_iter=w.max_iter)
+    t_solve = time.time() - t0
+    p_ref, info_ref = pr.solve(q, tol=1e-10, m=w.restart, max_iter=20 * w.max_iter)
+    rng = np.random.default_rng(12345)
+    idx = np.sort(rng.choice(w.nodes, size=min(SAMPLES, w.nodes), replace=False))
+    rec = {
+        "workload": w.name, "nodes": w.nodes, "levels": w.levels, "alpha": w.alpha,
+        "patch": w.patch, "intergrid": w.intergrid, "tol": w.tol,
+        "iters": info.iters, "relres_true": info.relres_true,
+        "iters_tight": info_ref.iters, "relres_tight": info_ref.relres_true,
+        "setup_s": t_setup, "solve_s": t_solve, "s_per_iter": t_solve / max(info.iters, 1),
+        "p_norm": float(np.linalg.norm(p)), "p_ref_norm": float(np.linalg.norm(p_ref)),
+        "err_at_tol": float(np.linalg.norm(p - p_ref) / np.linalg.norm(p_ref)),
+        "sample_idx": idx.tolist(),
+        "p_ref_re": p_ref[idx].real.tolist(), "p_ref_im": p_ref[idx].imag.tolist(),
+    }
+    path = os.path.join(out_dir, f"oracle_{name}.json")
+    with open(path, "w") as f:
+        json.dump(rec, f)
+    return rec
+
+
+if __name__ == "__main__":
+    for nm in sys.argv[1:] or ["config2"]:
+        r = run(nm)
+        print(nm, "iters", r["iters"], "tight", r["iters_tight"], "s/iter", round(r["s_per_iter"], 3))

@@ -1,0 +1,387 @@
+// C ABI of libhz (declarations and contracts in include/hz.h).
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "common.cuh"
+
+namespace hz {
+
+static thread_local std::string g_last_error;
+
+void* ctx_alloc(Ctx& c, size_t bytes) {
+  void* p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    throw Error(e == cudaErrorMemoryAllocation ? HZ_ERR_OOM : HZ_ERR_CUDA,
+                std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+  }
+  c.allocations.push_back(p);
+  return p;
+}
+
+void ctx_free_all(Ctx& c) {
+  if (c.cycle_graph) cudaGraphExecDestroy(c.cycle_graph);
+  c.cycle_graph = nullptr;
+  for (void* p : c.allocations) cudaFree(p);
+  c.allocations.clear();
+  if (c.ks_host) cudaFreeHost(c.ks_host);
+  c.ks_host = nullptr;
+}
+
+namespace {
+
+struct BusyGuard {
+  Ctx* c;
+  explicit BusyGuard(Ctx* ctx) : c(ctx) {
+    int expected = 0;
+    if (!c->busy.compare_exchange_strong(expected, 1)) throw Error(HZ_ERR_BUSY, "context in use");
+  }
+  ~BusyGuard() { c->busy.store(0); }
+};
+
+template <typename F>
+hz_status guarded(F&& f) {
+  try {
+    f();
+    g_last_error.clear();
+    return HZ_OK;
+  } catch (const Error& e) {
+    g_last_error = e.what();
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    g_last_error = "host allocation failed";
+    return HZ_ERR_OOM;
+  } catch (const std::exception& e) {
+    g_last_error = e.what();
+    return HZ_ERR_CUDA;
+  } catch (...) {
+    g_last_error = "unknown error";
+    return HZ_ERR_CUDA;
+  }
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+long long grid_nodes(const hz_grid& g) {
+  return (long long)g.n[0] * g.n[1] * (g.dim == 3 ? g.n[2] : 1);
+}
+
+void validate(const hz_grid* g, const hz_opts* o) {
+  require(g && o, "null grid or options");
+  require(g->dim == 2 || g->dim == 3, "dim must be 2 or 3");
+  require(g->h > 0 && std::isfinite(g->h), "h must be positive");
+  require(o->levels >= 1 && o->levels <= HZ_MAX_LEVELS, "levels out of range");
+  for (int a = 0; a < g->dim; ++a) {
+    require(g->n[a] >= 3, "need at least 3 nodes per axis");
+    const int div = 1 << (o->levels - 1);
+    require((g->n[a] - 1) % div == 0, "n-1 must be divisible by 2^(levels-1) on every axis");
+    require((g->n[a] - 1) / div >= 2, "coarsest grid needs at least 3 nodes per axis");
+  }
+  require(o->nu1 >= 0 && o->nu2 >= 0 && o->nu1 + o->nu2 <= 16, "nu1/nu2 out of range");
+  require(o->restart_m >= 1 && o->restart_m <= 16, "restart_m out of range");
+  require(o->tol > 0 && o->max_iter >= 1, "tol/max_iter out of range");
+  require(o->nrhs_max >= 1, "nrhs_max must be >= 1");
+  require(o->precision == HZ_PREC_FP64 || o->precision == HZ_PREC_MIXED, "bad precision");
+  require(o->intergrid >= HZ_IG_LINEAR && o->intergrid <= HZ_IG_LEVELDEP, "bad intergrid");
+  for (int l = 0; l < o->levels - 1; ++l) {
+    require(o->patch[l] >= HZ_PATCH_JACOBI && o->patch[l] <= HZ_PATCH_FULL, "bad patch");
+    require(std::isfinite(o->damping[l]), "bad damping");
+  }
+}
+
+// Table relaxParam (Section 5.2) damping per level; rows: fine, 1st, 2nd and
+// 3rd coarse level; deeper levels reuse the last row; patches with no column
+// use the plus-patch column.
+double default_damping(int dim, hz_patch p, int level) {
+  static const double d2[4][4] = {{0.89, 0.9, 0.3, 0.71},      // Jacobi
+                                  {0.97, 0.66, 0.48, 0.88},    // Element
+                                  {0.87, 0.57, 0.55, 0.74},    // Plus
+                                  {0.83, 0.5, 0.4, 0.65}};     // RB
+  static const double d3[3][4] = {{0.6, 0.4, 0.3, 0.5},        // Jacobi
+                                  {1.1, 0.7, 0.45, 0.6},       // Element
+                                  {0.92, 0.55, 0.45, 0.55}};   // Plus
+  const int r = level < 3 ? level : 3;
+  if (dim == 2) {
+    int col = p == HZ_PATCH_JACOBI ? 0 : p == HZ_PATCH_ELEMENT ? 1 : p == HZ_PATCH_RB ? 3 : 2;
+    return d2[col][r];
+  }
+  int col = p == HZ_PATCH_JACOBI ? 0 : p == HZ_PATCH_ELEMENT ? 1 : 2;
+  return d3[col][r];
+}
+
+}  // namespace
+}  // namespace hz
+
+using namespace hz;
+
+struct hz_ctx {
+  Ctx c;
+};
+
+extern "C" {
+
+int hz_abi_version(void) { return HZ_ABI_VERSION; }
+
+const char* hz_status_string(hz_status s) {
+  switch (s) {
+    case HZ_OK: return "ok";
+    case HZ_ERR_INVALID_ARG: return "invalid argument";
+    case HZ_ERR_OOM: return "out of device memory";
+    case HZ_ERR_CUDA: return "CUDA error";
+    case HZ_ERR_NOT_CONVERGED: return "not converged";
+    case HZ_ERR_BREAKDOWN: return "Krylov breakdown";
+    case HZ_ERR_TIMEOUT: return "device wait timed out";
+    case HZ_ERR_BUSY: return "context busy";
+    case HZ_ERR_NO_DEVICE: return "no suitable CUDA device";
+  }
+  return "unknown status";
+}
+
+const char* hz_last_error(void) { return g_last_error.c_str(); }
+
+hz_status hz_opts_default(int dim, hz_opts* out) {
+  return guarded([&] {
+    require(out != nullptr, "null output");
+    require(dim == 2 || dim == 3, "dim must be 2 or 3");
+    std::memset(out, 0, sizeof(*out));
+    out->levels = 4;
+    const hz_patch p = dim == 2 ? HZ_PATCH_RB : HZ_PATCH_ELEMENT;
+    for (int l = 0; l < HZ_MAX_LEVELS; ++l) {
+      out->patch[l] = p;
+      out->damping[l] = default_damping(dim, p, l);
+    }
+    out->nu1 = 1;
+    out->nu2 = 1;
+    out->intergrid = dim == 2 ? HZ_IG_LEVELDEP : HZ_IG_LINEAR;
+    out->precision = HZ_PREC_MIXED;
+    out->restart_m = 5;
+    out->tol = 1e-6;
+    out->max_iter = 2000;
+    out->nrhs_max = 1;
+  });
+}
+
+double hz_default_damping(int dim, hz_patch patch, int level) {
+  if ((dim != 2 && dim != 3) || level < 0) return std::nan("");
+  return default_damping(dim, patch, level);
+}
+
+hz_status hz_setup_bytes(const hz_grid* g, const hz_opts* opts, size_t* bytes) {
+  return guarded([&] {
+    validate(g, opts);
+    require(bytes != nullptr, "null output");
+    *bytes = hierarchy_bytes(*g, *opts) + krylov_bytes(*g, *opts);
+  });
+}
+
+hz_status hz_setup(const hz_grid* g, const double* kappa, double omega, const double* gamma, double gamma0,
+                   double shift_alpha, const hz_opts* opts, void* cuda_stream, hz_ctx** out) {
+  hz_ctx* h = nullptr;
+  hz_status st = guarded([&] {
+    validate(g, opts);
+    require(out != nullptr && kappa != nullptr, "null kappa or output");
+    require(omega > 0 && std::isfinite(omega), "omega must be positive");
+    require(shift_alpha >= 0 && std::isfinite(shift_alpha), "shift must be >= 0");
+    require(std::isfinite(gamma0), "gamma0 must be finite");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+      (void)cudaGetLastError();
+      throw Error(HZ_ERR_NO_DEVICE, "no CUDA device");
+    }
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    h = new hz_ctx();
+    Ctx& c = h->c;
+    c.grid = *g;
+    if (g->dim == 2) c.grid.n[2] = 1;
+    c.opts = *opts;
+    c.omega = omega;
+    c.alpha = shift_alpha;
+    c.h = g->h;
+    c.mixed = opts->precision == HZ_PREC_MIXED;
+    HZ_CUDA(cudaGetDevice(&c.dev));
+    const long long N = grid_nodes(c.grid);
+    // stage kappa / gamma on the device and check kappa
+    double* dk = (double*)ctx_alloc(c, sizeof(double) * N);
+    double* dg = gamma ? (double*)ctx_alloc(c, sizeof(double) * N) : nullptr;
+    HZ_CUDA(cudaMemcpyAsync(dk, kappa, sizeof(double) * N, cudaMemcpyDefault, s));
+    if (gamma) HZ_CUDA(cudaMemcpyAsync(dg, gamma, sizeof(double) * N, cudaMemcpyDefault, s));
+    if (!is_device_ptr(kappa)) {
+      for (long long i = 0; i < N; ++i)
+        require(std::isfinite(kappa[i]) && kappa[i] > 0, "kappa must be finite and positive");
+    }
+    build_hierarchy(c, dk, dg, gamma0, s);
+    krylov_alloc(c);
+    HZ_CUDA(cudaStreamSynchronize(s));
+  });
+  if (st != HZ_OK) {
+    if (h) {
+      ctx_free_all(h->c);
+      delete h;
+    }
+    return st;
+  }
+  *out = h;
+  return HZ_OK;
+}
+
+hz_status hz_destroy(hz_ctx* ctx) {
+  return guarded([&] {
+    if (!ctx) return;
+    cudaDeviceSynchronize();
+    ctx_free_all(ctx->c);
+    delete ctx;
+  });
+}
+
+hz_status hz_solve(hz_ctx* ctx, const void* q, void* p, int nrhs, hz_info* info, void* cuda_stream) {
+  return guarded([&] {
+    require(ctx && q && p && info, "null argument");
+    Ctx& c = ctx->c;
+    require(nrhs == 1, "this build solves one right-hand side per call");
+    BusyGuard bg(&c);
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const long long N = c.L[0].g.N;
+    const double2* qd = (const double2*)q;
+    double2* pd = (double2*)p;
+    const bool q_host = !is_device_ptr(q), p_host = !is_device_ptr(p);
+    if (q_host) {
+      if (!c.qstage) c.qstage = (double2*)ctx_alloc(c, sizeof(double2) * N);
+      HZ_CUDA(cudaMemcpyAsync(c.qstage, q, sizeof(double2) * N, cudaMemcpyHostToDevice, s));
+      qd = c.qstage;
+    }
+    if (p_host) {
+      if (!c.p) c.p = (double2*)ctx_alloc(c, sizeof(double2) * N);
+      pd = c.p;
+    }
+    fgmres_solve(c, qd, pd, info, s);
+    if (p_host) {
+      HZ_CUDA(cudaMemcpyAsync(p, pd, sizeof(double2) * N, cudaMemcpyDeviceToHost, s));
+      HZ_CUDA(cudaStreamSynchronize(s));
+    }
+    if (!info->converged) throw Error(HZ_ERR_NOT_CONVERGED, "FGMRES did not reach tol within max_iter");
+  });
+}
+
+hz_status hz_precond_apply(hz_ctx* ctx, const void* r, void* z, int nrhs, void* cuda_stream) {
+  return guarded([&] {
+    require(ctx && r && z, "null argument");
+    require(nrhs == 1, "this build applies one right-hand side per call");
+    BusyGuard bg(&ctx->c);
+    precond_apply_c128(ctx->c, (const double2*)r, (double2*)z, (cudaStream_t)cuda_stream);
+  });
+}
+
+hz_status hz_apply_operator(hz_ctx* ctx, const void* v, void* w, int nrhs, int shifted, void* cuda_stream) {
+  return guarded([&] {
+    require(ctx && v && w, "null argument");
+    require(nrhs == 1, "this build applies one right-hand side per call");
+    BusyGuard bg(&ctx->c);
+    fine_apply_f64(ctx->c, v, false, (double2*)w, shifted != 0, (cudaStream_t)cuda_stream);
+  });
+}
+
+hz_status hz_level_count(const hz_ctx* ctx, int* levels) {
+  return guarded([&] {
+    require(ctx && levels, "null argument");
+    *levels = (int)ctx->c.L.size();
+  });
+}
+
+hz_status hz_level_describe(const hz_ctx* ctx, int level, hz_level_desc* out) {
+  return guarded([&] {
+    require(ctx && out, "null argument");
+    const Ctx& c = ctx->c;
+    require(level >= 0 && level < (int)c.L.size(), "level out of range");
+    const Level& L = c.L[level];
+    std::memset(out, 0, sizeof(*out));
+    out->n[0] = L.g.nx;
+    out->n[1] = L.g.ny;
+    out->n[2] = L.g.nz;
+    out->nodes = L.g.N;
+    out->stencil_size = L.A.off.n;
+    for (int k = 0; k < L.A.off.n; ++k)
+      for (int a = 0; a < 3; ++a) out->stencil_off[k][a] = L.A.off.d[k][a];
+    out->smoother_size = L.coarsest ? 0 : L.M.off.n;
+    for (int k = 0; k < out->smoother_size; ++k)
+      for (int a = 0; a < 3; ++a) out->smoother_off[k][a] = L.M.off.d[k][a];
+    out->patch = L.patch;
+    out->damping = L.damping;
+    out->is_coarsest = L.coarsest ? 1 : 0;
+  });
+}
+
+hz_status hz_level_export(const hz_ctx* ctx, int level, int what, void* host_out) {
+  return guarded([&] {
+    require(ctx && host_out, "null argument");
+    const Ctx& c = ctx->c;
+    require(level >= 0 && level < (int)c.L.size(), "level out of range");
+    const Level& L = c.L[level];
+    require(what == 0 || (what == 1 && !L.coarsest), "nothing to export");
+    const double2* src = what == 0 ? L.A64 : L.M64;
+    const int n = what == 0 ? L.A.off.n : L.M.off.n;
+    HZ_CUDA(cudaMemcpy(host_out, src, sizeof(double2) * L.g.N * n, cudaMemcpyDeviceToHost));
+  });
+}
+
+static void check_level(const hz_ctx* ctx, int level, bool need_next) {
+  require(ctx != nullptr, "null context");
+  require(level >= 0 && level < (int)ctx->c.L.size(), "level out of range");
+  if (need_next) require(level + 1 < (int)ctx->c.L.size(), "no coarser level");
+}
+
+hz_status hz_level_residual(hz_ctx* ctx, int level, const void* u, const void* f, void* r, void* cuda_stream) {
+  return guarded([&] {
+    check_level(ctx, level, false);
+    require(u && f && r, "null argument");
+    BusyGuard bg(&ctx->c);
+    level_residual(ctx->c, level, u, f, r, nullptr, (cudaStream_t)cuda_stream);
+  });
+}
+
+hz_status hz_level_smooth(hz_ctx* ctx, int level, void* u, const void* f, void* cuda_stream) {
+  return guarded([&] {
+    check_level(ctx, level, false);
+    require(u && f, "null argument");
+    require(!ctx->c.L[level].coarsest, "the coarsest level has no smoother");
+    BusyGuard bg(&ctx->c);
+    level_smooth(ctx->c, level, u, f, false, nullptr, (cudaStream_t)cuda_stream);
+  });
+}
+
+hz_status hz_level_restrict(hz_ctx* ctx, int level, const void* r, void* fc, void* cuda_stream) {
+  return guarded([&] {
+    check_level(ctx, level, true);
+    require(r && fc, "null argument");
+    BusyGuard bg(&ctx->c);
+    level_restrict(ctx->c, level, r, fc, nullptr, (cudaStream_t)cuda_stream);
+  });
+}
+
+hz_status hz_level_prolong_add(hz_ctx* ctx, int level, const void* ec, void* u, void* cuda_stream) {
+  return guarded([&] {
+    check_level(ctx, level, true);
+    require(ec && u, "null argument");
+    BusyGuard bg(&ctx->c);
+    level_prolong_add(ctx->c, level, ec, u, nullptr, (cudaStream_t)cuda_stream);
+  });
+}
+
+hz_status hz_coarse_solve(hz_ctx* ctx, const void* f, void* u, void* cuda_stream) {
+  return guarded([&] {
+    require(ctx && f && u, "null argument");
+    BusyGuard bg(&ctx->c);
+    coarse_solve(ctx->c, f, u, nullptr, (cudaStream_t)cuda_stream);
+  });
+}
+
+}  // extern "C"

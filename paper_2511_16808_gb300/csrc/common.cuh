@@ -1,0 +1,261 @@
+// Internal definitions shared by the CUDA translation units of libhz.
+//
+// Layout in HBM (one context):
+//   level fields       interleaved complex, node-major, x fastest; with R
+//                      right-hand sides the RHS index is innermost
+//   stencils           plane-major ("SoA"): entry s of node p at [s*N + p], so a
+//                      warp reading one entry of 32 consecutive nodes issues one
+//                      coalesced 256 B (c64) / 512 B (c128) request
+//   fine level         only the complex diagonal of A_s is stored; the 2d
+//                      off-diagonal couplings -prod_{a'!=a} w_a'/h^2 follow from
+//                      the node's coordinates (half-cell weights of Section 2.1)
+//   coarse levels      full box stencils of radius rho (Galerkin products)
+//   Vanka smoother     the assembled sum M = sum_i V_i^T W_i H_i^{-1} V_i as a
+//                      per-node stencil over the offsets d_l - d_k of the patch
+//                      (Eq. smoother); a sweep is a gather, conflict-free
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <array>
+#include <atomic>
+#include <cstdint>
+#include <cstdio>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "hz.h"
+
+namespace hz {
+
+struct Error : std::runtime_error {
+  hz_status code;
+  Error(hz_status c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+#define HZ_CUDA(call)                                                                        \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess) {                                                                 \
+      (void)cudaGetLastError();                                                              \
+      throw ::hz::Error(e_ == cudaErrorMemoryAllocation ? HZ_ERR_OOM : HZ_ERR_CUDA,          \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                 \
+    }                                                                                        \
+  } while (0)
+
+#define HZ_LAUNCHED() HZ_CUDA(cudaGetLastError())
+
+inline void require(bool ok, const std::string& what) {
+  if (!ok) throw Error(HZ_ERR_INVALID_ARG, what);
+}
+
+// ---------------------------------------------------------------- complex
+template <typename T> struct cplx;
+template <> struct cplx<float> { using t = float2; };
+template <> struct cplx<double> { using t = double2; };
+template <typename T> using c_t = typename cplx<T>::t;
+
+template <typename V> __host__ __device__ __forceinline__ V cmk(double re, double im);
+template <> __host__ __device__ __forceinline__ float2 cmk<float2>(double re, double im) {
+  return make_float2((float)re, (float)im);
+}
+template <> __host__ __device__ __forceinline__ double2 cmk<double2>(double re, double im) {
+  return make_double2(re, im);
+}
+
+__host__ __device__ __forceinline__ double2 operator+(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ double2 operator-(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ double2 operator*(double s, double2 a) { return make_double2(s * a.x, s * a.y); }
+__host__ __device__ __forceinline__ float2 operator+(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2 operator-(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ float2 operator*(float s, float2 a) { return make_float2(s * a.x, s * a.y); }
+
+__host__ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// acc + a*b
+__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 acc) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+  return acc;
+}
+__device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 acc) {
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(-a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  acc.y = fmaf(a.y, b.x, acc.y);
+  return acc;
+}
+// conj(a)*b
+__host__ __device__ __forceinline__ double2 cconjmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+__host__ __device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+  double d = b.x * b.x + b.y * b.y;
+  return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+__host__ __device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+
+__device__ __forceinline__ double2 to_c128(double2 a) { return a; }
+__device__ __forceinline__ double2 to_c128(float2 a) { return make_double2(a.x, a.y); }
+template <typename V> __device__ __forceinline__ V from_c128(double2 a);
+template <> __device__ __forceinline__ double2 from_c128<double2>(double2 a) { return a; }
+template <> __device__ __forceinline__ float2 from_c128<float2>(double2 a) {
+  return make_float2((float)a.x, (float)a.y);
+}
+
+// ---------------------------------------------------------------- grid
+struct GridDev {
+  int dim;
+  int nx, ny, nz;     // nz = 1 in 2D
+  long long N;
+};
+
+inline GridDev make_grid(int dim, const int n[3]) {
+  GridDev g;
+  g.dim = dim;
+  g.nx = n[0];
+  g.ny = n[1];
+  g.nz = dim == 3 ? n[2] : 1;
+  g.N = (long long)g.nx * g.ny * g.nz;
+  return g;
+}
+
+// Half-cell weight of index i on an axis of n nodes (Section 2.1 boundary rows).
+__host__ __device__ __forceinline__ double wgt(int i, int n) { return (i == 0 || i == n - 1) ? 0.5 : 1.0; }
+
+// 1D prolongation weight P(j, J): fine node j, coarse node J (fine node 2J),
+// kind 0 = linear (Eq. biliniearIntergrid), 1 = cubic (Eq. bicubicIntergrid),
+// with P = 2 R^T per axis.  The cubic rule needs c_{-1} and c_{nc} at the two
+// ends; they are mirrored (c_{-1} := c_1, c_{nc} := c_{nc-2}).
+__host__ __device__ __forceinline__ double p1(int kind, int nf, int nc, int j, int J) {
+  int d = j - 2 * J;
+  int ad = d < 0 ? -d : d;
+  double w;
+  if (kind == 0) {
+    w = ad == 0 ? 1.0 : (ad == 1 ? 0.5 : 0.0);
+  } else {
+    w = ad == 0 ? 0.75 : (ad == 1 ? 0.5 : (ad == 2 ? 0.125 : 0.0));
+    if (j == 0 && J == 1) w += 0.125;
+    if (j == nf - 1 && J == nc - 2) w += 0.125;
+  }
+  return w;
+}
+// 1D restriction weight R(J, j) = P(j, J) / 2.
+__host__ __device__ __forceinline__ double r1(int kind, int nf, int nc, int J, int j) {
+  return 0.5 * p1(kind, nf, nc, j, J);
+}
+__host__ __device__ __forceinline__ int transfer_radius(int kind) { return kind ? 2 : 1; }
+
+// ---------------------------------------------------------------- stencils
+constexpr int kLutR = 3;                       // offsets in [-3, 3]^3
+constexpr int kLutW = 2 * kLutR + 1;
+constexpr int kLutN = kLutW * kLutW * kLutW;   // 343
+
+__host__ __device__ __forceinline__ int lut_index(int dx, int dy, int dz) {
+  return ((dz + kLutR) * kLutW + (dy + kLutR)) * kLutW + (dx + kLutR);
+}
+
+// Offsets of a stencil, passed by value to kernels (lives in parameter space).
+struct StencilOff {
+  int n;
+  int rho;                                     // max |offset| over axes
+  signed char d[HZ_MAX_STENCIL][3];
+};
+// Offsets plus an offset -> entry lookup, for setup kernels.
+struct StencilLut {
+  StencilOff off;
+  short lut[kLutN];
+};
+
+StencilLut make_lut(const std::vector<std::array<int, 3>>& offs);
+std::vector<std::array<int, 3>> fine_offsets(int dim);
+std::vector<std::array<int, 3>> box_offsets(int dim, int rho);
+std::vector<std::array<int, 3>> patch_offsets(int dim, hz_patch kind);
+std::vector<std::array<int, 3>> patch_difference_offsets(int dim, hz_patch kind);
+
+// ---------------------------------------------------------------- context
+struct Level {
+  GridDev g;
+  bool fine = false;
+  bool coarsest = false;
+  // operator A_s at this level
+  StencilLut A;                 // fine: the 2d+1 point offsets; coarse: box of radius rho
+  double2* A64 = nullptr;       // FP64 planes [A.n][N] (setup; kept for export when asked)
+  void* Aw = nullptr;           // working precision: fine = diag of A_s [N]; coarse = planes
+  // smoother
+  hz_patch patch = HZ_PATCH_JACOBI;
+  double damping = 1.0;
+  StencilLut M;                 // offsets of the assembled Vanka sum (zero planes dropped)
+  double2* M64 = nullptr;       // FP64 planes [M.n][N]
+  void* Mw = nullptr;           // working precision planes
+  // transfers to the next coarser level (0 = linear, 1 = cubic)
+  int rkind = 0, pkind = 0;
+  // work vectors, working precision, N * nrhs_max
+  void* u = nullptr;
+  void* f = nullptr;
+  void* r = nullptr;
+  // coarsest level: dense inverse [N][N] row-major
+  double2* Ainv64 = nullptr;
+  void* Ainvw = nullptr;
+};
+
+struct KrylovState;              // device-side FGMRES state, krylov.cu
+
+struct Ctx {
+  hz_grid grid;
+  hz_opts opts;
+  double omega = 0, alpha = 0, h = 0;
+  int dev = 0;
+  bool mixed = true;
+  std::vector<Level> L;
+  double2* diagA64 = nullptr;   // fine, unshifted A diagonal (FGMRES matvec), c128 [N]
+  double* wmass = nullptr;      // fine prod_a w_a per node (q_hat = wmass * q) [N]
+  // Krylov workspace (c128 unless noted), nrhs_max wide
+  double2* V = nullptr;         // (m+1) vectors
+  void* Z = nullptr;            // m vectors, working precision
+  double2* qhat = nullptr;
+  double2* p = nullptr;         // solution staging when the caller passes host memory
+  double2* qstage = nullptr;    // source staging for host sources
+  double2* partials = nullptr;  // reduction partials [vector][block]
+  KrylovState* ks = nullptr;    // device state, one per RHS
+  void* ks_host = nullptr;      // pinned host copy of the status
+  int red_blocks = 0;
+  std::vector<void*> allocations;
+  std::atomic<int> busy{0};
+  cudaGraphExec_t cycle_graph = nullptr;
+  int cycle_graph_nrhs = 0;
+  cudaStream_t graph_stream = nullptr;
+};
+
+// allocation helpers (all device memory of a context goes through these)
+void* ctx_alloc(Ctx& c, size_t bytes);
+void ctx_free_all(Ctx& c);
+
+// setup.cu
+void build_hierarchy(Ctx& c, const double* kappa_dev, const double* gamma_dev, double gamma0,
+                     cudaStream_t s);
+size_t hierarchy_bytes(const hz_grid& g, const hz_opts& o);
+
+// cycle.cu (working-precision V-cycle pieces; `active` may be null)
+void level_residual(Ctx& c, int l, const void* u, const void* f, void* r, const int* active, cudaStream_t s);
+void level_smooth(Ctx& c, int l, void* u, const void* f, bool u_is_zero, const int* active, cudaStream_t s);
+void level_restrict(Ctx& c, int l, const void* r, void* fc, const int* active, cudaStream_t s);
+void level_prolong_add(Ctx& c, int l, const void* ec, void* u, const int* active, cudaStream_t s);
+void coarse_solve(Ctx& c, const void* f, void* u, const int* active, cudaStream_t s);
+void vcycle(Ctx& c, const void* f, void* u, const int* active, cudaStream_t s);   // level 0: f -> u
+void fine_apply_f64(Ctx& c, const void* v, bool v_single, double2* w, bool shifted, cudaStream_t s);
+
+// krylov.cu
+size_t krylov_bytes(const hz_grid& g, const hz_opts& o);
+void krylov_alloc(Ctx& c);
+void fgmres_solve(Ctx& c, const double2* q_dev, double2* p_dev, hz_info* info, cudaStream_t s);
+void precond_apply_c128(Ctx& c, const double2* r, double2* z, cudaStream_t s);
+
+}  // namespace hz

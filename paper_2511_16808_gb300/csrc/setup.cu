@@ -1,0 +1,645 @@
+// Hierarchy setup on the device, all arithmetic in FP64.
+//
+//   a1  fine coefficients: diagonal of A (Eq. 1 discretised, Section 2.1) and of
+//       A_s = A + i alpha omega^2 M (Eq. shift, M the lumped mass)
+//   a3  Galerkin coarse operators A_{l+1} = R_l A_l P_l (Section 3.1), one
+//       thread per (coarse node, coarse offset)
+//   a4  Vanka patches (Sections 3.2-3.3): for every node j and every patch i
+//       containing it, H_i = V_i A_s V_i^T is inverted by Gauss-Jordan with
+//       partial pivoting and row (j) of W_i H_i^{-1} is gathered into the
+//       per-node stencil of M = sum_i V_i^T W_i H_i^{-1} V_i
+//   a8  coarsest level: dense inverse by Gauss-Jordan with partial pivoting
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+
+#include "common.cuh"
+
+namespace hz {
+
+// ------------------------------------------------------------------ offsets
+StencilLut make_lut(const std::vector<std::array<int, 3>>& offs) {
+  require(offs.size() <= HZ_MAX_STENCIL, "stencil too large");
+  StencilLut s;
+  std::memset(&s, 0, sizeof(s));
+  s.off.n = (int)offs.size();
+  s.off.rho = 0;
+  for (int i = 0; i < kLutN; ++i) s.lut[i] = -1;
+  for (size_t k = 0; k < offs.size(); ++k) {
+    for (int a = 0; a < 3; ++a) {
+      require(std::abs(offs[k][a]) <= kLutR, "stencil offset out of range");
+      s.off.d[k][a] = (signed char)offs[k][a];
+      s.off.rho = std::max(s.off.rho, std::abs(offs[k][a]));
+    }
+    s.lut[lut_index(offs[k][0], offs[k][1], offs[k][2])] = (short)k;
+  }
+  return s;
+}
+
+std::vector<std::array<int, 3>> fine_offsets(int dim) {
+  std::vector<std::array<int, 3>> o = {{0, 0, 0}, {-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}};
+  if (dim == 3) {
+    o.push_back({0, 0, -1});
+    o.push_back({0, 0, 1});
+  }
+  return o;
+}
+
+std::vector<std::array<int, 3>> box_offsets(int dim, int rho) {
+  std::vector<std::array<int, 3>> o;
+  int rz = dim == 3 ? rho : 0;
+  for (int dz = -rz; dz <= rz; ++dz)
+    for (int dy = -rho; dy <= rho; ++dy)
+      for (int dx = -rho; dx <= rho; ++dx) o.push_back({dx, dy, dz});
+  return o;
+}
+
+// Patch offsets about the anchor (Section 3.2).
+std::vector<std::array<int, 3>> patch_offsets(int dim, hz_patch kind) {
+  std::vector<std::array<int, 3>> o;
+  int rz = dim == 3 ? 1 : 0;
+  if (kind == HZ_PATCH_ELEMENT) {
+    for (int dz = 0; dz <= rz; ++dz)
+      for (int dy = 0; dy <= 1; ++dy)
+        for (int dx = 0; dx <= 1; ++dx) o.push_back({dx, dy, dz});
+    return o;
+  }
+  for (int dz = -rz; dz <= rz; ++dz)
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        int m = std::abs(dx) + std::abs(dy) + std::abs(dz);
+        bool take = false;
+        switch (kind) {
+          case HZ_PATCH_JACOBI: take = m == 0; break;
+          case HZ_PATCH_PLUS: take = m <= 1; break;
+          case HZ_PATCH_RB: take = (m % 2) == 0; break;
+          case HZ_PATCH_FULL: take = true; break;
+          default: break;
+        }
+        if (take) o.push_back({dx, dy, dz});
+      }
+  return o;
+}
+
+// All differences d_l - d_k of a patch's offsets: the entries of the assembled
+// Vanka sum at one node, in z-y-x lexicographic order.
+std::vector<std::array<int, 3>> patch_difference_offsets(int dim, hz_patch kind) {
+  auto p = patch_offsets(dim, kind);
+  std::map<std::array<int, 3>, int> seen;
+  for (auto& a : p)
+    for (auto& b : p) seen[{b[2] - a[2], b[1] - a[1], b[0] - a[0]}] = 1;
+  std::vector<std::array<int, 3>> o;
+  for (auto& kv : seen) o.push_back({kv.first[2], kv.first[1], kv.first[0]});
+  return o;
+}
+
+// ------------------------------------------------------------------ helpers
+__device__ __forceinline__ void node_coords(const GridDev& g, long long p, int& x, int& y, int& z) {
+  x = (int)(p % g.nx);
+  long long t = p / g.nx;
+  y = (int)(t % g.ny);
+  z = (int)(t / g.ny);
+}
+__device__ __forceinline__ bool in_grid(const GridDev& g, int x, int y, int z) {
+  return x >= 0 && x < g.nx && y >= 0 && y < g.ny && z >= 0 && z < g.nz;
+}
+__device__ __forceinline__ long long flat(const GridDev& g, int x, int y, int z) {
+  return ((long long)z * g.ny + y) * g.nx + x;
+}
+
+// ------------------------------------------------------------------ a1
+// diagA: unshifted diagonal of A (Laplacian diagonal part included);
+// planes: the fine A_s as 2d+1 planes (setup only); wmass = prod_a w_a.
+__global__ void k_fine_coeffs(GridDev g, double h, double omega, double alpha,
+                              const double* __restrict__ kappa, const double* __restrict__ gamma,
+                              double gamma0, double2* __restrict__ diagA, double* __restrict__ wmass,
+                              StencilOff off, double2* __restrict__ planes) {
+  long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= g.N) return;
+  int x, y, z;
+  node_coords(g, p, x, y, z);
+  const double wx = wgt(x, g.nx), wy = wgt(y, g.ny);
+  const double wz = g.dim == 3 ? wgt(z, g.nz) : 1.0;
+  const double bx = (x == 0 || x == g.nx - 1) ? 1.0 : 0.0;
+  const double by = (y == 0 || y == g.ny - 1) ? 1.0 : 0.0;
+  const double bz = (g.dim == 3 && (z == 0 || z == g.nz - 1)) ? 1.0 : 0.0;
+  const double W = wx * wy * wz;
+  const double ox = wy * wz, oy = wx * wz, oz = wx * wy;      // weights of the other axes
+  const double invh2 = 1.0 / (h * h);
+  double lapd = ox * ((x > 0) + (x < g.nx - 1)) + oy * ((y > 0) + (y < g.ny - 1));
+  if (g.dim == 3) lapd += oz * ((z > 0) + (z < g.nz - 1));
+  const double kap = kappa[p];
+  const double gam = gamma ? gamma[p] : gamma0;
+  // c = -omega^2 kappa^2 (1 - i gamma/omega)
+  const double cre = -omega * omega * kap * kap;
+  const double cim = omega * kap * kap * gam;
+  const double abc = bx * ox + by * oy + bz * oz;
+  double2 d = make_double2(lapd * invh2 + W * cre, W * cim + (omega * kap / h) * abc);
+  diagA[p] = d;
+  wmass[p] = W;
+  double2 ds = make_double2(d.x, d.y + alpha * omega * omega * W);
+  for (int s = 0; s < off.n; ++s) {
+    int dx = off.d[s][0], dy = off.d[s][1], dz = off.d[s][2];
+    double2 v = make_double2(0.0, 0.0);
+    if (dx == 0 && dy == 0 && dz == 0) {
+      v = ds;
+    } else if (in_grid(g, x + dx, y + dy, z + dz)) {
+      double o = dx ? ox : (dy ? oy : oz);
+      v = make_double2(-o * invh2, 0.0);
+    }
+    planes[(long long)s * g.N + p] = v;
+  }
+}
+
+// ------------------------------------------------------------------ a3
+// Ac(I, I+D) = sum_i R(I,i) sum_s Af(i, off_s) P(i + off_s, I + D)
+__global__ void k_galerkin(GridDev gf, StencilOff sf, const double2* __restrict__ Af, GridDev gc,
+                           StencilOff sc, double2* __restrict__ Ac, int rk, int pk) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= gc.N * sc.n) return;
+  const int e = (int)(t / gc.N);
+  const long long I = t - (long long)e * gc.N;
+  int X, Y, Z;
+  node_coords(gc, I, X, Y, Z);
+  const int JX = X + sc.d[e][0], JY = Y + sc.d[e][1], JZ = Z + sc.d[e][2];
+  double2 acc = make_double2(0.0, 0.0);
+  if (in_grid(gc, JX, JY, JZ)) {
+    const int rr = transfer_radius(rk), rp = transfer_radius(pk);
+    const int rz = gf.dim == 3 ? rr : 0;
+    for (int iz = 2 * Z - rz; iz <= 2 * Z + rz; ++iz) {
+      if (iz < 0 || iz >= gf.nz) continue;
+      const double wz = gf.dim == 3 ? r1(rk, gf.nz, gc.nz, Z, iz) : 1.0;
+      if (wz == 0.0) continue;
+      for (int iy = 2 * Y - rr; iy <= 2 * Y + rr; ++iy) {
+        if (iy < 0 || iy >= gf.ny) continue;
+        const double wy = r1(rk, gf.ny, gc.ny, Y, iy);
+        if (wy == 0.0) continue;
+        for (int ix = 2 * X - rr; ix <= 2 * X + rr; ++ix) {
+          if (ix < 0 || ix >= gf.nx) continue;
+          const double wx = r1(rk, gf.nx, gc.nx, X, ix);
+          if (wx == 0.0) continue;
+          const double wr = wx * wy * wz;
+          const long long i = flat(gf, ix, iy, iz);
+          for (int s = 0; s < sf.n; ++s) {
+            const int jx = ix + sf.d[s][0], jy = iy + sf.d[s][1], jz = iz + sf.d[s][2];
+            if (!in_grid(gf, jx, jy, jz)) continue;
+            if (abs(jx - 2 * JX) > rp + 1 || abs(jy - 2 * JY) > rp + 1 || abs(jz - 2 * JZ) > rp + 1) continue;
+            double pw = p1(pk, gf.nx, gc.nx, jx, JX) * p1(pk, gf.ny, gc.ny, jy, JY);
+            if (gf.dim == 3) pw *= p1(pk, gf.nz, gc.nz, jz, JZ);
+            if (pw == 0.0) continue;
+            const double2 a = Af[(long long)s * gf.N + i];
+            acc.x += wr * pw * a.x;
+            acc.y += wr * pw * a.y;
+          }
+        }
+      }
+    }
+  }
+  Ac[(long long)e * gc.N + I] = acc;
+}
+
+// ------------------------------------------------------------------ a4
+struct PatchDesc {
+  int np;
+  int element;                 // 1: anchors are cells (never clipped)
+  signed char d[27][3];
+};
+
+// In-place Gauss-Jordan inversion with partial (row) pivoting of an m x m
+// complex matrix stored row-major with leading dimension ld; the column
+// interchanges that undo the row pivoting are applied at the end.  Returns
+// false for an exactly singular pivot.
+__host__ __device__ inline bool gj_invert(double2* H, int m, int ld, int* piv) {
+  for (int k = 0; k < m; ++k) {
+    int p = k;
+    double best = cabs2(H[k * ld + k]);
+    for (int i = k + 1; i < m; ++i) {
+      double v = cabs2(H[i * ld + k]);
+      if (v > best) {
+        best = v;
+        p = i;
+      }
+    }
+    piv[k] = p;
+    if (best == 0.0) return false;
+    if (p != k)
+      for (int c = 0; c < m; ++c) {
+        double2 t = H[k * ld + c];
+        H[k * ld + c] = H[p * ld + c];
+        H[p * ld + c] = t;
+      }
+    const double2 inv = cdiv(make_double2(1.0, 0.0), H[k * ld + k]);
+    H[k * ld + k] = make_double2(1.0, 0.0);
+    for (int c = 0; c < m; ++c) H[k * ld + c] = cmul(H[k * ld + c], inv);
+    for (int i = 0; i < m; ++i) {
+      if (i == k) continue;
+      const double2 f = H[i * ld + k];
+      if (f.x == 0.0 && f.y == 0.0) continue;
+      H[i * ld + k] = make_double2(0.0, 0.0);
+      for (int c = 0; c < m; ++c) H[i * ld + c] = H[i * ld + c] - cmul(f, H[k * ld + c]);
+    }
+  }
+  for (int k = m - 1; k >= 0; --k) {
+    const int p = piv[k];
+    if (p != k)
+      for (int i = 0; i < m; ++i) {
+        double2 t = H[i * ld + k];
+        H[i * ld + k] = H[i * ld + p];
+        H[i * ld + p] = t;
+      }
+  }
+  return true;
+}
+
+template <int NP>
+__global__ void k_vanka_assemble(GridDev g, StencilLut A, const double2* __restrict__ Ap, PatchDesc pd,
+                                 StencilLut Ml, double2* __restrict__ Mp, int* __restrict__ singular) {
+  long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= g.N) return;
+  int x, y, z;
+  node_coords(g, j, x, y, z);
+  auto anchor_ok = [&](int ax, int ay, int az) {
+    if (pd.element) {
+      return ax >= 0 && ax < g.nx - 1 && ay >= 0 && ay < g.ny - 1 &&
+             (g.dim == 2 ? az == 0 : (az >= 0 && az < g.nz - 1));
+    }
+    return in_grid(g, ax, ay, az);
+  };
+  int count = 0;
+  for (int k = 0; k < pd.np; ++k)
+    if (anchor_ok(x - pd.d[k][0], y - pd.d[k][1], z - pd.d[k][2])) ++count;
+  if (count == 0) return;
+  const double W = 1.0 / count;
+  double2 H[NP * NP];
+  int slot[NP], piv[NP];
+  long long idx[NP];
+  for (int k = 0; k < pd.np; ++k) {
+    const int ax = x - pd.d[k][0], ay = y - pd.d[k][1], az = z - pd.d[k][2];
+    if (!anchor_ok(ax, ay, az)) continue;
+    int m = 0, kk = -1;
+    for (int l = 0; l < pd.np; ++l) {
+      const int nx = ax + pd.d[l][0], ny = ay + pd.d[l][1], nz = az + pd.d[l][2];
+      if (!in_grid(g, nx, ny, nz)) continue;
+      if (l == k) kk = m;
+      slot[m] = l;
+      idx[m] = flat(g, nx, ny, nz);
+      ++m;
+    }
+    for (int a = 0; a < m; ++a)
+      for (int b = 0; b < m; ++b) {
+        const int dx = pd.d[slot[b]][0] - pd.d[slot[a]][0];
+        const int dy = pd.d[slot[b]][1] - pd.d[slot[a]][1];
+        const int dz = pd.d[slot[b]][2] - pd.d[slot[a]][2];
+        const int e = A.lut[lut_index(dx, dy, dz)];
+        H[a * m + b] = e >= 0 ? Ap[(long long)e * g.N + idx[a]] : make_double2(0.0, 0.0);
+      }
+    if (!gj_invert(H, m, m, piv)) {
+      atomicAdd(singular, 1);
+      continue;
+    }
+    // row kk of H^{-1}, weighted by W_j, lands on node j at offset d_l - d_k
+    for (int b = 0; b < m; ++b) {
+      const int l = slot[b];
+      const int e = Ml.lut[lut_index(pd.d[l][0] - pd.d[k][0], pd.d[l][1] - pd.d[k][1],
+                                     pd.d[l][2] - pd.d[k][2])];
+      double2* dst = Mp + (long long)e * g.N + j;
+      const double2 v = H[kk * m + b];
+      *dst = *dst + W * v;
+    }
+  }
+}
+
+// max over a plane of |v|^2, as the bit pattern of a non-negative double
+__global__ void k_plane_absmax(const double2* __restrict__ planes, long long N, int nplanes,
+                               unsigned long long* __restrict__ out) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= N * nplanes) return;
+  const int e = (int)(t / N);
+  const double v = cabs2(planes[t]);
+  if (v > 0.0) atomicMax(out + e, (unsigned long long)__double_as_longlong(v));
+}
+
+// ------------------------------------------------------------------ casts
+template <typename V>
+__global__ void k_cast(const double2* __restrict__ in, V* __restrict__ out, long long n) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) out[t] = from_c128<V>(in[t]);
+}
+
+// ------------------------------------------------------------------ a8
+__global__ void k_dense_from_planes(GridDev g, StencilOff so, const double2* __restrict__ planes,
+                                    double2* __restrict__ D) {
+  long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= g.N) return;
+  int x, y, z;
+  node_coords(g, p, x, y, z);
+  for (int s = 0; s < so.n; ++s) {
+    const int xx = x + so.d[s][0], yy = y + so.d[s][1], zz = z + so.d[s][2];
+    if (!in_grid(g, xx, yy, zz)) continue;
+    D[p * g.N + flat(g, xx, yy, zz)] = planes[(long long)s * g.N + p];
+  }
+}
+
+// pivot search for column k (one block)
+__global__ void k_gj_pivot(double2* __restrict__ D, int n, int k, int* __restrict__ piv,
+                           int* __restrict__ singular) {
+  __shared__ double bv[1024];
+  __shared__ int bi[1024];
+  double best = -1.0;
+  int arg = k;
+  for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
+    const double v = cabs2(D[(long long)i * n + k]);
+    if (v > best) {
+      best = v;
+      arg = i;
+    }
+  }
+  bv[threadIdx.x] = best;
+  bi[threadIdx.x] = arg;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      const double o = bv[threadIdx.x + s];
+      const int oi = bi[threadIdx.x + s];
+      if (o > bv[threadIdx.x] || (o == bv[threadIdx.x] && oi < bi[threadIdx.x])) {
+        bv[threadIdx.x] = o;
+        bi[threadIdx.x] = oi;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    piv[k] = bi[0];
+    if (bv[0] <= 0.0) atomicAdd(singular, 1);
+  }
+}
+
+// swap rows k and piv[k], scale the pivot row, save column k
+__global__ void k_gj_swap_scale(double2* __restrict__ D, int n, int k, const int* __restrict__ piv,
+                                double2* __restrict__ col) {
+  const int p = piv[k];
+  __shared__ double2 inv;
+  if (threadIdx.x == 0) {
+    const double2 a = D[(long long)p * n + k];
+    inv = (a.x == 0.0 && a.y == 0.0) ? make_double2(0.0, 0.0) : cdiv(make_double2(1.0, 0.0), a);
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+    double2 rk = D[(long long)k * n + c];
+    double2 rp = D[(long long)p * n + c];
+    if (p != k) D[(long long)p * n + c] = rk;
+    if (c == k) rp = make_double2(1.0, 0.0);
+    D[(long long)k * n + c] = cmul(rp, inv);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) col[i] = D[(long long)i * n + k];
+}
+
+// H[i][c] = (c == k ? 0 : H[i][c]) - col[i] * H[k][c] for all i != k
+__global__ void k_gj_eliminate(double2* __restrict__ D, int n, int k, const double2* __restrict__ col) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.y;
+  if (c >= n || i == k) return;
+  const double2 f = col[i];
+  if (f.x == 0.0 && f.y == 0.0) return;
+  double2 v = c == k ? make_double2(0.0, 0.0) : D[(long long)i * n + c];
+  D[(long long)i * n + c] = v - cmul(f, D[(long long)k * n + c]);
+}
+
+// undo the row pivoting: column swaps in reverse order, composed into one
+// permutation (single thread), then a gather
+__global__ void k_gj_compose(const int* __restrict__ piv, int n, int* __restrict__ perm) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int c = 0; c < n; ++c) perm[c] = c;
+  for (int k = n - 1; k >= 0; --k) {
+    const int p = piv[k];
+    const int t = perm[k];
+    perm[k] = perm[p];
+    perm[p] = t;
+  }
+}
+__global__ void k_gj_permute_cols(const double2* __restrict__ X, int n, const int* __restrict__ perm,
+                                  double2* __restrict__ Y) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.y;
+  if (c >= n) return;
+  Y[(long long)i * n + c] = X[(long long)i * n + perm[c]];
+}
+
+// ------------------------------------------------------------------ host
+static inline unsigned nblk(long long n, int b) { return (unsigned)((n + b - 1) / b); }
+
+static void invert_dense(Ctx& c, Level& L, cudaStream_t s) {
+  const long long n = L.g.N;
+  require(n <= 20000, "coarsest level too large for a dense inverse (use more levels)");
+  double2* D = (double2*)ctx_alloc(c, sizeof(double2) * n * n);
+  HZ_CUDA(cudaMemsetAsync(D, 0, sizeof(double2) * n * n, s));
+  k_dense_from_planes<<<nblk(n, 256), 256, 0, s>>>(L.g, L.A.off, L.A64, D);
+  HZ_LAUNCHED();
+  double2* col = nullptr;
+  int *piv = nullptr, *perm = nullptr, *sing = nullptr;
+  HZ_CUDA(cudaMallocAsync(&col, sizeof(double2) * n, s));
+  HZ_CUDA(cudaMallocAsync(&piv, sizeof(int) * n, s));
+  HZ_CUDA(cudaMallocAsync(&perm, sizeof(int) * n, s));
+  HZ_CUDA(cudaMallocAsync(&sing, sizeof(int), s));
+  HZ_CUDA(cudaMemsetAsync(sing, 0, sizeof(int), s));
+  for (int k = 0; k < n; ++k) {
+    k_gj_pivot<<<1, 1024, 0, s>>>(D, (int)n, k, piv, sing);
+    k_gj_swap_scale<<<1, 1024, 0, s>>>(D, (int)n, k, piv, col);
+    dim3 gr(nblk(n, 256), (unsigned)n);
+    k_gj_eliminate<<<gr, 256, 0, s>>>(D, (int)n, k, col);
+  }
+  HZ_LAUNCHED();
+  k_gj_compose<<<1, 1, 0, s>>>(piv, (int)n, perm);
+  L.Ainv64 = (double2*)ctx_alloc(c, sizeof(double2) * n * n);
+  dim3 gr(nblk(n, 256), (unsigned)n);
+  k_gj_permute_cols<<<gr, 256, 0, s>>>(D, (int)n, perm, L.Ainv64);
+  HZ_LAUNCHED();
+  int hsing = 0;
+  HZ_CUDA(cudaMemcpyAsync(&hsing, sing, sizeof(int), cudaMemcpyDeviceToHost, s));
+  HZ_CUDA(cudaStreamSynchronize(s));
+  cudaFreeAsync(col, s);
+  cudaFreeAsync(piv, s);
+  cudaFreeAsync(perm, s);
+  cudaFreeAsync(sing, s);
+  if (hsing) throw Error(HZ_ERR_INVALID_ARG, "coarsest-level operator is singular");
+}
+
+template <int NP>
+static void launch_vanka(Level& L, const PatchDesc& pd, const StencilLut& Mfull, double2* Mp, int* sing,
+                         cudaStream_t s) {
+  k_vanka_assemble<NP><<<nblk(L.g.N, 128), 128, 0, s>>>(L.g, L.A, L.A64, pd, Mfull, Mp, sing);
+  HZ_LAUNCHED();
+}
+
+static void assemble_smoother(Ctx& c, Level& L, cudaStream_t s) {
+  const int dim = c.grid.dim;
+  auto po = patch_offsets(dim, L.patch);
+  PatchDesc pd;
+  std::memset(&pd, 0, sizeof(pd));
+  pd.np = (int)po.size();
+  pd.element = L.patch == HZ_PATCH_ELEMENT;
+  for (int k = 0; k < pd.np; ++k)
+    for (int a = 0; a < 3; ++a) pd.d[k][a] = (signed char)po[k][a];
+  auto moffs = patch_difference_offsets(dim, L.patch);
+  StencilLut Mfull = make_lut(moffs);
+  const long long N = L.g.N;
+  double2* Mp = nullptr;
+  HZ_CUDA(cudaMallocAsync(&Mp, sizeof(double2) * N * Mfull.off.n, s));
+  HZ_CUDA(cudaMemsetAsync(Mp, 0, sizeof(double2) * N * Mfull.off.n, s));
+  int* sing = nullptr;
+  unsigned long long* amax = nullptr;
+  HZ_CUDA(cudaMallocAsync(&sing, sizeof(int), s));
+  HZ_CUDA(cudaMemsetAsync(sing, 0, sizeof(int), s));
+  HZ_CUDA(cudaMallocAsync(&amax, sizeof(unsigned long long) * Mfull.off.n, s));
+  HZ_CUDA(cudaMemsetAsync(amax, 0, sizeof(unsigned long long) * Mfull.off.n, s));
+  switch (pd.np) {
+    case 1: launch_vanka<1>(L, pd, Mfull, Mp, sing, s); break;
+    case 4: launch_vanka<4>(L, pd, Mfull, Mp, sing, s); break;
+    case 5: launch_vanka<5>(L, pd, Mfull, Mp, sing, s); break;
+    case 7: launch_vanka<7>(L, pd, Mfull, Mp, sing, s); break;
+    case 8: launch_vanka<8>(L, pd, Mfull, Mp, sing, s); break;
+    case 9: launch_vanka<9>(L, pd, Mfull, Mp, sing, s); break;
+    case 13: launch_vanka<13>(L, pd, Mfull, Mp, sing, s); break;
+    case 27: launch_vanka<27>(L, pd, Mfull, Mp, sing, s); break;
+    default: throw Error(HZ_ERR_INVALID_ARG, "unsupported patch size");
+  }
+  k_plane_absmax<<<nblk(N * Mfull.off.n, 256), 256, 0, s>>>(Mp, N, Mfull.off.n, amax);
+  HZ_LAUNCHED();
+  std::vector<unsigned long long> hmax(Mfull.off.n);
+  int hsing = 0;
+  HZ_CUDA(cudaMemcpyAsync(hmax.data(), amax, sizeof(unsigned long long) * Mfull.off.n,
+                          cudaMemcpyDeviceToHost, s));
+  HZ_CUDA(cudaMemcpyAsync(&hsing, sing, sizeof(int), cudaMemcpyDeviceToHost, s));
+  HZ_CUDA(cudaStreamSynchronize(s));
+  if (hsing) {
+    cudaFreeAsync(Mp, s);
+    throw Error(HZ_ERR_INVALID_ARG, "a Vanka patch matrix is singular");
+  }
+  // drop planes that are identically zero (e.g. the RB patch on a 5-point
+  // stencil, whose patch matrices are diagonal: the sum is damped Jacobi)
+  std::vector<std::array<int, 3>> keep;
+  std::vector<int> src;
+  for (int e = 0; e < Mfull.off.n; ++e)
+    if (hmax[e] != 0ull) {
+      keep.push_back({Mfull.off.d[e][0], Mfull.off.d[e][1], Mfull.off.d[e][2]});
+      src.push_back(e);
+    }
+  L.M = make_lut(keep);
+  L.M64 = (double2*)ctx_alloc(c, sizeof(double2) * N * keep.size());
+  for (size_t k = 0; k < src.size(); ++k)
+    HZ_CUDA(cudaMemcpyAsync(L.M64 + (long long)k * N, Mp + (long long)src[k] * N, sizeof(double2) * N,
+                            cudaMemcpyDeviceToDevice, s));
+  cudaFreeAsync(Mp, s);
+  cudaFreeAsync(sing, s);
+  cudaFreeAsync(amax, s);
+}
+
+static void* working_copy(Ctx& c, const double2* src, long long n, cudaStream_t s) {
+  if (!c.mixed) return (void*)src;             // FP64 path works on the setup arrays
+  float2* dst = (float2*)ctx_alloc(c, sizeof(float2) * n);
+  k_cast<float2><<<nblk(n, 256), 256, 0, s>>>(src, dst, n);
+  HZ_LAUNCHED();
+  return dst;
+}
+
+static int rkind_of(hz_intergrid ig, int level) {
+  switch (ig) {
+    case HZ_IG_LINEAR: return 0;
+    case HZ_IG_CUBIC: return 1;
+    case HZ_IG_MIXED: return 0;
+    case HZ_IG_LEVELDEP: return level == 0 ? 1 : 0;
+  }
+  return 0;
+}
+static int pkind_of(hz_intergrid ig, int level) {
+  (void)level;
+  return ig == HZ_IG_LINEAR ? 0 : 1;
+}
+
+void build_hierarchy(Ctx& c, const double* kappa, const double* gamma, double gamma0, cudaStream_t s) {
+  const int dim = c.grid.dim;
+  const int levels = c.opts.levels;
+  const size_t vb = c.mixed ? sizeof(float2) : sizeof(double2);
+  const int R = std::max(1, c.opts.nrhs_max);
+  c.L.assign(levels, Level());
+  int n[3] = {c.grid.n[0], c.grid.n[1], dim == 3 ? c.grid.n[2] : 1};
+  for (int l = 0; l < levels; ++l) {
+    Level& L = c.L[l];
+    L.g = make_grid(dim, n);
+    L.fine = l == 0;
+    L.coarsest = l == levels - 1;
+    L.patch = c.opts.patch[l];
+    L.damping = c.opts.damping[l];
+    L.rkind = rkind_of(c.opts.intergrid, l);
+    L.pkind = pkind_of(c.opts.intergrid, l);
+    for (int a = 0; a < dim; ++a) n[a] = (n[a] - 1) / 2 + 1;
+  }
+  // a1: fine coefficients
+  {
+    Level& L = c.L[0];
+    const long long N = L.g.N;
+    L.A = make_lut(fine_offsets(dim));
+    L.A64 = (double2*)ctx_alloc(c, sizeof(double2) * N * L.A.off.n);
+    c.diagA64 = (double2*)ctx_alloc(c, sizeof(double2) * N);
+    c.wmass = (double*)ctx_alloc(c, sizeof(double) * N);
+    k_fine_coeffs<<<nblk(N, 256), 256, 0, s>>>(L.g, c.h, c.omega, c.alpha, kappa, gamma, gamma0,
+                                                c.diagA64, c.wmass, L.A.off, L.A64);
+    HZ_LAUNCHED();
+  }
+  for (int l = 0; l < levels; ++l) {
+    Level& L = c.L[l];
+    const long long N = L.g.N;
+    if (L.coarsest) {
+      invert_dense(c, L, s);
+      L.Ainvw = working_copy(c, L.Ainv64, N * N, s);
+    } else {
+      assemble_smoother(c, L, s);
+      // a3: Galerkin operator of the next level
+      Level& C = c.L[l + 1];
+      const int rho = (transfer_radius(L.rkind) + L.A.off.rho + transfer_radius(L.pkind)) / 2;
+      C.A = make_lut(box_offsets(dim, std::min(rho, kLutR)));
+      C.A64 = (double2*)ctx_alloc(c, sizeof(double2) * C.g.N * C.A.off.n);
+      const long long T = C.g.N * C.A.off.n;
+      k_galerkin<<<nblk(T, 128), 128, 0, s>>>(L.g, L.A.off, L.A64, C.g, C.A.off, C.A64, L.rkind, L.pkind);
+      HZ_LAUNCHED();
+      L.Mw = working_copy(c, L.M64, N * L.M.off.n, s);
+    }
+    // working operator: fine = diagonal of A_s (plane 0), coarse = all planes
+    L.Aw = working_copy(c, L.A64, L.fine ? N : N * L.A.off.n, s);
+    L.u = ctx_alloc(c, vb * N * R);
+    L.f = ctx_alloc(c, vb * N * R);
+    L.r = ctx_alloc(c, vb * N * R);
+  }
+  HZ_CUDA(cudaStreamSynchronize(s));
+}
+
+size_t hierarchy_bytes(const hz_grid& g, const hz_opts& o) {
+  const int dim = g.dim;
+  const size_t vb = o.precision == HZ_PREC_MIXED ? 8 : 16;
+  const int R = std::max(1, o.nrhs_max);
+  long long n[3] = {g.n[0], g.n[1], dim == 3 ? g.n[2] : 1};
+  size_t total = 0;
+  int rho = 1;
+  for (int l = 0; l < o.levels; ++l) {
+    const long long N = n[0] * n[1] * n[2];
+    const int sA = l == 0 ? 2 * dim + 1 : (int)std::pow(2 * rho + 1, dim);
+    total += 16ull * N * sA;                                   // FP64 operator planes
+    if (l == 0) total += 16ull * N + 8ull * N + vb * N;         // diag A, wmass, working diag
+    else if (vb == 8) total += 8ull * N * sA;
+    if (l == o.levels - 1) {
+      total += 16ull * N * N * 2 + (vb == 8 ? 8ull * N * N : 0);   // dense work + inverse
+    } else {
+      const int sM = (int)patch_difference_offsets(dim, o.patch[l]).size();
+      total += (16ull + (vb == 8 ? 8 : 0)) * N * sM;
+      const int rk = rkind_of(o.intergrid, l), pk = pkind_of(o.intergrid, l);
+      rho = (transfer_radius(rk) + (l == 0 ? 1 : rho) + transfer_radius(pk)) / 2;
+    }
+    total += 3ull * vb * N * R;
+    for (int a = 0; a < dim; ++a) n[a] = (n[a] - 1) / 2 + 1;
+  }
+  return total;
+}
+
+}  // namespace hz

@@ -1,0 +1,251 @@
+"""Python binding of the libhz C ABI (include/hz.h): argument marshalling only.
+
+Every function has the name of the C entry point it calls.  Device arrays are
+torch CUDA tensors (contiguous); host arrays are numpy arrays or CPU tensors.
+Complex fields are complex128 (c128) or complex64 (c64) tensors.  No compute
+happens here: a missing or unloadable libhz.so raises at import time.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.environ.get("HZ_LIB", os.path.join(_PKG, "_build", "libhz.so"))
+HEADER_PATH = os.path.join(os.path.dirname(_PKG), "include", "hz.h")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libhz.so not found at {LIB_PATH}: build it with "
+                      f"`python -m paper_2511_16808_gb300.build` (there is no CPU fallback)")
+lib = C.CDLL(LIB_PATH)
+
+MAX_LEVELS = 10
+MAX_STENCIL = 343
+
+PATCH = {"jacobi": 0, "element": 1, "plus": 2, "rb": 3, "full": 4}
+INTERGRID = {"linear": 0, "cubic": 1, "mixed": 2, "leveldep": 3}
+PRECISION = {"fp64": 0, "mixed": 1}
+STATUS = {0: "HZ_OK", 1: "HZ_ERR_INVALID_ARG", 2: "HZ_ERR_OOM", 3: "HZ_ERR_CUDA",
+          4: "HZ_ERR_NOT_CONVERGED", 5: "HZ_ERR_BREAKDOWN", 6: "HZ_ERR_TIMEOUT",
+          7: "HZ_ERR_BUSY", 8: "HZ_ERR_NO_DEVICE"}
+HZ_OK, HZ_ERR_NOT_CONVERGED = 0, 4
+
+
+class hz_grid(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n", C.c_int * 3), ("h", C.c_double)]
+
+
+class hz_opts(C.Structure):
+    _fields_ = [("levels", C.c_int), ("patch", C.c_int * MAX_LEVELS),
+                ("damping", C.c_double * MAX_LEVELS), ("nu1", C.c_int), ("nu2", C.c_int),
+                ("intergrid", C.c_int), ("precision", C.c_int), ("restart_m", C.c_int),
+                ("tol", C.c_double), ("max_iter", C.c_int), ("nrhs_max", C.c_int)]
+
+
+class hz_info(C.Structure):
+    _fields_ = [("iters", C.c_int), ("converged", C.c_int), ("relres_est", C.c_double),
+                ("relres_true", C.c_double)]
+
+
+class hz_level_desc(C.Structure):
+    _fields_ = [("n", C.c_int * 3), ("nodes", C.c_int64), ("stencil_size", C.c_int),
+                ("stencil_off", (C.c_int * 3) * MAX_STENCIL), ("smoother_size", C.c_int),
+                ("smoother_off", (C.c_int * 3) * MAX_STENCIL), ("patch", C.c_int),
+                ("damping", C.c_double), ("is_coarsest", C.c_int)]
+
+
+class HzError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = lib.hz_last_error().decode()
+        super().__init__(f"{where}: {STATUS.get(status, status)} ({msg})")
+
+
+_P = C.c_void_p
+_SIGS = {
+    "hz_abi_version": ([], C.c_int),
+    "hz_status_string": ([C.c_int], C.c_char_p),
+    "hz_last_error": ([], C.c_char_p),
+    "hz_opts_default": ([C.c_int, C.POINTER(hz_opts)], C.c_int),
+    "hz_default_damping": ([C.c_int, C.c_int, C.c_int], C.c_double),
+    "hz_setup_bytes": ([C.POINTER(hz_grid), C.POINTER(hz_opts), C.POINTER(C.c_size_t)], C.c_int),
+    "hz_setup": ([C.POINTER(hz_grid), _P, C.c_double, _P, C.c_double, C.c_double,
+                  C.POINTER(hz_opts), _P, C.POINTER(_P)], C.c_int),
+    "hz_destroy": ([_P], C.c_int),
+    "hz_solve": ([_P, _P, _P, C.c_int, C.POINTER(hz_info), _P], C.c_int),
+    "hz_precond_apply": ([_P, _P, _P, C.c_int, _P], C.c_int),
+    "hz_apply_operator": ([_P, _P, _P, C.c_int, C.c_int, _P], C.c_int),
+    "hz_level_count": ([_P, C.POINTER(C.c_int)], C.c_int),
+    "hz_level_describe": ([_P, C.c_int, C.POINTER(hz_level_desc)], C.c_int),
+    "hz_level_export": ([_P, C.c_int, C.c_int, _P], C.c_int),
+    "hz_level_residual": ([_P, C.c_int, _P, _P, _P, _P], C.c_int),
+    "hz_level_smooth": ([_P, C.c_int, _P, _P, _P], C.c_int),
+    "hz_level_restrict": ([_P, C.c_int, _P, _P, _P], C.c_int),
+    "hz_level_prolong_add": ([_P, C.c_int, _P, _P, _P], C.c_int),
+    "hz_coarse_solve": ([_P, _P, _P, _P], C.c_int),
+}
+for _name, (_args, _res) in _SIGS.items():
+    _f = getattr(lib, _name)
+    _f.argtypes = _args
+    _f.restype = _res
+
+
+def declared_symbols(header: str = HEADER_PATH):
+    """Names of the functions declared in include/hz.h."""
+    text = open(header).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(hz_[a-z0-9_]+)\s*\(", text)))
+
+
+def _check(status: int, where: str, ok=(HZ_OK,)):
+    if status not in ok:
+        raise HzError(status, where)
+    return status
+
+
+def _ptr(a):
+    """Raw address of a torch tensor or numpy array (must be contiguous)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _stream(s):
+    if s is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:  # noqa: BLE001
+            pass
+        return None
+    return getattr(s, "cuda_stream", s)
+
+
+# ------------------------------------------------------------------ library
+
+def hz_abi_version() -> int:
+    return lib.hz_abi_version()
+
+
+def hz_status_string(s: int) -> str:
+    return lib.hz_status_string(s).decode()
+
+
+def hz_last_error() -> str:
+    return lib.hz_last_error().decode()
+
+
+def hz_opts_default(dim: int) -> hz_opts:
+    o = hz_opts()
+    _check(lib.hz_opts_default(dim, C.byref(o)), "hz_opts_default")
+    return o
+
+
+def hz_default_damping(dim: int, patch, level: int) -> float:
+    return lib.hz_default_damping(dim, PATCH.get(patch, patch), level)
+
+
+def make_grid(dim: int, n, h: float) -> hz_grid:
+    g = hz_grid()
+    g.dim = dim
+    n = list(n) + [1] * (3 - len(n))
+    for a in range(3):
+        g.n[a] = int(n[a])
+    g.h = float(h)
+    return g
+
+
+def hz_setup_bytes(grid: hz_grid, opts: hz_opts) -> int:
+    out = C.c_size_t()
+    _check(lib.hz_setup_bytes(C.byref(grid), C.byref(opts), C.byref(out)), "hz_setup_bytes")
+    return out.value
+
+
+def hz_setup(grid: hz_grid, kappa, omega: float, gamma, gamma0: float, shift_alpha: float,
+             opts: hz_opts, stream=None):
+    """Returns an opaque context handle (int)."""
+    ctx = C.c_void_p()
+    _check(lib.hz_setup(C.byref(grid), _ptr(kappa), float(omega), _ptr(gamma), float(gamma0),
+                        float(shift_alpha), C.byref(opts), _stream(stream), C.byref(ctx)), "hz_setup")
+    return ctx.value
+
+
+def hz_destroy(ctx) -> None:
+    _check(lib.hz_destroy(ctx), "hz_destroy")
+
+
+def hz_solve(ctx, q, p, nrhs: int = 1, stream=None):
+    """Returns (converged: bool, [hz_info] * nrhs)."""
+    infos = (hz_info * nrhs)()
+    st = lib.hz_solve(ctx, _ptr(q), _ptr(p), nrhs, infos, _stream(stream))
+    _check(st, "hz_solve", ok=(HZ_OK, HZ_ERR_NOT_CONVERGED))
+    return st == HZ_OK, list(infos)
+
+
+def hz_precond_apply(ctx, r, z, nrhs: int = 1, stream=None) -> None:
+    _check(lib.hz_precond_apply(ctx, _ptr(r), _ptr(z), nrhs, _stream(stream)), "hz_precond_apply")
+
+
+def hz_apply_operator(ctx, v, w, nrhs: int = 1, shifted: int = 0, stream=None) -> None:
+    _check(lib.hz_apply_operator(ctx, _ptr(v), _ptr(w), nrhs, int(shifted), _stream(stream)),
+           "hz_apply_operator")
+
+
+# ------------------------------------------------------------------ components
+
+def hz_level_count(ctx) -> int:
+    out = C.c_int()
+    _check(lib.hz_level_count(ctx, C.byref(out)), "hz_level_count")
+    return out.value
+
+
+def hz_level_describe(ctx, level: int) -> dict:
+    d = hz_level_desc()
+    _check(lib.hz_level_describe(ctx, level, C.byref(d)), "hz_level_describe")
+    return {
+        "n": tuple(d.n), "nodes": d.nodes,
+        "stencil": [tuple(d.stencil_off[k]) for k in range(d.stencil_size)],
+        "smoother": [tuple(d.smoother_off[k]) for k in range(d.smoother_size)],
+        "patch": d.patch, "damping": d.damping, "is_coarsest": bool(d.is_coarsest),
+    }
+
+
+def hz_level_export(ctx, level: int, what: int) -> np.ndarray:
+    """Stencil planes as a complex128 array [entries, nodes] (what 0: A_s, 1: Vanka sum)."""
+    d = hz_level_describe(ctx, level)
+    n = len(d["stencil"] if what == 0 else d["smoother"])
+    out = np.zeros((n, d["nodes"]), dtype=np.complex128)
+    _check(lib.hz_level_export(ctx, level, what, out.ctypes.data), "hz_level_export")
+    return out
+
+
+def hz_level_residual(ctx, level, u, f, r, stream=None):
+    _check(lib.hz_level_residual(ctx, level, _ptr(u), _ptr(f), _ptr(r), _stream(stream)), "hz_level_residual")
+
+
+def hz_level_smooth(ctx, level, u, f, stream=None):
+    _check(lib.hz_level_smooth(ctx, level, _ptr(u), _ptr(f), _stream(stream)), "hz_level_smooth")
+
+
+def hz_level_restrict(ctx, level, r, fc, stream=None):
+    _check(lib.hz_level_restrict(ctx, level, _ptr(r), _ptr(fc), _stream(stream)), "hz_level_restrict")
+
+
+def hz_level_prolong_add(ctx, level, ec, u, stream=None):
+    _check(lib.hz_level_prolong_add(ctx, level, _ptr(ec), _ptr(u), _stream(stream)), "hz_level_prolong_add")
+
+
+def hz_coarse_solve(ctx, f, u, stream=None):
+    _check(lib.hz_coarse_solve(ctx, _ptr(f), _ptr(u), _stream(stream)), "hz_coarse_solve")

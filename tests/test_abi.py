@@ -1,0 +1,71 @@
+"""C-ABI checks that need no GPU: the library loads, exports every symbol the
+header declares, validates arguments, and its constant tables match the
+paper's printed damping table (Table relaxParam, golden fixture)."""
+import numpy as np
+import pytest
+
+from conftest import read_golden
+
+hz = pytest.importorskip("paper_2511_16808_gb300.hz")
+
+
+def test_exports_every_declared_symbol():
+    names = hz.declared_symbols()
+    assert len(names) >= 19
+    for n in names:
+        assert hasattr(hz.lib, n), n
+        assert callable(getattr(hz, n)), n          # binding has the same name
+
+
+def test_abi_version_and_status_strings():
+    assert hz.hz_abi_version() == 1
+    for code in hz.STATUS:
+        assert hz.hz_status_string(code)
+
+
+def test_default_damping_matches_printed_table():
+    rows = [[float(v) for v in r] for r in read_golden("damping_table.txt")]
+    cols = [(2, "jacobi"), (2, "element"), (2, "plus"), (2, "rb"), (3, "jacobi"), (3, "element"), (3, "plus")]
+    for level in range(6):
+        for c, (dim, patch) in enumerate(cols):
+            assert hz.hz_default_damping(dim, patch, level) == rows[min(level, 3)][c]
+
+
+def test_oracle_damping_matches_printed_table():
+    from oracle import defaults
+    rows = [[float(v) for v in r] for r in read_golden("damping_table.txt")]
+    cols = [(2, "jacobi"), (2, "element"), (2, "plus"), (2, "rb"), (3, "jacobi"), (3, "element"), (3, "plus")]
+    for level in range(6):
+        for c, (dim, patch) in enumerate(cols):
+            assert defaults.damping(dim, patch, level) == rows[min(level, 3)][c]
+
+
+def test_opts_default_and_setup_bytes():
+    o = hz.hz_opts_default(2)
+    assert o.levels == 4 and o.restart_m == 5 and o.nu1 == 1 and o.nu2 == 1
+    g = hz.make_grid(2, [129, 129], 1 / 128)
+    b = hz.hz_setup_bytes(g, o)
+    assert 129 * 129 * 16 * 6 < b < 1 << 31
+    o3 = hz.hz_opts_default(3)
+    g3 = hz.make_grid(3, [65, 65, 65], 1 / 64)
+    assert hz.hz_setup_bytes(g3, o3) > b
+
+
+@pytest.mark.parametrize("n,levels", [(128, 4), (129, 9), (2, 1)])
+def test_invalid_grid_rejected(n, levels):
+    o = hz.hz_opts_default(2)
+    o.levels = levels
+    g = hz.make_grid(2, [n, n], 1.0 / max(n - 1, 1))
+    with pytest.raises(hz.HzError) as e:
+        hz.hz_setup(g, np.ones(n * n), 10.0, None, 0.1, 0.2, o)
+    assert e.value.status == 1                       # HZ_ERR_INVALID_ARG
+
+
+def test_invalid_options_rejected():
+    g = hz.make_grid(2, [33, 33], 1 / 32)
+    for field, value in [("restart_m", 0), ("restart_m", 17), ("tol", 0.0), ("nrhs_max", 0)]:
+        o = hz.hz_opts_default(2)
+        setattr(o, field, value)
+        with pytest.raises(hz.HzError) as e:
+            hz.hz_setup_bytes(g, o)
+        assert e.value.status == 1

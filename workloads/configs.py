@@ -89,7 +89,7 @@ def config2(n: int = 1025, levels: int = 6, seed: int = 0, layer_cells: int = 20
     kappa = media.layered_kappa_2d(n, seed)
     gamma = media.absorbing_gamma(kappa.shape, omega, 0.01, layer_cells)
     w = Workload(name=f"2d-layered-{n}", dim=2, n=n, omega=omega, kappa=kappa, gamma=gamma,
-                 sources=[_centre(n, 2)], levels=levels, alpha=0.25, patch="plus",
+                 sources=[_centre(n, 2)], levels=levels, alpha=0.1, patch="rb",
                  intergrid="leveldep", tol=1e-6, precision="mixed", layer_cells=layer_cells,
                  meta={"seed": seed})
     return replace(w, **kw)
