@@ -196,6 +196,26 @@ hz_status hz_level_residual(hz_ctx* ctx, int level, const void* u, const void* f
                             void* cuda_stream);
 /* One additive Vanka relaxation (Eq. smoother): u += w M (f - A_s u). */
 hz_status hz_level_smooth(hz_ctx* ctx, int level, void* u, const void* f, void* cuda_stream);
+/* Allocation-free variant of hz_level_smooth.  The paper has no counterpart:
+ * this entry point exists for callers that must not allocate device memory
+ * on the call path, e.g. code whose device memory is fully reserved up
+ * front by another allocator or by a fixed per-process budget, where a
+ * cudaMalloc could fail or fragment that reservation.  It computes the same
+ * sweep, u += w M (f - A_s u), but keeps the level residual in scratch that
+ * the library holds in static device memory (4 MiB per GPU that loads the
+ * library, held until the process exits) instead of the context's buffer;
+ * it calls no cudaMalloc, cudaFree or other allocating routine.
+ *   - The level may have at most HZ_NOALLOC_MAX_NODES nodes; larger levels
+ *     return HZ_ERR_INVALID_ARG with a message.
+ *   - The scratch address is looked up on the first call on each device
+ *     (with that device made current); make that first call before any
+ *     stream capture.
+ *   - All calls share the one scratch array and it keeps the last call's
+ *     contents.  Nothing in it needs clearing (the residual overwrites it
+ *     before use), but calls whose work overlaps on the GPU race on it:
+ *     order them on one stream or synchronise between them. */
+#define HZ_NOALLOC_MAX_NODES 262144
+hz_status hz_level_smooth_noalloc(hz_ctx* ctx, int level, void* u, const void* f, void* cuda_stream);
 /* fc = R_level r (to level+1). */
 hz_status hz_level_restrict(hz_ctx* ctx, int level, const void* r, void* fc, void* cuda_stream);
 /* u += P_level ec (from level+1). */

@@ -1,6 +1,7 @@
 // C ABI of libhz (declarations and contracts in include/hz.h).
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "common.cuh"
@@ -8,6 +9,12 @@
 namespace hz {
 
 static thread_local std::string g_last_error;
+
+// Scratch of the allocation-free sweep (hz_level_smooth_noalloc): the
+// residual of one level, c64 or c128, at most HZ_NOALLOC_MAX_NODES nodes.
+// It lives in the module's static device memory, so every GPU that loads the
+// library holds these 4 MiB until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[(size_t)HZ_NOALLOC_MAX_NODES * 16];
 
 void* ctx_alloc(Ctx& c, size_t bytes) {
   void* p = nullptr;
@@ -117,6 +124,30 @@ double default_damping(int dim, hz_patch p, int level) {
   }
   int col = p == HZ_PATCH_JACOBI ? 0 : p == HZ_PATCH_ELEMENT ? 1 : 2;
   return d3[col][r];
+}
+
+// Device address of g_noalloc_scratch on `dev`.  Host code only sees a
+// host-side stand-in under the array's name, so the address is looked up once
+// per device, with that device current, and cached.
+void* noalloc_scratch(int dev) {
+  static std::mutex mu;
+  static void* addr[256] = {};
+  require(dev >= 0 && dev < 256, "device ordinal out of range");
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[dev]) {
+    int prev = -1;
+    HZ_CUDA(cudaGetDevice(&prev));
+    if (prev != dev) HZ_CUDA(cudaSetDevice(dev));
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (prev != dev) cudaSetDevice(prev);
+    if (e != cudaSuccess || p == nullptr) {
+      (void)cudaGetLastError();
+      throw Error(HZ_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
+    }
+    addr[dev] = p;
+  }
+  return addr[dev];
 }
 
 }  // namespace
@@ -355,6 +386,30 @@ hz_status hz_level_smooth(hz_ctx* ctx, int level, void* u, const void* f, void* 
     require(!ctx->c.L[level].coarsest, "the coarsest level has no smoother");
     BusyGuard bg(&ctx->c);
     level_smooth(ctx->c, level, u, f, false, nullptr, (cudaStream_t)cuda_stream);
+  });
+}
+
+hz_status hz_level_smooth_noalloc(hz_ctx* ctx, int level, void* u, const void* f, void* cuda_stream) {
+  return guarded([&] {
+    check_level(ctx, level, false);
+    require(u && f, "null argument");
+    Ctx& c = ctx->c;
+    const Level& L = c.L[level];
+    require(!L.coarsest, "the coarsest level has no smoother");
+    if (L.g.N > HZ_NOALLOC_MAX_NODES)
+      throw Error(HZ_ERR_INVALID_ARG, "level has " + std::to_string(L.g.N) +
+                                          " nodes; the allocation-free sweep handles at most " +
+                                          std::to_string(HZ_NOALLOC_MAX_NODES));
+    BusyGuard bg(&c);
+    void* r = noalloc_scratch(c.dev);
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    int prev = -1;
+    HZ_CUDA(cudaGetDevice(&prev));
+    if (prev != c.dev) HZ_CUDA(cudaSetDevice(c.dev));
+    // every scratch entry is written by the residual before it is read: no clearing needed
+    level_residual(c, level, u, f, r, nullptr, s);
+    level_vanka_apply(c, level, r, u, s);
+    if (prev != c.dev) HZ_CUDA(cudaSetDevice(prev));
   });
 }
 

@@ -249,6 +249,7 @@ void level_smooth(Ctx& c, int l, void* u, const void* f, bool u_is_zero, const i
 void level_restrict(Ctx& c, int l, const void* r, void* fc, const int* active, cudaStream_t s);
 void level_prolong_add(Ctx& c, int l, const void* ec, void* u, const int* active, cudaStream_t s);
 void coarse_solve(Ctx& c, const void* f, void* u, const int* active, cudaStream_t s);
+void level_vanka_apply(Ctx& c, int l, const void* r, void* u, cudaStream_t s);   // u += w M r
 void vcycle(Ctx& c, const void* f, void* u, const int* active, cudaStream_t s);   // level 0: f -> u
 void fine_apply_f64(Ctx& c, const void* v, bool v_single, double2* w, bool shifted, cudaStream_t s);
 

@@ -308,6 +308,17 @@ void level_prolong_add(Ctx& c, int l, const void* ec, void* u, const int* active
   if (c.mixed) prolong_t<float>(c, l, ec, u, active, s);
   else prolong_t<double>(c, l, ec, u, active, s);
 }
+void level_vanka_apply(Ctx& c, int l, const void* r, void* u, cudaStream_t s) {
+  Level& L = c.L[l];
+  const long long N = L.g.N;
+  if (c.mixed)
+    k_vanka_apply<float, 1><<<nblk(N, kBlock), kBlock, 0, s>>>(L.g, L.M.off, (const float2*)L.Mw, (float)L.damping,
+                                                               (const float2*)r, (float2*)u, nullptr);
+  else
+    k_vanka_apply<double, 1><<<nblk(N, kBlock), kBlock, 0, s>>>(L.g, L.M.off, (const double2*)L.Mw, L.damping,
+                                                                (const double2*)r, (double2*)u, nullptr);
+  HZ_LAUNCHED();
+}
 void coarse_solve(Ctx& c, const void* f, void* u, const int* active, cudaStream_t s) {
   if (c.mixed) coarse_t<float>(c, f, u, active, s);
   else coarse_t<double>(c, f, u, active, s);

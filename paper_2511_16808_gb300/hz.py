@@ -24,6 +24,7 @@ lib = C.CDLL(LIB_PATH)
 
 MAX_LEVELS = 10
 MAX_STENCIL = 343
+NOALLOC_MAX_NODES = 262144
 
 PATCH = {"jacobi": 0, "element": 1, "plus": 2, "rb": 3, "full": 4}
 INTERGRID = {"linear": 0, "cubic": 1, "mixed": 2, "leveldep": 3}
@@ -83,6 +84,7 @@ _SIGS = {
     "hz_level_export": ([_P, C.c_int, C.c_int, _P], C.c_int),
     "hz_level_residual": ([_P, C.c_int, _P, _P, _P, _P], C.c_int),
     "hz_level_smooth": ([_P, C.c_int, _P, _P, _P], C.c_int),
+    "hz_level_smooth_noalloc": ([_P, C.c_int, _P, _P, _P], C.c_int),
     "hz_level_restrict": ([_P, C.c_int, _P, _P, _P], C.c_int),
     "hz_level_prolong_add": ([_P, C.c_int, _P, _P, _P], C.c_int),
     "hz_coarse_solve": ([_P, _P, _P, _P], C.c_int),
@@ -237,6 +239,12 @@ def hz_level_residual(ctx, level, u, f, r, stream=None):
 
 def hz_level_smooth(ctx, level, u, f, stream=None):
     _check(lib.hz_level_smooth(ctx, level, _ptr(u), _ptr(f), _stream(stream)), "hz_level_smooth")
+
+
+def hz_level_smooth_noalloc(ctx, level, u, f, stream=None):
+    """hz_level_smooth without any device allocation (scratch in static device memory)."""
+    _check(lib.hz_level_smooth_noalloc(ctx, level, _ptr(u), _ptr(f), _stream(stream)),
+           "hz_level_smooth_noalloc")
 
 
 def hz_level_restrict(ctx, level, r, fc, stream=None):
