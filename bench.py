@@ -181,8 +181,11 @@ def run_ours(args):
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
+    from paper_2511_16808_gb300 import hz as _hz
+    launches0 = _hz.hz_kernel_launches(solver.ctx)
     with ClockSampler(local) as clk:
         ms, infos = time_solves(torch, solver, q, p, args.steps, stream)
+    launches = _hz.hz_kernel_launches(solver.ctx) - launches0
     if dist:
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -242,7 +245,7 @@ def run_ours(args):
             "clocks": clk.summary(),
             "roofline": None,
             "cpu_baseline": cpu,
-            "gpu_launches": None,
+            "gpu_launches": launches,
             "peak_source": src,
             "vanka_dof_per_s": vdofs,
         }

@@ -178,6 +178,11 @@ hz_status hz_precond_apply(hz_ctx* ctx, const void* r, void* z, int nrhs, void* 
 hz_status hz_apply_operator(hz_ctx* ctx, const void* v, void* w, int nrhs, int shifted,
                             void* cuda_stream);
 
+/* Number of kernels hz_solve has launched on this context so far (direct
+ * launches plus the kernel nodes of every replayed restart-cycle graph;
+ * kernels of an iteration skipped on the device after convergence count). */
+hz_status hz_kernel_launches(const hz_ctx* ctx, int64_t* count);
+
 /* ---- component entry points (one row of the method each) ---------------
  * Level fields are device arrays in the context's V-cycle precision (c128
  * for HZ_PREC_FP64, c64 for HZ_PREC_MIXED) of the level's node count. */

@@ -32,6 +32,11 @@ void* ctx_alloc(Ctx& c, size_t bytes) {
 void ctx_free_all(Ctx& c) {
   if (c.cycle_graph) cudaGraphExecDestroy(c.cycle_graph);
   c.cycle_graph = nullptr;
+  if (c.ev_in) cudaEventDestroy(c.ev_in);
+  if (c.ev_out) cudaEventDestroy(c.ev_out);
+  if (c.graph_stream) cudaStreamDestroy(c.graph_stream);
+  c.ev_in = c.ev_out = nullptr;
+  c.graph_stream = nullptr;
   for (void* p : c.allocations) cudaFree(p);
   c.allocations.clear();
   if (c.ks_host) cudaFreeHost(c.ks_host);
@@ -100,6 +105,8 @@ void validate(const hz_grid* g, const hz_opts* o) {
   require(o->nrhs_max >= 1, "nrhs_max must be >= 1");
   require(o->precision == HZ_PREC_FP64 || o->precision == HZ_PREC_MIXED, "bad precision");
   require(o->intergrid >= HZ_IG_LINEAR && o->intergrid <= HZ_IG_LEVELDEP, "bad intergrid");
+  require(!(g->dim == 3 && o->intergrid == HZ_IG_CUBIC && o->levels >= 3),
+          "cubic intergrid in 3D is limited to 2 levels (7x7x7 Galerkin stencils beyond); use leveldep");
   for (int l = 0; l < o->levels - 1; ++l) {
     require(o->patch[l] >= HZ_PATCH_JACOBI && o->patch[l] <= HZ_PATCH_FULL, "bad patch");
     require(std::isfinite(o->damping[l]), "bad damping");
@@ -290,10 +297,7 @@ hz_status hz_solve(hz_ctx* ctx, const void* q, void* p, int nrhs, hz_info* info,
       HZ_CUDA(cudaMemcpyAsync(c.qstage, q, sizeof(double2) * N, cudaMemcpyHostToDevice, s));
       qd = c.qstage;
     }
-    if (p_host) {
-      if (!c.p) c.p = (double2*)ctx_alloc(c, sizeof(double2) * N);
-      pd = c.p;
-    }
+    if (p_host) pd = c.p;
     fgmres_solve(c, qd, pd, info, s);
     if (p_host) {
       HZ_CUDA(cudaMemcpyAsync(p, pd, sizeof(double2) * N, cudaMemcpyDeviceToHost, s));
@@ -318,6 +322,13 @@ hz_status hz_apply_operator(hz_ctx* ctx, const void* v, void* w, int nrhs, int s
     require(nrhs == 1, "this build applies one right-hand side per call");
     BusyGuard bg(&ctx->c);
     fine_apply_f64(ctx->c, v, false, (double2*)w, shifted != 0, (cudaStream_t)cuda_stream);
+  });
+}
+
+hz_status hz_kernel_launches(const hz_ctx* ctx, int64_t* count) {
+  return guarded([&] {
+    require(ctx && count, "null argument");
+    *count = ctx->c.launches;
   });
 }
 

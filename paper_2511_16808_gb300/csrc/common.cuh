@@ -110,6 +110,33 @@ template <> __device__ __forceinline__ float2 from_c128<float2>(double2 a) {
   return make_float2((float)a.x, (float)a.y);
 }
 
+// float <-> double on the integer pipe.  GB300 executes FP64 instructions,
+// conversions included, at 1/64 of the FP32 rate, and converting the FP32
+// preconditioned vectors for the FP64 Krylov passes saturated that pipe.
+// These repack sign / exponent / mantissa with 32-bit integer operations and
+// give exactly the IEEE results (round to nearest even for the narrowing
+// conversion); zero, subnormal, infinite, NaN and out-of-range inputs take the
+// hardware conversion.
+__device__ __forceinline__ double f2d_exact(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  if (e == 0u || e == 0xffu) return (double)f;
+  const unsigned m = u & 0x7fffffu;
+  const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | (m >> 3);
+  return __hiloint2double((int)hi, (int)(m << 29));
+}
+__device__ __forceinline__ float d2f_rn(double d) {
+  const unsigned hi = (unsigned)__double2hiint(d);
+  const unsigned lo = (unsigned)__double2loint(d);
+  const int e = (int)((hi >> 20) & 0x7ffu) - 896;          // float exponent field
+  if (e <= 0 || e >= 255) return __double2float_rn(d);
+  const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);   // 23-bit mantissa
+  const unsigned rem = lo & 0x1fffffffu;                    // 29 dropped bits
+  unsigned bits = ((unsigned)e << 23) | m;
+  bits += (rem > 0x10000000u || (rem == 0x10000000u && (m & 1u))) ? 1u : 0u;   // carry may reach exponent
+  return __uint_as_float(bits | (hi & 0x80000000u));
+}
+
 // ---------------------------------------------------------------- grid
 struct GridDev {
   int dim;
@@ -198,9 +225,11 @@ struct Level {
   // transfers to the next coarser level (0 = linear, 1 = cubic)
   int rkind = 0, pkind = 0;
   // work vectors, working precision, N * nrhs_max
-  void* u = nullptr;
-  void* f = nullptr;
-  void* r = nullptr;
+  void* u = nullptr;             // cycle output on coarse levels
+  void* f = nullptr;             // right-hand side
+  void* r = nullptr;             // residual
+  void* t = nullptr;             // pre-smoothed iterate (the post-smoothing writes the output)
+  bool m_diag = false;           // assembled Vanka sum is diagonal (Jacobi / RB on 2d+1 points)
   // coarsest level: dense inverse [N][N] row-major
   double2* Ainv64 = nullptr;
   void* Ainvw = nullptr;
@@ -221,7 +250,7 @@ struct Ctx {
   double2* V = nullptr;         // (m+1) vectors
   void* Z = nullptr;            // m vectors, working precision
   double2* qhat = nullptr;
-  double2* p = nullptr;         // solution staging when the caller passes host memory
+  double2* p = nullptr;         // solution accumulator (copied to the caller's buffer)
   double2* qstage = nullptr;    // source staging for host sources
   double2* partials = nullptr;  // reduction partials [vector][block]
   KrylovState* ks = nullptr;    // device state, one per RHS
@@ -231,7 +260,10 @@ struct Ctx {
   std::atomic<int> busy{0};
   cudaGraphExec_t cycle_graph = nullptr;
   int cycle_graph_nrhs = 0;
-  cudaStream_t graph_stream = nullptr;
+  cudaStream_t graph_stream = nullptr;   // library stream the solve runs on (graph capture needs one)
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  int graph_kernels = 0;        // kernel nodes in the captured restart cycle
+  long long launches = 0;       // kernels launched by hz_solve on this context
 };
 
 // allocation helpers (all device memory of a context goes through these)

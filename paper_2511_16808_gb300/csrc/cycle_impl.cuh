@@ -1,0 +1,660 @@
+// V-cycle kernels in the working precision T (float for the mixed path,
+// double for the plain FP64 path) and the recursive driver (Algorithm 1).
+//
+//   residual    r = f - A_s u          fine: diagonal + index weights (5/7-point);
+//                                      coarse: stored Galerkin planes (box radius rho)
+//   sweep       u += w M r             M = assembled Vanka sum (Eq. smoother); the
+//                                      first sweep from u = 0 is u = w M f
+//   restrict    f_c = R r              Eqs. biliniearIntergrid / bicubicIntergrid (gather)
+//   prolong     u += P e_c             P = 2^d R^T of the same kind (gather)
+//   coarse      u = A_L^{-1} f         dense inverse from setup, one warp per row
+//
+// Fused forms (one HBM pass instead of two or three):
+//   sweep0+residual   when M is diagonal (Jacobi; RB on a 2d+1-point stencil):
+//                     u = w m0 f and r = f - A(w m0 f) in one kernel
+//   prolong+residual  2D: u' = t + P e_c on a shared-memory tile with halo, then
+//                     r = f - A u' from the tile
+//   prolong+sweep     2D with diagonal M: u = u' + w m0 (f - A u') from the tile
+// Thread mapping: 32 x 8 threads per block over (x, y), blockIdx.z = z, one
+// thread per output node, 32-bit indices; blocks whose stencil reach stays
+// inside the grid take an unchecked path (block-uniform branch).  Kernels take
+// an optional device flag `active`: when it reads 0 they return at once (a
+// captured FGMRES cycle uses it to skip the iterations after convergence).
+#pragma once
+#include <type_traits>
+
+#include "common.cuh"
+
+namespace hz {
+namespace cyc {
+
+constexpr int BX = 32, BY = 8;
+constexpr int kMaxM = 125;
+
+struct Geo {
+  int nx, ny, nz, sxy, N;
+};
+inline Geo geo(const GridDev& g) { return Geo{g.nx, g.ny, g.nz, g.nx * g.ny, (int)g.N}; }
+inline dim3 grid_of(const Geo& g) { return dim3((g.nx + BX - 1) / BX, (g.ny + BY - 1) / BY, g.nz); }
+inline unsigned nblk(long long n, int b) { return (unsigned)((n + b - 1) / b); }
+
+// Offsets of an assembled Vanka sum with their flat index offsets on one level.
+struct MList {
+  int n, rho;
+  int flat[kMaxM];
+  signed char d[kMaxM][3];
+};
+
+inline MList mlist(const Level& L) {
+  require(L.M.off.n <= kMaxM, "Vanka stencil too large");
+  MList m;
+  m.n = L.M.off.n;
+  m.rho = L.M.off.rho;
+  for (int s = 0; s < m.n; ++s) {
+    for (int a = 0; a < 3; ++a) m.d[s][a] = L.M.off.d[s][a];
+    m.flat[s] = L.M.off.d[s][0] + L.M.off.d[s][1] * L.g.nx + L.M.off.d[s][2] * L.g.nx * L.g.ny;
+  }
+  return m;
+}
+
+__device__ __forceinline__ bool node_xyz(const Geo& g, int& x, int& y, int& z) {
+  x = blockIdx.x * BX + threadIdx.x;
+  y = blockIdx.y * BY + threadIdx.y;
+  z = blockIdx.z;
+  return x < g.nx && y < g.ny;
+}
+
+// true when every node of this block and its neighbours within r lie in the grid
+template <int DIM>
+__device__ __forceinline__ bool interior_block(const Geo& g, int r) {
+  const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
+  bool ok = x0 >= r && x0 + BX - 1 + r < g.nx && y0 >= r && y0 + BY - 1 + r < g.ny;
+  if (DIM == 3) ok = ok && (int)blockIdx.z >= r && (int)blockIdx.z + r < g.nz;
+  return ok;
+}
+
+template <typename V>
+__device__ __forceinline__ V scale(V a, decltype(a.x) s) {
+  a.x *= s;
+  a.y *= s;
+  return a;
+}
+
+// A u at node p for the fine 5-/7-point operator (diag d at p).
+template <typename T, int DIM, bool CHECK, typename LD>
+__device__ __forceinline__ c_t<T> fine_Au(const Geo& g, T invh2, c_t<T> d, const LD& ld, int p, int x, int y,
+                                          int z) {
+  using V = c_t<T>;
+  V acc = cmul(d, ld(p));
+  if (!CHECK) {
+    V s = ld(p - 1) + ld(p + 1) + ld(p - g.nx) + ld(p + g.nx);
+    if (DIM == 3) s = s + ld(p - g.sxy) + ld(p + g.sxy);
+    acc.x -= invh2 * s.x;
+    acc.y -= invh2 * s.y;
+    return acc;
+  }
+  const T wx = (x == 0 || x == g.nx - 1) ? T(0.5) : T(1);
+  const T wy = (y == 0 || y == g.ny - 1) ? T(0.5) : T(1);
+  const T wz = (DIM == 3 && (z == 0 || z == g.nz - 1)) ? T(0.5) : T(1);
+  V sx = cmk<V>(0, 0), sy = cmk<V>(0, 0);
+  if (x > 0) sx = sx + ld(p - 1);
+  if (x < g.nx - 1) sx = sx + ld(p + 1);
+  if (y > 0) sy = sy + ld(p - g.nx);
+  if (y < g.ny - 1) sy = sy + ld(p + g.nx);
+  const T cx = wy * wz * invh2, cy = wx * wz * invh2;
+  acc.x -= cx * sx.x + cy * sy.x;
+  acc.y -= cx * sx.y + cy * sy.y;
+  if (DIM == 3) {
+    V sz = cmk<V>(0, 0);
+    if (z > 0) sz = sz + ld(p - g.sxy);
+    if (z < g.nz - 1) sz = sz + ld(p + g.sxy);
+    const T cz = wx * wy * invh2;
+    acc.x -= cz * sz.x;
+    acc.y -= cz * sz.y;
+  }
+  return acc;
+}
+
+// A u at node p for a stored box stencil of radius RHO (planes [s][N]).
+template <typename T, int DIM, int RHO, bool CHECK, typename LD>
+__device__ __forceinline__ c_t<T> box_Au(const Geo& g, const c_t<T>* __restrict__ P, const LD& ld, int p, int x,
+                                         int y, int z) {
+  using V = c_t<T>;
+  V acc = cmk<V>(0, 0);
+  constexpr int RZ = DIM == 3 ? RHO : 0;
+  constexpr int W = 2 * RHO + 1;
+#pragma unroll
+  for (int dz = -RZ; dz <= RZ; ++dz)
+#pragma unroll
+    for (int dy = -RHO; dy <= RHO; ++dy)
+#pragma unroll
+      for (int dx = -RHO; dx <= RHO; ++dx) {
+        const int s = ((dz + RZ) * W + (dy + RHO)) * W + (dx + RHO);
+        if (CHECK) {
+          if (x + dx < 0 || x + dx >= g.nx || y + dy < 0 || y + dy >= g.ny) continue;
+          if (DIM == 3 && (z + dz < 0 || z + dz >= g.nz)) continue;
+        }
+        acc = cfma(P[s * g.N + p], ld(p + dx + dy * g.nx + dz * g.sxy), acc);
+      }
+  return acc;
+}
+
+// AK = 0: fine analytic operator; AK = rho > 0: stored box stencil.
+template <typename T, int DIM, int AK, bool CHECK, typename LD>
+__device__ __forceinline__ c_t<T> apply_A(const Geo& g, T invh2, const c_t<T>* __restrict__ A, const LD& ld, int p,
+                                          int x, int y, int z) {
+  if constexpr (AK == 0)
+    return fine_Au<T, DIM, CHECK>(g, invh2, A[p], ld, p, x, y, z);
+  else
+    return box_Au<T, DIM, AK, CHECK>(g, A, ld, p, x, y, z);
+}
+
+template <typename T, int DIM, bool CHECK, typename LD>
+__device__ __forceinline__ c_t<T> list_Au(const Geo& g, const MList& m, const c_t<T>* __restrict__ P, const LD& ld,
+                                          int p, int x, int y, int z) {
+  using V = c_t<T>;
+  V acc = cmk<V>(0, 0);
+  for (int s = 0; s < m.n; ++s) {
+    if (CHECK) {
+      const int xx = x + m.d[s][0], yy = y + m.d[s][1], zz = z + m.d[s][2];
+      if (xx < 0 || xx >= g.nx || yy < 0 || yy >= g.ny) continue;
+      if (DIM == 3 && (zz < 0 || zz >= g.nz)) continue;
+    }
+    acc = cfma(P[s * g.N + p], ld(p + m.flat[s]), acc);
+  }
+  return acc;
+}
+
+// ------------------------------------------------------------------ kernels
+
+// r = f - A u
+template <typename T, int DIM, int AK>
+__global__ void __launch_bounds__(BX* BY) k_resid(Geo g, T invh2, const c_t<T>* __restrict__ A,
+                                                  const c_t<T>* __restrict__ u, const c_t<T>* __restrict__ f,
+                                                  c_t<T>* __restrict__ r, const int* active) {
+  if (active && !*active) return;
+  constexpr int RA = AK == 0 ? 1 : AK;
+  const bool in = interior_block<DIM>(g, RA);
+  int x, y, z;
+  if (!node_xyz(g, x, y, z)) return;
+  const int p = (z * g.ny + y) * g.nx + x;
+  auto ld = [u](int q) { return u[q]; };
+  const c_t<T> a = in ? apply_A<T, DIM, AK, false>(g, invh2, A, ld, p, x, y, z)
+                      : apply_A<T, DIM, AK, true>(g, invh2, A, ld, p, x, y, z);
+  r[p] = f[p] - a;
+}
+
+// u = w M f  (first sweep from u = 0)
+template <typename T, int DIM>
+__global__ void __launch_bounds__(BX* BY) k_sweep0(Geo g, MList m, const c_t<T>* __restrict__ M, T w,
+                                                   const c_t<T>* __restrict__ f, c_t<T>* __restrict__ u,
+                                                   const int* active) {
+  if (active && !*active) return;
+  const bool in = interior_block<DIM>(g, m.rho);
+  int x, y, z;
+  if (!node_xyz(g, x, y, z)) return;
+  const int p = (z * g.ny + y) * g.nx + x;
+  auto ld = [f](int q) { return f[q]; };
+  const c_t<T> v = in ? list_Au<T, DIM, false>(g, m, M, ld, p, x, y, z) : list_Au<T, DIM, true>(g, m, M, ld, p, x, y, z);
+  u[p] = scale(v, w);
+}
+
+// diagonal M: u = w m0 f and r = f - A u in one pass
+template <typename T, int DIM, int AK>
+__global__ void __launch_bounds__(BX* BY) k_sweep0_resid_diag(Geo g, T invh2, const c_t<T>* __restrict__ A,
+                                                              const c_t<T>* __restrict__ m0, T w,
+                                                              const c_t<T>* __restrict__ f, c_t<T>* __restrict__ u,
+                                                              c_t<T>* __restrict__ r, const int* active) {
+  if (active && !*active) return;
+  constexpr int RA = AK == 0 ? 1 : AK;
+  const bool in = interior_block<DIM>(g, RA);
+  int x, y, z;
+  if (!node_xyz(g, x, y, z)) return;
+  const int p = (z * g.ny + y) * g.nx + x;
+  auto ld = [m0, f, w](int q) { return scale(cmul(m0[q], f[q]), w); };
+  const c_t<T> a = in ? apply_A<T, DIM, AK, false>(g, invh2, A, ld, p, x, y, z)
+                      : apply_A<T, DIM, AK, true>(g, invh2, A, ld, p, x, y, z);
+  const c_t<T> fp = f[p];
+  u[p] = scale(cmul(m0[p], fp), w);
+  r[p] = fp - a;
+}
+
+// out = in + w M r  (out may alias in)
+template <typename T, int DIM>
+__global__ void __launch_bounds__(BX* BY) k_sweep_out(Geo g, MList m, const c_t<T>* __restrict__ M, T w,
+                                                      const c_t<T>* __restrict__ r, const c_t<T>* in, c_t<T>* out,
+                                                      const int* active) {
+  if (active && !*active) return;
+  const bool inb = interior_block<DIM>(g, m.rho);
+  int x, y, z;
+  if (!node_xyz(g, x, y, z)) return;
+  const int p = (z * g.ny + y) * g.nx + x;
+  auto ld = [r](int q) { return r[q]; };
+  const c_t<T> v = inb ? list_Au<T, DIM, false>(g, m, M, ld, p, x, y, z) : list_Au<T, DIM, true>(g, m, M, ld, p, x, y, z);
+  out[p] = in[p] + scale(v, w);
+}
+
+// diagonal M: out = in + w m0 (f - A in)   (out != in)
+template <typename T, int DIM, int AK>
+__global__ void __launch_bounds__(BX* BY) k_resid_sweep_diag(Geo g, T invh2, const c_t<T>* __restrict__ A,
+                                                             const c_t<T>* __restrict__ m0, T w,
+                                                             const c_t<T>* __restrict__ f, const c_t<T>* __restrict__ in,
+                                                             c_t<T>* __restrict__ out, const int* active) {
+  if (active && !*active) return;
+  constexpr int RA = AK == 0 ? 1 : AK;
+  const bool inb = interior_block<DIM>(g, RA);
+  int x, y, z;
+  if (!node_xyz(g, x, y, z)) return;
+  const int p = (z * g.ny + y) * g.nx + x;
+  auto ld = [in](int q) { return in[q]; };
+  const c_t<T> a = inb ? apply_A<T, DIM, AK, false>(g, invh2, A, ld, p, x, y, z)
+                       : apply_A<T, DIM, AK, true>(g, invh2, A, ld, p, x, y, z);
+  out[p] = in[p] + scale(cmul(m0[p], f[p] - a), w);
+}
+
+// 1D prolongation weight P(j, J) in single precision (the same exact dyadic
+// values as p1; computed with integer tests and float constants only, since
+// FP64 arithmetic and conversions are slow on this GPU)
+__device__ __forceinline__ float p1f(int kind, int nf, int nc, int j, int J) {
+  const int d = j - 2 * J;
+  const int ad = d < 0 ? -d : d;
+  if (kind == 0) return ad == 0 ? 1.0f : (ad == 1 ? 0.5f : 0.0f);
+  float w = ad == 0 ? 0.75f : (ad == 1 ? 0.5f : (ad == 2 ? 0.125f : 0.0f));
+  if (j == 0 && J == 1) w += 0.125f;
+  if (j == nf - 1 && J == nc - 2) w += 0.125f;
+  return w;
+}
+
+// f_c = R r, one thread per coarse node
+template <typename T, int DIM, int KIND>
+__global__ void __launch_bounds__(BX* BY) k_restrict(Geo gf, Geo gc, const c_t<T>* __restrict__ r,
+                                                     c_t<T>* __restrict__ fc, const int* active) {
+  if (active && !*active) return;
+  int X, Y, Z;
+  if (!node_xyz(gc, X, Y, Z)) return;
+  constexpr int RAD = KIND ? 2 : 1;
+  constexpr int RZ = DIM == 3 ? RAD : 0;
+  T wx[2 * RAD + 1], wy[2 * RAD + 1], wz[2 * RZ + 1];
+#pragma unroll
+  for (int k = 0; k <= 2 * RAD; ++k) {
+    const int ix = 2 * X - RAD + k, iy = 2 * Y - RAD + k;
+    wx[k] = (ix >= 0 && ix < gf.nx) ? (T)(0.5f * p1f(KIND, gf.nx, gc.nx, ix, X)) : T(0);
+    wy[k] = (iy >= 0 && iy < gf.ny) ? (T)(0.5f * p1f(KIND, gf.ny, gc.ny, iy, Y)) : T(0);
+  }
+#pragma unroll
+  for (int k = 0; k <= 2 * RZ; ++k) {
+    const int iz = 2 * Z - RZ + k;
+    wz[k] = DIM == 3 ? ((iz >= 0 && iz < gf.nz) ? (T)(0.5f * p1f(KIND, gf.nz, gc.nz, iz, Z)) : T(0)) : T(1);
+  }
+  c_t<T> acc = cmk<c_t<T>>(0, 0);
+#pragma unroll
+  for (int kz = 0; kz <= 2 * RZ; ++kz) {
+    if (wz[kz] == T(0)) continue;
+    const int iz = 2 * Z - RZ + kz;
+#pragma unroll
+    for (int ky = 0; ky <= 2 * RAD; ++ky) {
+      const T wyz = wy[ky] * wz[kz];
+      if (wyz == T(0)) continue;
+      const int row = (iz * gf.ny + (2 * Y - RAD + ky)) * gf.nx + 2 * X - RAD;
+#pragma unroll
+      for (int kx = 0; kx <= 2 * RAD; ++kx) {
+        if (wx[kx] == T(0)) continue;
+        const c_t<T> v = r[row + kx];
+        const T ww = wyz * wx[kx];
+        acc.x += ww * v.x;
+        acc.y += ww * v.y;
+      }
+    }
+  }
+  fc[(Z * gc.ny + Y) * gc.nx + X] = acc;
+}
+
+// 1D prolongation stencil of fine index j: coarse nodes J0, J0+1, J0+2 with
+// weights w[0..2] (zero where unused).  Odd j = 2J+1: (c_J + c_{J+1})/2 for both
+// kinds; even j = 2J: c_J (linear) or (c_{J-1} + 6 c_J + c_{J+1})/8 (cubic), the
+// two end nodes using the mirrored ghost (3/4, 1/4).  Same values as p1.
+template <int KIND>
+__device__ __forceinline__ int p1_stencil(int j, int nf, int nc, float (&w)[3]) {
+  const int J = j >> 1;
+  if (j & 1) {
+    w[0] = 0.5f; w[1] = 0.5f; w[2] = 0.0f;
+    return J;
+  }
+  if (KIND == 0) {
+    w[0] = 1.0f; w[1] = 0.0f; w[2] = 0.0f;
+    return J;
+  }
+  if (j == 0) {
+    w[0] = 0.75f; w[1] = 0.25f; w[2] = 0.0f;
+    return 0;
+  }
+  if (j == nf - 1) {
+    w[0] = 0.25f; w[1] = 0.75f; w[2] = 0.0f;
+    return nc - 2;
+  }
+  w[0] = 0.125f; w[1] = 0.75f; w[2] = 0.125f;
+  return J - 1;
+}
+
+// (P e_c) at fine node (x, y, z)
+template <typename T, int DIM, int KIND>
+__device__ __forceinline__ c_t<T> prolong_at(const Geo& gf, const Geo& gc, const c_t<T>* __restrict__ ec, int x, int y,
+                                             int z) {
+  float wx[3], wy[3], wz[3] = {1.0f, 0.0f, 0.0f};
+  const int X0 = p1_stencil<KIND>(x, gf.nx, gc.nx, wx);
+  const int Y0 = p1_stencil<KIND>(y, gf.ny, gc.ny, wy);
+  const int Z0 = DIM == 3 ? p1_stencil<KIND>(z, gf.nz, gc.nz, wz) : 0;
+  c_t<T> acc = cmk<c_t<T>>(0, 0);
+#pragma unroll
+  for (int c = 0; c < (DIM == 3 ? 3 : 1); ++c) {
+    if (wz[c] == 0.0f) continue;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const float wyz = wz[c] * wy[b];
+      if (wyz == 0.0f) continue;
+      const int row = ((Z0 + c) * gc.ny + Y0 + b) * gc.nx + X0;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        if (wx[a] == 0.0f) continue;
+        const T w3 = (T)(wyz * wx[a]);
+        const c_t<T> v = ec[row + a];
+        acc.x += w3 * v.x;
+        acc.y += w3 * v.y;
+      }
+    }
+  }
+  return acc;
+}
+
+// out = in + P e_c (pointwise; out may alias in)
+template <typename T, int DIM, int KIND>
+__global__ void __launch_bounds__(BX* BY) k_prolong(Geo gf, Geo gc, const c_t<T>* __restrict__ ec, const c_t<T>* in,
+                                                    c_t<T>* out, const int* active) {
+  if (active && !*active) return;
+  int x, y, z;
+  if (!node_xyz(gf, x, y, z)) return;
+  const int p = (z * gf.ny + y) * gf.nx + x;
+  out[p] = in[p] + prolong_at<T, DIM, KIND>(gf, gc, ec, x, y, z);
+}
+
+// 2D: u' = t + P e_c on a tile with halo RA in shared memory, then
+//   DIAG = false: out = u', r = f - A u'
+//   DIAG = true : out = u' + w m0 (f - A u')
+template <typename T, int AK, int KIND, bool DIAG>
+__global__ void __launch_bounds__(BX* BY) k_prolong_fused_2d(Geo gf, Geo gc, T invh2, const c_t<T>* __restrict__ A,
+                                                             const c_t<T>* __restrict__ ec, const c_t<T>* __restrict__ t,
+                                                             const c_t<T>* __restrict__ f, const c_t<T>* __restrict__ m0,
+                                                             T w, c_t<T>* __restrict__ out, c_t<T>* __restrict__ r,
+                                                             const int* active) {
+  if (active && !*active) return;
+  constexpr int RA = AK == 0 ? 1 : AK;
+  constexpr int TX = BX + 2 * RA, TY = BY + 2 * RA;
+  __shared__ c_t<T> sm[TY][TX];
+  const int x0 = blockIdx.x * BX - RA, y0 = blockIdx.y * BY - RA;
+  const int tid = threadIdx.y * BX + threadIdx.x;
+  for (int i = tid; i < TX * TY; i += BX * BY) {
+    const int ty = i / TX, tx = i - ty * TX;
+    const int gx = x0 + tx, gy = y0 + ty;
+    c_t<T> v = cmk<c_t<T>>(0, 0);
+    if (gx >= 0 && gx < gf.nx && gy >= 0 && gy < gf.ny)
+      v = t[gy * gf.nx + gx] + prolong_at<T, 2, KIND>(gf, gc, ec, gx, gy, 0);
+    sm[ty][tx] = v;
+  }
+  __syncthreads();
+  int x, y, z;
+  if (!node_xyz(gf, x, y, z)) return;
+  const int p = y * gf.nx + x;
+  const int lx = threadIdx.x + RA, ly = threadIdx.y + RA;
+  const c_t<T> up = sm[ly][lx];
+  c_t<T> a;
+  if constexpr (AK == 0) {
+    // zeros outside the grid in the tile: the neighbour sums are the in-grid sums
+    const T wx = (x == 0 || x == gf.nx - 1) ? T(0.5) : T(1);
+    const T wy = (y == 0 || y == gf.ny - 1) ? T(0.5) : T(1);
+    const c_t<T> sx = sm[ly][lx - 1] + sm[ly][lx + 1];
+    const c_t<T> sy = sm[ly - 1][lx] + sm[ly + 1][lx];
+    a = cmul(A[p], up);
+    a.x -= invh2 * (wy * sx.x + wx * sy.x);
+    a.y -= invh2 * (wy * sx.y + wx * sy.y);
+  } else {
+    // coefficients reaching outside the grid are stored as zeros
+    a = cmk<c_t<T>>(0, 0);
+    constexpr int W = 2 * AK + 1;
+#pragma unroll
+    for (int dy = -AK; dy <= AK; ++dy)
+#pragma unroll
+      for (int dx = -AK; dx <= AK; ++dx)
+        a = cfma(A[((dy + AK) * W + (dx + AK)) * gf.N + p], sm[ly + dy][lx + dx], a);
+  }
+  const c_t<T> res = f[p] - a;
+  if (DIAG) {
+    out[p] = up + scale(cmul(m0[p], res), w);
+  } else {
+    out[p] = up;
+    r[p] = res;
+  }
+}
+
+// u = Ainv f, one warp per row
+template <typename T>
+__global__ void k_dense_gemv(int n, const c_t<T>* __restrict__ A, const c_t<T>* __restrict__ f, c_t<T>* __restrict__ u,
+                             const int* active) {
+  if (active && !*active) return;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= n) return;
+  c_t<T> acc = cmk<c_t<T>>(0, 0);
+  const c_t<T>* row = A + (long long)warp * n;
+  for (int j = lane; j < n; j += 32) acc = cfma(row[j], f[j], acc);
+  for (int o = 16; o > 0; o >>= 1) {
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+  }
+  if (lane == 0) u[warp] = acc;
+}
+
+// ------------------------------------------------------------------ dispatch
+template <typename F>
+void with_dim_ak(int dim, int ak, F&& f) {
+#define HZ_DA(D, K) \
+  if (dim == D && ak == K) return f(std::integral_constant<int, D>{}, std::integral_constant<int, K>{});
+  HZ_DA(2, 0) HZ_DA(2, 1) HZ_DA(2, 2) HZ_DA(2, 3) HZ_DA(3, 0) HZ_DA(3, 1) HZ_DA(3, 2)
+#undef HZ_DA
+  throw Error(HZ_ERR_INVALID_ARG, "unsupported stencil radius");
+}
+
+inline int akind(const Level& L) { return L.fine ? 0 : L.A.off.rho; }
+
+template <typename T>
+void resid(Ctx& c, int l, const void* u, const void* f, void* r, const int* active, cudaStream_t s) {
+  Level& L = c.L[l];
+  const Geo g = geo(L.g);
+  const T invh2 = (T)(1.0 / (c.h * c.h));
+  with_dim_ak(L.g.dim, akind(L), [&](auto D, auto K) {
+    k_resid<T, D, K><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, invh2, (const c_t<T>*)L.Aw, (const c_t<T>*)u,
+                                                         (const c_t<T>*)f, (c_t<T>*)r, active);
+  });
+  HZ_LAUNCHED();
+}
+
+template <typename T>
+void sweep_out(Ctx& c, int l, const void* r, const void* in, void* out, const int* active, cudaStream_t s) {
+  Level& L = c.L[l];
+  const Geo g = geo(L.g);
+  const MList m = mlist(L);
+  if (L.g.dim == 2)
+    k_sweep_out<T, 2><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, m, (const c_t<T>*)L.Mw, (T)L.damping,
+                                                          (const c_t<T>*)r, (const c_t<T>*)in, (c_t<T>*)out, active);
+  else
+    k_sweep_out<T, 3><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, m, (const c_t<T>*)L.Mw, (T)L.damping,
+                                                          (const c_t<T>*)r, (const c_t<T>*)in, (c_t<T>*)out, active);
+  HZ_LAUNCHED();
+}
+
+template <typename T>
+void sweep0(Ctx& c, int l, const void* f, void* u, const int* active, cudaStream_t s) {
+  Level& L = c.L[l];
+  const Geo g = geo(L.g);
+  const MList m = mlist(L);
+  if (L.g.dim == 2)
+    k_sweep0<T, 2><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, m, (const c_t<T>*)L.Mw, (T)L.damping, (const c_t<T>*)f,
+                                                       (c_t<T>*)u, active);
+  else
+    k_sweep0<T, 3><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, m, (const c_t<T>*)L.Mw, (T)L.damping, (const c_t<T>*)f,
+                                                       (c_t<T>*)u, active);
+  HZ_LAUNCHED();
+}
+
+template <typename T>
+void sweep0_resid_diag(Ctx& c, int l, const void* f, void* u, void* r, const int* active, cudaStream_t s) {
+  Level& L = c.L[l];
+  const Geo g = geo(L.g);
+  const T invh2 = (T)(1.0 / (c.h * c.h));
+  with_dim_ak(L.g.dim, akind(L), [&](auto D, auto K) {
+    k_sweep0_resid_diag<T, D, K><<<grid_of(g), dim3(BX, BY), 0, s>>>(
+        g, invh2, (const c_t<T>*)L.Aw, (const c_t<T>*)L.Mw, (T)L.damping, (const c_t<T>*)f, (c_t<T>*)u, (c_t<T>*)r,
+        active);
+  });
+  HZ_LAUNCHED();
+}
+
+template <typename T>
+void resid_sweep_diag(Ctx& c, int l, const void* f, const void* in, void* out, const int* active, cudaStream_t s) {
+  Level& L = c.L[l];
+  const Geo g = geo(L.g);
+  const T invh2 = (T)(1.0 / (c.h * c.h));
+  with_dim_ak(L.g.dim, akind(L), [&](auto D, auto K) {
+    k_resid_sweep_diag<T, D, K><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, invh2, (const c_t<T>*)L.Aw,
+                                                                    (const c_t<T>*)L.Mw, (T)L.damping, (const c_t<T>*)f,
+                                                                    (const c_t<T>*)in, (c_t<T>*)out, active);
+  });
+  HZ_LAUNCHED();
+}
+
+template <typename T>
+void restrict_t(Ctx& c, int l, const void* r, void* fc, const int* active, cudaStream_t s) {
+  Level& L = c.L[l];
+  Level& C = c.L[l + 1];
+  const Geo gf = geo(L.g), gc = geo(C.g);
+  auto go = [&](auto D, auto KIND) {
+    k_restrict<T, D, KIND><<<grid_of(gc), dim3(BX, BY), 0, s>>>(gf, gc, (const c_t<T>*)r, (c_t<T>*)fc, active);
+  };
+  using I2 = std::integral_constant<int, 2>;
+  using I3 = std::integral_constant<int, 3>;
+  using K0 = std::integral_constant<int, 0>;
+  using K1 = std::integral_constant<int, 1>;
+  if (L.g.dim == 2) L.rkind ? go(I2{}, K1{}) : go(I2{}, K0{});
+  else L.rkind ? go(I3{}, K1{}) : go(I3{}, K0{});
+  HZ_LAUNCHED();
+}
+
+template <typename T>
+void prolong_t(Ctx& c, int l, const void* ec, const void* in, void* out, const int* active, cudaStream_t s) {
+  Level& L = c.L[l];
+  Level& C = c.L[l + 1];
+  const Geo gf = geo(L.g), gc = geo(C.g);
+  auto go = [&](auto D, auto KIND) {
+    k_prolong<T, D, KIND><<<grid_of(gf), dim3(BX, BY), 0, s>>>(gf, gc, (const c_t<T>*)ec, (const c_t<T>*)in,
+                                                              (c_t<T>*)out, active);
+  };
+  using I2 = std::integral_constant<int, 2>;
+  using I3 = std::integral_constant<int, 3>;
+  using K0 = std::integral_constant<int, 0>;
+  using K1 = std::integral_constant<int, 1>;
+  if (L.g.dim == 2) L.pkind ? go(I2{}, K1{}) : go(I2{}, K0{});
+  else L.pkind ? go(I3{}, K1{}) : go(I3{}, K0{});
+  HZ_LAUNCHED();
+}
+
+// 2D fused prolongation + residual (DIAG: + diagonal sweep)
+template <typename T, bool DIAG>
+void prolong_fused_2d(Ctx& c, int l, const void* ec, const void* t, const void* f, void* out, void* r,
+                      const int* active, cudaStream_t s) {
+  Level& L = c.L[l];
+  Level& C = c.L[l + 1];
+  const Geo gf = geo(L.g), gc = geo(C.g);
+  const T invh2 = (T)(1.0 / (c.h * c.h));
+  auto go = [&](auto K, auto KIND) {
+    k_prolong_fused_2d<T, K, KIND, DIAG><<<grid_of(gf), dim3(BX, BY), 0, s>>>(
+        gf, gc, invh2, (const c_t<T>*)L.Aw, (const c_t<T>*)ec, (const c_t<T>*)t, (const c_t<T>*)f,
+        (const c_t<T>*)L.Mw, (T)L.damping, (c_t<T>*)out, (c_t<T>*)r, active);
+  };
+  using K0 = std::integral_constant<int, 0>;
+  using K1 = std::integral_constant<int, 1>;
+  auto kind = [&](auto K) { L.pkind ? go(K, K1{}) : go(K, K0{}); };
+  switch (akind(L)) {
+    case 0: kind(std::integral_constant<int, 0>{}); break;
+    case 1: kind(std::integral_constant<int, 1>{}); break;
+    case 2: kind(std::integral_constant<int, 2>{}); break;
+    case 3: kind(std::integral_constant<int, 3>{}); break;
+    default: throw Error(HZ_ERR_INVALID_ARG, "unsupported stencil radius");
+  }
+  HZ_LAUNCHED();
+}
+
+template <typename T>
+void coarse_t(Ctx& c, const void* f, void* u, const int* active, cudaStream_t s) {
+  Level& L = c.L.back();
+  const int n = (int)L.g.N;
+  k_dense_gemv<T><<<nblk((long long)n * 32, 256), 256, 0, s>>>(n, (const c_t<T>*)L.Ainvw, (const c_t<T>*)f,
+                                                              (c_t<T>*)u, active);
+  HZ_LAUNCHED();
+}
+
+// One V(nu1, nu2) cycle at level l for A_l u = f from u = 0; result in `out`.
+template <typename T>
+void vcycle_t(Ctx& c, int l, const void* f, void* out, const int* active, cudaStream_t s) {
+  Level& L = c.L[l];
+  if (L.coarsest) {
+    coarse_t<T>(c, f, out, active, s);
+    return;
+  }
+  const int nu1 = c.opts.nu1, nu2 = c.opts.nu2;
+  const bool d2 = L.g.dim == 2;
+  // steps 1-2: pre-relaxation into t, residual into r
+  const void* rr = L.r;
+  if (nu1 == 0) {
+    HZ_CUDA(cudaMemsetAsync(L.t, 0, sizeof(c_t<T>) * L.g.N, s));
+    rr = f;
+  } else if (L.m_diag && nu1 == 1) {
+    sweep0_resid_diag<T>(c, l, f, L.t, L.r, active, s);
+  } else {
+    sweep0<T>(c, l, f, L.t, active, s);
+    for (int i = 1; i < nu1; ++i) {
+      resid<T>(c, l, L.t, f, L.r, active, s);
+      sweep_out<T>(c, l, L.r, L.t, L.t, active, s);
+    }
+    resid<T>(c, l, L.t, f, L.r, active, s);
+  }
+  Level& C = c.L[l + 1];
+  restrict_t<T>(c, l, rr, C.f, active, s);
+  vcycle_t<T>(c, l + 1, C.f, C.u, active, s);                   // step 3 (recursive)
+  // steps 4-5: coarse-grid correction and post-relaxation into out
+  if (nu2 == 0) {
+    prolong_t<T>(c, l, C.u, L.t, out, active, s);
+    return;
+  }
+  if (d2 && L.m_diag && nu2 == 1) {
+    prolong_fused_2d<T, true>(c, l, C.u, L.t, f, out, nullptr, active, s);
+    return;
+  }
+  if (d2) {
+    prolong_fused_2d<T, false>(c, l, C.u, L.t, f, out, L.r, active, s);
+    sweep_out<T>(c, l, L.r, out, out, active, s);
+  } else {
+    prolong_t<T>(c, l, C.u, L.t, L.t, active, s);
+    if (L.m_diag && nu2 == 1) {
+      resid_sweep_diag<T>(c, l, f, L.t, out, active, s);
+      return;
+    }
+    resid<T>(c, l, L.t, f, L.r, active, s);
+    sweep_out<T>(c, l, L.r, L.t, out, active, s);
+  }
+  for (int i = 1; i < nu2; ++i) {
+    resid<T>(c, l, out, f, L.r, active, s);
+    sweep_out<T>(c, l, L.r, out, out, active, s);
+  }
+}
+
+}  // namespace cyc
+}  // namespace hz

@@ -6,16 +6,22 @@
 //   z_j = V-cycle(f0)              stored in the working precision (the
 //                                  Arnoldi relation A Z = V H holds for the
 //                                  stored z_j, so FP32 storage loses nothing)
-//   w = A z_j  fused with  h1 = V^H w               (one pass)
-//   w -= V h1  fused with  h2 = V^H w, ||w||^2      (classical Gram-Schmidt,
-//   w -= V h2  fused with  ||w||^2                    applied twice: CGS2)
-//   H(:, j) = h1 + h2, H(j+1, j) = ||w||, complex Givens update of H and g,
+//   modified Gram-Schmidt, one pass per basis vector with each update fused
+//   with the next inner product:
+//     pass 0      w = A z_j,           h_0j = v_0^H w
+//     pass i      w -= h_{i-1,j} v_{i-1}, h_ij = v_i^H w      (i = 1..j)
+//     pass j+1    w -= h_jj v_j,       ||w||^2
+//   (half the FP64 operations of classical Gram-Schmidt applied twice,
+//   whose second pass was needed at every iteration here)
+//   H(:, j), H(j+1, j) = ||w||, complex Givens update of H and g,
 //   residual estimate |g_{j+1}| / ||q_hat|| and the stop flag: all on the
-//   device, no host synchronisation inside a restart cycle.
+//   device.
 // v_{j+1} is stored unnormalised with its scale 1/||w|| (deferred
 // normalisation).  At the end of a cycle: y = H^{-1} g (back substitution),
-// p += Z y, true residual q_hat - A p in FP64, restart.  The host reads one
-// small status record per restart cycle.
+// p += Z y, true residual q_hat - A p in FP64, restart.  One restart cycle is
+// captured once as a CUDA graph and replayed; the host reads one small status
+// record per cycle.  GB300's FP64 rate is 1/64 of FP32, so the FP64 passes
+// are organised to minimise FP64 operations per node, not just bytes.
 //
 // Reductions are two-stage and deterministic: each pass kernel writes one
 // partial per block, a second kernel sums the partials in a fixed order.
@@ -28,6 +34,9 @@ namespace hz {
 
 constexpr int kMaxM = 16;
 constexpr int kRedBlock = 256;
+constexpr int BX = 32, BY = 8;
+constexpr int kRows = 4;        // y rows per thread in the 2D passes
+constexpr int kPerThread = 4;   // nodes per thread in the 1D passes
 
 struct KrylovStatus {       // first bytes of KrylovState, copied to the host each cycle
   int iters;
@@ -50,37 +59,62 @@ struct KrylovState {
   double2 g[kMaxM + 1];
   double scale[kMaxM + 1];  // v_i = scale[i] * V[i]
   double2 y[kMaxM];
-  double2 h1[kMaxM + 1];    // raw dots conj(V_i) . w of the two CGS passes
-  double2 h2[kMaxM + 2];
-  double2 nrm2;             // .x = ||w||^2
+  double2 h1[kMaxM + 2];    // raw dots conj(V_i) . w of the Gram-Schmidt passes
+  double2 nrm2;             // .x = ||w||^2 after orthogonalisation
+  unsigned counter;         // blocks finished in the current reduction (last block resets it)
 };
 
 namespace {
 
 inline unsigned nblk(long long n, int b) { return (unsigned)((n + b - 1) / b); }
 
-__device__ __forceinline__ void coords(const GridDev& g, long long p, int& x, int& y, int& z) {
-  x = (int)(p % g.nx);
-  long long t = p / g.nx;
-  y = (int)(t % g.ny);
-  z = (int)(t / g.ny);
+struct Geo {
+  int nx, ny, nz, sxy, N, dim;
+};
+inline Geo geo(const GridDev& g) { return Geo{g.nx, g.ny, g.nz, g.nx * g.ny, (int)g.N, g.dim}; }
+// 2D grid of 32 x 8 blocks over (x, y), kRows rows per thread; blockIdx.z strides over z
+inline dim3 grid_xy(const Geo& g) {
+  return dim3((g.nx + BX - 1) / BX, (g.ny + BY * kRows - 1) / (BY * kRows), g.nz < 8 ? g.nz : 8);
+}
+inline unsigned grid_1d(long long N) { return nblk(N, kRedBlock * kPerThread); }
+inline int grid_blocks(const Geo& g) {
+  const dim3 d = grid_xy(g);
+  return (int)(d.x * d.y * d.z);
 }
 
-template <typename U>
-__device__ __forceinline__ double2 ld64(const U* __restrict__ a, long long i) {
-  const U v = a[i];
-  return make_double2((double)v.x, (double)v.y);
+// w - c v with two DFMA per component
+__device__ __forceinline__ double2 axmy(double2 w, double2 c, double2 v) {
+  return make_double2(fma(c.y, v.y, fma(-c.x, v.x, w.x)), fma(-c.y, v.x, fma(-c.x, v.y, w.y)));
+}
+// acc + conj(v) w with two DFMA per component
+__device__ __forceinline__ double2 dot_acc(double2 acc, double2 v, double2 w) {
+  return make_double2(fma(v.y, w.y, fma(v.x, w.x, acc.x)), fma(-v.y, w.x, fma(v.x, w.y, acc.y)));
+}
+// acc + |w|^2
+__device__ __forceinline__ double nrm_acc(double acc, double2 w) { return fma(w.y, w.y, fma(w.x, w.x, acc)); }
+
+__device__ __forceinline__ double2 ld64(const double2* __restrict__ a, int i) { return a[i]; }
+__device__ __forceinline__ double2 ld64(const float2* __restrict__ a, int i) {
+  const float2 v = a[i];
+  return make_double2(f2d_exact(v.x), f2d_exact(v.y));
 }
 
-// FP64 fine-level A v at node p (5-/7-point, half-cell weights)
+// FP64 fine-level (A v)_p, 5-/7-point with half-cell weights
 template <typename U>
-__device__ __forceinline__ double2 apply_A(const GridDev& g, double invh2, const double2* __restrict__ diag,
-                                           const U* __restrict__ v, long long p) {
-  int x, y, z;
-  coords(g, p, x, y, z);
-  const double wx = wgt(x, g.nx), wy = wgt(y, g.ny);
-  const double wz = g.dim == 3 ? wgt(z, g.nz) : 1.0;
-  double2 acc = cmul(diag[p], ld64(v, p));
+__device__ __forceinline__ double2 apply_A(const Geo& g, double invh2, const double2* __restrict__ diag,
+                                           const U* __restrict__ v, int p, int x, int y, int z) {
+  const double2 d = diag[p], vp = ld64(v, p);
+  const bool inx = x > 0 && x < g.nx - 1, iny = y > 0 && y < g.ny - 1;
+  const bool inz = g.dim == 2 || (z > 0 && z < g.nz - 1);
+  if (inx && iny && inz) {
+    double2 s = ld64(v, p - 1) + ld64(v, p + 1) + ld64(v, p - g.nx) + ld64(v, p + g.nx);
+    if (g.dim == 3) s = s + ld64(v, p - g.sxy) + ld64(v, p + g.sxy);
+    // d v - invh2 s, with FMAs
+    return make_double2(fma(d.x, vp.x, fma(-d.y, vp.y, -invh2 * s.x)), fma(d.x, vp.y, fma(d.y, vp.x, -invh2 * s.y)));
+  }
+  double2 acc = cmul(d, vp);
+  const double wx = inx ? 1.0 : 0.5, wy = iny ? 1.0 : 0.5;
+  const double wz = (g.dim == 3 && !inz) ? 0.5 : 1.0;
   double2 sx = make_double2(0, 0), sy = make_double2(0, 0);
   if (x > 0) sx = sx + ld64(v, p - 1);
   if (x < g.nx - 1) sx = sx + ld64(v, p + 1);
@@ -90,10 +124,9 @@ __device__ __forceinline__ double2 apply_A(const GridDev& g, double invh2, const
   acc.x -= cx * sx.x + cy * sy.x;
   acc.y -= cx * sx.y + cy * sy.y;
   if (g.dim == 3) {
-    const long long pl = (long long)g.nx * g.ny;
     double2 sz = make_double2(0, 0);
-    if (z > 0) sz = sz + ld64(v, p - pl);
-    if (z < g.nz - 1) sz = sz + ld64(v, p + pl);
+    if (z > 0) sz = sz + ld64(v, p - g.sxy);
+    if (z < g.nz - 1) sz = sz + ld64(v, p + g.sxy);
     const double cz = wx * wy * invh2;
     acc.x -= cz * sz.x;
     acc.y -= cz * sz.y;
@@ -101,98 +134,114 @@ __device__ __forceinline__ double2 apply_A(const GridDev& g, double invh2, const
   return acc;
 }
 
-// Block-reduce K double2 accumulators; thread 0 writes partials[k*nb + block].
-template <int K>
-__device__ __forceinline__ void block_store(double2 (&acc)[K], double2* __restrict__ partials, int nb) {
-  __shared__ double2 sm[K][kRedBlock / 32];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    double2 v = acc[k];
-    for (int o = 16; o > 0; o >>= 1) {
-      v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
-      v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
-    }
-    if (lane == 0) sm[k][wid] = v;
+// Block-reduce one double2 accumulator per thread; thread 0 writes partials[block].
+__device__ __forceinline__ void block_store(double2 acc, double2* __restrict__ partials, int block) {
+  __shared__ double2 sm[kRedBlock / 32];
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int lane = tid & 31, wid = tid >> 5;
+  for (int o = 16; o > 0; o >>= 1) {
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
   }
+  if (lane == 0) sm[wid] = acc;
   __syncthreads();
-  if (threadIdx.x < K) {
+  if (tid == 0) {
     double2 s = make_double2(0, 0);
-    for (int w = 0; w < kRedBlock / 32; ++w) s = s + sm[threadIdx.x][w];
-    partials[(long long)threadIdx.x * nb + blockIdx.x] = s;
+    for (int w = 0; w < kRedBlock / 32; ++w) s = s + sm[w];
+    partials[block] = s;
   }
 }
 
-// w = A z_j -> V[NV]; partial dots conj(V_i) . w, i < NV
-template <int NV, typename TZ>
-__global__ void __launch_bounds__(kRedBlock) k_matvec_dots(GridDev g, double invh2, const double2* __restrict__ diag,
-                                                           const TZ* __restrict__ z, double2* __restrict__ V,
-                                                           double2* __restrict__ partials, int nb,
-                                                           const KrylovState* __restrict__ st) {
-  if (!st->active) return;
-  double2 acc[NV];
-#pragma unroll
-  for (int i = 0; i < NV; ++i) acc[i] = make_double2(0, 0);
-  const long long N = g.N;
-  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
-    const double2 w = apply_A(g, invh2, diag, z, p);
-    V[(long long)NV * N + p] = w;
-#pragma unroll
-    for (int i = 0; i < NV; ++i) acc[i] = acc[i] + cconjmul(V[(long long)i * N + p], w);
-  }
-  block_store<NV>(acc, partials, nb);
-}
-
-// w -= sum_i c_i V_i with c_i = raw_i * scale_i^2; FIRST: partial dots of the
-// result with V_i (i < NV) and ||w||^2 (slot NV); else only ||w||^2 (slot 0).
-template <int NV, bool FIRST>
-__global__ void __launch_bounds__(kRedBlock) k_orth(long long N, double2* __restrict__ V, double2* __restrict__ partials,
-                                                    int nb, const KrylovState* __restrict__ st) {
-  if (!st->active) return;
-  double2 c[NV];
-#pragma unroll
-  for (int i = 0; i < NV; ++i) {
-    const double s = st->scale[i];
-    const double2 raw = FIRST ? st->h1[i] : st->h2[i];
-    c[i] = (s * s) * raw;
-  }
-  constexpr int K = FIRST ? NV + 1 : 1;
-  double2 acc[K];
-#pragma unroll
-  for (int i = 0; i < K; ++i) acc[i] = make_double2(0, 0);
-  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
-    double2 w = V[(long long)NV * N + p];
-    double2 vi[NV];
-#pragma unroll
-    for (int i = 0; i < NV; ++i) {
-      vi[i] = V[(long long)i * N + p];
-      w = w - cmul(c[i], vi[i]);
-    }
-    V[(long long)NV * N + p] = w;
-    if (FIRST) {
-#pragma unroll
-      for (int i = 0; i < NV; ++i) acc[i] = acc[i] + cconjmul(vi[i], w);
-    }
-    acc[K - 1].x += cabs2(w);
-  }
-  block_store<K>(acc, partials, nb);
-}
-
-// out[v] = sum_b partials[v*nb + b], one block per v; runs when *flag != 0
-__global__ void k_reduce(const double2* __restrict__ partials, int nb, double2* __restrict__ out, const int* flag,
-                         int flag_value) {
-  if (flag && *flag != flag_value) return;
-  __shared__ double2 sm[kRedBlock];
-  const int v = blockIdx.x;
-  double2 s = make_double2(0, 0);
-  for (int b = threadIdx.x; b < nb; b += blockDim.x) s = s + partials[(long long)v * nb + b];
-  sm[threadIdx.x] = s;
+// Two-stage deterministic reduction finished by the last block to arrive:
+// every block stores its partial, the last one sums all partials in index
+// order into *out and returns true (in all its threads).
+__device__ __forceinline__ bool reduce_last(double2 acc, double2* __restrict__ partials, int nb, int block,
+                                            unsigned* counter, double2* out) {
+  block_store(acc, partials, block);
+  __threadfence();
   __syncthreads();
-  for (int k = blockDim.x / 2; k > 0; k >>= 1) {
-    if (threadIdx.x < k) sm[threadIdx.x] = sm[threadIdx.x] + sm[threadIdx.x + k];
+  __shared__ int is_last;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  if (tid == 0) is_last = atomicAdd(counter, 1u) == (unsigned)(nb - 1);
+  __syncthreads();
+  if (!is_last) return false;
+  __threadfence();
+  __shared__ double2 red[kRedBlock];
+  double2 s = make_double2(0, 0);
+  int b = tid;
+  for (; b + 3 * kRedBlock < nb; b += 4 * kRedBlock) {
+    const double2 a0 = __ldcg(partials + b), a1 = __ldcg(partials + b + kRedBlock);
+    const double2 a2 = __ldcg(partials + b + 2 * kRedBlock), a3 = __ldcg(partials + b + 3 * kRedBlock);
+    s = s + ((a0 + a1) + (a2 + a3));
+  }
+  for (; b < nb; b += kRedBlock) s = s + __ldcg(partials + b);
+  red[tid] = s;
+  __syncthreads();
+  for (int k = kRedBlock / 2; k > 0; k >>= 1) {
+    if (tid < k) red[tid] = red[tid] + red[tid + k];
     __syncthreads();
   }
-  if (threadIdx.x == 0) out[v] = sm[0];
+  if (tid == 0) {
+    *out = red[0];
+    *counter = 0u;
+  }
+  return true;
+}
+
+__device__ __forceinline__ int block_linear() { return (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x; }
+
+__device__ void arnoldi_update(KrylovState* st, int j);
+
+// pass 0: w = A z_j -> V[j+1]; h_0j (raw) = conj(V_0) . w
+template <typename TZ>
+__global__ void __launch_bounds__(kRedBlock) k_mgs_first(Geo g, double invh2, const double2* __restrict__ diag,
+                                                         const TZ* __restrict__ z, double2* __restrict__ V, int j,
+                                                         double2* __restrict__ partials, KrylovState* st) {
+  if (!st->active) return;
+  double2 acc = make_double2(0, 0);
+  const int x = blockIdx.x * BX + threadIdx.x;
+  double2* w = V + (j + 1) * g.N;
+  if (x < g.nx) {
+    for (int zz = blockIdx.z; zz < g.nz; zz += gridDim.z) {
+#pragma unroll
+      for (int k = 0; k < kRows; ++k) {
+        const int y = (blockIdx.y * kRows + k) * BY + threadIdx.y;
+        if (y >= g.ny) break;
+        const int p = (zz * g.ny + y) * g.nx + x;
+        const double2 a = apply_A(g, invh2, diag, z, p, x, y, zz);
+        w[p] = a;
+        acc = dot_acc(acc, V[p], a);
+      }
+    }
+  }
+  reduce_last(acc, partials, gridDim.x * gridDim.y * gridDim.z, block_linear(), &st->counter, &st->h1[0]);
+}
+
+// pass i (1..j): w -= h_{i-1} v_{i-1}; h_ij (raw) = conj(V_i) . w
+// pass j+1 (LAST): w -= h_j v_j; ||w||^2, then (last block) the Arnoldi column
+template <bool LAST>
+__global__ void __launch_bounds__(kRedBlock) k_mgs_step(int N, double2* __restrict__ V, int j, int i,
+                                                        double2* __restrict__ partials, KrylovState* st) {
+  if (!st->active) return;
+  const double s = st->scale[i - 1];
+  const double2 c = (s * s) * st->h1[i - 1];          // h_{i-1,j} * scale_{i-1}
+  const double2* vp = V + (i - 1) * N;
+  const double2* vi = V + i * N;
+  double2* w = V + (j + 1) * N;
+  double2 acc = make_double2(0, 0);
+  const int base = blockIdx.x * (kRedBlock * kPerThread) + threadIdx.x;
+#pragma unroll
+  for (int k = 0; k < kPerThread; ++k) {
+    const int p = base + k * kRedBlock;
+    if (p < N) {
+      const double2 ww = axmy(w[p], c, vp[p]);
+      w[p] = ww;
+      if (LAST) acc.x = nrm_acc(acc.x, ww);
+      else acc = dot_acc(acc, vi[p], ww);
+    }
+  }
+  const bool last = reduce_last(acc, partials, gridDim.x, blockIdx.x, &st->counter, LAST ? &st->nrm2 : &st->h1[i]);
+  if (LAST && last && threadIdx.x == 0) arnoldi_update(st, j);
 }
 
 __device__ void givens(double2 a, double2 b, double& c, double2& s) {
@@ -214,10 +263,10 @@ __device__ void givens(double2 a, double2 b, double& c, double2& s) {
   s = (1.0 / t) * cmul(ph, make_double2(b.x, -b.y));
 }
 
-// Column j of the Hessenberg matrix, Givens rotations, residual estimate.
-__global__ void k_arnoldi(KrylovState* __restrict__ st, int j) {
-  if (!st->active) return;
-  for (int i = 0; i <= j; ++i) st->H[i][j] = st->scale[i] * (st->h1[i] + st->h2[i]);
+// Column j of the Hessenberg matrix, Givens rotations, residual estimate
+// (one thread, in the last block of the final Gram-Schmidt pass).
+__device__ void arnoldi_update(KrylovState* st, int j) {
+  for (int i = 0; i <= j; ++i) st->H[i][j] = st->scale[i] * st->h1[i];
   const double hn = sqrt(st->nrm2.x);
   st->H[j + 1][j] = make_double2(hn, 0.0);
   for (int i = 0; i < j; ++i) {
@@ -251,12 +300,18 @@ __global__ void k_arnoldi(KrylovState* __restrict__ st, int j) {
 }
 
 template <typename V>
-__global__ void k_cast_in(long long N, const double2* __restrict__ v, const KrylovState* __restrict__ st, int j,
+__global__ void k_cast_in(int N, const double2* __restrict__ v, const KrylovState* __restrict__ st, int j,
                           V* __restrict__ f) {
   if (!st->active) return;
-  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= N) return;
-  f[p] = from_c128<V>(st->scale[j] * v[p]);
+  const double2 a = v[p];
+  if constexpr (std::is_same<V, float2>::value) {
+    const float sc = d2f_rn(st->scale[j]);
+    f[p] = make_float2(d2f_rn(a.x) * sc, d2f_rn(a.y) * sc);
+  } else {
+    f[p] = st->scale[j] * a;
+  }
 }
 
 __global__ void k_solve_y(KrylovState* __restrict__ st) {
@@ -270,35 +325,49 @@ __global__ void k_solve_y(KrylovState* __restrict__ st) {
 }
 
 template <typename TZ>
-__global__ void k_update_p(long long N, const TZ* __restrict__ Z, const KrylovState* __restrict__ st,
+__global__ void k_update_p(int N, const TZ* __restrict__ Z, const KrylovState* __restrict__ st,
                            double2* __restrict__ p) {
   if (st->st.done) return;
-  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= N) return;
   const int k = st->kcyc;
   double2 acc = p[q];
-  for (int i = 0; i < k; ++i) acc = acc + cmul(st->y[i], ld64(Z, (long long)i * N + q));
+  for (int i = 0; i < k; ++i) {
+    const double2 yi = st->y[i], zi = ld64(Z, i * N + q);
+    acc = make_double2(fma(yi.x, zi.x, fma(-yi.y, zi.y, acc.x)), fma(yi.x, zi.y, fma(yi.y, zi.x, acc.y)));
+  }
   p[q] = acc;
 }
 
-// r = q_hat - A p -> V_0; partial ||r||^2
-__global__ void __launch_bounds__(kRedBlock) k_true_residual(GridDev g, double invh2, const double2* __restrict__ diag,
+__device__ void restart_update(KrylovState* st);
+
+// r = q_hat - A p -> V_0; ||r||^2, then (last block) the restart decision
+__global__ void __launch_bounds__(kRedBlock) k_true_residual(Geo g, double invh2, const double2* __restrict__ diag,
                                                              const double2* __restrict__ p,
                                                              const double2* __restrict__ qhat, double2* __restrict__ r,
-                                                             double2* __restrict__ partials, int nb,
-                                                             const KrylovState* __restrict__ st) {
+                                                             double2* __restrict__ partials, KrylovState* st) {
   if (st->st.done) return;
-  double2 acc[1] = {make_double2(0, 0)};
-  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < g.N; q += (long long)gridDim.x * blockDim.x) {
-    const double2 v = qhat[q] - apply_A(g, invh2, diag, p, q);
-    r[q] = v;
-    acc[0].x += cabs2(v);
+  double2 acc = make_double2(0, 0);
+  const int x = blockIdx.x * BX + threadIdx.x;
+  if (x < g.nx) {
+    for (int zz = blockIdx.z; zz < g.nz; zz += gridDim.z) {
+#pragma unroll
+      for (int k = 0; k < kRows; ++k) {
+        const int y = (blockIdx.y * kRows + k) * BY + threadIdx.y;
+        if (y >= g.ny) break;
+        const int q = (zz * g.ny + y) * g.nx + x;
+        const double2 v = qhat[q] - apply_A(g, invh2, diag, p, q, x, y, zz);
+        r[q] = v;
+        acc.x = nrm_acc(acc.x, v);
+      }
+    }
   }
-  block_store<1>(acc, partials, nb);
+  const bool last = reduce_last(acc, partials, gridDim.x * gridDim.y * gridDim.z, block_linear(), &st->counter,
+                                &st->nrm2);
+  if (last && threadIdx.x == 0 && threadIdx.y == 0) restart_update(st);
 }
 
-__global__ void k_restart(KrylovState* __restrict__ st) {
-  if (st->st.done) return;
+__device__ void restart_update(KrylovState* st) {
   const double beta = sqrt(st->nrm2.x);
   st->st.relres_true = beta / st->bnorm;
   st->active = 0;
@@ -319,63 +388,55 @@ __global__ void k_restart(KrylovState* __restrict__ st) {
   st->active = 1;
 }
 
-// q_hat = wmass * q; partial ||q_hat||^2
-__global__ void __launch_bounds__(kRedBlock) k_scale_rhs(long long N, const double* __restrict__ wmass,
+// q_hat = wmass * q; ||q_hat||^2, then (last block) the solver state
+__global__ void __launch_bounds__(kRedBlock) k_scale_rhs(int N, const double* __restrict__ wmass,
                                                          const double2* __restrict__ q, double2* __restrict__ qhat,
-                                                         double2* __restrict__ partials, int nb) {
-  double2 acc[1] = {make_double2(0, 0)};
-  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+                                                         double2* __restrict__ partials, KrylovState* st, double tol,
+                                                         int max_iter, int m) {
+  double2 acc = make_double2(0, 0);
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < N) {
     const double2 v = wmass[p] * q[p];
     qhat[p] = v;
-    acc[0].x += cabs2(v);
+    acc.x = cabs2(v);
   }
-  block_store<1>(acc, partials, nb);
-}
-
-__global__ void k_init(KrylovState* __restrict__ st, double tol, int max_iter, int m) {
-  const double bn = sqrt(st->nrm2.x);
-  st->bnorm = bn;
-  st->tol = tol;
-  st->max_iter = max_iter;
-  st->m = m;
-  st->st.iters = 0;
-  st->st.breakdown = 0;
-  st->st.relres_est = bn > 0 ? 1.0 : 0.0;
-  st->st.relres_true = bn > 0 ? 1.0 : 0.0;
-  st->st.done = bn > 0 ? 0 : 1;
-  st->st.converged = bn > 0 ? 0 : 1;
-  st->active = 0;
-  st->kcyc = 0;
+  const bool last = reduce_last(acc, partials, gridDim.x, blockIdx.x, &st->counter, &st->nrm2);
+  if (last && threadIdx.x == 0) {
+    const double bn = sqrt(st->nrm2.x);
+    st->bnorm = bn;
+    st->tol = tol;
+    st->max_iter = max_iter;
+    st->m = m;
+    st->st.iters = 0;
+    st->st.breakdown = 0;
+    st->st.relres_est = bn > 0 ? 1.0 : 0.0;
+    st->st.relres_true = bn > 0 ? 1.0 : 0.0;
+    st->st.done = bn > 0 ? 0 : 1;
+    st->st.converged = bn > 0 ? 0 : 1;
+    st->active = 0;
+    st->kcyc = 0;
+  }
 }
 
 template <typename V>
-__global__ void k_cast_vec(long long N, const double2* __restrict__ in, V* __restrict__ out) {
-  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void k_cast_vec(int N, const double2* __restrict__ in, V* __restrict__ out) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p < N) out[p] = from_c128<V>(in[p]);
 }
 template <typename V>
-__global__ void k_widen_vec(long long N, const V* __restrict__ in, double2* __restrict__ out) {
-  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void k_widen_vec(int N, const V* __restrict__ in, double2* __restrict__ out) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p < N) out[p] = ld64(in, p);
 }
 
-template <typename F>
-void dispatch_nv(int nv, F&& f) {
-  switch (nv) {
-#define HZ_NV(k) case k: f(std::integral_constant<int, k>{}); break;
-    HZ_NV(1) HZ_NV(2) HZ_NV(3) HZ_NV(4) HZ_NV(5) HZ_NV(6) HZ_NV(7) HZ_NV(8)
-    HZ_NV(9) HZ_NV(10) HZ_NV(11) HZ_NV(12) HZ_NV(13) HZ_NV(14) HZ_NV(15) HZ_NV(16)
-#undef HZ_NV
-    default: throw Error(HZ_ERR_INVALID_ARG, "restart length out of range");
-  }
-}
-
+// One restart cycle: m inner iterations (skipped on the device once stopped),
+// the solution update and the true residual; solution accumulates in c.p.
 template <typename TZ>
-void run_cycle(Ctx& c, double2* p, cudaStream_t s) {
+void run_cycle(Ctx& c, cudaStream_t s) {
   Level& L0 = c.L[0];
-  const long long N = L0.g.N;
+  const Geo g = geo(L0.g);
+  const int N = g.N;
   const int m = c.opts.restart_m;
-  const int nb = c.red_blocks;
   const double invh2 = 1.0 / (c.h * c.h);
   KrylovState* st = c.ks;
   const int* active = &st->active;
@@ -383,50 +444,77 @@ void run_cycle(Ctx& c, double2* p, cudaStream_t s) {
   for (int j = 0; j < m; ++j) {
     k_cast_in<TZ><<<nblk(N, 256), 256, 0, s>>>(N, c.V + (long long)j * N, st, j, (TZ*)L0.f);
     vcycle(c, L0.f, Z + (long long)j * N, active, s);
-    dispatch_nv(j + 1, [&](auto nvc) {
-      constexpr int NV = decltype(nvc)::value;
-      k_matvec_dots<NV, TZ><<<nb, kRedBlock, 0, s>>>(L0.g, invh2, c.diagA64, Z + (long long)j * N, c.V,
-                                                     c.partials, nb, st);
-      k_reduce<<<NV, kRedBlock, 0, s>>>(c.partials, nb, st->h1, active, 1);
-      k_orth<NV, true><<<nb, kRedBlock, 0, s>>>(N, c.V, c.partials, nb, st);
-      k_reduce<<<NV + 1, kRedBlock, 0, s>>>(c.partials, nb, st->h2, active, 1);
-      k_orth<NV, false><<<nb, kRedBlock, 0, s>>>(N, c.V, c.partials, nb, st);
-      k_reduce<<<1, kRedBlock, 0, s>>>(c.partials, nb, &st->nrm2, active, 1);
-    });
-    k_arnoldi<<<1, 1, 0, s>>>(st, j);
+    k_mgs_first<TZ><<<grid_xy(g), dim3(BX, BY), 0, s>>>(g, invh2, c.diagA64, Z + (long long)j * N, c.V, j,
+                                                         c.partials, st);
+    for (int i = 1; i <= j; ++i)
+      k_mgs_step<false><<<grid_1d(N), kRedBlock, 0, s>>>(N, c.V, j, i, c.partials, st);
+    k_mgs_step<true><<<grid_1d(N), kRedBlock, 0, s>>>(N, c.V, j, j + 1, c.partials, st);
   }
   HZ_LAUNCHED();
-  const int* done = &st->st.done;
   k_solve_y<<<1, 1, 0, s>>>(st);
-  k_update_p<TZ><<<nblk(N, 256), 256, 0, s>>>(N, Z, st, p);
-  k_true_residual<<<nb, kRedBlock, 0, s>>>(L0.g, invh2, c.diagA64, p, c.qhat, c.V, c.partials, nb, st);
-  k_reduce<<<1, kRedBlock, 0, s>>>(c.partials, nb, &st->nrm2, done, 0);
-  k_restart<<<1, 1, 0, s>>>(st);
+  k_update_p<TZ><<<nblk(N, 256), 256, 0, s>>>(N, Z, st, c.p);
+  k_true_residual<<<grid_xy(g), dim3(BX, BY), 0, s>>>(g, invh2, c.diagA64, c.p, c.qhat, c.V, c.partials, st);
   HZ_LAUNCHED();
 }
 
 template <typename TZ>
-void solve_t(Ctx& c, const double2* q, double2* p, hz_info* info, cudaStream_t s) {
+void ensure_graph(Ctx& c) {
+  if (c.cycle_graph) return;
+  cudaGraph_t graph = nullptr;
+  HZ_CUDA(cudaStreamBeginCapture(c.graph_stream, cudaStreamCaptureModeThreadLocal));
+  try {
+    run_cycle<TZ>(c, c.graph_stream);
+  } catch (...) {
+    cudaStreamEndCapture(c.graph_stream, &graph);
+    if (graph) cudaGraphDestroy(graph);
+    throw;
+  }
+  HZ_CUDA(cudaStreamEndCapture(c.graph_stream, &graph));
+  size_t nn = 0;
+  HZ_CUDA(cudaGraphGetNodes(graph, nullptr, &nn));
+  std::vector<cudaGraphNode_t> nodes(nn);
+  HZ_CUDA(cudaGraphGetNodes(graph, nodes.data(), &nn));
+  c.graph_kernels = 0;
+  for (auto n : nodes) {
+    cudaGraphNodeType t;
+    HZ_CUDA(cudaGraphNodeGetType(n, &t));
+    if (t == cudaGraphNodeTypeKernel) ++c.graph_kernels;
+  }
+  const cudaError_t e = cudaGraphInstantiate(&c.cycle_graph, graph, 0);
+  cudaGraphDestroy(graph);
+  HZ_CUDA(e);
+}
+
+template <typename TZ>
+void solve_t(Ctx& c, const double2* q, double2* p, hz_info* info, cudaStream_t user) {
   Level& L0 = c.L[0];
-  const long long N = L0.g.N;
-  const int nb = c.red_blocks;
+  const Geo g = geo(L0.g);
+  const int N = g.N;
   const double invh2 = 1.0 / (c.h * c.h);
   KrylovState* st = c.ks;
   KrylovStatus* hs = (KrylovStatus*)c.ks_host;
-  k_scale_rhs<<<nb, kRedBlock, 0, s>>>(N, c.wmass, q, c.qhat, c.partials, nb);
-  k_reduce<<<1, kRedBlock, 0, s>>>(c.partials, nb, &st->nrm2, nullptr, 0);
-  k_init<<<1, 1, 0, s>>>(st, c.opts.tol, c.opts.max_iter, c.opts.restart_m);
-  HZ_CUDA(cudaMemsetAsync(p, 0, sizeof(double2) * N, s));
-  k_true_residual<<<nb, kRedBlock, 0, s>>>(L0.g, invh2, c.diagA64, p, c.qhat, c.V, c.partials, nb, st);
-  k_reduce<<<1, kRedBlock, 0, s>>>(c.partials, nb, &st->nrm2, &st->st.done, 0);
-  k_restart<<<1, 1, 0, s>>>(st);
+  ensure_graph<TZ>(c);
+  // the work runs on the library's stream, ordered after the caller's stream
+  cudaStream_t s = c.graph_stream;
+  HZ_CUDA(cudaEventRecord(c.ev_in, user));
+  HZ_CUDA(cudaStreamWaitEvent(s, c.ev_in, 0));
+  HZ_CUDA(cudaMemsetAsync(&st->counter, 0, sizeof(unsigned), s));
+  k_scale_rhs<<<nblk(N, kRedBlock), kRedBlock, 0, s>>>(N, c.wmass, q, c.qhat, c.partials, st, c.opts.tol,
+                                                       c.opts.max_iter, c.opts.restart_m);
+  HZ_CUDA(cudaMemsetAsync(c.p, 0, sizeof(double2) * N, s));
+  k_true_residual<<<grid_xy(g), dim3(BX, BY), 0, s>>>(g, invh2, c.diagA64, c.p, c.qhat, c.V, c.partials, st);
   HZ_LAUNCHED();
+  c.launches += 2;
   for (;;) {
     HZ_CUDA(cudaMemcpyAsync(hs, &st->st, sizeof(KrylovStatus), cudaMemcpyDeviceToHost, s));
     HZ_CUDA(cudaStreamSynchronize(s));
     if (hs->done) break;
-    run_cycle<TZ>(c, p, s);
+    HZ_CUDA(cudaGraphLaunch(c.cycle_graph, s));
+    c.launches += c.graph_kernels;
   }
+  if (p != c.p) HZ_CUDA(cudaMemcpyAsync(p, c.p, sizeof(double2) * N, cudaMemcpyDeviceToDevice, s));
+  HZ_CUDA(cudaEventRecord(c.ev_out, s));
+  HZ_CUDA(cudaStreamWaitEvent(user, c.ev_out, 0));
   info->iters = hs->iters;
   info->converged = hs->converged;
   info->relres_est = hs->relres_est;
@@ -439,7 +527,8 @@ size_t krylov_bytes(const hz_grid& g, const hz_opts& o) {
   long long N = (long long)g.n[0] * g.n[1] * (g.dim == 3 ? g.n[2] : 1);
   const size_t vb = o.precision == HZ_PREC_MIXED ? 8 : 16;
   const int m = o.restart_m;
-  return 16ull * N * (m + 1) + vb * N * m + 16ull * N * 3 + 16ull * (kMaxM + 2) * 2048 + sizeof(KrylovState);
+  const long long nb = nblk(N, kRedBlock) * 2;
+  return 16ull * N * (m + 1) + vb * N * m + 16ull * N * 4 + 16ull * nb + sizeof(KrylovState);
 }
 
 void krylov_alloc(Ctx& c) {
@@ -447,14 +536,20 @@ void krylov_alloc(Ctx& c) {
   const int m = c.opts.restart_m;
   const size_t vb = c.mixed ? sizeof(float2) : sizeof(double2);
   require(m >= 1 && m <= kMaxM, "restart_m must be in 1..16");
+  require(N * (m + 1) < (1ll << 31), "grid too large for 32-bit Krylov indexing");
   c.V = (double2*)ctx_alloc(c, sizeof(double2) * N * (m + 1));
   c.Z = ctx_alloc(c, vb * N * m);
   c.qhat = (double2*)ctx_alloc(c, sizeof(double2) * N);
-  c.red_blocks = (int)std::min<long long>(nblk(N, kRedBlock), 1216);
-  c.partials = (double2*)ctx_alloc(c, sizeof(double2) * (kMaxM + 2) * c.red_blocks);
+  c.p = (double2*)ctx_alloc(c, sizeof(double2) * N);
+  const Geo g = geo(c.L[0].g);
+  const int nb = std::max<int>(grid_blocks(g), (int)nblk(N, kRedBlock));
+  c.partials = (double2*)ctx_alloc(c, sizeof(double2) * nb);
   c.ks = (KrylovState*)ctx_alloc(c, sizeof(KrylovState));
   HZ_CUDA(cudaMemset(c.ks, 0, sizeof(KrylovState)));
   HZ_CUDA(cudaMallocHost(&c.ks_host, sizeof(KrylovStatus)));
+  HZ_CUDA(cudaStreamCreateWithFlags(&c.graph_stream, cudaStreamNonBlocking));
+  HZ_CUDA(cudaEventCreateWithFlags(&c.ev_in, cudaEventDisableTiming));
+  HZ_CUDA(cudaEventCreateWithFlags(&c.ev_out, cudaEventDisableTiming));
 }
 
 void fgmres_solve(Ctx& c, const double2* q, double2* p, hz_info* info, cudaStream_t s) {
@@ -464,7 +559,7 @@ void fgmres_solve(Ctx& c, const double2* q, double2* p, hz_info* info, cudaStrea
 
 void precond_apply_c128(Ctx& c, const double2* r, double2* z, cudaStream_t s) {
   Level& L0 = c.L[0];
-  const long long N = L0.g.N;
+  const int N = (int)L0.g.N;
   if (c.mixed) {
     k_cast_vec<float2><<<nblk(N, 256), 256, 0, s>>>(N, r, (float2*)L0.f);
     vcycle(c, L0.f, L0.u, nullptr, s);

@@ -527,6 +527,7 @@ static void assemble_smoother(Ctx& c, Level& L, cudaStream_t s) {
       src.push_back(e);
     }
   L.M = make_lut(keep);
+  L.m_diag = keep.size() == 1 && keep[0][0] == 0 && keep[0][1] == 0 && keep[0][2] == 0;
   L.M64 = (double2*)ctx_alloc(c, sizeof(double2) * N * keep.size());
   for (size_t k = 0; k < src.size(); ++k)
     HZ_CUDA(cudaMemcpyAsync(L.M64 + (long long)k * N, Mp + (long long)src[k] * N, sizeof(double2) * N,
@@ -611,6 +612,9 @@ void build_hierarchy(Ctx& c, const double* kappa, const double* gamma, double ga
     L.u = ctx_alloc(c, vb * N * R);
     L.f = ctx_alloc(c, vb * N * R);
     L.r = ctx_alloc(c, vb * N * R);
+    L.t = ctx_alloc(c, vb * N * R);
+    require(N * (long long)std::max(L.A.off.n, L.coarsest ? 1 : L.M.off.n) < (1ll << 31),
+            "level too large for 32-bit plane indexing");
   }
   HZ_CUDA(cudaStreamSynchronize(s));
 }

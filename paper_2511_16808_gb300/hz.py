@@ -79,6 +79,7 @@ _SIGS = {
     "hz_solve": ([_P, _P, _P, C.c_int, C.POINTER(hz_info), _P], C.c_int),
     "hz_precond_apply": ([_P, _P, _P, C.c_int, _P], C.c_int),
     "hz_apply_operator": ([_P, _P, _P, C.c_int, C.c_int, _P], C.c_int),
+    "hz_kernel_launches": ([_P, C.POINTER(C.c_int64)], C.c_int),
     "hz_level_count": ([_P, C.POINTER(C.c_int)], C.c_int),
     "hz_level_describe": ([_P, C.c_int, C.POINTER(hz_level_desc)], C.c_int),
     "hz_level_export": ([_P, C.c_int, C.c_int, _P], C.c_int),
@@ -203,6 +204,12 @@ def hz_precond_apply(ctx, r, z, nrhs: int = 1, stream=None) -> None:
 def hz_apply_operator(ctx, v, w, nrhs: int = 1, shifted: int = 0, stream=None) -> None:
     _check(lib.hz_apply_operator(ctx, _ptr(v), _ptr(w), nrhs, int(shifted), _stream(stream)),
            "hz_apply_operator")
+
+
+def hz_kernel_launches(ctx) -> int:
+    out = C.c_int64()
+    _check(lib.hz_kernel_launches(ctx, C.byref(out)), "hz_kernel_launches")
+    return out.value
 
 
 # ------------------------------------------------------------------ components
