@@ -183,6 +183,19 @@ hz_status hz_apply_operator(hz_ctx* ctx, const void* v, void* w, int nrhs, int s
  * kernels of an iteration skipped on the device after convergence count). */
 hz_status hz_kernel_launches(const hz_ctx* ctx, int64_t* count);
 
+/* Measurement hooks.  hz_profile_select makes every later hz_solve on this
+ * context record CUDA events around each launch of one kernel class:
+ *   0 none, 1 the Gram-Schmidt update passes, 2 the first Gram-Schmidt pass
+ *   (FP64 operator apply + inner product), 3 the whole V-cycle.
+ * Only launches of inner iterations that did work are counted.  The restart
+ * cycle graph is re-captured with the events; the overhead is two event
+ * records per bracketed launch.  hz_profile_read returns the accumulated
+ * device time, launch count, and the algorithmic bytes and FP64 flops of
+ * those launches (per-node counts documented with each kernel).  Selecting a
+ * class resets the accumulators. */
+hz_status hz_profile_select(hz_ctx* ctx, int kernel_class);
+hz_status hz_profile_read(const hz_ctx* ctx, double* total_ms, int64_t* launches, double* bytes, double* flops);
+
 /* ---- component entry points (one row of the method each) ---------------
  * Level fields are device arrays in the context's V-cycle precision (c128
  * for HZ_PREC_FP64, c64 for HZ_PREC_MIXED) of the level's node count. */

@@ -32,6 +32,8 @@ void* ctx_alloc(Ctx& c, size_t bytes) {
 void ctx_free_all(Ctx& c) {
   if (c.cycle_graph) cudaGraphExecDestroy(c.cycle_graph);
   c.cycle_graph = nullptr;
+  for (auto e : c.prof_ev) cudaEventDestroy(e);
+  c.prof_ev.clear();
   if (c.ev_in) cudaEventDestroy(c.ev_in);
   if (c.ev_out) cudaEventDestroy(c.ev_out);
   if (c.graph_stream) cudaStreamDestroy(c.graph_stream);
@@ -329,6 +331,26 @@ hz_status hz_kernel_launches(const hz_ctx* ctx, int64_t* count) {
   return guarded([&] {
     require(ctx && count, "null argument");
     *count = ctx->c.launches;
+  });
+}
+
+hz_status hz_profile_select(hz_ctx* ctx, int kernel_class) {
+  return guarded([&] {
+    require(ctx != nullptr, "null context");
+    require(kernel_class >= 0 && kernel_class <= 3, "unknown kernel class");
+    BusyGuard bg(&ctx->c);
+    profile_select(ctx->c, kernel_class);
+  });
+}
+
+hz_status hz_profile_read(const hz_ctx* ctx, double* total_ms, int64_t* launches, double* bytes, double* flops) {
+  return guarded([&] {
+    require(ctx && total_ms && launches && bytes && flops, "null argument");
+    const Ctx& c = ctx->c;
+    *total_ms = c.prof_ms;
+    *launches = c.prof_launches;
+    *bytes = c.prof_bytes;
+    *flops = c.prof_flops;
   });
 }
 

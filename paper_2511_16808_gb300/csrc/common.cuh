@@ -263,6 +263,14 @@ struct Ctx {
   cudaStream_t graph_stream = nullptr;   // library stream the solve runs on (graph capture needs one)
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   int graph_kernels = 0;        // kernel nodes in the captured restart cycle
+  // measurement hooks (hz_profile_select / hz_profile_read): CUDA events around
+  // the launches of one kernel class inside the captured cycle
+  int prof_class = 0;
+  std::vector<cudaEvent_t> prof_ev;            // 2 per bracketed launch
+  std::vector<int> prof_j;                     // inner iteration of each bracketed launch
+  std::vector<double> prof_b, prof_f;          // algorithmic bytes / flops of each launch
+  double prof_ms = 0, prof_bytes = 0, prof_flops = 0;
+  long long prof_launches = 0;
   long long launches = 0;       // kernels launched by hz_solve on this context
 };
 
@@ -290,5 +298,6 @@ size_t krylov_bytes(const hz_grid& g, const hz_opts& o);
 void krylov_alloc(Ctx& c);
 void fgmres_solve(Ctx& c, const double2* q_dev, double2* p_dev, hz_info* info, cudaStream_t s);
 void precond_apply_c128(Ctx& c, const double2* r, double2* z, cudaStream_t s);
+void profile_select(Ctx& c, int cls);
 
 }  // namespace hz

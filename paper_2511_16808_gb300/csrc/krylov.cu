@@ -429,6 +429,60 @@ __global__ void k_widen_vec(int N, const V* __restrict__ in, double2* __restrict
   if (p < N) out[p] = ld64(in, p);
 }
 
+// ---- measurement hooks: events around the launches of the selected class
+// (1 = Gram-Schmidt update passes k_mgs_step, 2 = first pass k_mgs_first with
+// the FP64 operator, 3 = whole V-cycle preconditioner application)
+int prof_begin(Ctx& c, int cls, int j, double bytes, double flops, cudaStream_t s) {
+  if (c.prof_class != cls) return -1;
+  const int k = (int)c.prof_j.size();
+  if ((int)c.prof_ev.size() < 2 * (k + 1)) {
+    cudaEvent_t a, b;
+    HZ_CUDA(cudaEventCreate(&a));
+    HZ_CUDA(cudaEventCreate(&b));
+    c.prof_ev.push_back(a);
+    c.prof_ev.push_back(b);
+  }
+  c.prof_j.push_back(j);
+  c.prof_b.push_back(bytes);
+  c.prof_f.push_back(flops);
+  HZ_CUDA(cudaEventRecordWithFlags(c.prof_ev[2 * k], s, cudaEventRecordExternal));
+  return k;
+}
+void prof_end(Ctx& c, int k, cudaStream_t s) {
+  if (k >= 0) HZ_CUDA(cudaEventRecordWithFlags(c.prof_ev[2 * k + 1], s, cudaEventRecordExternal));
+}
+// after a replayed cycle in which `ran` inner iterations did work
+void prof_collect(Ctx& c, int ran) {
+  for (size_t k = 0; k < c.prof_j.size(); ++k) {
+    if (c.prof_j[k] >= ran) continue;
+    float ms = 0.f;
+    HZ_CUDA(cudaEventElapsedTime(&ms, c.prof_ev[2 * k], c.prof_ev[2 * k + 1]));
+    c.prof_ms += ms;
+    c.prof_bytes += c.prof_b[k];
+    c.prof_flops += c.prof_f[k];
+    c.prof_launches += 1;
+  }
+}
+
+// Algorithmic (compulsory) bytes of one V-cycle with the kernels of cycle_impl.cuh
+double vcycle_bytes(const Ctx& c) {
+  const double b = c.mixed ? 8.0 : 16.0;
+  double tot = 0;
+  for (size_t l = 0; l < c.L.size(); ++l) {
+    const Level& L = c.L[l];
+    const double N = (double)L.g.N;
+    if (L.coarsest) {
+      tot += N * N * b + 2 * N * b;
+      continue;
+    }
+    const double sA = L.fine ? 1.0 : L.A.off.n, sM = L.M.off.n;
+    const double rc = L.g.dim == 3 ? 0.125 : 0.25;
+    if (L.m_diag) tot += N * b * (5 + (1 + rc) + (5 + rc)) + (sA - 1) * 2 * N * b;   // sweep0+resid, restrict, prolong+sweep
+    else tot += N * b * (2 * sM + 2 * sA + 13 + 2 * rc);
+  }
+  return tot;
+}
+
 // One restart cycle: m inner iterations (skipped on the device once stopped),
 // the solution update and the true residual; solution accumulates in c.p.
 template <typename TZ>
@@ -443,12 +497,24 @@ void run_cycle(Ctx& c, cudaStream_t s) {
   TZ* Z = (TZ*)c.Z;
   for (int j = 0; j < m; ++j) {
     k_cast_in<TZ><<<nblk(N, 256), 256, 0, s>>>(N, c.V + (long long)j * N, st, j, (TZ*)L0.f);
+    int pk = prof_begin(c, 3, j, vcycle_bytes(c), 0.0, s);
     vcycle(c, L0.f, Z + (long long)j * N, active, s);
+    prof_end(c, pk, s);
+    // k_mgs_first: z (b), diag, v_0 read, w written; 24 flops (A z: 16, dot: 8)
+    pk = prof_begin(c, 2, j, (double)N * (sizeof(TZ) + 48), 24.0 * N, s);
     k_mgs_first<TZ><<<grid_xy(g), dim3(BX, BY), 0, s>>>(g, invh2, c.diagA64, Z + (long long)j * N, c.V, j,
                                                          c.partials, st);
-    for (int i = 1; i <= j; ++i)
+    prof_end(c, pk, s);
+    for (int i = 1; i <= j; ++i) {
+      // w, v_{i-1}, v_i read, w written; 8 flops update + 8 flops dot
+      pk = prof_begin(c, 1, j, 64.0 * N, 16.0 * N, s);
       k_mgs_step<false><<<grid_1d(N), kRedBlock, 0, s>>>(N, c.V, j, i, c.partials, st);
+      prof_end(c, pk, s);
+    }
+    // w, v_j read, w written; 8 flops update + 4 flops norm
+    pk = prof_begin(c, 1, j, 48.0 * N, 12.0 * N, s);
     k_mgs_step<true><<<grid_1d(N), kRedBlock, 0, s>>>(N, c.V, j, j + 1, c.partials, st);
+    prof_end(c, pk, s);
   }
   HZ_LAUNCHED();
   k_solve_y<<<1, 1, 0, s>>>(st);
@@ -460,6 +526,9 @@ void run_cycle(Ctx& c, cudaStream_t s) {
 template <typename TZ>
 void ensure_graph(Ctx& c) {
   if (c.cycle_graph) return;
+  c.prof_j.clear();
+  c.prof_b.clear();
+  c.prof_f.clear();
   cudaGraph_t graph = nullptr;
   HZ_CUDA(cudaStreamBeginCapture(c.graph_stream, cudaStreamCaptureModeThreadLocal));
   try {
@@ -505,11 +574,16 @@ void solve_t(Ctx& c, const double2* q, double2* p, hz_info* info, cudaStream_t u
   k_true_residual<<<grid_xy(g), dim3(BX, BY), 0, s>>>(g, invh2, c.diagA64, c.p, c.qhat, c.V, c.partials, st);
   HZ_LAUNCHED();
   c.launches += 2;
+  int before = 0;
+  bool replayed = false;
   for (;;) {
     HZ_CUDA(cudaMemcpyAsync(hs, &st->st, sizeof(KrylovStatus), cudaMemcpyDeviceToHost, s));
     HZ_CUDA(cudaStreamSynchronize(s));
+    if (replayed && c.prof_class) prof_collect(c, hs->iters - before);
     if (hs->done) break;
+    before = hs->iters;
     HZ_CUDA(cudaGraphLaunch(c.cycle_graph, s));
+    replayed = true;
     c.launches += c.graph_kernels;
   }
   if (p != c.p) HZ_CUDA(cudaMemcpyAsync(p, c.p, sizeof(double2) * N, cudaMemcpyDeviceToDevice, s));
@@ -550,6 +624,14 @@ void krylov_alloc(Ctx& c) {
   HZ_CUDA(cudaStreamCreateWithFlags(&c.graph_stream, cudaStreamNonBlocking));
   HZ_CUDA(cudaEventCreateWithFlags(&c.ev_in, cudaEventDisableTiming));
   HZ_CUDA(cudaEventCreateWithFlags(&c.ev_out, cudaEventDisableTiming));
+}
+
+void profile_select(Ctx& c, int cls) {
+  if (c.cycle_graph) cudaGraphExecDestroy(c.cycle_graph);
+  c.cycle_graph = nullptr;
+  c.prof_class = cls;
+  c.prof_ms = c.prof_bytes = c.prof_flops = 0;
+  c.prof_launches = 0;
 }
 
 void fgmres_solve(Ctx& c, const double2* q, double2* p, hz_info* info, cudaStream_t s) {

@@ -80,6 +80,9 @@ _SIGS = {
     "hz_precond_apply": ([_P, _P, _P, C.c_int, _P], C.c_int),
     "hz_apply_operator": ([_P, _P, _P, C.c_int, C.c_int, _P], C.c_int),
     "hz_kernel_launches": ([_P, C.POINTER(C.c_int64)], C.c_int),
+    "hz_profile_select": ([_P, C.c_int], C.c_int),
+    "hz_profile_read": ([_P, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_double),
+                         C.POINTER(C.c_double)], C.c_int),
     "hz_level_count": ([_P, C.POINTER(C.c_int)], C.c_int),
     "hz_level_describe": ([_P, C.c_int, C.POINTER(hz_level_desc)], C.c_int),
     "hz_level_export": ([_P, C.c_int, C.c_int, _P], C.c_int),
@@ -210,6 +213,19 @@ def hz_kernel_launches(ctx) -> int:
     out = C.c_int64()
     _check(lib.hz_kernel_launches(ctx, C.byref(out)), "hz_kernel_launches")
     return out.value
+
+
+PROFILE = {"none": 0, "mgs_step": 1, "mgs_first": 2, "vcycle": 3}
+
+
+def hz_profile_select(ctx, kernel_class) -> None:
+    _check(lib.hz_profile_select(ctx, PROFILE.get(kernel_class, kernel_class)), "hz_profile_select")
+
+
+def hz_profile_read(ctx) -> dict:
+    ms, n, b, f = C.c_double(), C.c_int64(), C.c_double(), C.c_double()
+    _check(lib.hz_profile_read(ctx, C.byref(ms), C.byref(n), C.byref(b), C.byref(f)), "hz_profile_read")
+    return {"ms": ms.value, "launches": n.value, "bytes": b.value, "flops": f.value}
 
 
 # ------------------------------------------------------------------ components
