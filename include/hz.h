@@ -166,12 +166,16 @@ hz_status hz_destroy(hz_ctx* ctx);
 /* Solve A p = q_hat with FGMRES(m) preconditioned by one V(nu1,nu2)-cycle
  * (zero initial guess, Section 5).  q: unscaled source, c128, host or device,
  * nodes*nrhs values; p: c128 output, host or device; info: nrhs entries
- * (host).  Returns HZ_ERR_NOT_CONVERGED (with p and info filled) when any
- * right-hand side misses tol within max_iter. */
+ * (host).  nrhs is a power of two <= opts.nrhs_max (<= 64); with nrhs > 1 the
+ * right-hand sides share each batched V-cycle launch (RHS index innermost)
+ * while each keeps its own Krylov state and convergence, so its iteration
+ * count is the one it has alone.  Returns HZ_ERR_NOT_CONVERGED (with p and
+ * info filled) when any right-hand side misses tol within max_iter. */
 hz_status hz_solve(hz_ctx* ctx, const void* q, void* p, int nrhs, hz_info* info, void* cuda_stream);
 
 /* z = V-cycle(r) with zero initial guess (Algorithm 1, recursive).
- * r, z: c128 device arrays of nodes*nrhs values (r in the row-scaled space). */
+ * r, z: c128 device arrays of nodes*nrhs values (r in the row-scaled space);
+ * nrhs as for hz_solve. */
 hz_status hz_precond_apply(hz_ctx* ctx, const void* r, void* z, int nrhs, void* cuda_stream);
 
 /* w = A v (shifted = 0) or w = A_s v (shifted = 1), FP64; c128 device arrays. */

@@ -32,6 +32,8 @@ void* ctx_alloc(Ctx& c, size_t bytes) {
 void ctx_free_all(Ctx& c) {
   if (c.cycle_graph) cudaGraphExecDestroy(c.cycle_graph);
   c.cycle_graph = nullptr;
+  if (c.batch_graph) cudaGraphExecDestroy(c.batch_graph);
+  c.batch_graph = nullptr;
   for (auto e : c.prof_ev) cudaEventDestroy(e);
   c.prof_ev.clear();
   if (c.ev_in) cudaEventDestroy(c.ev_in);
@@ -104,7 +106,7 @@ void validate(const hz_grid* g, const hz_opts* o) {
   require(o->nu1 >= 0 && o->nu2 >= 0 && o->nu1 + o->nu2 <= 16, "nu1/nu2 out of range");
   require(o->restart_m >= 1 && o->restart_m <= 16, "restart_m out of range");
   require(o->tol > 0 && o->max_iter >= 1, "tol/max_iter out of range");
-  require(o->nrhs_max >= 1, "nrhs_max must be >= 1");
+  require(o->nrhs_max >= 1 && o->nrhs_max <= 64, "nrhs_max must be in 1..64");
   require(o->precision == HZ_PREC_FP64 || o->precision == HZ_PREC_MIXED, "bad precision");
   require(o->intergrid >= HZ_IG_LINEAR && o->intergrid <= HZ_IG_LEVELDEP, "bad intergrid");
   require(!(g->dim == 3 && o->intergrid == HZ_IG_CUBIC && o->levels >= 3),
@@ -287,43 +289,50 @@ hz_status hz_solve(hz_ctx* ctx, const void* q, void* p, int nrhs, hz_info* info,
   return guarded([&] {
     require(ctx && q && p && info, "null argument");
     Ctx& c = ctx->c;
-    require(nrhs == 1, "this build solves one right-hand side per call");
+    require(nrhs >= 1 && nrhs <= c.opts.nrhs_max && (nrhs & (nrhs - 1)) == 0,
+            "nrhs must be a power of two <= nrhs_max (and <= 64)");
     BusyGuard bg(&c);
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    const long long N = c.L[0].g.N;
+    const long long N = c.L[0].g.N * nrhs;
     const double2* qd = (const double2*)q;
     double2* pd = (double2*)p;
     const bool q_host = !is_device_ptr(q), p_host = !is_device_ptr(p);
     if (q_host) {
-      if (!c.qstage) c.qstage = (double2*)ctx_alloc(c, sizeof(double2) * N);
+      if (!c.qstage) c.qstage = (double2*)ctx_alloc(c, sizeof(double2) * c.L[0].g.N * c.opts.nrhs_max);
       HZ_CUDA(cudaMemcpyAsync(c.qstage, q, sizeof(double2) * N, cudaMemcpyHostToDevice, s));
       qd = c.qstage;
     }
     if (p_host) pd = c.p;
-    fgmres_solve(c, qd, pd, info, s);
+    if (nrhs == 1) fgmres_solve(c, qd, pd, info, s);
+    else fgmres_solve_batch(c, qd, pd, nrhs, info, s);
     if (p_host) {
       HZ_CUDA(cudaMemcpyAsync(p, pd, sizeof(double2) * N, cudaMemcpyDeviceToHost, s));
       HZ_CUDA(cudaStreamSynchronize(s));
     }
-    if (!info->converged) throw Error(HZ_ERR_NOT_CONVERGED, "FGMRES did not reach tol within max_iter");
+    for (int r = 0; r < nrhs; ++r)
+      if (!info[r].converged) throw Error(HZ_ERR_NOT_CONVERGED, "FGMRES did not reach tol within max_iter");
   });
 }
 
 hz_status hz_precond_apply(hz_ctx* ctx, const void* r, void* z, int nrhs, void* cuda_stream) {
   return guarded([&] {
     require(ctx && r && z, "null argument");
-    require(nrhs == 1, "this build applies one right-hand side per call");
+    require(nrhs >= 1 && nrhs <= ctx->c.opts.nrhs_max && (nrhs & (nrhs - 1)) == 0,
+            "nrhs must be a power of two <= nrhs_max (and <= 64)");
     BusyGuard bg(&ctx->c);
-    precond_apply_c128(ctx->c, (const double2*)r, (double2*)z, (cudaStream_t)cuda_stream);
+    precond_apply_c128(ctx->c, (const double2*)r, (double2*)z, nrhs, (cudaStream_t)cuda_stream);
   });
 }
 
 hz_status hz_apply_operator(hz_ctx* ctx, const void* v, void* w, int nrhs, int shifted, void* cuda_stream) {
   return guarded([&] {
     require(ctx && v && w, "null argument");
-    require(nrhs == 1, "this build applies one right-hand side per call");
+    require(nrhs >= 1 && nrhs <= ctx->c.opts.nrhs_max && (nrhs & (nrhs - 1)) == 0,
+            "nrhs must be a power of two <= nrhs_max (and <= 64)");
     BusyGuard bg(&ctx->c);
+    ctx->c.nrhs = nrhs;
     fine_apply_f64(ctx->c, v, false, (double2*)w, shifted != 0, (cudaStream_t)cuda_stream);
+    ctx->c.nrhs = 1;
   });
 }
 
@@ -408,6 +417,7 @@ hz_status hz_level_residual(hz_ctx* ctx, int level, const void* u, const void* f
     check_level(ctx, level, false);
     require(u && f && r, "null argument");
     BusyGuard bg(&ctx->c);
+    ctx->c.nrhs = 1;
     level_residual(ctx->c, level, u, f, r, nullptr, (cudaStream_t)cuda_stream);
   });
 }
@@ -418,6 +428,7 @@ hz_status hz_level_smooth(hz_ctx* ctx, int level, void* u, const void* f, void* 
     require(u && f, "null argument");
     require(!ctx->c.L[level].coarsest, "the coarsest level has no smoother");
     BusyGuard bg(&ctx->c);
+    ctx->c.nrhs = 1;
     level_smooth(ctx->c, level, u, f, false, nullptr, (cudaStream_t)cuda_stream);
   });
 }
@@ -435,6 +446,7 @@ hz_status hz_level_smooth_noalloc(hz_ctx* ctx, int level, void* u, const void* f
                                           std::to_string(HZ_NOALLOC_MAX_NODES));
     BusyGuard bg(&c);
     void* r = noalloc_scratch(c.dev);
+    c.nrhs = 1;
     cudaStream_t s = (cudaStream_t)cuda_stream;
     int prev = -1;
     HZ_CUDA(cudaGetDevice(&prev));
@@ -451,6 +463,7 @@ hz_status hz_level_restrict(hz_ctx* ctx, int level, const void* r, void* fc, voi
     check_level(ctx, level, true);
     require(r && fc, "null argument");
     BusyGuard bg(&ctx->c);
+    ctx->c.nrhs = 1;
     level_restrict(ctx->c, level, r, fc, nullptr, (cudaStream_t)cuda_stream);
   });
 }
@@ -460,6 +473,7 @@ hz_status hz_level_prolong_add(hz_ctx* ctx, int level, const void* ec, void* u, 
     check_level(ctx, level, true);
     require(ec && u, "null argument");
     BusyGuard bg(&ctx->c);
+    ctx->c.nrhs = 1;
     level_prolong_add(ctx->c, level, ec, u, nullptr, (cudaStream_t)cuda_stream);
   });
 }
@@ -468,6 +482,7 @@ hz_status hz_coarse_solve(hz_ctx* ctx, const void* f, void* u, void* cuda_stream
   return guarded([&] {
     require(ctx && f && u, "null argument");
     BusyGuard bg(&ctx->c);
+    ctx->c.nrhs = 1;
     coarse_solve(ctx->c, f, u, nullptr, (cudaStream_t)cuda_stream);
   });
 }

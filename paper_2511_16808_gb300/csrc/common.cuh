@@ -243,6 +243,7 @@ struct Ctx {
   double omega = 0, alpha = 0, h = 0;
   int dev = 0;
   bool mixed = true;
+  int nrhs = 1;                 // right-hand sides of the current call (V-cycle batch width)
   std::vector<Level> L;
   double2* diagA64 = nullptr;   // fine, unshifted A diagonal (FGMRES matvec), c128 [N]
   double* wmass = nullptr;      // fine prod_a w_a per node (q_hat = wmass * q) [N]
@@ -259,6 +260,9 @@ struct Ctx {
   std::vector<void*> allocations;
   std::atomic<int> busy{0};
   cudaGraphExec_t cycle_graph = nullptr;
+  cudaGraphExec_t batch_graph = nullptr;   // restart cycle for nrhs > 1
+  int batch_graph_nrhs = 0, batch_graph_kernels = 0;
+  int* n_active = nullptr;                 // right-hand sides still iterating (batched solve)
   int cycle_graph_nrhs = 0;
   cudaStream_t graph_stream = nullptr;   // library stream the solve runs on (graph capture needs one)
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -297,7 +301,8 @@ void fine_apply_f64(Ctx& c, const void* v, bool v_single, double2* w, bool shift
 size_t krylov_bytes(const hz_grid& g, const hz_opts& o);
 void krylov_alloc(Ctx& c);
 void fgmres_solve(Ctx& c, const double2* q_dev, double2* p_dev, hz_info* info, cudaStream_t s);
-void precond_apply_c128(Ctx& c, const double2* r, double2* z, cudaStream_t s);
+void fgmres_solve_batch(Ctx& c, const double2* q_dev, double2* p_dev, int nrhs, hz_info* info, cudaStream_t s);
+void precond_apply_c128(Ctx& c, const double2* r, double2* z, int nrhs, cudaStream_t s);
 void profile_select(Ctx& c, int cls);
 
 }  // namespace hz

@@ -57,18 +57,16 @@ void vcycle(Ctx& c, const void* f, void* u, const int* active, cudaStream_t s) {
 
 namespace {
 template <typename U>
-__global__ void k_fine_apply64(GridDev g, double invh2, const double2* __restrict__ diag, const U* __restrict__ v,
-                               double2* __restrict__ w) {
-  const Geo gg{g.nx, g.ny, g.nz, g.nx * g.ny, (int)g.N};
-  int x, y, z;
-  if (!node_xyz(gg, x, y, z)) return;
-  const int p = (z * gg.ny + y) * gg.nx + x;
-  auto ld = [v](int q) {
-    const U a = v[q];
+__global__ void k_fine_apply64(Geo gg, int dim, double invh2, const double2* __restrict__ diag,
+                               const U* __restrict__ v, double2* __restrict__ w) {
+  int x, y, z, p, q;
+  if (!node_xyz(gg, x, y, z, p, q)) return;
+  auto ld = [v](int i) {
+    const U a = v[i];
     return make_double2((double)a.x, (double)a.y);
   };
-  w[p] = g.dim == 3 ? fine_Au<double, 3, true>(gg, invh2, diag[p], ld, p, x, y, z)
-                    : fine_Au<double, 2, true>(gg, invh2, diag[p], ld, p, x, y, z);
+  w[q] = dim == 3 ? fine_Au<double, 3, true>(gg, invh2, diag[p], ld, q, x, y, z)
+                  : fine_Au<double, 2, true>(gg, invh2, diag[p], ld, q, x, y, z);
 }
 }  // namespace
 
@@ -76,11 +74,11 @@ void fine_apply_f64(Ctx& c, const void* v, bool v_single, double2* w, bool shift
   Level& L = c.L[0];
   const double2* diag = shifted ? L.A64 : c.diagA64;    // plane 0 of the FP64 fine planes is diag(A_s)
   const double invh2 = 1.0 / (c.h * c.h);
-  const Geo g = geo(L.g);
+  const Geo g = geo(L.g, c.nrhs);
   if (v_single)
-    k_fine_apply64<float2><<<grid_of(g), dim3(BX, BY), 0, s>>>(L.g, invh2, diag, (const float2*)v, w);
+    k_fine_apply64<float2><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, L.g.dim, invh2, diag, (const float2*)v, w);
   else
-    k_fine_apply64<double2><<<grid_of(g), dim3(BX, BY), 0, s>>>(L.g, invh2, diag, (const double2*)v, w);
+    k_fine_apply64<double2><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, L.g.dim, invh2, diag, (const double2*)v, w);
   HZ_LAUNCHED();
 }
 

@@ -15,8 +15,13 @@
 //   prolong+residual  2D: u' = t + P e_c on a shared-memory tile with halo, then
 //                     r = f - A u' from the tile
 //   prolong+sweep     2D with diagonal M: u = u' + w m0 (f - A u') from the tile
-// Thread mapping: 32 x 8 threads per block over (x, y), blockIdx.z = z, one
-// thread per output node, 32-bit indices; blocks whose stencil reach stays
+// Batched right-hand sides: with R (a power of two <= 64) right-hand sides the
+// RHS index is innermost (field index node*R + r); every kernel then sees a
+// grid whose x extent is nx*R (x neighbours at +-R, y at +-nx*R), reads each
+// coefficient once per node (broadcast across the warp's RHS), and the fused
+// shared-memory tile kernels are used only for R = 1.
+// Thread mapping: 32 x 8 threads per block over (x*R + r, y), blockIdx.z = z,
+// one thread per output value, 32-bit indices; blocks whose stencil reach stays
 // inside the grid take an unchecked path (block-uniform branch).  Kernels take
 // an optional device flag `active`: when it reads 0 they return at once (a
 // captured FGMRES cycle uses it to skip the iterations after convergence).
@@ -32,10 +37,17 @@ constexpr int BX = 32, BY = 8;
 constexpr int kMaxM = 125;
 
 struct Geo {
-  int nx, ny, nz, sxy, N;
+  int nx, ny, nz, sxy, N;     // nodes
+  int R, lr;                  // right-hand sides (R = 1 << lr)
+  int nxR, sxyR;              // field strides in y and z
 };
-inline Geo geo(const GridDev& g) { return Geo{g.nx, g.ny, g.nz, g.nx * g.ny, (int)g.N}; }
-inline dim3 grid_of(const Geo& g) { return dim3((g.nx + BX - 1) / BX, (g.ny + BY - 1) / BY, g.nz); }
+inline Geo geo(const GridDev& g, int R = 1) {
+  int lr = 0;
+  while ((1 << lr) < R) ++lr;
+  require((1 << lr) == R && R <= 64, "nrhs must be a power of two <= 64");
+  return Geo{g.nx, g.ny, g.nz, g.nx * g.ny, (int)g.N, R, lr, g.nx * R, g.nx * g.ny * R};
+}
+inline dim3 grid_of(const Geo& g) { return dim3((g.nxR + BX - 1) / BX, (g.ny + BY - 1) / BY, g.nz); }
 inline unsigned nblk(long long n, int b) { return (unsigned)((n + b - 1) / b); }
 
 // Offsets of an assembled Vanka sum with their flat index offsets on one level.
@@ -45,30 +57,36 @@ struct MList {
   signed char d[kMaxM][3];
 };
 
-inline MList mlist(const Level& L) {
+inline MList mlist(const Level& L, int R = 1) {
   require(L.M.off.n <= kMaxM, "Vanka stencil too large");
   MList m;
   m.n = L.M.off.n;
   m.rho = L.M.off.rho;
   for (int s = 0; s < m.n; ++s) {
     for (int a = 0; a < 3; ++a) m.d[s][a] = L.M.off.d[s][a];
-    m.flat[s] = L.M.off.d[s][0] + L.M.off.d[s][1] * L.g.nx + L.M.off.d[s][2] * L.g.nx * L.g.ny;
+    m.flat[s] = (L.M.off.d[s][0] + L.M.off.d[s][1] * L.g.nx + L.M.off.d[s][2] * L.g.nx * L.g.ny) * R;
   }
   return m;
 }
 
-__device__ __forceinline__ bool node_xyz(const Geo& g, int& x, int& y, int& z) {
-  x = blockIdx.x * BX + threadIdx.x;
+// Thread -> (node x, y, z), node index p and field index q; false past the edge.
+__device__ __forceinline__ bool node_xyz(const Geo& g, int& x, int& y, int& z, int& p, int& q) {
+  const int X = blockIdx.x * BX + threadIdx.x;
   y = blockIdx.y * BY + threadIdx.y;
   z = blockIdx.z;
-  return x < g.nx && y < g.ny;
+  if (X >= g.nxR || y >= g.ny) return false;
+  x = X >> g.lr;
+  const int row = z * g.ny + y;
+  p = row * g.nx + x;
+  q = row * g.nxR + X;
+  return true;
 }
 
 // true when every node of this block and its neighbours within r lie in the grid
 template <int DIM>
 __device__ __forceinline__ bool interior_block(const Geo& g, int r) {
-  const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
-  bool ok = x0 >= r && x0 + BX - 1 + r < g.nx && y0 >= r && y0 + BY - 1 + r < g.ny;
+  const int x0 = (blockIdx.x * BX) >> g.lr, x1 = (blockIdx.x * BX + BX - 1) >> g.lr, y0 = blockIdx.y * BY;
+  bool ok = x0 >= r && x1 + r < g.nx && y0 >= r && y0 + BY - 1 + r < g.ny;
   if (DIM == 3) ok = ok && (int)blockIdx.z >= r && (int)blockIdx.z + r < g.nz;
   return ok;
 }
@@ -82,13 +100,13 @@ __device__ __forceinline__ V scale(V a, decltype(a.x) s) {
 
 // A u at node p for the fine 5-/7-point operator (diag d at p).
 template <typename T, int DIM, bool CHECK, typename LD>
-__device__ __forceinline__ c_t<T> fine_Au(const Geo& g, T invh2, c_t<T> d, const LD& ld, int p, int x, int y,
+__device__ __forceinline__ c_t<T> fine_Au(const Geo& g, T invh2, c_t<T> d, const LD& ld, int q, int x, int y,
                                           int z) {
   using V = c_t<T>;
-  V acc = cmul(d, ld(p));
+  V acc = cmul(d, ld(q));
   if (!CHECK) {
-    V s = ld(p - 1) + ld(p + 1) + ld(p - g.nx) + ld(p + g.nx);
-    if (DIM == 3) s = s + ld(p - g.sxy) + ld(p + g.sxy);
+    V s = ld(q - g.R) + ld(q + g.R) + ld(q - g.nxR) + ld(q + g.nxR);
+    if (DIM == 3) s = s + ld(q - g.sxyR) + ld(q + g.sxyR);
     acc.x -= invh2 * s.x;
     acc.y -= invh2 * s.y;
     return acc;
@@ -97,17 +115,17 @@ __device__ __forceinline__ c_t<T> fine_Au(const Geo& g, T invh2, c_t<T> d, const
   const T wy = (y == 0 || y == g.ny - 1) ? T(0.5) : T(1);
   const T wz = (DIM == 3 && (z == 0 || z == g.nz - 1)) ? T(0.5) : T(1);
   V sx = cmk<V>(0, 0), sy = cmk<V>(0, 0);
-  if (x > 0) sx = sx + ld(p - 1);
-  if (x < g.nx - 1) sx = sx + ld(p + 1);
-  if (y > 0) sy = sy + ld(p - g.nx);
-  if (y < g.ny - 1) sy = sy + ld(p + g.nx);
+  if (x > 0) sx = sx + ld(q - g.R);
+  if (x < g.nx - 1) sx = sx + ld(q + g.R);
+  if (y > 0) sy = sy + ld(q - g.nxR);
+  if (y < g.ny - 1) sy = sy + ld(q + g.nxR);
   const T cx = wy * wz * invh2, cy = wx * wz * invh2;
   acc.x -= cx * sx.x + cy * sy.x;
   acc.y -= cx * sx.y + cy * sy.y;
   if (DIM == 3) {
     V sz = cmk<V>(0, 0);
-    if (z > 0) sz = sz + ld(p - g.sxy);
-    if (z < g.nz - 1) sz = sz + ld(p + g.sxy);
+    if (z > 0) sz = sz + ld(q - g.sxyR);
+    if (z < g.nz - 1) sz = sz + ld(q + g.sxyR);
     const T cz = wx * wy * invh2;
     acc.x -= cz * sz.x;
     acc.y -= cz * sz.y;
@@ -117,8 +135,8 @@ __device__ __forceinline__ c_t<T> fine_Au(const Geo& g, T invh2, c_t<T> d, const
 
 // A u at node p for a stored box stencil of radius RHO (planes [s][N]).
 template <typename T, int DIM, int RHO, bool CHECK, typename LD>
-__device__ __forceinline__ c_t<T> box_Au(const Geo& g, const c_t<T>* __restrict__ P, const LD& ld, int p, int x,
-                                         int y, int z) {
+__device__ __forceinline__ c_t<T> box_Au(const Geo& g, const c_t<T>* __restrict__ P, const LD& ld, int p, int q,
+                                         int x, int y, int z) {
   using V = c_t<T>;
   V acc = cmk<V>(0, 0);
   constexpr int RZ = DIM == 3 ? RHO : 0;
@@ -134,7 +152,7 @@ __device__ __forceinline__ c_t<T> box_Au(const Geo& g, const c_t<T>* __restrict_
           if (x + dx < 0 || x + dx >= g.nx || y + dy < 0 || y + dy >= g.ny) continue;
           if (DIM == 3 && (z + dz < 0 || z + dz >= g.nz)) continue;
         }
-        acc = cfma(P[s * g.N + p], ld(p + dx + dy * g.nx + dz * g.sxy), acc);
+        acc = cfma(P[s * g.N + p], ld(q + dx * g.R + dy * g.nxR + dz * g.sxyR), acc);
       }
   return acc;
 }
@@ -142,16 +160,16 @@ __device__ __forceinline__ c_t<T> box_Au(const Geo& g, const c_t<T>* __restrict_
 // AK = 0: fine analytic operator; AK = rho > 0: stored box stencil.
 template <typename T, int DIM, int AK, bool CHECK, typename LD>
 __device__ __forceinline__ c_t<T> apply_A(const Geo& g, T invh2, const c_t<T>* __restrict__ A, const LD& ld, int p,
-                                          int x, int y, int z) {
+                                          int q, int x, int y, int z) {
   if constexpr (AK == 0)
-    return fine_Au<T, DIM, CHECK>(g, invh2, A[p], ld, p, x, y, z);
+    return fine_Au<T, DIM, CHECK>(g, invh2, A[p], ld, q, x, y, z);
   else
-    return box_Au<T, DIM, AK, CHECK>(g, A, ld, p, x, y, z);
+    return box_Au<T, DIM, AK, CHECK>(g, A, ld, p, q, x, y, z);
 }
 
 template <typename T, int DIM, bool CHECK, typename LD>
 __device__ __forceinline__ c_t<T> list_Au(const Geo& g, const MList& m, const c_t<T>* __restrict__ P, const LD& ld,
-                                          int p, int x, int y, int z) {
+                                          int p, int q, int x, int y, int z) {
   using V = c_t<T>;
   V acc = cmk<V>(0, 0);
   for (int s = 0; s < m.n; ++s) {
@@ -160,7 +178,7 @@ __device__ __forceinline__ c_t<T> list_Au(const Geo& g, const MList& m, const c_
       if (xx < 0 || xx >= g.nx || yy < 0 || yy >= g.ny) continue;
       if (DIM == 3 && (zz < 0 || zz >= g.nz)) continue;
     }
-    acc = cfma(P[s * g.N + p], ld(p + m.flat[s]), acc);
+    acc = cfma(P[s * g.N + p], ld(q + m.flat[s]), acc);
   }
   return acc;
 }
@@ -175,13 +193,12 @@ __global__ void __launch_bounds__(BX* BY) k_resid(Geo g, T invh2, const c_t<T>* 
   if (active && !*active) return;
   constexpr int RA = AK == 0 ? 1 : AK;
   const bool in = interior_block<DIM>(g, RA);
-  int x, y, z;
-  if (!node_xyz(g, x, y, z)) return;
-  const int p = (z * g.ny + y) * g.nx + x;
-  auto ld = [u](int q) { return u[q]; };
-  const c_t<T> a = in ? apply_A<T, DIM, AK, false>(g, invh2, A, ld, p, x, y, z)
-                      : apply_A<T, DIM, AK, true>(g, invh2, A, ld, p, x, y, z);
-  r[p] = f[p] - a;
+  int x, y, z, p, q;
+  if (!node_xyz(g, x, y, z, p, q)) return;
+  auto ld = [u](int i) { return u[i]; };
+  const c_t<T> a = in ? apply_A<T, DIM, AK, false>(g, invh2, A, ld, p, q, x, y, z)
+                      : apply_A<T, DIM, AK, true>(g, invh2, A, ld, p, q, x, y, z);
+  r[q] = f[q] - a;
 }
 
 // u = w M f  (first sweep from u = 0)
@@ -191,12 +208,12 @@ __global__ void __launch_bounds__(BX* BY) k_sweep0(Geo g, MList m, const c_t<T>*
                                                    const int* active) {
   if (active && !*active) return;
   const bool in = interior_block<DIM>(g, m.rho);
-  int x, y, z;
-  if (!node_xyz(g, x, y, z)) return;
-  const int p = (z * g.ny + y) * g.nx + x;
-  auto ld = [f](int q) { return f[q]; };
-  const c_t<T> v = in ? list_Au<T, DIM, false>(g, m, M, ld, p, x, y, z) : list_Au<T, DIM, true>(g, m, M, ld, p, x, y, z);
-  u[p] = scale(v, w);
+  int x, y, z, p, q;
+  if (!node_xyz(g, x, y, z, p, q)) return;
+  auto ld = [f](int i) { return f[i]; };
+  const c_t<T> v = in ? list_Au<T, DIM, false>(g, m, M, ld, p, q, x, y, z)
+                      : list_Au<T, DIM, true>(g, m, M, ld, p, q, x, y, z);
+  u[q] = scale(v, w);
 }
 
 // diagonal M: u = w m0 f and r = f - A u in one pass
@@ -208,15 +225,15 @@ __global__ void __launch_bounds__(BX* BY) k_sweep0_resid_diag(Geo g, T invh2, co
   if (active && !*active) return;
   constexpr int RA = AK == 0 ? 1 : AK;
   const bool in = interior_block<DIM>(g, RA);
-  int x, y, z;
-  if (!node_xyz(g, x, y, z)) return;
-  const int p = (z * g.ny + y) * g.nx + x;
-  auto ld = [m0, f, w](int q) { return scale(cmul(m0[q], f[q]), w); };
-  const c_t<T> a = in ? apply_A<T, DIM, AK, false>(g, invh2, A, ld, p, x, y, z)
-                      : apply_A<T, DIM, AK, true>(g, invh2, A, ld, p, x, y, z);
-  const c_t<T> fp = f[p];
-  u[p] = scale(cmul(m0[p], fp), w);
-  r[p] = fp - a;
+  int x, y, z, p, q;
+  if (!node_xyz(g, x, y, z, p, q)) return;
+  const int lr = g.lr;
+  auto ld = [m0, f, w, lr](int i) { return scale(cmul(m0[i >> lr], f[i]), w); };
+  const c_t<T> a = in ? apply_A<T, DIM, AK, false>(g, invh2, A, ld, p, q, x, y, z)
+                      : apply_A<T, DIM, AK, true>(g, invh2, A, ld, p, q, x, y, z);
+  const c_t<T> fp = f[q];
+  u[q] = scale(cmul(m0[p], fp), w);
+  r[q] = fp - a;
 }
 
 // out = in + w M r  (out may alias in)
@@ -226,12 +243,12 @@ __global__ void __launch_bounds__(BX* BY) k_sweep_out(Geo g, MList m, const c_t<
                                                       const int* active) {
   if (active && !*active) return;
   const bool inb = interior_block<DIM>(g, m.rho);
-  int x, y, z;
-  if (!node_xyz(g, x, y, z)) return;
-  const int p = (z * g.ny + y) * g.nx + x;
-  auto ld = [r](int q) { return r[q]; };
-  const c_t<T> v = inb ? list_Au<T, DIM, false>(g, m, M, ld, p, x, y, z) : list_Au<T, DIM, true>(g, m, M, ld, p, x, y, z);
-  out[p] = in[p] + scale(v, w);
+  int x, y, z, p, q;
+  if (!node_xyz(g, x, y, z, p, q)) return;
+  auto ld = [r](int i) { return r[i]; };
+  const c_t<T> v = inb ? list_Au<T, DIM, false>(g, m, M, ld, p, q, x, y, z)
+                       : list_Au<T, DIM, true>(g, m, M, ld, p, q, x, y, z);
+  out[q] = in[q] + scale(v, w);
 }
 
 // diagonal M: out = in + w m0 (f - A in)   (out != in)
@@ -243,13 +260,12 @@ __global__ void __launch_bounds__(BX* BY) k_resid_sweep_diag(Geo g, T invh2, con
   if (active && !*active) return;
   constexpr int RA = AK == 0 ? 1 : AK;
   const bool inb = interior_block<DIM>(g, RA);
-  int x, y, z;
-  if (!node_xyz(g, x, y, z)) return;
-  const int p = (z * g.ny + y) * g.nx + x;
-  auto ld = [in](int q) { return in[q]; };
-  const c_t<T> a = inb ? apply_A<T, DIM, AK, false>(g, invh2, A, ld, p, x, y, z)
-                       : apply_A<T, DIM, AK, true>(g, invh2, A, ld, p, x, y, z);
-  out[p] = in[p] + scale(cmul(m0[p], f[p] - a), w);
+  int x, y, z, p, q;
+  if (!node_xyz(g, x, y, z, p, q)) return;
+  auto ld = [in](int i) { return in[i]; };
+  const c_t<T> a = inb ? apply_A<T, DIM, AK, false>(g, invh2, A, ld, p, q, x, y, z)
+                       : apply_A<T, DIM, AK, true>(g, invh2, A, ld, p, q, x, y, z);
+  out[q] = in[q] + scale(cmul(m0[p], f[q] - a), w);
 }
 
 // 1D prolongation weight P(j, J) in single precision (the same exact dyadic
@@ -270,8 +286,9 @@ template <typename T, int DIM, int KIND>
 __global__ void __launch_bounds__(BX* BY) k_restrict(Geo gf, Geo gc, const c_t<T>* __restrict__ r,
                                                      c_t<T>* __restrict__ fc, const int* active) {
   if (active && !*active) return;
-  int X, Y, Z;
-  if (!node_xyz(gc, X, Y, Z)) return;
+  int X, Y, Z, pc, qc;
+  if (!node_xyz(gc, X, Y, Z, pc, qc)) return;
+  const int rr = qc & (gc.R - 1);
   constexpr int RAD = KIND ? 2 : 1;
   constexpr int RZ = DIM == 3 ? RAD : 0;
   T wx[2 * RAD + 1], wy[2 * RAD + 1], wz[2 * RZ + 1];
@@ -295,18 +312,18 @@ __global__ void __launch_bounds__(BX* BY) k_restrict(Geo gf, Geo gc, const c_t<T
     for (int ky = 0; ky <= 2 * RAD; ++ky) {
       const T wyz = wy[ky] * wz[kz];
       if (wyz == T(0)) continue;
-      const int row = (iz * gf.ny + (2 * Y - RAD + ky)) * gf.nx + 2 * X - RAD;
+      const int row = ((iz * gf.ny + (2 * Y - RAD + ky)) * gf.nx + 2 * X - RAD) * gf.R + rr;
 #pragma unroll
       for (int kx = 0; kx <= 2 * RAD; ++kx) {
         if (wx[kx] == T(0)) continue;
-        const c_t<T> v = r[row + kx];
+        const c_t<T> v = r[row + kx * gf.R];
         const T ww = wyz * wx[kx];
         acc.x += ww * v.x;
         acc.y += ww * v.y;
       }
     }
   }
-  fc[(Z * gc.ny + Y) * gc.nx + X] = acc;
+  fc[qc] = acc;
 }
 
 // 1D prolongation stencil of fine index j: coarse nodes J0, J0+1, J0+2 with
@@ -339,7 +356,7 @@ __device__ __forceinline__ int p1_stencil(int j, int nf, int nc, float (&w)[3]) 
 // (P e_c) at fine node (x, y, z)
 template <typename T, int DIM, int KIND>
 __device__ __forceinline__ c_t<T> prolong_at(const Geo& gf, const Geo& gc, const c_t<T>* __restrict__ ec, int x, int y,
-                                             int z) {
+                                             int z, int rr = 0) {
   float wx[3], wy[3], wz[3] = {1.0f, 0.0f, 0.0f};
   const int X0 = p1_stencil<KIND>(x, gf.nx, gc.nx, wx);
   const int Y0 = p1_stencil<KIND>(y, gf.ny, gc.ny, wy);
@@ -352,12 +369,12 @@ __device__ __forceinline__ c_t<T> prolong_at(const Geo& gf, const Geo& gc, const
     for (int b = 0; b < 3; ++b) {
       const float wyz = wz[c] * wy[b];
       if (wyz == 0.0f) continue;
-      const int row = ((Z0 + c) * gc.ny + Y0 + b) * gc.nx + X0;
+      const int row = (((Z0 + c) * gc.ny + Y0 + b) * gc.nx + X0) * gc.R + rr;
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         if (wx[a] == 0.0f) continue;
         const T w3 = (T)(wyz * wx[a]);
-        const c_t<T> v = ec[row + a];
+        const c_t<T> v = ec[row + a * gc.R];
         acc.x += w3 * v.x;
         acc.y += w3 * v.y;
       }
@@ -371,10 +388,9 @@ template <typename T, int DIM, int KIND>
 __global__ void __launch_bounds__(BX* BY) k_prolong(Geo gf, Geo gc, const c_t<T>* __restrict__ ec, const c_t<T>* in,
                                                     c_t<T>* out, const int* active) {
   if (active && !*active) return;
-  int x, y, z;
-  if (!node_xyz(gf, x, y, z)) return;
-  const int p = (z * gf.ny + y) * gf.nx + x;
-  out[p] = in[p] + prolong_at<T, DIM, KIND>(gf, gc, ec, x, y, z);
+  int x, y, z, p, q;
+  if (!node_xyz(gf, x, y, z, p, q)) return;
+  out[q] = in[q] + prolong_at<T, DIM, KIND>(gf, gc, ec, x, y, z, q & (gf.R - 1));
 }
 
 // 2D: u' = t + P e_c on a tile with halo RA in shared memory, then
@@ -401,9 +417,8 @@ __global__ void __launch_bounds__(BX* BY) k_prolong_fused_2d(Geo gf, Geo gc, T i
     sm[ty][tx] = v;
   }
   __syncthreads();
-  int x, y, z;
-  if (!node_xyz(gf, x, y, z)) return;
-  const int p = y * gf.nx + x;
+  int x, y, z, p, q;
+  if (!node_xyz(gf, x, y, z, p, q)) return;
   const int lx = threadIdx.x + RA, ly = threadIdx.y + RA;
   const c_t<T> up = sm[ly][lx];
   c_t<T> a;
@@ -453,6 +468,26 @@ __global__ void k_dense_gemv(int n, const c_t<T>* __restrict__ A, const c_t<T>* 
   if (lane == 0) u[warp] = acc;
 }
 
+// u[i][r] = sum_j Ainv[i][j] f[j][r] for R right-hand sides: one block per row,
+// one thread per right-hand side, the row staged through shared memory
+template <typename T>
+__global__ void k_dense_gemm_rhs(int n, int R, const c_t<T>* __restrict__ A, const c_t<T>* __restrict__ f,
+                                 c_t<T>* __restrict__ u, const int* active) {
+  if (active && !*active) return;
+  __shared__ c_t<T> row[256];
+  const int i = blockIdx.x, r = threadIdx.x;
+  c_t<T> acc = cmk<c_t<T>>(0, 0);
+  for (int j0 = 0; j0 < n; j0 += 256) {
+    __syncthreads();
+    for (int k = threadIdx.x; k < 256 && j0 + k < n; k += blockDim.x) row[k] = A[(long long)i * n + j0 + k];
+    __syncthreads();
+    const int jn = min(256, n - j0);
+    if (r < R)
+      for (int k = 0; k < jn; ++k) acc = cfma(row[k], f[(j0 + k) * R + r], acc);
+  }
+  if (r < R) u[i * R + r] = acc;
+}
+
 // ------------------------------------------------------------------ dispatch
 template <typename F>
 void with_dim_ak(int dim, int ak, F&& f) {
@@ -468,7 +503,7 @@ inline int akind(const Level& L) { return L.fine ? 0 : L.A.off.rho; }
 template <typename T>
 void resid(Ctx& c, int l, const void* u, const void* f, void* r, const int* active, cudaStream_t s) {
   Level& L = c.L[l];
-  const Geo g = geo(L.g);
+  const Geo g = geo(L.g, c.nrhs);
   const T invh2 = (T)(1.0 / (c.h * c.h));
   with_dim_ak(L.g.dim, akind(L), [&](auto D, auto K) {
     k_resid<T, D, K><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, invh2, (const c_t<T>*)L.Aw, (const c_t<T>*)u,
@@ -480,8 +515,8 @@ void resid(Ctx& c, int l, const void* u, const void* f, void* r, const int* acti
 template <typename T>
 void sweep_out(Ctx& c, int l, const void* r, const void* in, void* out, const int* active, cudaStream_t s) {
   Level& L = c.L[l];
-  const Geo g = geo(L.g);
-  const MList m = mlist(L);
+  const Geo g = geo(L.g, c.nrhs);
+  const MList m = mlist(L, c.nrhs);
   if (L.g.dim == 2)
     k_sweep_out<T, 2><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, m, (const c_t<T>*)L.Mw, (T)L.damping,
                                                           (const c_t<T>*)r, (const c_t<T>*)in, (c_t<T>*)out, active);
@@ -494,8 +529,8 @@ void sweep_out(Ctx& c, int l, const void* r, const void* in, void* out, const in
 template <typename T>
 void sweep0(Ctx& c, int l, const void* f, void* u, const int* active, cudaStream_t s) {
   Level& L = c.L[l];
-  const Geo g = geo(L.g);
-  const MList m = mlist(L);
+  const Geo g = geo(L.g, c.nrhs);
+  const MList m = mlist(L, c.nrhs);
   if (L.g.dim == 2)
     k_sweep0<T, 2><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, m, (const c_t<T>*)L.Mw, (T)L.damping, (const c_t<T>*)f,
                                                        (c_t<T>*)u, active);
@@ -508,7 +543,7 @@ void sweep0(Ctx& c, int l, const void* f, void* u, const int* active, cudaStream
 template <typename T>
 void sweep0_resid_diag(Ctx& c, int l, const void* f, void* u, void* r, const int* active, cudaStream_t s) {
   Level& L = c.L[l];
-  const Geo g = geo(L.g);
+  const Geo g = geo(L.g, c.nrhs);
   const T invh2 = (T)(1.0 / (c.h * c.h));
   with_dim_ak(L.g.dim, akind(L), [&](auto D, auto K) {
     k_sweep0_resid_diag<T, D, K><<<grid_of(g), dim3(BX, BY), 0, s>>>(
@@ -521,7 +556,7 @@ void sweep0_resid_diag(Ctx& c, int l, const void* f, void* u, void* r, const int
 template <typename T>
 void resid_sweep_diag(Ctx& c, int l, const void* f, const void* in, void* out, const int* active, cudaStream_t s) {
   Level& L = c.L[l];
-  const Geo g = geo(L.g);
+  const Geo g = geo(L.g, c.nrhs);
   const T invh2 = (T)(1.0 / (c.h * c.h));
   with_dim_ak(L.g.dim, akind(L), [&](auto D, auto K) {
     k_resid_sweep_diag<T, D, K><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, invh2, (const c_t<T>*)L.Aw,
@@ -535,7 +570,7 @@ template <typename T>
 void restrict_t(Ctx& c, int l, const void* r, void* fc, const int* active, cudaStream_t s) {
   Level& L = c.L[l];
   Level& C = c.L[l + 1];
-  const Geo gf = geo(L.g), gc = geo(C.g);
+  const Geo gf = geo(L.g, c.nrhs), gc = geo(C.g, c.nrhs);
   auto go = [&](auto D, auto KIND) {
     k_restrict<T, D, KIND><<<grid_of(gc), dim3(BX, BY), 0, s>>>(gf, gc, (const c_t<T>*)r, (c_t<T>*)fc, active);
   };
@@ -552,7 +587,7 @@ template <typename T>
 void prolong_t(Ctx& c, int l, const void* ec, const void* in, void* out, const int* active, cudaStream_t s) {
   Level& L = c.L[l];
   Level& C = c.L[l + 1];
-  const Geo gf = geo(L.g), gc = geo(C.g);
+  const Geo gf = geo(L.g, c.nrhs), gc = geo(C.g, c.nrhs);
   auto go = [&](auto D, auto KIND) {
     k_prolong<T, D, KIND><<<grid_of(gf), dim3(BX, BY), 0, s>>>(gf, gc, (const c_t<T>*)ec, (const c_t<T>*)in,
                                                               (c_t<T>*)out, active);
@@ -572,6 +607,7 @@ void prolong_fused_2d(Ctx& c, int l, const void* ec, const void* t, const void* 
                       const int* active, cudaStream_t s) {
   Level& L = c.L[l];
   Level& C = c.L[l + 1];
+  require(c.nrhs == 1, "fused tile kernels take one right-hand side");
   const Geo gf = geo(L.g), gc = geo(C.g);
   const T invh2 = (T)(1.0 / (c.h * c.h));
   auto go = [&](auto K, auto KIND) {
@@ -596,8 +632,11 @@ template <typename T>
 void coarse_t(Ctx& c, const void* f, void* u, const int* active, cudaStream_t s) {
   Level& L = c.L.back();
   const int n = (int)L.g.N;
-  k_dense_gemv<T><<<nblk((long long)n * 32, 256), 256, 0, s>>>(n, (const c_t<T>*)L.Ainvw, (const c_t<T>*)f,
-                                                              (c_t<T>*)u, active);
+  if (c.nrhs == 1)
+    k_dense_gemv<T><<<nblk((long long)n * 32, 256), 256, 0, s>>>(n, (const c_t<T>*)L.Ainvw, (const c_t<T>*)f,
+                                                                (c_t<T>*)u, active);
+  else
+    k_dense_gemm_rhs<T><<<n, 64, 0, s>>>(n, c.nrhs, (const c_t<T>*)L.Ainvw, (const c_t<T>*)f, (c_t<T>*)u, active);
   HZ_LAUNCHED();
 }
 
@@ -610,11 +649,11 @@ void vcycle_t(Ctx& c, int l, const void* f, void* out, const int* active, cudaSt
     return;
   }
   const int nu1 = c.opts.nu1, nu2 = c.opts.nu2;
-  const bool d2 = L.g.dim == 2;
+  const bool d2 = L.g.dim == 2 && c.nrhs == 1;     // shared-memory tile kernels: one RHS
   // steps 1-2: pre-relaxation into t, residual into r
   const void* rr = L.r;
   if (nu1 == 0) {
-    HZ_CUDA(cudaMemsetAsync(L.t, 0, sizeof(c_t<T>) * L.g.N, s));
+    HZ_CUDA(cudaMemsetAsync(L.t, 0, sizeof(c_t<T>) * L.g.N * c.nrhs, s));
     rr = f;
   } else if (L.m_diag && nu1 == 1) {
     sweep0_resid_diag<T>(c, l, f, L.t, L.r, active, s);

@@ -28,111 +28,11 @@
 #include <cstddef>
 #include <type_traits>
 
-#include "common.cuh"
+#include "krylov_impl.cuh"
 
 namespace hz {
 
-constexpr int kMaxM = 16;
-constexpr int kRedBlock = 256;
-constexpr int BX = 32, BY = 8;
-constexpr int kRows = 4;        // y rows per thread in the 2D passes
-constexpr int kPerThread = 4;   // nodes per thread in the 1D passes
-
-struct KrylovStatus {       // first bytes of KrylovState, copied to the host each cycle
-  int iters;
-  int done;
-  int converged;
-  int breakdown;
-  double relres_est;
-  double relres_true;
-};
-
-struct KrylovState {
-  KrylovStatus st;
-  int active;               // iteration kernels run while 1
-  int kcyc;                 // iterations done in the current cycle
-  int m, max_iter;
-  double tol, bnorm;
-  double2 H[kMaxM + 1][kMaxM];
-  double cs[kMaxM];
-  double2 sn[kMaxM];
-  double2 g[kMaxM + 1];
-  double scale[kMaxM + 1];  // v_i = scale[i] * V[i]
-  double2 y[kMaxM];
-  double2 h1[kMaxM + 2];    // raw dots conj(V_i) . w of the Gram-Schmidt passes
-  double2 nrm2;             // .x = ||w||^2 after orthogonalisation
-  unsigned counter;         // blocks finished in the current reduction (last block resets it)
-};
-
 namespace {
-
-inline unsigned nblk(long long n, int b) { return (unsigned)((n + b - 1) / b); }
-
-struct Geo {
-  int nx, ny, nz, sxy, N, dim;
-};
-inline Geo geo(const GridDev& g) { return Geo{g.nx, g.ny, g.nz, g.nx * g.ny, (int)g.N, g.dim}; }
-// 2D grid of 32 x 8 blocks over (x, y), kRows rows per thread; blockIdx.z strides over z
-inline dim3 grid_xy(const Geo& g) {
-  return dim3((g.nx + BX - 1) / BX, (g.ny + BY * kRows - 1) / (BY * kRows), g.nz < 8 ? g.nz : 8);
-}
-inline unsigned grid_1d(long long N) { return nblk(N, kRedBlock * kPerThread); }
-inline int grid_blocks(const Geo& g) {
-  const dim3 d = grid_xy(g);
-  return (int)(d.x * d.y * d.z);
-}
-
-// w - c v with two DFMA per component
-__device__ __forceinline__ double2 axmy(double2 w, double2 c, double2 v) {
-  return make_double2(fma(c.y, v.y, fma(-c.x, v.x, w.x)), fma(-c.y, v.x, fma(-c.x, v.y, w.y)));
-}
-// acc + conj(v) w with two DFMA per component
-__device__ __forceinline__ double2 dot_acc(double2 acc, double2 v, double2 w) {
-  return make_double2(fma(v.y, w.y, fma(v.x, w.x, acc.x)), fma(-v.y, w.x, fma(v.x, w.y, acc.y)));
-}
-// acc + |w|^2
-__device__ __forceinline__ double nrm_acc(double acc, double2 w) { return fma(w.y, w.y, fma(w.x, w.x, acc)); }
-
-__device__ __forceinline__ double2 ld64(const double2* __restrict__ a, int i) { return a[i]; }
-__device__ __forceinline__ double2 ld64(const float2* __restrict__ a, int i) {
-  const float2 v = a[i];
-  return make_double2(f2d_exact(v.x), f2d_exact(v.y));
-}
-
-// FP64 fine-level (A v)_p, 5-/7-point with half-cell weights
-template <typename U>
-__device__ __forceinline__ double2 apply_A(const Geo& g, double invh2, const double2* __restrict__ diag,
-                                           const U* __restrict__ v, int p, int x, int y, int z) {
-  const double2 d = diag[p], vp = ld64(v, p);
-  const bool inx = x > 0 && x < g.nx - 1, iny = y > 0 && y < g.ny - 1;
-  const bool inz = g.dim == 2 || (z > 0 && z < g.nz - 1);
-  if (inx && iny && inz) {
-    double2 s = ld64(v, p - 1) + ld64(v, p + 1) + ld64(v, p - g.nx) + ld64(v, p + g.nx);
-    if (g.dim == 3) s = s + ld64(v, p - g.sxy) + ld64(v, p + g.sxy);
-    // d v - invh2 s, with FMAs
-    return make_double2(fma(d.x, vp.x, fma(-d.y, vp.y, -invh2 * s.x)), fma(d.x, vp.y, fma(d.y, vp.x, -invh2 * s.y)));
-  }
-  double2 acc = cmul(d, vp);
-  const double wx = inx ? 1.0 : 0.5, wy = iny ? 1.0 : 0.5;
-  const double wz = (g.dim == 3 && !inz) ? 0.5 : 1.0;
-  double2 sx = make_double2(0, 0), sy = make_double2(0, 0);
-  if (x > 0) sx = sx + ld64(v, p - 1);
-  if (x < g.nx - 1) sx = sx + ld64(v, p + 1);
-  if (y > 0) sy = sy + ld64(v, p - g.nx);
-  if (y < g.ny - 1) sy = sy + ld64(v, p + g.nx);
-  const double cx = wy * wz * invh2, cy = wx * wz * invh2;
-  acc.x -= cx * sx.x + cy * sy.x;
-  acc.y -= cx * sx.y + cy * sy.y;
-  if (g.dim == 3) {
-    double2 sz = make_double2(0, 0);
-    if (z > 0) sz = sz + ld64(v, p - g.sxy);
-    if (z < g.nz - 1) sz = sz + ld64(v, p + g.sxy);
-    const double cz = wx * wy * invh2;
-    acc.x -= cz * sz.x;
-    acc.y -= cz * sz.y;
-  }
-  return acc;
-}
 
 // Block-reduce one double2 accumulator per thread; thread 0 writes partials[block].
 __device__ __forceinline__ void block_store(double2 acc, double2* __restrict__ partials, int block) {
@@ -190,7 +90,6 @@ __device__ __forceinline__ bool reduce_last(double2 acc, double2* __restrict__ p
 
 __device__ __forceinline__ int block_linear() { return (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x; }
 
-__device__ void arnoldi_update(KrylovState* st, int j);
 
 // pass 0: w = A z_j -> V[j+1]; h_0j (raw) = conj(V_0) . w
 template <typename TZ>
@@ -244,61 +143,6 @@ __global__ void __launch_bounds__(kRedBlock) k_mgs_step(int N, double2* __restri
   if (LAST && last && threadIdx.x == 0) arnoldi_update(st, j);
 }
 
-__device__ void givens(double2 a, double2 b, double& c, double2& s) {
-  const double ab = sqrt(cabs2(b));
-  if (ab == 0.0) {
-    c = 1.0;
-    s = make_double2(0, 0);
-    return;
-  }
-  const double aa = sqrt(cabs2(a));
-  if (aa == 0.0) {
-    c = 0.0;
-    s = make_double2(b.x / ab, -b.y / ab);     // conj(b)/|b|
-    return;
-  }
-  const double t = hypot(aa, ab);
-  c = aa / t;
-  const double2 ph = make_double2(a.x / aa, a.y / aa);
-  s = (1.0 / t) * cmul(ph, make_double2(b.x, -b.y));
-}
-
-// Column j of the Hessenberg matrix, Givens rotations, residual estimate
-// (one thread, in the last block of the final Gram-Schmidt pass).
-__device__ void arnoldi_update(KrylovState* st, int j) {
-  for (int i = 0; i <= j; ++i) st->H[i][j] = st->scale[i] * st->h1[i];
-  const double hn = sqrt(st->nrm2.x);
-  st->H[j + 1][j] = make_double2(hn, 0.0);
-  for (int i = 0; i < j; ++i) {
-    const double2 a = st->H[i][j], b = st->H[i + 1][j];
-    const double c = st->cs[i];
-    const double2 s = st->sn[i];
-    st->H[i][j] = c * a + cmul(s, b);
-    st->H[i + 1][j] = cmul(make_double2(-s.x, s.y), a) + c * b;      // -conj(s) a + c b
-  }
-  double c;
-  double2 s;
-  givens(st->H[j][j], st->H[j + 1][j], c, s);
-  st->cs[j] = c;
-  st->sn[j] = s;
-  st->H[j][j] = c * st->H[j][j] + cmul(s, st->H[j + 1][j]);
-  st->H[j + 1][j] = make_double2(0, 0);
-  const double2 gj = st->g[j];
-  st->g[j + 1] = cmul(make_double2(-s.x, s.y), gj);
-  st->g[j] = c * gj;
-  st->st.iters += 1;
-  st->kcyc = j + 1;
-  st->st.relres_est = sqrt(cabs2(st->g[j + 1])) / st->bnorm;
-  if (!(hn > 0.0)) {
-    st->st.breakdown = 1;
-    st->scale[j + 1] = 0.0;
-  } else {
-    st->scale[j + 1] = 1.0 / hn;
-  }
-  if (st->st.relres_est < st->tol || st->st.iters >= st->max_iter || st->st.breakdown || st->kcyc >= st->m)
-    st->active = 0;
-}
-
 template <typename V>
 __global__ void k_cast_in(int N, const double2* __restrict__ v, const KrylovState* __restrict__ st, int j,
                           V* __restrict__ f) {
@@ -339,7 +183,6 @@ __global__ void k_update_p(int N, const TZ* __restrict__ Z, const KrylovState* _
   p[q] = acc;
 }
 
-__device__ void restart_update(KrylovState* st);
 
 // r = q_hat - A p -> V_0; ||r||^2, then (last block) the restart decision
 __global__ void __launch_bounds__(kRedBlock) k_true_residual(Geo g, double invh2, const double2* __restrict__ diag,
@@ -365,27 +208,6 @@ __global__ void __launch_bounds__(kRedBlock) k_true_residual(Geo g, double invh2
   const bool last = reduce_last(acc, partials, gridDim.x * gridDim.y * gridDim.z, block_linear(), &st->counter,
                                 &st->nrm2);
   if (last && threadIdx.x == 0 && threadIdx.y == 0) restart_update(st);
-}
-
-__device__ void restart_update(KrylovState* st) {
-  const double beta = sqrt(st->nrm2.x);
-  st->st.relres_true = beta / st->bnorm;
-  st->active = 0;
-  if (st->st.relres_true < st->tol) {
-    st->st.converged = 1;
-    st->st.done = 1;
-    return;
-  }
-  if (st->st.iters >= st->max_iter) {
-    st->st.done = 1;
-    return;
-  }
-  st->st.breakdown = 0;
-  st->scale[0] = 1.0 / beta;
-  st->g[0] = make_double2(beta, 0.0);
-  for (int i = 1; i <= kMaxM; ++i) st->g[i] = make_double2(0, 0);
-  st->kcyc = 0;
-  st->active = 1;
 }
 
 // q_hat = wmass * q; ||q_hat||^2, then (last block) the solver state
@@ -562,6 +384,7 @@ void solve_t(Ctx& c, const double2* q, double2* p, hz_info* info, cudaStream_t u
   const double invh2 = 1.0 / (c.h * c.h);
   KrylovState* st = c.ks;
   KrylovStatus* hs = (KrylovStatus*)c.ks_host;
+  c.nrhs = 1;
   ensure_graph<TZ>(c);
   // the work runs on the library's stream, ordered after the caller's stream
   cudaStream_t s = c.graph_stream;
@@ -601,26 +424,32 @@ size_t krylov_bytes(const hz_grid& g, const hz_opts& o) {
   long long N = (long long)g.n[0] * g.n[1] * (g.dim == 3 ? g.n[2] : 1);
   const size_t vb = o.precision == HZ_PREC_MIXED ? 8 : 16;
   const int m = o.restart_m;
-  const long long nb = nblk(N, kRedBlock) * 2;
-  return 16ull * N * (m + 1) + vb * N * m + 16ull * N * 4 + 16ull * nb + sizeof(KrylovState);
+  const long long R = std::max(1, o.nrhs_max);
+  const long long nb = nblk(N * R, kRedBlock) * 2;
+  return (16ull * N * (m + 1) + vb * N * m + 16ull * N * 4) * R + 16ull * nb * R + sizeof(KrylovState) * R;
 }
 
 void krylov_alloc(Ctx& c) {
   const long long N = c.L[0].g.N;
   const int m = c.opts.restart_m;
+  const long long R = std::max(1, c.opts.nrhs_max);
   const size_t vb = c.mixed ? sizeof(float2) : sizeof(double2);
   require(m >= 1 && m <= kMaxM, "restart_m must be in 1..16");
-  require(N * (m + 1) < (1ll << 31), "grid too large for 32-bit Krylov indexing");
-  c.V = (double2*)ctx_alloc(c, sizeof(double2) * N * (m + 1));
-  c.Z = ctx_alloc(c, vb * N * m);
-  c.qhat = (double2*)ctx_alloc(c, sizeof(double2) * N);
-  c.p = (double2*)ctx_alloc(c, sizeof(double2) * N);
+  require(N * R * (m + 1) < (1ll << 31), "grid too large for 32-bit Krylov indexing");
+  c.V = (double2*)ctx_alloc(c, sizeof(double2) * N * R * (m + 1));
+  c.Z = ctx_alloc(c, vb * N * R * m);
+  c.qhat = (double2*)ctx_alloc(c, sizeof(double2) * N * R);
+  c.p = (double2*)ctx_alloc(c, sizeof(double2) * N * R);
   const Geo g = geo(c.L[0].g);
-  const int nb = std::max<int>(grid_blocks(g), (int)nblk(N, kRedBlock));
-  c.partials = (double2*)ctx_alloc(c, sizeof(double2) * nb);
-  c.ks = (KrylovState*)ctx_alloc(c, sizeof(KrylovState));
-  HZ_CUDA(cudaMemset(c.ks, 0, sizeof(KrylovState)));
-  HZ_CUDA(cudaMallocHost(&c.ks_host, sizeof(KrylovStatus)));
+  // single RHS: one partial per block; batched: one per block and RHS (blocks of
+  // at least 8 values per thread, see krylov_batch.cu)
+  const long long nb1 = std::max<long long>(grid_blocks(g), nblk(N, kRedBlock));
+  const long long nbR = R > 1 ? R * (nblk(N * R, kRedBlock * 8) + grid_blocks(g) * R) : 0;
+  c.partials = (double2*)ctx_alloc(c, sizeof(double2) * std::max(nb1, nbR));
+  c.ks = (KrylovState*)ctx_alloc(c, sizeof(KrylovState) * R);
+  HZ_CUDA(cudaMemset(c.ks, 0, sizeof(KrylovState) * R));
+  c.n_active = (int*)ctx_alloc(c, sizeof(int));
+  HZ_CUDA(cudaMallocHost(&c.ks_host, sizeof(KrylovStatus) * R));
   HZ_CUDA(cudaStreamCreateWithFlags(&c.graph_stream, cudaStreamNonBlocking));
   HZ_CUDA(cudaEventCreateWithFlags(&c.ev_in, cudaEventDisableTiming));
   HZ_CUDA(cudaEventCreateWithFlags(&c.ev_out, cudaEventDisableTiming));
@@ -639,19 +468,21 @@ void fgmres_solve(Ctx& c, const double2* q, double2* p, hz_info* info, cudaStrea
   else solve_t<double2>(c, q, p, info, s);
 }
 
-void precond_apply_c128(Ctx& c, const double2* r, double2* z, cudaStream_t s) {
+void precond_apply_c128(Ctx& c, const double2* r, double2* z, int nrhs, cudaStream_t s) {
   Level& L0 = c.L[0];
-  const int N = (int)L0.g.N;
+  const int NR = (int)L0.g.N * nrhs;
+  c.nrhs = nrhs;
   if (c.mixed) {
-    k_cast_vec<float2><<<nblk(N, 256), 256, 0, s>>>(N, r, (float2*)L0.f);
+    k_cast_vec<float2><<<nblk(NR, 256), 256, 0, s>>>(NR, r, (float2*)L0.f);
     vcycle(c, L0.f, L0.u, nullptr, s);
-    k_widen_vec<float2><<<nblk(N, 256), 256, 0, s>>>(N, (const float2*)L0.u, z);
+    k_widen_vec<float2><<<nblk(NR, 256), 256, 0, s>>>(NR, (const float2*)L0.u, z);
   } else {
-    HZ_CUDA(cudaMemcpyAsync(L0.f, r, sizeof(double2) * N, cudaMemcpyDeviceToDevice, s));
+    HZ_CUDA(cudaMemcpyAsync(L0.f, r, sizeof(double2) * NR, cudaMemcpyDeviceToDevice, s));
     vcycle(c, L0.f, L0.u, nullptr, s);
-    HZ_CUDA(cudaMemcpyAsync(z, L0.u, sizeof(double2) * N, cudaMemcpyDeviceToDevice, s));
+    HZ_CUDA(cudaMemcpyAsync(z, L0.u, sizeof(double2) * NR, cudaMemcpyDeviceToDevice, s));
   }
   HZ_LAUNCHED();
+  c.nrhs = 1;
 }
 
 }  // namespace hz

@@ -1,0 +1,191 @@
+// FGMRES state and device helpers shared by the single- and multi-RHS drivers
+// (krylov.cu, krylov_batch.cu).
+#pragma once
+#include <cstddef>
+#include <type_traits>
+
+#include "common.cuh"
+
+namespace hz {
+
+constexpr int kMaxM = 16;
+constexpr int kRedBlock = 256;
+constexpr int BX = 32, BY = 8;
+constexpr int kRows = 4;        // y rows per thread in the 2D passes
+constexpr int kPerThread = 4;   // nodes per thread in the 1D passes
+
+struct KrylovStatus {       // first bytes of KrylovState, copied to the host each cycle
+  int iters;
+  int done;
+  int converged;
+  int breakdown;
+  double relres_est;
+  double relres_true;
+};
+
+struct KrylovState {
+  KrylovStatus st;
+  int active;               // iteration kernels run while 1
+  int kcyc;                 // iterations done in the current cycle
+  int m, max_iter;
+  double tol, bnorm;
+  double2 H[kMaxM + 1][kMaxM];
+  double cs[kMaxM];
+  double2 sn[kMaxM];
+  double2 g[kMaxM + 1];
+  double scale[kMaxM + 1];  // v_i = scale[i] * V[i]
+  double2 y[kMaxM];
+  double2 h1[kMaxM + 2];    // raw dots conj(V_i) . w of the Gram-Schmidt passes
+  double2 nrm2;             // .x = ||w||^2 after orthogonalisation
+  unsigned counter;         // blocks finished in the current reduction (last block resets it)
+};
+
+
+inline unsigned nblk(long long n, int b) { return (unsigned)((n + b - 1) / b); }
+
+struct Geo {
+  int nx, ny, nz, sxy, N, dim;
+};
+inline Geo geo(const GridDev& g) { return Geo{g.nx, g.ny, g.nz, g.nx * g.ny, (int)g.N, g.dim}; }
+// 2D grid of 32 x 8 blocks over (x, y), kRows rows per thread; blockIdx.z strides over z
+inline dim3 grid_xy(const Geo& g) {
+  return dim3((g.nx + BX - 1) / BX, (g.ny + BY * kRows - 1) / (BY * kRows), g.nz < 8 ? g.nz : 8);
+}
+inline unsigned grid_1d(long long N) { return nblk(N, kRedBlock * kPerThread); }
+inline int grid_blocks(const Geo& g) {
+  const dim3 d = grid_xy(g);
+  return (int)(d.x * d.y * d.z);
+}
+
+// w - c v with two DFMA per component
+__device__ __forceinline__ double2 axmy(double2 w, double2 c, double2 v) {
+  return make_double2(fma(c.y, v.y, fma(-c.x, v.x, w.x)), fma(-c.y, v.x, fma(-c.x, v.y, w.y)));
+}
+// acc + conj(v) w with two DFMA per component
+__device__ __forceinline__ double2 dot_acc(double2 acc, double2 v, double2 w) {
+  return make_double2(fma(v.y, w.y, fma(v.x, w.x, acc.x)), fma(-v.y, w.x, fma(v.x, w.y, acc.y)));
+}
+// acc + |w|^2
+__device__ __forceinline__ double nrm_acc(double acc, double2 w) { return fma(w.y, w.y, fma(w.x, w.x, acc)); }
+
+__device__ __forceinline__ double2 ld64(const double2* __restrict__ a, int i) { return a[i]; }
+__device__ __forceinline__ double2 ld64(const float2* __restrict__ a, int i) {
+  const float2 v = a[i];
+  return make_double2(f2d_exact(v.x), f2d_exact(v.y));
+}
+
+// FP64 fine-level (A v)_p, 5-/7-point with half-cell weights
+template <typename U>
+__device__ __forceinline__ double2 apply_A(const Geo& g, double invh2, const double2* __restrict__ diag,
+                                           const U* __restrict__ v, int p, int x, int y, int z) {
+  const double2 d = diag[p], vp = ld64(v, p);
+  const bool inx = x > 0 && x < g.nx - 1, iny = y > 0 && y < g.ny - 1;
+  const bool inz = g.dim == 2 || (z > 0 && z < g.nz - 1);
+  if (inx && iny && inz) {
+    double2 s = ld64(v, p - 1) + ld64(v, p + 1) + ld64(v, p - g.nx) + ld64(v, p + g.nx);
+    if (g.dim == 3) s = s + ld64(v, p - g.sxy) + ld64(v, p + g.sxy);
+    // d v - invh2 s, with FMAs
+    return make_double2(fma(d.x, vp.x, fma(-d.y, vp.y, -invh2 * s.x)), fma(d.x, vp.y, fma(d.y, vp.x, -invh2 * s.y)));
+  }
+  double2 acc = cmul(d, vp);
+  const double wx = inx ? 1.0 : 0.5, wy = iny ? 1.0 : 0.5;
+  const double wz = (g.dim == 3 && !inz) ? 0.5 : 1.0;
+  double2 sx = make_double2(0, 0), sy = make_double2(0, 0);
+  if (x > 0) sx = sx + ld64(v, p - 1);
+  if (x < g.nx - 1) sx = sx + ld64(v, p + 1);
+  if (y > 0) sy = sy + ld64(v, p - g.nx);
+  if (y < g.ny - 1) sy = sy + ld64(v, p + g.nx);
+  const double cx = wy * wz * invh2, cy = wx * wz * invh2;
+  acc.x -= cx * sx.x + cy * sy.x;
+  acc.y -= cx * sx.y + cy * sy.y;
+  if (g.dim == 3) {
+    double2 sz = make_double2(0, 0);
+    if (z > 0) sz = sz + ld64(v, p - g.sxy);
+    if (z < g.nz - 1) sz = sz + ld64(v, p + g.sxy);
+    const double cz = wx * wy * invh2;
+    acc.x -= cz * sz.x;
+    acc.y -= cz * sz.y;
+  }
+  return acc;
+}
+
+__device__ inline void givens(double2 a, double2 b, double& c, double2& s) {
+  const double ab = sqrt(cabs2(b));
+  if (ab == 0.0) {
+    c = 1.0;
+    s = make_double2(0, 0);
+    return;
+  }
+  const double aa = sqrt(cabs2(a));
+  if (aa == 0.0) {
+    c = 0.0;
+    s = make_double2(b.x / ab, -b.y / ab);     // conj(b)/|b|
+    return;
+  }
+  const double t = hypot(aa, ab);
+  c = aa / t;
+  const double2 ph = make_double2(a.x / aa, a.y / aa);
+  s = (1.0 / t) * cmul(ph, make_double2(b.x, -b.y));
+}
+
+// Column j of the Hessenberg matrix, Givens rotations, residual estimate
+// (one thread, in the last block of the final Gram-Schmidt pass).
+__device__ inline void arnoldi_update(KrylovState* st, int j, int* n_active = nullptr) {
+  for (int i = 0; i <= j; ++i) st->H[i][j] = st->scale[i] * st->h1[i];
+  const double hn = sqrt(st->nrm2.x);
+  st->H[j + 1][j] = make_double2(hn, 0.0);
+  for (int i = 0; i < j; ++i) {
+    const double2 a = st->H[i][j], b = st->H[i + 1][j];
+    const double c = st->cs[i];
+    const double2 s = st->sn[i];
+    st->H[i][j] = c * a + cmul(s, b);
+    st->H[i + 1][j] = cmul(make_double2(-s.x, s.y), a) + c * b;      // -conj(s) a + c b
+  }
+  double c;
+  double2 s;
+  givens(st->H[j][j], st->H[j + 1][j], c, s);
+  st->cs[j] = c;
+  st->sn[j] = s;
+  st->H[j][j] = c * st->H[j][j] + cmul(s, st->H[j + 1][j]);
+  st->H[j + 1][j] = make_double2(0, 0);
+  const double2 gj = st->g[j];
+  st->g[j + 1] = cmul(make_double2(-s.x, s.y), gj);
+  st->g[j] = c * gj;
+  st->st.iters += 1;
+  st->kcyc = j + 1;
+  st->st.relres_est = sqrt(cabs2(st->g[j + 1])) / st->bnorm;
+  if (!(hn > 0.0)) {
+    st->st.breakdown = 1;
+    st->scale[j + 1] = 0.0;
+  } else {
+    st->scale[j + 1] = 1.0 / hn;
+  }
+  if (st->st.relres_est < st->tol || st->st.iters >= st->max_iter || st->st.breakdown || st->kcyc >= st->m) {
+    st->active = 0;
+    if (n_active) atomicSub(n_active, 1);
+  }
+}
+
+__device__ inline void restart_update(KrylovState* st, int* n_active = nullptr) {
+  const double beta = sqrt(st->nrm2.x);
+  st->st.relres_true = beta / st->bnorm;
+  st->active = 0;
+  if (st->st.relres_true < st->tol) {
+    st->st.converged = 1;
+    st->st.done = 1;
+    return;
+  }
+  if (st->st.iters >= st->max_iter) {
+    st->st.done = 1;
+    return;
+  }
+  st->st.breakdown = 0;
+  st->scale[0] = 1.0 / beta;
+  st->g[0] = make_double2(beta, 0.0);
+  for (int i = 1; i <= kMaxM; ++i) st->g[i] = make_double2(0, 0);
+  st->kcyc = 0;
+  st->active = 1;
+  if (n_active) atomicAdd(n_active, 1);
+}
+
+}  // namespace hz

@@ -55,14 +55,25 @@ class HelmholtzSolver:
         ok, infos = hz.hz_solve(self.ctx, q, p, 1, self.stream)
         return p, infos[0]
 
+    def solve_batch(self, Q, P=None):
+        """Q: complex128 [nodes, R] sources (RHS innermost), R a power of two
+        <= nrhs_max; returns (P, [info] * R)."""
+        R = Q.shape[1]
+        if P is None:
+            P = torch.empty_like(Q)
+        ok, infos = hz.hz_solve(self.ctx, Q, P, R, self.stream)
+        return P, infos
+
     def precond(self, r):
         z = torch.empty_like(r)
-        hz.hz_precond_apply(self.ctx, r, z, 1, self.stream)
+        nrhs = r.shape[1] if r.dim() == 2 else 1
+        hz.hz_precond_apply(self.ctx, r, z, nrhs, self.stream)
         return z
 
     def apply(self, v, shifted=False):
         w = torch.empty_like(v)
-        hz.hz_apply_operator(self.ctx, v, w, 1, int(shifted), self.stream)
+        nrhs = v.shape[1] if v.dim() == 2 else 1
+        hz.hz_apply_operator(self.ctx, v, w, nrhs, int(shifted), self.stream)
         return w
 
     def close(self):

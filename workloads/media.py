@@ -48,7 +48,7 @@ def _correlated_noise(shape, rng: np.random.Generator, corr_cells: float) -> np.
         sh[ax] = k.size
         k2 = k2 + (k.reshape(sh)) ** 2
     spec *= np.exp(-0.5 * corr_cells ** 2 * k2)
-    field = np.fft.irfftn(spec, s=shape)
+    field = np.fft.irfftn(spec, s=shape, axes=list(range(len(shape))))
     field -= field.mean()
     std = field.std()
     return field / std if std > 0 else field
