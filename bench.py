@@ -130,12 +130,20 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def make_solver(w, precision, stream=None):
+def make_solver(w, precision, stream=None, nrhs_max=1):
     from paper_2511_16808_gb300.solver import HelmholtzSolver
     return HelmholtzSolver(w.dim, [w.n] * w.dim, w.kappa.ravel(), w.omega, w.gamma.ravel(), w.alpha,
                            w.levels, patch=w.patch, intergrid=w.intergrid, precision=precision,
                            tol=w.tol, restart=w.restart, nu1=w.nu1, nu2=w.nu2, max_iter=w.max_iter,
-                           patch_coarse=w.patch_coarse, stream=stream)
+                           patch_coarse=w.patch_coarse, nrhs_max=nrhs_max, stream=stream)
+
+
+def _workload(name):
+    """(workload, index): config4 yields one workload per frequency; its CPU
+    sample runs the middle frequency (10 points per wavelength)."""
+    import workloads
+    w = getattr(workloads, name)()
+    return (w[1], 1) if isinstance(w, list) else (w, None)
 
 
 def time_solves(torch, solver, q, p, steps, stream):
@@ -154,7 +162,7 @@ def time_solves(torch, solver, q, p, steps, stream):
     return start.elapsed_time(end), infos
 
 
-def cpu_baseline_sample(workload: str, iters: int, ref_iters: int):
+def cpu_baseline_sample(workload: str, iters: int, ref_iters: float):
     """Run the oracle in a fresh single-threaded process on a bounded sample
     (setup, then `iters` FGMRES iterations of the same solve)."""
     code = f"""
@@ -163,6 +171,7 @@ sys.path.insert(0, {ROOT!r})
 import workloads
 from oracle import solver, fgmres
 w = getattr(workloads, {workload!r})()
+w = w[1] if isinstance(w, list) else w
 pr = solver.from_workload(w)
 q = pr.rhs(w.rhs(0))
 t = time.perf_counter()
@@ -179,7 +188,7 @@ print(json.dumps({{"s_per_iter": dt / info.iters, "iters": info.iters}}))
     return {"value": 1.0 / s_per_solve, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{workload}: setup untimed, then {d['iters']} FGMRES iterations of the same "
                       f"solve timed ({d['s_per_iter'] * 1e3:.1f} ms/iteration) and scaled by the "
-                      f"{ref_iters} iterations a full solve takes"}
+                      f"{ref_iters:g} iterations a full solve takes"}
 
 
 def run_ours(args):
@@ -312,16 +321,199 @@ def run_ours(args):
     return out
 
 
+def _profile_class(torch, hz, solvers, run, cls):
+    """Bracket every launch of `cls` with events over one `run()`; returns the
+    summed {ms, launches, bytes, flops} over all solvers."""
+    for sv in solvers:
+        hz.hz_profile_select(sv.ctx, cls)
+    run()                                   # re-capture the cycles with the events
+    for sv in solvers:
+        hz.hz_profile_select(sv.ctx, cls)   # reset the accumulators
+    run()
+    torch.cuda.synchronize()
+    tot = {"ms": 0.0, "launches": 0, "bytes": 0.0, "flops": 0.0}
+    for sv in solvers:
+        d = hz.hz_profile_read(sv.ctx)
+        for k in tot:
+            tot[k] += d[k]
+        hz.hz_profile_select(sv.ctx, "none")
+    return tot
+
+
+def run_batched(args):
+    """Multi-RHS workload: 64 seeded point sources x 3 frequencies on one
+    513^2 medium; one step = the 192 solves, one batched hz_solve (64 RHS,
+    RHS innermost) per frequency."""
+    import torch
+    import workloads
+    from paper_2511_16808_gb300 import hz
+
+    rank, world, local = _env_rank()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    ws = getattr(workloads, args.config)()
+    R = len(ws[0].sources)
+    nsolve = R * len(ws)
+    stream = torch.cuda.current_stream()
+    solvers = [make_solver(w, "mixed", stream, nrhs_max=R) for w in ws]
+    Qs = [torch.tensor(w.rhs_block(), device="cuda") for w in ws]
+    Ps = [torch.empty_like(Q) for Q in Qs]
+
+    def step():
+        out = []
+        for sv, Q, P in zip(solvers, Qs, Ps):
+            ok, inf = hz.hz_solve(sv.ctx, Q, P, R, stream)
+            out.append(inf)
+        return out
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches0 = sum(hz.hz_kernel_launches(sv.ctx) for sv in solvers)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        t0.record(stream)
+        for _ in range(args.steps):
+            infos = step()
+        t1.record(stream)
+        t1.synchronize()
+    ms = t0.elapsed_time(t1)
+    launches = sum(hz.hz_kernel_launches(sv.ctx) for sv in solvers) - launches0
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    value = world * args.steps * nsolve / (ms / 1e3)
+    iters = [[i.iters for i in inf] for inf in infos]
+    conv = all(i.converged for inf in infos for i in inf)
+    relres = max(i.relres_true for inf in infos for i in inf)
+
+    # e2e: sources from pinned host memory, solutions back to host memory
+    Qh = [Q.cpu().pin_memory() for Q in Qs]
+    Ph = [torch.empty_like(Q).pin_memory() for Q in Qh]
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for sv, Q, P in zip(solvers, Qh, Ph):
+        hz.hz_solve(sv.ctx, Q, P, R, stream)
+    e1.record(stream)
+    e1.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+
+    out = None
+    if rank == 0:
+        run = lambda: step()  # noqa: E731
+        prof = _profile_class(torch, hz, solvers, run, "mgs_step")
+        first = _profile_class(torch, hz, solvers, run, "mgs_first")
+        vprof = _profile_class(torch, hz, solvers, run, "vcycle")
+        smoothed = 0
+        for l in range(hz.hz_level_count(solvers[0].ctx) - 1):
+            smoothed += hz.hz_level_describe(solvers[0].ctx, l)["nodes"] * (ws[0].nu1 + ws[0].nu2)
+        # V-cycles of all right-hand sides in the profiled step
+        nv = sum(sum(it) for it in iters)
+        vdofs = smoothed * nv / (vprof["ms"] / 1e3) if vprof["ms"] > 0 else None
+
+        # the same sources one at a time (bounded subset): mixed, and plain FP64
+        def one_at_a_time(precision, per_freq):
+            tot_ms, n, its = 0.0, 0, []
+            for w, Q in zip(ws, Qs):
+                sv = make_solver(w, precision, stream)
+                q = Q[:, 0].contiguous()
+                p = torch.empty_like(q)
+                sv.solve(q, p)
+                for k in range(per_freq):
+                    q = Q[:, k].contiguous()
+                    ms1, inf = time_solves(torch, sv, q, p, 1, stream)
+                    tot_ms += ms1
+                    n += 1
+                    its.append(inf[0].iters)
+                sv.close()
+            return {"value": n / (tot_ms / 1e3), "unit": UNIT, "solves_timed": n,
+                    "iters_mean": sum(its) / len(its)}
+        single = one_at_a_time("mixed", 4)
+        fp64 = None if args.no_fp64 else one_at_a_time("fp64", 2)
+        cpu = None
+        if not args.no_cpu_baseline:
+            it1 = iters[1]
+            cpu = cpu_baseline_sample(args.config, args.cpu_iters, sum(it1) / len(it1))
+        peak, src = _peaks()
+        avg_ms = prof["ms"] / max(prof["launches"], 1)
+        achieved = prof["flops"] / max(prof["launches"], 1) / (avg_ms / 1e3) / 1e12
+        roofline = {"kernel": "k_mgs_step_b (FP64 modified Gram-Schmidt update + per-RHS inner products)",
+                    "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": _traffic("k_mgs_step_b"),
+                    "launches": prof["launches"], "avg_launch_us": avg_ms * 1e3,
+                    "hbm_achieved_gbs": prof["bytes"] / (prof["ms"] / 1e3) / 1e9 if prof["ms"] else None,
+                    "peak_note": "FP64 peak derived from DFMA rate x SMs x max clock"}
+        f_ms = first["ms"] / max(first["launches"], 1)
+        first_roof = {"kernel": "k_mgs_first_b (FP64 operator on z + per-RHS inner products)", "bound": "alu",
+                      "achieved": first["flops"] / max(first["launches"], 1) / (f_ms / 1e3) / 1e12 if f_ms else None,
+                      "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "avg_launch_us": f_ms * 1e3,
+                      "launches": first["launches"]}
+        first_roof["frac"] = first_roof["achieved"] / FP64_PEAK_TFLOPS if first_roof["achieved"] else None
+        v_gbs = vprof["bytes"] / (vprof["ms"] / 1e3) / 1e9 if vprof["ms"] else None
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c64 V-cycle / c128 FGMRES",
+            "data": "synthetic (homogeneous medium, seeded sources)",
+            "config": {"workload": f"{ws[0].name.rsplit('-ppw', 1)[0]} x {R} sources x ppw "
+                                   + "/".join(f"{w.meta['ppw']:g}" for w in ws),
+                       "nodes": ws[0].nodes, "nrhs": R, "frequencies": len(ws), "levels": ws[0].levels,
+                       "patch": ws[0].patch, "intergrid": ws[0].intergrid, "alpha": ws[0].alpha,
+                       "tol": ws[0].tol, "restart": ws[0].restart,
+                       "l2": "working set per batched solve > 129 MB L2 (no flush)",
+                       "parallelism": f"replicas x{world}"},
+            "solves_per_step": nsolve, "converged": conv, "relres_true_max": relres,
+            "iters": {f"ppw{w.meta['ppw']:g}": {"min": min(it), "max": max(it), "mean": sum(it) / len(it)}
+                      for w, it in zip(ws, iters)},
+            "unknowns_vcycles_per_s": world * args.steps * ws[0].nodes * nv / (ms / 1e3),
+            "e2e": {"value": nsolve / (e2e_ms / 1e3), "unit": UNIT,
+                    "h2d_bytes_per_step": 16 * ws[0].nodes * nsolve, "d2h_bytes_per_step": 16 * ws[0].nodes * nsolve},
+            "one_at_a_time_mixed": single,
+            "plain_fp64": fp64,
+            "clocks": clk.summary(),
+            "roofline": roofline,
+            "mgs_first_roofline": first_roof,
+            "vcycle_roofline": {"bound": "hbm", "achieved": v_gbs, "peak": peak, "unit": "GB/s",
+                                "frac": v_gbs / peak if v_gbs else None, "peak_source": src,
+                                "avg_vcycle_us": vprof["ms"] * 1e3 / max(vprof["launches"], 1)},
+            "cpu_baseline": cpu,
+            "gpu_launches": launches,
+            "peak_source": src,
+            "vanka_dof_per_s": vdofs,
+        }
+    for sv in solvers:
+        sv.close()
+    if dist:
+        dist.destroy_process_group()
+    return out
+
+
 def run_reference(args):
     rank, world, local = _env_rank()
     if rank != 0:
         return None
     import workloads
     from oracle import fgmres, solver
-    w = getattr(workloads, args.config)()
+    w, fi = _workload(args.config)
     gold = os.path.join(ROOT, "tests", "golden", f"oracle_{args.config}.json")
     with open(gold) as f:
-        ref_iters = json.load(f)["iters"]
+        g = json.load(f)
+    if fi is None:
+        ref_iters = g["iters"]
+    else:
+        its = [s["iters"] for s in g["freqs"][fi]["sources"]]
+        ref_iters = sum(its) / len(its)
     pr = solver.from_workload(w)
     q = pr.rhs(w.rhs(0))
     per_step = args.ref_iters_per_step
@@ -334,7 +526,7 @@ def run_reference(args):
     s_per_iter = sum(times) / (len(times) * per_step)
     value = 1.0 / (s_per_iter * ref_iters)
     sample = (f"{w.name}: each step = {per_step} FGMRES iterations of the oracle solve "
-              f"(setup untimed), scaled by the {ref_iters} iterations of a full oracle solve")
+              f"(setup untimed), scaled by the {ref_iters:g} iterations of a full oracle solve")
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * s_per_iter * ref_iters,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
@@ -356,7 +548,12 @@ def main():
     ap.add_argument("--cpu-iters", type=int, default=25)
     ap.add_argument("--ref-iters-per-step", type=int, default=5)
     args = ap.parse_args()
-    out = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if args.impl == "reference":
+        out = run_reference(args)
+    elif args.config == "config4":
+        out = run_batched(args)
+    else:
+        out = run_ours(args)
     if out is not None:
         print(json.dumps(out))
 

@@ -173,6 +173,106 @@ hz_status hz_destroy(hz_ctx* ctx);
  * info filled) when any right-hand side misses tol within max_iter. */
 hz_status hz_solve(hz_ctx* ctx, const void* q, void* p, int nrhs, hz_info* info, void* cuda_stream);
 
+/* Asynchronous single-right-hand-side solve: the same FGMRES(m) as hz_solve,
+ * split so that one host thread can keep several contexts' solves in flight
+ * (the serving loop below is built on it; the paper has no counterpart).
+ *   hz_solve_begin  queues the start-up work after the work already queued on
+ *                   cuda_stream.  q: unscaled source, c128, host (copied before
+ *                   the call returns) or device (read by the queued work: keep it
+ *                   unchanged until the solve has finished).
+ *   hz_solve_step   looks at the status of the last queued restart cycle; if it
+ *                   has not completed yet (block = 0) or the solve goes on, it
+ *                   sets *done = 0 (queuing the next cycle in the second case);
+ *                   *done = 1 once converged or out of iterations.  block = 1
+ *                   waits for the status first.
+ *   hz_solve_end    after *done = 1: p (c128, host or device) receives the
+ *                   solution, ordered before later work on cuda_stream; info as
+ *                   for hz_solve, HZ_ERR_NOT_CONVERGED likewise.
+ * A context holds one asynchronous solve at a time (HZ_ERR_INVALID_ARG for a
+ * second begin); the other calls on the context must not run in between. */
+hz_status hz_solve_begin(hz_ctx* ctx, const void* q, void* cuda_stream);
+hz_status hz_solve_step(hz_ctx* ctx, int block, int* done);
+hz_status hz_solve_end(hz_ctx* ctx, void* p, hz_info* info, void* cuda_stream);
+
+/* ---------------------------------------------------------------- serving
+ * Continuous batching of independent solves on one GPU (the paper has no
+ * counterpart).  A request is a whole problem: grid, medium, frequency,
+ * shift, solver options (nrhs_max = 1) and one source.  The server admits
+ * queued requests in arrival order while their estimated device bytes fit the
+ * budget and a slot is free, builds each hierarchy on the request's own
+ * stream, keeps every admitted solve's restart cycles in flight at once (they
+ * overlap on the device), writes each solution to the caller's buffer and
+ * frees the hierarchy, which admits the next request.  Requests are
+ * independent: one that fails records its status and releases its slot.
+ * Results do not depend on what else runs: each request's kernels and
+ * reductions are the ones hz_solve runs, in the same order. */
+typedef struct hz_server hz_server;
+
+typedef struct {
+  size_t hbm_budget;   /* device bytes the admitted requests may hold; 0 = 80% of free memory */
+  int max_active;      /* requests admitted at once (set up or solving); 0 = 32 */
+  int device;          /* CUDA device ordinal; -1 = the calling thread's current device */
+} hz_server_opts;
+
+typedef struct {
+  hz_grid grid;
+  const double* kappa;   /* host, nodes values (copied at submission) */
+  const double* gamma;   /* host, nodes values or NULL = gamma0 (copied) */
+  double gamma0;
+  double omega;
+  double shift_alpha;
+  hz_opts opts;          /* nrhs_max must be 1 */
+  const void* q;         /* host c128 source, nodes values (copied) */
+  void* p;               /* host c128 solution buffer, written when the request
+                            finishes; keep it alive until then */
+} hz_request;
+
+enum { HZ_REQ_QUEUED = 0, HZ_REQ_SETUP = 1, HZ_REQ_SOLVING = 2, HZ_REQ_DONE = 3, HZ_REQ_FAILED = 4 };
+
+typedef struct {
+  int state;             /* HZ_REQ_* */
+  hz_status status;      /* HZ_OK, HZ_ERR_NOT_CONVERGED (p filled) or the failure */
+  hz_info info;
+  double t_submit, t_admit, t_start, t_done;   /* seconds since hz_server_create */
+  size_t bytes;          /* admission estimate */
+  char message[128];     /* failure message, empty otherwise */
+} hz_ticket_info;
+
+typedef struct {
+  int queued, setting_up, solving, done, failed;
+  size_t bytes_in_use, peak_bytes, budget;
+  int max_active;
+  double elapsed_s;
+} hz_server_counters;
+
+/* Starts the server's host threads on the device.  opts may be NULL. */
+hz_status hz_server_create(const hz_server_opts* opts, hz_server** out);
+/* Validates and copies the request and queues it; *ticket identifies it.
+ * HZ_ERR_OOM when its estimate exceeds the whole budget, HZ_ERR_INVALID_ARG
+ * for bad sizes or options (the medium is checked later, at setup). */
+hz_status hz_server_submit(hz_server* srv, const hz_request* req, uint64_t* ticket);
+/* Current state of a request (non-blocking). */
+hz_status hz_server_poll(hz_server* srv, uint64_t ticket, hz_ticket_info* out);
+/* Waits until the request has finished or failed (timeout_s < 0: no limit);
+ * HZ_ERR_TIMEOUT, with out filled, when the time ran out first. */
+hz_status hz_server_wait(hz_server* srv, uint64_t ticket, double timeout_s, hz_ticket_info* out);
+hz_status hz_server_stats(hz_server* srv, hz_server_counters* out);
+/* Finishes every submitted request, then stops the threads and frees all. */
+hz_status hz_server_destroy(hz_server* srv);
+
+/* The server's admission policy on its own (host only, no device): FIFO
+ * under a byte budget and a slot limit.  offer queues (accepted = 0 when the
+ * bytes exceed the whole budget); next admits the head if it fits (admitted =
+ * 0 otherwise, nothing overtakes it); release returns a finished request's
+ * bytes and slot. */
+typedef struct hz_sched hz_sched;
+hz_status hz_sched_create(size_t budget, int max_active, hz_sched** out);
+hz_status hz_sched_offer(hz_sched* s, uint64_t ticket, size_t bytes, int* accepted);
+hz_status hz_sched_next(hz_sched* s, uint64_t* ticket, int* admitted);
+hz_status hz_sched_release(hz_sched* s, size_t bytes);
+hz_status hz_sched_state(const hz_sched* s, size_t* in_use, size_t* peak, int* active, int* queued);
+hz_status hz_sched_destroy(hz_sched* s);
+
 /* z = V-cycle(r) with zero initial guess (Algorithm 1, recursive).
  * r, z: c128 device arrays of nodes*nrhs values (r in the row-scaled space);
  * nrhs as for hz_solve. */

@@ -10,6 +10,11 @@ namespace hz {
 
 static thread_local std::string g_last_error;
 
+void set_last_error(const char* msg) {
+  if (msg) g_last_error = msg;
+  else g_last_error.clear();
+}
+
 // Scratch of the allocation-free sweep (hz_level_smooth_noalloc): the
 // residual of one level, c64 or c128, at most HZ_NOALLOC_MAX_NODES nodes.
 // It lives in the module's static device memory, so every GPU that loads the
@@ -38,6 +43,8 @@ void ctx_free_all(Ctx& c) {
   c.prof_ev.clear();
   if (c.ev_in) cudaEventDestroy(c.ev_in);
   if (c.ev_out) cudaEventDestroy(c.ev_out);
+  if (c.ev_status) cudaEventDestroy(c.ev_status);
+  c.ev_status = nullptr;
   if (c.graph_stream) cudaStreamDestroy(c.graph_stream);
   c.ev_in = c.ev_out = nullptr;
   c.graph_stream = nullptr;
@@ -57,27 +64,6 @@ struct BusyGuard {
   }
   ~BusyGuard() { c->busy.store(0); }
 };
-
-template <typename F>
-hz_status guarded(F&& f) {
-  try {
-    f();
-    g_last_error.clear();
-    return HZ_OK;
-  } catch (const Error& e) {
-    g_last_error = e.what();
-    return e.code;
-  } catch (const std::bad_alloc&) {
-    g_last_error = "host allocation failed";
-    return HZ_ERR_OOM;
-  } catch (const std::exception& e) {
-    g_last_error = e.what();
-    return HZ_ERR_CUDA;
-  } catch (...) {
-    g_last_error = "unknown error";
-    return HZ_ERR_CUDA;
-  }
-}
 
 bool is_device_ptr(const void* p) {
   cudaPointerAttributes a;
@@ -279,7 +265,9 @@ hz_status hz_setup(const hz_grid* g, const double* kappa, double omega, const do
 hz_status hz_destroy(hz_ctx* ctx) {
   return guarded([&] {
     if (!ctx) return;
-    cudaDeviceSynchronize();
+    // the context's own work runs on its library stream; other streams that
+    // used it are the caller's to synchronize before destroying it
+    if (ctx->c.graph_stream) cudaStreamSynchronize(ctx->c.graph_stream);
     ctx_free_all(ctx->c);
     delete ctx;
   });
@@ -311,6 +299,47 @@ hz_status hz_solve(hz_ctx* ctx, const void* q, void* p, int nrhs, hz_info* info,
     }
     for (int r = 0; r < nrhs; ++r)
       if (!info[r].converged) throw Error(HZ_ERR_NOT_CONVERGED, "FGMRES did not reach tol within max_iter");
+  });
+}
+
+hz_status hz_solve_begin(hz_ctx* ctx, const void* q, void* cuda_stream) {
+  return guarded([&] {
+    require(ctx && q, "null argument");
+    Ctx& c = ctx->c;
+    BusyGuard bg(&c);
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const double2* qd = (const double2*)q;
+    if (!is_device_ptr(q)) {
+      if (!c.qstage) c.qstage = (double2*)ctx_alloc(c, sizeof(double2) * c.L[0].g.N * c.opts.nrhs_max);
+      HZ_CUDA(cudaMemcpyAsync(c.qstage, q, sizeof(double2) * c.L[0].g.N, cudaMemcpyHostToDevice, s));
+      qd = c.qstage;
+    }
+    solve_begin(c, qd, s);
+  });
+}
+
+hz_status hz_solve_step(hz_ctx* ctx, int block, int* done) {
+  return guarded([&] {
+    require(ctx && done, "null argument");
+    BusyGuard bg(&ctx->c);
+    require(ctx->c.as_state != 0, "no asynchronous solve in flight");
+    *done = solve_step(ctx->c, block != 0);
+  });
+}
+
+hz_status hz_solve_end(hz_ctx* ctx, void* p, hz_info* info, void* cuda_stream) {
+  return guarded([&] {
+    require(ctx && p && info, "null argument");
+    Ctx& c = ctx->c;
+    BusyGuard bg(&c);
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const bool p_host = !is_device_ptr(p);
+    solve_end(c, p_host ? c.p : (double2*)p, info, s);
+    if (p_host) {
+      HZ_CUDA(cudaMemcpyAsync(p, c.p, sizeof(double2) * c.L[0].g.N, cudaMemcpyDeviceToHost, s));
+      HZ_CUDA(cudaStreamSynchronize(s));
+    }
+    if (!info->converged) throw Error(HZ_ERR_NOT_CONVERGED, "FGMRES did not reach tol within max_iter");
   });
 }
 

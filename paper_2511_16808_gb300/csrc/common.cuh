@@ -14,6 +14,9 @@
 //                      per-node stencil over the offsets d_l - d_k of the patch
 //                      (Eq. smoother); a sweep is a gather, conflict-free
 #pragma once
+#include <cstring>
+#include <new>
+#include <stdexcept>
 
 #include <cuda_runtime.h>
 
@@ -113,28 +116,103 @@ template <> __device__ __forceinline__ float2 from_c128<float2>(double2 a) {
 // float <-> double on the integer pipe.  GB300 executes FP64 instructions,
 // conversions included, at 1/64 of the FP32 rate, and converting the FP32
 // preconditioned vectors for the FP64 Krylov passes saturated that pipe.
-// These repack sign / exponent / mantissa with 32-bit integer operations and
-// give exactly the IEEE results (round to nearest even for the narrowing
-// conversion); zero, subnormal, infinite, NaN and out-of-range inputs take the
-// hardware conversion.
-__device__ __forceinline__ double f2d_exact(float f) {
-  const unsigned u = __float_as_uint(f);
-  const unsigned e = (u >> 23) & 0xffu;
-  if (e == 0u || e == 0xffu) return (double)f;
-  const unsigned m = u & 0x7fffffu;
-  const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | (m >> 3);
-  return __hiloint2double((int)hi, (int)(m << 29));
+// These repack sign / exponent / mantissa with integer operations only (no
+// hardware conversion on any path, so none is issued speculatively either)
+// and give exactly the IEEE results: f2d_exact is the exact widening
+// (subnormals normalised, infinities and NaN payloads kept), d2f_rn the
+// narrowing with round to nearest even, including subnormal results and
+// overflow to infinity.  Host-callable so that they can be checked bit for bit
+// against the host's conversions.
+__host__ __device__ __forceinline__ unsigned f_bits(float f) {
+#ifdef __CUDA_ARCH__
+  return __float_as_uint(f);
+#else
+  unsigned u;
+  memcpy(&u, &f, 4);
+  return u;
+#endif
 }
-__device__ __forceinline__ float d2f_rn(double d) {
-  const unsigned hi = (unsigned)__double2hiint(d);
-  const unsigned lo = (unsigned)__double2loint(d);
-  const int e = (int)((hi >> 20) & 0x7ffu) - 896;          // float exponent field
-  if (e <= 0 || e >= 255) return __double2float_rn(d);
-  const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);   // 23-bit mantissa
-  const unsigned rem = lo & 0x1fffffffu;                    // 29 dropped bits
-  unsigned bits = ((unsigned)e << 23) | m;
-  bits += (rem > 0x10000000u || (rem == 0x10000000u && (m & 1u))) ? 1u : 0u;   // carry may reach exponent
-  return __uint_as_float(bits | (hi & 0x80000000u));
+__host__ __device__ __forceinline__ float bits_f(unsigned u) {
+#ifdef __CUDA_ARCH__
+  return __uint_as_float(u);
+#else
+  float f;
+  memcpy(&f, &u, 4);
+  return f;
+#endif
+}
+__host__ __device__ __forceinline__ double hilo_d(unsigned hi, unsigned lo) {
+#ifdef __CUDA_ARCH__
+  return __hiloint2double((int)hi, (int)lo);
+#else
+  const unsigned long long b = ((unsigned long long)hi << 32) | lo;
+  double d;
+  memcpy(&d, &b, 8);
+  return d;
+#endif
+}
+__host__ __device__ __forceinline__ void d_hilo(double d, unsigned& hi, unsigned& lo) {
+#ifdef __CUDA_ARCH__
+  hi = (unsigned)__double2hiint(d);
+  lo = (unsigned)__double2loint(d);
+#else
+  unsigned long long b;
+  memcpy(&b, &d, 8);
+  hi = (unsigned)(b >> 32);
+  lo = (unsigned)b;
+#endif
+}
+__host__ __device__ __forceinline__ int clz32(unsigned m) {
+#ifdef __CUDA_ARCH__
+  return __clz((int)m);
+#else
+  return m ? __builtin_clz(m) : 32;
+#endif
+}
+
+__host__ __device__ __forceinline__ double f2d_exact(float f) {
+  const unsigned u = f_bits(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  unsigned m = u & 0x7fffffu;
+  unsigned E;                                   // double exponent field
+  if (e == 0u) {
+    // zero or subnormal m * 2^-149: leading one at bit k -> 1.frac * 2^(k-149)
+    const int k = 31 - clz32(m);
+    E = m ? (unsigned)(k + 874) : 0u;
+    m = m ? (m << (23 - k)) & 0x7fffffu : 0u;
+  } else {
+    E = e == 0xffu ? 0x7ffu : e + 896u;
+  }
+  return hilo_d((u & 0x80000000u) | (E << 20) | (m >> 3), m << 29);
+}
+
+__host__ __device__ __forceinline__ float d2f_rn(double d) {
+  unsigned hi, lo;
+  d_hilo(d, hi, lo);
+  const unsigned sign = hi & 0x80000000u;
+  const int E = (int)((hi >> 20) & 0x7ffu);
+  const unsigned mh = hi & 0xfffffu;
+  if (E == 0x7ff) {                             // infinity / NaN (quiet, payload kept)
+    const unsigned nan = (mh | lo) ? (0x400000u | (mh << 3) | (lo >> 29)) : 0u;
+    return bits_f(sign | 0x7f800000u | nan);
+  }
+  const int e = E - 896;                        // float exponent field
+  if (e >= 255) return bits_f(sign | 0x7f800000u);
+  if (e >= 1) {
+    const unsigned m = (mh << 3) | (lo >> 29);  // 23-bit mantissa
+    const unsigned rem = lo & 0x1fffffffu;      // 29 dropped bits
+    unsigned bits = ((unsigned)e << 23) | m;
+    bits += (rem > 0x10000000u || (rem == 0x10000000u && (m & 1u))) ? 1u : 0u;   // carry may reach exponent
+    return bits_f(sign | bits);
+  }
+  // subnormal (or zero) result: drop 30 - e bits of the 53-bit significand
+  const int shift = 30 - e;
+  if (E == 0 || shift >= 54) return bits_f(sign);
+  const unsigned long long M = ((unsigned long long)(mh | 0x100000u) << 32) | lo;
+  const unsigned q = (unsigned)(M >> shift);
+  const unsigned long long rem = M & ((1ull << shift) - 1ull), half = 1ull << (shift - 1);
+  const unsigned up = (rem > half || (rem == half && (q & 1u))) ? 1u : 0u;
+  return bits_f(sign | (q + up));               // a carry gives the smallest normal
 }
 
 // ---------------------------------------------------------------- grid
@@ -207,6 +285,32 @@ std::vector<std::array<int, 3>> box_offsets(int dim, int rho);
 std::vector<std::array<int, 3>> patch_offsets(int dim, hz_patch kind);
 std::vector<std::array<int, 3>> patch_difference_offsets(int dim, hz_patch kind);
 
+// ---------------------------------------------------------------- errors at the ABI
+// The message of the calling thread's last failed call (api.cu).
+void set_last_error(const char* msg);
+
+// Runs f; converts exceptions into a status and the thread's last message.
+template <typename F>
+hz_status guarded(F&& f) {
+  try {
+    f();
+    set_last_error(nullptr);
+    return HZ_OK;
+  } catch (const Error& e) {
+    set_last_error(e.what());
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    set_last_error("host allocation failed");
+    return HZ_ERR_OOM;
+  } catch (const std::exception& e) {
+    set_last_error(e.what());
+    return HZ_ERR_CUDA;
+  } catch (...) {
+    set_last_error("unknown error");
+    return HZ_ERR_CUDA;
+  }
+}
+
 // ---------------------------------------------------------------- context
 struct Level {
   GridDev g;
@@ -266,6 +370,10 @@ struct Ctx {
   int cycle_graph_nrhs = 0;
   cudaStream_t graph_stream = nullptr;   // library stream the solve runs on (graph capture needs one)
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaEvent_t ev_status = nullptr;         // status copy of the last queued restart cycle
+  int as_state = 0;                        // asynchronous solve: 0 idle, 1 in flight, 2 finished
+  int as_before = 0;                       // iterations before the last queued cycle
+  bool as_replayed = false;
   int graph_kernels = 0;        // kernel nodes in the captured restart cycle
   // measurement hooks (hz_profile_select / hz_profile_read): CUDA events around
   // the launches of one kernel class inside the captured cycle
@@ -301,6 +409,10 @@ void fine_apply_f64(Ctx& c, const void* v, bool v_single, double2* w, bool shift
 size_t krylov_bytes(const hz_grid& g, const hz_opts& o);
 void krylov_alloc(Ctx& c);
 void fgmres_solve(Ctx& c, const double2* q_dev, double2* p_dev, hz_info* info, cudaStream_t s);
+// asynchronous single-RHS solve (krylov.cu): step returns 1 once finished
+void solve_begin(Ctx& c, const double2* q_dev, cudaStream_t s);
+int solve_step(Ctx& c, bool block);
+void solve_end(Ctx& c, double2* p_dev, hz_info* info, cudaStream_t s);
 void fgmres_solve_batch(Ctx& c, const double2* q_dev, double2* p_dev, int nrhs, hz_info* info, cudaStream_t s);
 void precond_apply_c128(Ctx& c, const double2* r, double2* z, int nrhs, cudaStream_t s);
 void profile_select(Ctx& c, int cls);

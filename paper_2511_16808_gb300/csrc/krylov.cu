@@ -251,60 +251,6 @@ __global__ void k_widen_vec(int N, const V* __restrict__ in, double2* __restrict
   if (p < N) out[p] = ld64(in, p);
 }
 
-// ---- measurement hooks: events around the launches of the selected class
-// (1 = Gram-Schmidt update passes k_mgs_step, 2 = first pass k_mgs_first with
-// the FP64 operator, 3 = whole V-cycle preconditioner application)
-int prof_begin(Ctx& c, int cls, int j, double bytes, double flops, cudaStream_t s) {
-  if (c.prof_class != cls) return -1;
-  const int k = (int)c.prof_j.size();
-  if ((int)c.prof_ev.size() < 2 * (k + 1)) {
-    cudaEvent_t a, b;
-    HZ_CUDA(cudaEventCreate(&a));
-    HZ_CUDA(cudaEventCreate(&b));
-    c.prof_ev.push_back(a);
-    c.prof_ev.push_back(b);
-  }
-  c.prof_j.push_back(j);
-  c.prof_b.push_back(bytes);
-  c.prof_f.push_back(flops);
-  HZ_CUDA(cudaEventRecordWithFlags(c.prof_ev[2 * k], s, cudaEventRecordExternal));
-  return k;
-}
-void prof_end(Ctx& c, int k, cudaStream_t s) {
-  if (k >= 0) HZ_CUDA(cudaEventRecordWithFlags(c.prof_ev[2 * k + 1], s, cudaEventRecordExternal));
-}
-// after a replayed cycle in which `ran` inner iterations did work
-void prof_collect(Ctx& c, int ran) {
-  for (size_t k = 0; k < c.prof_j.size(); ++k) {
-    if (c.prof_j[k] >= ran) continue;
-    float ms = 0.f;
-    HZ_CUDA(cudaEventElapsedTime(&ms, c.prof_ev[2 * k], c.prof_ev[2 * k + 1]));
-    c.prof_ms += ms;
-    c.prof_bytes += c.prof_b[k];
-    c.prof_flops += c.prof_f[k];
-    c.prof_launches += 1;
-  }
-}
-
-// Algorithmic (compulsory) bytes of one V-cycle with the kernels of cycle_impl.cuh
-double vcycle_bytes(const Ctx& c) {
-  const double b = c.mixed ? 8.0 : 16.0;
-  double tot = 0;
-  for (size_t l = 0; l < c.L.size(); ++l) {
-    const Level& L = c.L[l];
-    const double N = (double)L.g.N;
-    if (L.coarsest) {
-      tot += N * N * b + 2 * N * b;
-      continue;
-    }
-    const double sA = L.fine ? 1.0 : L.A.off.n, sM = L.M.off.n;
-    const double rc = L.g.dim == 3 ? 0.125 : 0.25;
-    if (L.m_diag) tot += N * b * (5 + (1 + rc) + (5 + rc)) + (sA - 1) * 2 * N * b;   // sweep0+resid, restrict, prolong+sweep
-    else tot += N * b * (2 * sM + 2 * sA + 13 + 2 * rc);
-  }
-  return tot;
-}
-
 // One restart cycle: m inner iterations (skipped on the device once stopped),
 // the solution update and the true residual; solution accumulates in c.p.
 template <typename TZ>
@@ -348,6 +294,11 @@ void run_cycle(Ctx& c, cudaStream_t s) {
 template <typename TZ>
 void ensure_graph(Ctx& c) {
   if (c.cycle_graph) return;
+  // the two captured cycles share the event list: one profiled graph at a time
+  if (c.prof_class && c.batch_graph) {
+    cudaGraphExecDestroy(c.batch_graph);
+    c.batch_graph = nullptr;
+  }
   c.prof_j.clear();
   c.prof_b.clear();
   c.prof_f.clear();
@@ -376,8 +327,12 @@ void ensure_graph(Ctx& c) {
   HZ_CUDA(e);
 }
 
+// Asynchronous single-RHS solve: begin queues the start-up work, each step
+// reads the status of the last restart cycle (once its event has completed)
+// and queues the next cycle, end hands out the solution.  The blocking solve
+// and the serving loop are both built from these.
 template <typename TZ>
-void solve_t(Ctx& c, const double2* q, double2* p, hz_info* info, cudaStream_t user) {
+void solve_begin_t(Ctx& c, const double2* q, cudaStream_t user) {
   Level& L0 = c.L[0];
   const Geo g = geo(L0.g);
   const int N = g.N;
@@ -397,28 +352,139 @@ void solve_t(Ctx& c, const double2* q, double2* p, hz_info* info, cudaStream_t u
   k_true_residual<<<grid_xy(g), dim3(BX, BY), 0, s>>>(g, invh2, c.diagA64, c.p, c.qhat, c.V, c.partials, st);
   HZ_LAUNCHED();
   c.launches += 2;
-  int before = 0;
-  bool replayed = false;
-  for (;;) {
-    HZ_CUDA(cudaMemcpyAsync(hs, &st->st, sizeof(KrylovStatus), cudaMemcpyDeviceToHost, s));
-    HZ_CUDA(cudaStreamSynchronize(s));
-    if (replayed && c.prof_class) prof_collect(c, hs->iters - before);
-    if (hs->done) break;
-    before = hs->iters;
-    HZ_CUDA(cudaGraphLaunch(c.cycle_graph, s));
-    replayed = true;
-    c.launches += c.graph_kernels;
+  HZ_CUDA(cudaMemcpyAsync(hs, &st->st, sizeof(KrylovStatus), cudaMemcpyDeviceToHost, s));
+  HZ_CUDA(cudaEventRecord(c.ev_status, s));
+  c.as_before = 0;
+  c.as_replayed = false;
+  c.as_state = 1;
+}
+
+}  // namespace
+
+int solve_step(Ctx& c, bool block) {
+  if (c.as_state != 1) return 1;
+  if (block) {
+    HZ_CUDA(cudaEventSynchronize(c.ev_status));
+  } else {
+    const cudaError_t e = cudaEventQuery(c.ev_status);
+    if (e == cudaErrorNotReady) return 0;
+    HZ_CUDA(e);
   }
+  KrylovStatus* hs = (KrylovStatus*)c.ks_host;
+  if (c.as_replayed && c.prof_class) prof_collect(c, hs->iters - c.as_before, nullptr, 1);
+  if (hs->done) {
+    c.as_state = 2;
+    return 1;
+  }
+  c.as_before = hs->iters;
+  cudaStream_t s = c.graph_stream;
+  HZ_CUDA(cudaGraphLaunch(c.cycle_graph, s));
+  c.as_replayed = true;
+  c.launches += c.graph_kernels;
+  HZ_CUDA(cudaMemcpyAsync(hs, &c.ks->st, sizeof(KrylovStatus), cudaMemcpyDeviceToHost, s));
+  HZ_CUDA(cudaEventRecord(c.ev_status, s));
+  return 0;
+}
+
+void solve_begin(Ctx& c, const double2* q, cudaStream_t user) {
+  require(c.as_state != 1, "an asynchronous solve is already in flight on this context");
+  if (c.mixed) solve_begin_t<float2>(c, q, user);
+  else solve_begin_t<double2>(c, q, user);
+}
+
+void solve_end(Ctx& c, double2* p, hz_info* info, cudaStream_t user) {
+  require(c.as_state == 2, "the solve has not finished");
+  const int N = (int)c.L[0].g.N;
+  cudaStream_t s = c.graph_stream;
   if (p != c.p) HZ_CUDA(cudaMemcpyAsync(p, c.p, sizeof(double2) * N, cudaMemcpyDeviceToDevice, s));
   HZ_CUDA(cudaEventRecord(c.ev_out, s));
   HZ_CUDA(cudaStreamWaitEvent(user, c.ev_out, 0));
+  const KrylovStatus* hs = (const KrylovStatus*)c.ks_host;
   info->iters = hs->iters;
   info->converged = hs->converged;
   info->relres_est = hs->relres_est;
   info->relres_true = hs->relres_true;
+  c.as_state = 0;
 }
 
+namespace {
+
 }  // namespace
+
+// ---- measurement hooks: events around the launches of the selected class
+// (1 = Gram-Schmidt update passes k_mgs_step, 2 = first pass k_mgs_first with
+// the FP64 operator, 3 = whole V-cycle preconditioner application)
+int prof_begin(Ctx& c, int cls, int j, double bytes, double flops, cudaStream_t s) {
+  if (c.prof_class != cls) return -1;
+  const int k = (int)c.prof_j.size();
+  if ((int)c.prof_ev.size() < 2 * (k + 1)) {
+    cudaEvent_t a, b;
+    HZ_CUDA(cudaEventCreate(&a));
+    HZ_CUDA(cudaEventCreate(&b));
+    c.prof_ev.push_back(a);
+    c.prof_ev.push_back(b);
+  }
+  c.prof_j.push_back(j);
+  c.prof_b.push_back(bytes);
+  c.prof_f.push_back(flops);
+  HZ_CUDA(cudaEventRecordWithFlags(c.prof_ev[2 * k], s, cudaEventRecordExternal));
+  return k;
+}
+void prof_end(Ctx& c, int k, cudaStream_t s) {
+  if (k >= 0) HZ_CUDA(cudaEventRecordWithFlags(c.prof_ev[2 * k + 1], s, cudaEventRecordExternal));
+}
+// After a replayed cycle in which `ran` inner iterations did work.  Batched
+// (ran_r: the inner iterations each of the R right-hand sides did): a bracketed
+// launch of inner iteration j counts the bytes / flops of the right-hand sides
+// still active there (prof_b / prof_f hold the all-active figures).
+void prof_collect(Ctx& c, int ran, const int* ran_r, int R) {
+  for (size_t k = 0; k < c.prof_j.size(); ++k) {
+    if (c.prof_j[k] >= ran) continue;
+    double frac = 1.0;
+    if (ran_r) {
+      int act = 0;
+      for (int r = 0; r < R; ++r) act += ran_r[r] > c.prof_j[k];
+      frac = (double)act / R;
+    }
+    float ms = 0.f;
+    HZ_CUDA(cudaEventElapsedTime(&ms, c.prof_ev[2 * k], c.prof_ev[2 * k + 1]));
+    c.prof_ms += ms;
+    c.prof_bytes += frac * c.prof_b[k];
+    c.prof_flops += frac * c.prof_f[k];
+    c.prof_launches += 1;
+  }
+}
+
+// Algorithmic (compulsory) bytes of one V-cycle with the kernels of
+// cycle_impl.cuh.  Single right-hand side: the fused 2D kernels' reads and
+// writes.  R > 1 right-hand sides: per level the field traffic of V(1,1)
+// (pre-smooth f -> u, residual, restriction, prolongation-add, residual,
+// post-smooth: 14 + 2 rc field passes, rc the coarse/fine node ratio) times R,
+// plus the stencil planes of A and M read twice each, shared by all R.
+double vcycle_bytes(const Ctx& c) {
+  const double b = c.mixed ? 8.0 : 16.0;
+  const double R = c.nrhs;
+  double tot = 0;
+  for (size_t l = 0; l < c.L.size(); ++l) {
+    const Level& L = c.L[l];
+    const double N = (double)L.g.N;
+    if (L.coarsest) {
+      tot += N * N * b + 2 * N * b * R;
+      continue;
+    }
+    if (c.nrhs > 1) {
+      const double sA = L.fine ? 1.0 : L.A.off.n, sM = L.m_diag ? 1.0 : L.M.off.n;
+      const double rc = L.g.dim == 3 ? 0.125 : 0.25;
+      tot += N * b * R * (14 + 2 * rc) + N * b * 2 * (sA + sM);
+      continue;
+    }
+    const double sA = L.fine ? 1.0 : L.A.off.n, sM = L.M.off.n;
+    const double rc = L.g.dim == 3 ? 0.125 : 0.25;
+    if (L.m_diag) tot += N * b * (5 + (1 + rc) + (5 + rc)) + (sA - 1) * 2 * N * b;   // sweep0+resid, restrict, prolong+sweep
+    else tot += N * b * (2 * sM + 2 * sA + 13 + 2 * rc);
+  }
+  return tot;
+}
 
 size_t krylov_bytes(const hz_grid& g, const hz_opts& o) {
   long long N = (long long)g.n[0] * g.n[1] * (g.dim == 3 ? g.n[2] : 1);
@@ -453,19 +519,24 @@ void krylov_alloc(Ctx& c) {
   HZ_CUDA(cudaStreamCreateWithFlags(&c.graph_stream, cudaStreamNonBlocking));
   HZ_CUDA(cudaEventCreateWithFlags(&c.ev_in, cudaEventDisableTiming));
   HZ_CUDA(cudaEventCreateWithFlags(&c.ev_out, cudaEventDisableTiming));
+  HZ_CUDA(cudaEventCreateWithFlags(&c.ev_status, cudaEventDisableTiming));
 }
 
 void profile_select(Ctx& c, int cls) {
   if (c.cycle_graph) cudaGraphExecDestroy(c.cycle_graph);
   c.cycle_graph = nullptr;
+  if (c.batch_graph) cudaGraphExecDestroy(c.batch_graph);
+  c.batch_graph = nullptr;
   c.prof_class = cls;
   c.prof_ms = c.prof_bytes = c.prof_flops = 0;
   c.prof_launches = 0;
 }
 
 void fgmres_solve(Ctx& c, const double2* q, double2* p, hz_info* info, cudaStream_t s) {
-  if (c.mixed) solve_t<float2>(c, q, p, info, s);
-  else solve_t<double2>(c, q, p, info, s);
+  solve_begin(c, q, s);
+  while (!solve_step(c, true)) {
+  }
+  solve_end(c, p, info, s);
 }
 
 void precond_apply_c128(Ctx& c, const double2* r, double2* z, int nrhs, cudaStream_t s) {

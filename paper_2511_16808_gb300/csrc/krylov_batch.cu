@@ -13,6 +13,9 @@
 // the iteration kernels; one restart cycle is one captured CUDA graph.
 #include "krylov_impl.cuh"
 
+#include <algorithm>
+#include <vector>
+
 namespace hz {
 
 namespace {
@@ -72,19 +75,32 @@ __device__ __forceinline__ double2 apply_A_b(const GeoB& g, double invh2, const 
 __device__ __forceinline__ int block_lin() { return (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x; }
 
 // Per-RHS block partials: thread t holds (acc, r); partials[r*nb + block] =
-// sum over the block's threads with that r, in thread order (zero if none).
+// the sum over the block's threads with that r (zero if none), in a fixed
+// order.  Within a warp the lanes of one RHS are those congruent mod R (every
+// layout here puts r = (32*k + lane) mod R), so a shuffle tree over offsets
+// 16..R leaves lane l < min(R, 32) holding its RHS's warp sum; thread t < R
+// then adds the 8 warps' sums for RHS t.
 __device__ __forceinline__ void block_store_r(double2 acc, int r, int R, double2* __restrict__ partials, int nb,
                                               int block) {
-  __shared__ double2 sv[kB];
-  __shared__ int sr[kB];
+  __shared__ double2 sv[kB / 32][32];
+  __shared__ int sr0[kB / 32];
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-  sv[tid] = acc;
-  sr[tid] = r;
+  const int lane = tid & 31, warp = tid >> 5;
+  for (int off = 16; off >= R; off >>= 1) {
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+  }
+  const int W = R < 32 ? R : 32;
+  if (lane < W) sv[warp][lane] = acc;
+  if (lane == 0) sr0[warp] = r;
   __syncthreads();
   if (tid < R) {
     double2 s = make_double2(0, 0);
-    for (int t = 0; t < kB; ++t)
-      if (sr[t] == tid) s = s + sv[t];
+#pragma unroll
+    for (int w = 0; w < kB / 32; ++w) {
+      const int l = (tid - sr0[w]) & (R - 1);
+      if (l < W) s = s + sv[w][l];
+    }
     partials[tid * nb + block] = s;
   }
 }
@@ -312,17 +328,29 @@ void run_cycle_b(Ctx& c, const GeoB& g, cudaStream_t s) {
   const int n2 = nb2(g), n1 = (int)grid1(g);
   const double tol = c.opts.tol;
   const int mi = c.opts.max_iter;
+  const double NR = g.NR;
   for (int j = 0; j < m; ++j) {
     k_cast_in_b<TZ><<<nblk(g.NR, 256), 256, 0, s>>>(g, c.V + (long long)j * g.NR, st, j, (TZ*)L0.f, na);
+    int pk = prof_begin(c, 3, j, vcycle_bytes(c), 0.0, s);
     vcycle(c, L0.f, Z + (long long)j * g.NR, na, s);
+    prof_end(c, pk, s);
+    // z (sizeof TZ), v_0 read, w written; diag once; 24 flops (A z: 16, dot: 8)
+    pk = prof_begin(c, 2, j, NR * (sizeof(TZ) + 32) + 16.0 * g.N, 24.0 * NR, s);
     k_mgs_first_b<TZ><<<grid2(g), dim3(BX, BY), 0, s>>>(g, invh2, c.diagA64, Z + (long long)j * g.NR, c.V, j,
                                                          c.partials, st, na);
+    prof_end(c, pk, s);
     k_reduce_b<<<R, kB, 0, s>>>(c.partials, n2, kH1, 0, st, na, tol, mi, m);
     for (int i = 1; i <= j; ++i) {
+      // w, v_{i-1}, v_i read, w written; 8 flops update + 8 flops dot
+      pk = prof_begin(c, 1, j, 64.0 * NR, 16.0 * NR, s);
       k_mgs_step_b<false><<<n1, kB, 0, s>>>(g, c.V, j, i, c.partials, st, na);
+      prof_end(c, pk, s);
       k_reduce_b<<<R, kB, 0, s>>>(c.partials, n1, kH1, i, st, na, tol, mi, m);
     }
+    // w, v_j read, w written; 8 flops update + 4 flops norm
+    pk = prof_begin(c, 1, j, 48.0 * NR, 12.0 * NR, s);
     k_mgs_step_b<true><<<n1, kB, 0, s>>>(g, c.V, j, j + 1, c.partials, st, na);
+    prof_end(c, pk, s);
     k_reduce_b<<<R, kB, 0, s>>>(c.partials, n1, kArnoldi, j, st, na, tol, mi, m);
   }
   HZ_LAUNCHED();
@@ -338,6 +366,14 @@ void ensure_graph_b(Ctx& c, const GeoB& g) {
   if (c.batch_graph && c.batch_graph_nrhs == g.R) return;
   if (c.batch_graph) cudaGraphExecDestroy(c.batch_graph);
   c.batch_graph = nullptr;
+  // the two captured cycles share the event list: one profiled graph at a time
+  if (c.prof_class && c.cycle_graph) {
+    cudaGraphExecDestroy(c.cycle_graph);
+    c.cycle_graph = nullptr;
+  }
+  c.prof_j.clear();
+  c.prof_b.clear();
+  c.prof_f.clear();
   cudaGraph_t graph = nullptr;
   HZ_CUDA(cudaStreamBeginCapture(c.graph_stream, cudaStreamCaptureModeThreadLocal));
   try {
@@ -386,14 +422,28 @@ void solve_b(Ctx& c, const double2* q, double2* p, int R, hz_info* info, cudaStr
   HZ_LAUNCHED();
   c.launches += 4;
   KrylovStatus* hs = (KrylovStatus*)c.ks_host;
+  std::vector<int> before(R, 0), ran(R, 0);
+  bool replayed = false;
   for (;;) {
     HZ_CUDA(cudaMemcpy2DAsync(hs, sizeof(KrylovStatus), st, sizeof(KrylovState), sizeof(KrylovStatus), R,
                               cudaMemcpyDeviceToHost, s));
     HZ_CUDA(cudaStreamSynchronize(s));
+    if (replayed && c.prof_class) {
+      int mx = 0;
+      for (int r = 0; r < R; ++r) {
+        ran[r] = hs[r].iters - before[r];
+        mx = std::max(mx, ran[r]);
+      }
+      prof_collect(c, mx, ran.data(), R);
+    }
     bool all = true;
-    for (int r = 0; r < R; ++r) all = all && hs[r].done;
+    for (int r = 0; r < R; ++r) {
+      all = all && hs[r].done;
+      before[r] = hs[r].iters;
+    }
     if (all) break;
     HZ_CUDA(cudaGraphLaunch(c.batch_graph, s));
+    replayed = true;
     c.launches += c.batch_graph_kernels;
   }
   if (p != c.p) HZ_CUDA(cudaMemcpyAsync(p, c.p, sizeof(double2) * g.NR, cudaMemcpyDeviceToDevice, s));

@@ -188,4 +188,12 @@ __device__ inline void restart_update(KrylovState* st, int* n_active = nullptr) 
   if (n_active) atomicAdd(n_active, 1);
 }
 
+// Measurement hooks (krylov.cu): CUDA events around the launches of the
+// selected class (1 = Gram-Schmidt update passes, 2 = first pass with the FP64
+// operator, 3 = whole V-cycle), recorded inside the captured restart cycle.
+int prof_begin(Ctx& c, int cls, int j, double bytes, double flops, cudaStream_t s);
+void prof_end(Ctx& c, int k, cudaStream_t s);
+void prof_collect(Ctx& c, int ran, const int* ran_r, int R);
+double vcycle_bytes(const Ctx& c);
+
 }  // namespace hz

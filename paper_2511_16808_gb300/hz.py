@@ -58,6 +58,31 @@ class hz_level_desc(C.Structure):
                 ("damping", C.c_double), ("is_coarsest", C.c_int)]
 
 
+class hz_server_opts(C.Structure):
+    _fields_ = [("hbm_budget", C.c_size_t), ("max_active", C.c_int), ("device", C.c_int)]
+
+
+class hz_request(C.Structure):
+    _fields_ = [("grid", hz_grid), ("kappa", C.c_void_p), ("gamma", C.c_void_p), ("gamma0", C.c_double),
+                ("omega", C.c_double), ("shift_alpha", C.c_double), ("opts", hz_opts),
+                ("q", C.c_void_p), ("p", C.c_void_p)]
+
+
+REQ_STATE = {0: "queued", 1: "setup", 2: "solving", 3: "done", 4: "failed"}
+
+
+class hz_ticket_info(C.Structure):
+    _fields_ = [("state", C.c_int), ("status", C.c_int), ("info", hz_info), ("t_submit", C.c_double),
+                ("t_admit", C.c_double), ("t_start", C.c_double), ("t_done", C.c_double),
+                ("bytes", C.c_size_t), ("message", C.c_char * 128)]
+
+
+class hz_server_counters(C.Structure):
+    _fields_ = [("queued", C.c_int), ("setting_up", C.c_int), ("solving", C.c_int), ("done", C.c_int),
+                ("failed", C.c_int), ("bytes_in_use", C.c_size_t), ("peak_bytes", C.c_size_t),
+                ("budget", C.c_size_t), ("max_active", C.c_int), ("elapsed_s", C.c_double)]
+
+
 class HzError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
@@ -92,6 +117,22 @@ _SIGS = {
     "hz_level_restrict": ([_P, C.c_int, _P, _P, _P], C.c_int),
     "hz_level_prolong_add": ([_P, C.c_int, _P, _P, _P], C.c_int),
     "hz_coarse_solve": ([_P, _P, _P, _P], C.c_int),
+    "hz_solve_begin": ([_P, _P, _P], C.c_int),
+    "hz_solve_step": ([_P, C.c_int, C.POINTER(C.c_int)], C.c_int),
+    "hz_solve_end": ([_P, _P, C.POINTER(hz_info), _P], C.c_int),
+    "hz_server_create": ([C.POINTER(hz_server_opts), C.POINTER(_P)], C.c_int),
+    "hz_server_submit": ([_P, C.POINTER(hz_request), C.POINTER(C.c_uint64)], C.c_int),
+    "hz_server_poll": ([_P, C.c_uint64, C.POINTER(hz_ticket_info)], C.c_int),
+    "hz_server_wait": ([_P, C.c_uint64, C.c_double, C.POINTER(hz_ticket_info)], C.c_int),
+    "hz_server_stats": ([_P, C.POINTER(hz_server_counters)], C.c_int),
+    "hz_server_destroy": ([_P], C.c_int),
+    "hz_sched_create": ([C.c_size_t, C.c_int, C.POINTER(_P)], C.c_int),
+    "hz_sched_offer": ([_P, C.c_uint64, C.c_size_t, C.POINTER(C.c_int)], C.c_int),
+    "hz_sched_next": ([_P, C.POINTER(C.c_uint64), C.POINTER(C.c_int)], C.c_int),
+    "hz_sched_release": ([_P, C.c_size_t], C.c_int),
+    "hz_sched_state": ([_P, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t), C.POINTER(C.c_int),
+                        C.POINTER(C.c_int)], C.c_int),
+    "hz_sched_destroy": ([_P], C.c_int),
 }
 for _name, (_args, _res) in _SIGS.items():
     _f = getattr(lib, _name)
@@ -200,6 +241,25 @@ def hz_solve(ctx, q, p, nrhs: int = 1, stream=None):
     return st == HZ_OK, list(infos)
 
 
+def hz_solve_begin(ctx, q, stream=None) -> None:
+    _check(lib.hz_solve_begin(ctx, _ptr(q), _stream(stream)), "hz_solve_begin")
+
+
+def hz_solve_step(ctx, block: bool = False) -> bool:
+    """True once the asynchronous solve has finished."""
+    done = C.c_int()
+    _check(lib.hz_solve_step(ctx, int(bool(block)), C.byref(done)), "hz_solve_step")
+    return bool(done.value)
+
+
+def hz_solve_end(ctx, p, stream=None):
+    """Returns (converged: bool, hz_info)."""
+    info = hz_info()
+    st = lib.hz_solve_end(ctx, _ptr(p), C.byref(info), _stream(stream))
+    _check(st, "hz_solve_end", ok=(HZ_OK, HZ_ERR_NOT_CONVERGED))
+    return st == HZ_OK, info
+
+
 def hz_precond_apply(ctx, r, z, nrhs: int = 1, stream=None) -> None:
     _check(lib.hz_precond_apply(ctx, _ptr(r), _ptr(z), nrhs, _stream(stream)), "hz_precond_apply")
 
@@ -280,3 +340,73 @@ def hz_level_prolong_add(ctx, level, ec, u, stream=None):
 
 def hz_coarse_solve(ctx, f, u, stream=None):
     _check(lib.hz_coarse_solve(ctx, _ptr(f), _ptr(u), _stream(stream)), "hz_coarse_solve")
+
+
+# ------------------------------------------------------------------ serving
+
+def hz_server_create(hbm_budget: int = 0, max_active: int = 0, device: int = -1):
+    o = hz_server_opts(int(hbm_budget), int(max_active), int(device))
+    out = C.c_void_p()
+    _check(lib.hz_server_create(C.byref(o), C.byref(out)), "hz_server_create")
+    return out.value
+
+
+def hz_server_submit(srv, req: hz_request) -> int:
+    t = C.c_uint64()
+    _check(lib.hz_server_submit(srv, C.byref(req), C.byref(t)), "hz_server_submit")
+    return t.value
+
+
+def hz_server_poll(srv, ticket: int) -> hz_ticket_info:
+    out = hz_ticket_info()
+    _check(lib.hz_server_poll(srv, ticket, C.byref(out)), "hz_server_poll")
+    return out
+
+
+def hz_server_wait(srv, ticket: int, timeout_s: float = -1.0) -> hz_ticket_info:
+    out = hz_ticket_info()
+    _check(lib.hz_server_wait(srv, ticket, float(timeout_s), C.byref(out)), "hz_server_wait")
+    return out
+
+
+def hz_server_stats(srv) -> dict:
+    c = hz_server_counters()
+    _check(lib.hz_server_stats(srv, C.byref(c)), "hz_server_stats")
+    return {k: getattr(c, k) for k, _ in hz_server_counters._fields_}
+
+
+def hz_server_destroy(srv) -> None:
+    _check(lib.hz_server_destroy(srv), "hz_server_destroy")
+
+
+def hz_sched_create(budget: int, max_active: int):
+    out = C.c_void_p()
+    _check(lib.hz_sched_create(int(budget), int(max_active), C.byref(out)), "hz_sched_create")
+    return out.value
+
+
+def hz_sched_offer(s, ticket: int, nbytes: int) -> bool:
+    ok = C.c_int()
+    _check(lib.hz_sched_offer(s, ticket, int(nbytes), C.byref(ok)), "hz_sched_offer")
+    return bool(ok.value)
+
+
+def hz_sched_next(s):
+    """The admitted ticket, or None when the head of the queue does not fit."""
+    t, ok = C.c_uint64(), C.c_int()
+    _check(lib.hz_sched_next(s, C.byref(t), C.byref(ok)), "hz_sched_next")
+    return t.value if ok.value else None
+
+
+def hz_sched_release(s, nbytes: int) -> None:
+    _check(lib.hz_sched_release(s, int(nbytes)), "hz_sched_release")
+
+
+def hz_sched_state(s) -> dict:
+    iu, pk, act, q = C.c_size_t(), C.c_size_t(), C.c_int(), C.c_int()
+    _check(lib.hz_sched_state(s, C.byref(iu), C.byref(pk), C.byref(act), C.byref(q)), "hz_sched_state")
+    return {"in_use": iu.value, "peak": pk.value, "active": act.value, "queued": q.value}
+
+
+def hz_sched_destroy(s) -> None:
+    _check(lib.hz_sched_destroy(s), "hz_sched_destroy")

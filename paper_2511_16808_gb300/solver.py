@@ -26,20 +26,9 @@ class HelmholtzSolver:
         self.nodes = int(np.prod(n[:dim]))
         self.h = 1.0 / (n[0] - 1)
         self.grid = hz.make_grid(dim, n, self.h)
-        o = hz.hz_opts_default(dim)
-        o.levels = levels
-        for l in range(hz.MAX_LEVELS):
-            p = patch if l == 0 else (patch_coarse or patch)
-            o.patch[l] = hz.PATCH[p]
-            o.damping[l] = damping[l] if damping is not None and l < len(damping) \
-                else hz.hz_default_damping(dim, p, l)
-        o.nu1, o.nu2 = nu1, nu2
-        o.intergrid = hz.INTERGRID[intergrid]
-        o.precision = hz.PRECISION[precision]
-        o.restart_m = restart
-        o.tol = tol
-        o.max_iter = max_iter
-        o.nrhs_max = nrhs_max
+        o = make_opts(dim, levels, patch=patch, intergrid=intergrid, precision=precision, tol=tol,
+                      restart=restart, nu1=nu1, nu2=nu2, max_iter=max_iter, patch_coarse=patch_coarse,
+                      damping=damping, nrhs_max=nrhs_max)
         self.opts = o
         self.mixed = precision == "mixed"
         self.stream = stream
@@ -86,6 +75,27 @@ class HelmholtzSolver:
             self.close()
         except Exception:  # noqa: BLE001
             pass
+
+
+def make_opts(dim, levels, patch="rb", intergrid="leveldep", precision="mixed", tol=1e-6, restart=5, nu1=1,
+              nu2=1, max_iter=2000, patch_coarse=None, damping=None, nrhs_max=1) -> hz.hz_opts:
+    """hz_opts from solver settings; damping defaults to the paper's table per
+    level and patch."""
+    o = hz.hz_opts_default(dim)
+    o.levels = levels
+    for l in range(hz.MAX_LEVELS):
+        p = patch if l == 0 else (patch_coarse or patch)
+        o.patch[l] = hz.PATCH[p]
+        o.damping[l] = damping[l] if damping is not None and l < len(damping) \
+            else hz.hz_default_damping(dim, p, l)
+    o.nu1, o.nu2 = nu1, nu2
+    o.intergrid = hz.INTERGRID[intergrid]
+    o.precision = hz.PRECISION[precision]
+    o.restart_m = restart
+    o.tol = tol
+    o.max_iter = max_iter
+    o.nrhs_max = nrhs_max
+    return o
 
 
 def _as_f64(a):

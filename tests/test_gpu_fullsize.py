@@ -54,3 +54,41 @@ def test_full_size_solve_matches_oracle(name, precision, bound):
     ref = np.array(g["p_ref_re"]) + 1j * np.array(g["p_ref_im"])
     err = np.linalg.norm(p[idx] - ref) / np.linalg.norm(ref)
     assert err < max(bound, 2 * g["err_at_tol"]), (err, g["err_at_tol"])
+
+
+@pytest.mark.parametrize("fi", [0, 1, 2])
+def test_config4_batched_sources_match_oracle(fi):
+    """The batched multi-source workload at full size: all 64 sources of one
+    frequency in one batched solve (RHS innermost).  Every source converges
+    with the host FP64 residual below tol; for the sources the oracle solved
+    (tests/golden/oracle_config4.json) the iteration count is within +-1 and
+    the sampled error within max(1e-5, 2x the oracle's own error at tol)."""
+    import workloads
+    from oracle import operator
+    from paper_2511_16808_gb300.solver import HelmholtzSolver
+    g = _gold("config4")
+    w = workloads.config4()[fi]
+    fr = g["freqs"][fi]
+    assert abs(fr["omega"] - w.omega) < 1e-12 * w.omega
+    R = len(w.sources)
+    s = HelmholtzSolver(w.dim, [w.n] * w.dim, w.kappa.ravel(), w.omega, w.gamma.ravel(), w.alpha, w.levels,
+                        patch=w.patch, intergrid=w.intergrid, precision="mixed", tol=w.tol,
+                        restart=w.restart, max_iter=w.max_iter, nrhs_max=R)
+    Q = w.rhs_block()
+    P, infos = s.solve_batch(torch.tensor(Q, device="cuda"))
+    P = P.cpu().numpy()
+    s.close()
+    assert all(i.converged == 1 for i in infos)
+    A = operator.helmholtz(w.shape, w.h, w.kappa, w.omega, w.gamma)
+    wq = operator.mass_diagonal(w.shape)
+    QH = Q * wq[:, None]
+    relres = np.linalg.norm(QH - A @ P, axis=0) / np.linalg.norm(QH, axis=0)
+    assert np.all(relres < w.tol), relres.max()
+    idx = np.array(g["sample_idx"])
+    for rec in fr["sources"]:
+        k = rec["source"]
+        assert tuple(rec["node"]) == tuple(w.sources[k])
+        assert abs(infos[k].iters - rec["iters"]) <= 1, (k, infos[k].iters, rec["iters"])
+        ref = np.array(rec["p_ref_re"]) + 1j * np.array(rec["p_ref_im"])
+        err = np.linalg.norm(P[idx, k] - ref) / np.linalg.norm(ref)
+        assert err < max(1e-5, 2 * rec["err_at_tol"]), (k, err, rec["err_at_tol"])

@@ -15,4 +15,6 @@ from .media import (  # noqa: F401
     point_source,
     random_interior_nodes,
 )
-from .configs import Workload, config1, config2, config3, config4, small_variant  # noqa: F401
+from .configs import (  # noqa: F401
+    SERVE_LEVELS, ServeRequest, Workload, config1, config2, config3, config4, config5, small_variant,
+)

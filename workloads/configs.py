@@ -10,6 +10,8 @@ own copy of the paper's damping table.
   config2  2D layered 1025^2 (seed 0), 20-cell absorbing layer, tol 1e-6
   config3  3D geophysical 257^3 (seed 0), 16-cell layer, surface source
   config4  2D homogeneous 513^2, 64 seeded sources x 3 frequencies (seed 1)
+  config5  serving stream: Poisson arrivals of mixed 2D / 3D requests, each its
+           own seeded medium (seed 1000 + request id), frequency and source
 """
 from __future__ import annotations
 
@@ -127,6 +129,71 @@ def config4(n: int = 513, levels: int = 5, nsrc: int = 64, seed: int = 1,
                      patch="plus", intergrid="leveldep", tol=1e-6, precision="mixed",
                      meta={"seed": seed, "ppw": ppw})
         out.append(replace(w, **kw))
+    return out
+
+
+# Levels per grid side: coarsest side <= 33 (2D) or <= 17 (3D) nodes.
+SERVE_LEVELS = {2: {257: 4, 513: 5, 1025: 6, 2049: 7}, 3: {65: 3, 129: 4, 193: 5}}
+
+
+@dataclass
+class ServeRequest:
+    """One request of the serving stream; `workload()` builds its problem."""
+    rid: int
+    arrival_s: float
+    dim: int
+    n: int
+    generator: str              # 'homogeneous' (config 1's) | 'layered' (config 2's; 3D: config 3's)
+    ppw: float
+    seed: int
+    src_u: tuple                # source position as fractions of the interior, in [0, 1)
+
+    def workload(self) -> Workload:
+        n, dim = self.n, self.dim
+        levels = SERVE_LEVELS[dim][n]
+        layer = max(4, (20 * (n - 1)) // 1024) if dim == 2 else max(3, (16 * (n - 1)) // 256)
+        if self.generator == "homogeneous" and dim == 2:
+            w = config1(n=n, levels=levels, tol=1e-6, precision="mixed")
+            v_min = 1.0
+        elif dim == 2:
+            w = config2(n=n, levels=levels, seed=self.seed, layer_cells=layer)
+            v_min = 1.5
+        elif self.generator == "homogeneous":
+            w = config3(n=n, levels=levels, seed=self.seed, layer_cells=layer)
+            w = replace(w, kappa=media.homogeneous_kappa(n, 3, 1.0))
+            v_min = 1.0
+        else:
+            w = config3(n=n, levels=levels, seed=self.seed, layer_cells=layer)
+            v_min = 1.5
+        omega = media.omega_for_ppw(self.ppw, w.h, v_min=v_min)
+        lay = layer if (self.generator == "layered" or dim == 3) else 0
+        gamma = media.absorbing_gamma(w.kappa.shape, omega, 0.01, lay)
+        lo, hi = lay + 1, n - 2 - lay
+        src = tuple(int(lo + u * (hi - lo + 1)) for u in self.src_u)
+        return replace(w, name=f"serve-{self.rid}-{dim}d-{n}-{self.generator}-ppw{self.ppw:.2f}",
+                       omega=omega, gamma=gamma, sources=[src], layer_cells=lay, tol=1e-6,
+                       precision="mixed", meta={"seed": self.seed, "ppw": self.ppw, "rid": self.rid})
+
+
+def config5(n_requests: int = 2000, rate: float = 40.0, seed: int = 5, sizes2d=(257, 513, 1025, 2049),
+            sizes3d=(65, 129, 193), p3d: float = 0.5) -> list:
+    """Serving stream: Poisson arrivals at `rate` per second; each request is
+    2D (side uniform over sizes2d) or 3D (side uniform over sizes3d) with
+    probability p3d, a homogeneous (config 1's generator) or layered (config
+    2's in 2D, config 3's in 3D) medium with seed 1000 + id, 8-12 points per
+    wavelength and a source uniform inside the absorbing layer."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for i in range(n_requests):
+        t += rng.exponential(1.0 / rate)
+        dim = 3 if rng.random() < p3d else 2
+        sizes = sizes3d if dim == 3 else sizes2d
+        n = int(sizes[rng.integers(len(sizes))])
+        gen = "layered" if rng.random() < 0.5 else "homogeneous"
+        ppw = float(rng.uniform(8.0, 12.0))
+        u = tuple(float(v) for v in rng.random(dim))
+        out.append(ServeRequest(i, t, dim, n, gen, ppw, 1000 + i, u))
     return out
 
 
