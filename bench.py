@@ -499,6 +499,125 @@ def run_batched(args):
     return out
 
 
+def _serve_problem(req):
+    """Media, source and settings of one serving request (run in a worker process)."""
+    w = req.workload()
+    return {"dim": w.dim, "n": w.n, "kappa": w.kappa.ravel(), "gamma": w.gamma.ravel(), "omega": w.omega,
+            "q": w.rhs(0), "alpha": w.alpha, "levels": w.levels,
+            "opts": dict(patch=w.patch, intergrid=w.intergrid, precision="mixed", tol=w.tol, restart=w.restart,
+                         max_iter=w.max_iter, patch_coarse=w.patch_coarse)}
+
+
+def run_serving(args):
+    """Serving stream: requests arrive (Poisson, 40/s) with their own medium,
+    size, frequency and source; the request server admits them under the HBM
+    budget and overlaps their solves.  One step = the whole stream, replayed
+    in real time; latency = completion - arrival."""
+    import multiprocessing as mp
+
+    import workloads
+    rank, world, local = _env_rank()
+    if rank != 0:
+        return None
+    reqs = workloads.config5(n_requests=args.requests, rate=args.rate)
+    # media are inputs: generate them before timing, in worker processes
+    # started with spawn before this process touches the GPU
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        probs = pool.map(_serve_problem, reqs, chunksize=1)
+    import numpy as np
+    import torch
+    from paper_2511_16808_gb300 import hz
+    from paper_2511_16808_gb300.serve import Server
+    from paper_2511_16808_gb300.solver import HelmholtzSolver
+    torch.cuda.set_device(local)
+
+    def submit(srv, pr, precision=None):
+        o = dict(pr["opts"])
+        if precision:
+            o["precision"] = precision
+        return srv.submit(pr["dim"], pr["n"], pr["kappa"], pr["omega"], pr["q"], gamma=pr["gamma"],
+                          alpha=pr["alpha"], levels=pr["levels"], **o)
+
+    # warm-up: a few small requests through a server (module load, graph code paths)
+    small = [pr for pr in probs if pr["n"] <= 257][:max(args.warmup, 1)]
+    with Server() as srv:
+        for t in [submit(srv, pr) for pr in small]:
+            srv.wait(t)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk, Server(max_active=args.max_active) as srv:
+        t0 = time.perf_counter()
+        tickets = []
+        for rq, pr in zip(reqs, probs):
+            dt = rq.arrival_s - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            tickets.append(submit(srv, pr))
+        res = [srv.wait(t) for t in tickets]
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+    infos = [d for _, d in res]
+    ok = [d for d in infos if d["state"] == "done" and d["status"] == "HZ_OK"]
+    lat = np.array([d["t_done"] - d["t_submit"] for d in ok])
+    qd = np.array([d["t_admit"] - d["t_submit"] for d in ok])
+    setup = np.array([d["t_start"] - d["t_admit"] for d in ok])
+    solve = np.array([d["t_done"] - d["t_start"] for d in ok])
+    span = max(d["t_done"] for d in infos) - min(d["t_submit"] for d in infos)
+    value = len(ok) / span
+
+    # one at a time on the same GPU (setup + solve, sequential), first K requests
+    def one_at_a_time(precision, k):
+        t = time.perf_counter()
+        its = []
+        for pr in probs[:k]:
+            o = dict(pr["opts"], precision=precision)
+            s = HelmholtzSolver(pr["dim"], [pr["n"]] * pr["dim"], pr["kappa"], pr["omega"], pr["gamma"],
+                                pr["alpha"], pr["levels"], **o)
+            p, info = s.solve(pr["q"], np.zeros_like(pr["q"]))
+            its.append(info.iters)
+            s.close()
+        torch.cuda.synchronize()
+        return {"value": k / (time.perf_counter() - t), "unit": UNIT, "requests": k,
+                "iters_mean": float(np.mean(its))}
+    k = min(args.one_at_a_time, len(probs))
+    seq_mixed = one_at_a_time("mixed", k)
+    seq_fp64 = one_at_a_time("fp64", k)
+    served_k = len([d for d in infos[:k] if d["state"] == "done"]) / max(
+        1e-9, max(d["t_done"] for d in infos[:k]) - min(d["t_submit"] for d in infos[:k]))
+    mix = {}
+    for rq in reqs:
+        key = f"{rq.dim}d-{rq.n}"
+        mix[key] = mix.get(key, 0) + 1
+    h2d = sum(pr["kappa"].nbytes + pr["gamma"].nbytes + pr["q"].nbytes for pr in probs)
+    d2h = sum(pr["q"].nbytes for pr in probs)
+    pct = lambda a, q: float(np.percentile(a, q)) if len(a) else None  # noqa: E731
+    return {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": len(small),
+        "ms_per_step": 1e3 * span, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "c64 V-cycle / c128 FGMRES", "data": "synthetic (seeded media per request)",
+        "config": {"workload": f"serving stream: {len(reqs)} requests, Poisson {args.rate:g}/s, "
+                               "2D sides 257-2049 / 3D sides 65-193, 8-12 points per wavelength",
+                   "requests": len(reqs), "rate_per_s": args.rate, "mix": mix, "max_active": st["max_active"],
+                   "hbm_budget_bytes": st["budget"], "tol": 1e-6,
+                   "l2": "each request's working set > 129 MB L2 except the smallest; no flush",
+                   "parallelism": "1 GPU, requests overlapped on streams"},
+        "served": len(ok), "failed": st["failed"],
+        "latency_s": {"p50": pct(lat, 50), "p99": pct(lat, 99), "mean": float(lat.mean()) if len(lat) else None},
+        "queue_delay_s": {"p50": pct(qd, 50), "p99": pct(qd, 99)},
+        "setup_s": {"p50": pct(setup, 50), "p99": pct(setup, 99)},
+        "solve_s": {"p50": pct(solve, 50), "p99": pct(solve, 99)},
+        "offered_span_s": reqs[-1].arrival_s, "wall_s": wall,
+        "peak_hbm_bytes": st["peak_bytes"],
+        "one_at_a_time_mixed": seq_mixed, "plain_fp64": seq_fp64,
+        "served_first_k": {"value": served_k, "unit": UNIT, "requests": k,
+                           "note": "first k requests of the stream, served (arrival to completion)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "note": "requests enter and leave through host buffers"},
+        "clocks": clk.summary(),
+        "roofline": None, "cpu_baseline": None,
+        "gpu_launches": st["kernel_launches"],
+    }
+
+
 def run_reference(args):
     rank, world, local = _env_rank()
     if rank != 0:
@@ -547,11 +666,17 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=25)
     ap.add_argument("--ref-iters-per-step", type=int, default=5)
+    ap.add_argument("--requests", type=int, default=100, help="config5: requests in the stream")
+    ap.add_argument("--rate", type=float, default=40.0, help="config5: Poisson arrival rate per second")
+    ap.add_argument("--max-active", type=int, default=32, help="config5: requests admitted at once")
+    ap.add_argument("--one-at-a-time", type=int, default=12, help="config5: requests timed one at a time")
     args = ap.parse_args()
     if args.impl == "reference":
         out = run_reference(args)
     elif args.config == "config4":
         out = run_batched(args)
+    elif args.config == "config5":
+        out = run_serving(args)
     else:
         out = run_ours(args)
     if out is not None:

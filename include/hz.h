@@ -212,6 +212,7 @@ typedef struct {
   size_t hbm_budget;   /* device bytes the admitted requests may hold; 0 = 80% of free memory */
   int max_active;      /* requests admitted at once (set up or solving); 0 = 32 */
   int device;          /* CUDA device ordinal; -1 = the calling thread's current device */
+  int setup_threads;   /* host threads building hierarchies concurrently (1..8); 0 = 2 */
 } hz_server_opts;
 
 typedef struct {
@@ -242,7 +243,8 @@ typedef struct {
   int queued, setting_up, solving, done, failed;
   size_t bytes_in_use, peak_bytes, budget;
   int max_active;
-  double elapsed_s;
+  double elapsed_s;          /* since hz_server_create */
+  int64_t kernel_launches;   /* kernels launched for the requests finished so far */
 } hz_server_counters;
 
 /* Starts the server's host threads on the device.  opts may be NULL. */

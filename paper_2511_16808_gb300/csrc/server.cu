@@ -5,10 +5,10 @@
 // A request carries a full problem (grid, medium, frequency, shift, solver
 // options, one source).  hz_server_submit copies it and queues it; three
 // host threads then run it through the C ABI:
-//   setup   admits queued requests in arrival order while the HBM budget and
-//           the slot count allow (Admission below), builds each hierarchy on
-//           the request's own stream (hz_setup) and starts its solve
-//           (hz_solve_begin);
+//   setup   (one or more threads) admits queued requests in arrival order
+//           while the HBM budget and the slot count allow (Admission below),
+//           builds each hierarchy on the request's own stream (hz_setup) and
+//           starts its solve (hz_solve_begin); several setups overlap;
 //   step    keeps every started solve going: each pass polls the status event
 //           of each request's last restart cycle and queues its next cycle (a
 //           captured graph) as soon as the previous one has finished, so the
@@ -19,6 +19,7 @@
 // Requests are independent: a request that fails (bad medium, out of memory,
 // no convergence) records its status and releases its slot; the others go on.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -104,7 +105,9 @@ struct hz_server {
   std::deque<Request*> retiring;           // finished or failed after admission (retire thread)
   int setting_up = 0;
   bool stop = false;
-  std::thread t_setup, t_step, t_retire;
+  std::atomic<int64_t> launches{0};        // kernels launched by finished requests
+  std::vector<std::thread> t_setup;
+  std::thread t_step, t_retire;
 
   double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
 };
@@ -227,6 +230,8 @@ void retire_loop(hz_server* S) {
       if (st != HZ_OK && st != HZ_ERR_NOT_CONVERGED) record(r, st);
       else r->status = st;
     }
+    int64_t nl = 0;
+    if (r->ctx && hz_kernel_launches(r->ctx, &nl) == HZ_OK) S->launches.fetch_add(nl);
     if (r->ctx) hz_destroy(r->ctx);
     r->ctx = nullptr;
     if (r->stream) cudaStreamDestroy(r->stream);
@@ -328,7 +333,8 @@ hz_status hz_server_create(const hz_server_opts* opts, hz_server** out) {
     HZ_CUDA(cudaMemGetInfo(&fr, &tot));
     S->adm.budget = (opts && opts->hbm_budget) ? opts->hbm_budget : (size_t)(0.8 * (double)fr);
     S->adm.max_active = (opts && opts->max_active > 0) ? opts->max_active : 32;
-    S->t_setup = std::thread(setup_loop, S);
+    const int nsetup = (opts && opts->setup_threads > 0) ? std::min(opts->setup_threads, 8) : 2;
+    for (int i = 0; i < nsetup; ++i) S->t_setup.emplace_back(setup_loop, S);
     S->t_step = std::thread(step_loop, S);
     S->t_retire = std::thread(retire_loop, S);
   });
@@ -419,6 +425,7 @@ hz_status hz_server_stats(hz_server* S, hz_server_counters* out) {
     out->budget = S->adm.budget;
     out->max_active = S->adm.max_active;
     out->elapsed_s = S->now();
+    out->kernel_launches = S->launches.load();
   });
 }
 
@@ -432,7 +439,8 @@ hz_status hz_server_destroy(hz_server* S) {
   S->cv_step.notify_all();
   S->cv_retire.notify_all();
   // the threads drain every submitted request before they leave
-  if (S->t_setup.joinable()) S->t_setup.join();
+  for (auto& t : S->t_setup)
+    if (t.joinable()) t.join();
   {
     std::lock_guard<std::mutex> lk(S->mu);
     S->cv_step.notify_all();

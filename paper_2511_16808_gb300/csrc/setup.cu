@@ -252,72 +252,123 @@ __host__ __device__ inline bool gj_invert(double2* H, int m, int ld, int* piv) {
   return true;
 }
 
+// Anchor test of a patch: element patches are anchored at cells (never
+// clipped), the others at nodes.
+__device__ __forceinline__ bool anchor_ok(const GridDev& g, const PatchDesc& pd, int ax, int ay, int az) {
+  if (pd.element)
+    return ax >= 0 && ax < g.nx - 1 && ay >= 0 && ay < g.ny - 1 &&
+           (g.dim == 2 ? az == 0 : (az >= 0 && az < g.nz - 1));
+  return in_grid(g, ax, ay, az);
+}
+
+// In-grid members of the patch anchored at (ax, ay, az): slot[m] = member
+// index, idx[m] = node; returns m.
 template <int NP>
-__global__ void k_vanka_assemble(GridDev g, StencilLut A, const double2* __restrict__ Ap, PatchDesc pd,
-                                 StencilLut Ml, double2* __restrict__ Mp, int* __restrict__ singular) {
-  long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= g.N) return;
+__device__ __forceinline__ int patch_members(const GridDev& g, const PatchDesc& pd, int ax, int ay, int az,
+                                             int (&slot)[NP], long long (&idx)[NP]) {
+  int m = 0;
+  for (int l = 0; l < pd.np; ++l) {
+    const int nx = ax + pd.d[l][0], ny = ay + pd.d[l][1], nz = az + pd.d[l][2];
+    if (!in_grid(g, nx, ny, nz)) continue;
+    slot[m] = l;
+    idx[m] = flat(g, nx, ny, nz);
+    ++m;
+  }
+  return m;
+}
+
+// Phase 1 of the Vanka sum (Section 3.2): the inverse of every patch matrix
+// H_i (the rows / columns of A_s on the patch's in-grid nodes), once per
+// patch.  Anchors are taken along the slow axis (z in 3D, y in 2D) from s0 to
+// s1; Hinv[(anchor - first anchor of s0) * NP*NP + a*m + b].
+template <int NP>
+__global__ void k_patch_inverse(GridDev g, StencilLut A, const double2* __restrict__ Ap, PatchDesc pd, int s0,
+                                int s1, double2* __restrict__ Hinv, int* __restrict__ singular) {
+  const long long per = g.dim == 3 ? (long long)g.nx * g.ny : g.nx;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= per * (s1 - s0)) return;
+  int ax, ay, az;
+  if (g.dim == 3) {
+    az = s0 + (int)(t / per);
+    const int r = (int)(t % per);
+    ay = r / g.nx;
+    ax = r % g.nx;
+  } else {
+    az = 0;
+    ay = s0 + (int)(t / per);
+    ax = (int)(t % per);
+  }
+  if (!anchor_ok(g, pd, ax, ay, az)) return;
+  int slot[NP], piv[NP];
+  long long idx[NP];
+  const int m = patch_members<NP>(g, pd, ax, ay, az, slot, idx);
+  double2 H[NP * NP];
+  for (int a = 0; a < m; ++a)
+    for (int b = 0; b < m; ++b) {
+      const int dx = pd.d[slot[b]][0] - pd.d[slot[a]][0];
+      const int dy = pd.d[slot[b]][1] - pd.d[slot[a]][1];
+      const int dz = pd.d[slot[b]][2] - pd.d[slot[a]][2];
+      const int e = A.lut[lut_index(dx, dy, dz)];
+      H[a * m + b] = e >= 0 ? Ap[(long long)e * g.N + idx[a]] : make_double2(0.0, 0.0);
+    }
+  if (!gj_invert(H, m, m, piv)) {
+    atomicAdd(singular, 1);
+    return;
+  }
+  double2* out = Hinv + t * (NP * NP);
+  for (int k = 0; k < m * m; ++k) out[k] = H[k];
+}
+
+// Phase 2: node j (slow-axis coordinate in [n0, n1)) adds, patch by patch in
+// the order of the patch offsets, its weighted row of each H_i^{-1} (weight
+// 1/count, count = patches containing j) to the planes of M at offsets
+// d_l - d_k.  The patches' anchors must lie in the slab [s0, s1) of Hinv.
+template <int NP>
+__global__ void k_vanka_gather(GridDev g, PatchDesc pd, StencilLut Ml, const double2* __restrict__ Hinv, int s0,
+                               int n0, int n1, double2* __restrict__ Mp) {
+  const long long per = g.dim == 3 ? (long long)g.nx * g.ny : g.nx;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= per * (n1 - n0)) return;
+  const long long j = (long long)n0 * per + t;
   int x, y, z;
   node_coords(g, j, x, y, z);
-  auto anchor_ok = [&](int ax, int ay, int az) {
-    if (pd.element) {
-      return ax >= 0 && ax < g.nx - 1 && ay >= 0 && ay < g.ny - 1 &&
-             (g.dim == 2 ? az == 0 : (az >= 0 && az < g.nz - 1));
-    }
-    return in_grid(g, ax, ay, az);
-  };
   int count = 0;
   for (int k = 0; k < pd.np; ++k)
-    if (anchor_ok(x - pd.d[k][0], y - pd.d[k][1], z - pd.d[k][2])) ++count;
+    if (anchor_ok(g, pd, x - pd.d[k][0], y - pd.d[k][1], z - pd.d[k][2])) ++count;
   if (count == 0) return;
   const double W = 1.0 / count;
-  double2 H[NP * NP];
-  int slot[NP], piv[NP];
+  int slot[NP];
   long long idx[NP];
   for (int k = 0; k < pd.np; ++k) {
     const int ax = x - pd.d[k][0], ay = y - pd.d[k][1], az = z - pd.d[k][2];
-    if (!anchor_ok(ax, ay, az)) continue;
-    int m = 0, kk = -1;
-    for (int l = 0; l < pd.np; ++l) {
-      const int nx = ax + pd.d[l][0], ny = ay + pd.d[l][1], nz = az + pd.d[l][2];
-      if (!in_grid(g, nx, ny, nz)) continue;
-      if (l == k) kk = m;
-      slot[m] = l;
-      idx[m] = flat(g, nx, ny, nz);
-      ++m;
-    }
-    for (int a = 0; a < m; ++a)
-      for (int b = 0; b < m; ++b) {
-        const int dx = pd.d[slot[b]][0] - pd.d[slot[a]][0];
-        const int dy = pd.d[slot[b]][1] - pd.d[slot[a]][1];
-        const int dz = pd.d[slot[b]][2] - pd.d[slot[a]][2];
-        const int e = A.lut[lut_index(dx, dy, dz)];
-        H[a * m + b] = e >= 0 ? Ap[(long long)e * g.N + idx[a]] : make_double2(0.0, 0.0);
-      }
-    if (!gj_invert(H, m, m, piv)) {
-      atomicAdd(singular, 1);
-      continue;
-    }
-    // row kk of H^{-1}, weighted by W_j, lands on node j at offset d_l - d_k
+    if (!anchor_ok(g, pd, ax, ay, az)) continue;
+    const int m = patch_members<NP>(g, pd, ax, ay, az, slot, idx);
+    int kk = 0;
+    while (slot[kk] != k) ++kk;
+    const int sa = g.dim == 3 ? az : ay;
+    const long long at = (long long)(sa - s0) * per + (g.dim == 3 ? (long long)ay * g.nx + ax : ax);
+    const double2* Hi = Hinv + at * (NP * NP);
     for (int b = 0; b < m; ++b) {
       const int l = slot[b];
-      const int e = Ml.lut[lut_index(pd.d[l][0] - pd.d[k][0], pd.d[l][1] - pd.d[k][1],
-                                     pd.d[l][2] - pd.d[k][2])];
+      const int e = Ml.lut[lut_index(pd.d[l][0] - pd.d[k][0], pd.d[l][1] - pd.d[k][1], pd.d[l][2] - pd.d[k][2])];
       double2* dst = Mp + (long long)e * g.N + j;
-      const double2 v = H[kk * m + b];
-      *dst = *dst + W * v;
+      *dst = *dst + W * Hi[kk * m + b];
     }
   }
 }
 
-// max over a plane of |v|^2, as the bit pattern of a non-negative double
-__global__ void k_plane_absmax(const double2* __restrict__ planes, long long N, int nplanes,
-                               unsigned long long* __restrict__ out) {
-  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= N * nplanes) return;
-  const int e = (int)(t / N);
-  const double v = cabs2(planes[t]);
-  if (v > 0.0) atomicMax(out + e, (unsigned long long)__double_as_longlong(v));
+// 1 in out[e] when plane e of `planes` has a non-zero entry (block-wide OR,
+// one atomic per block)
+__global__ void k_plane_nonzero(const double2* __restrict__ planes, long long N, unsigned long long* __restrict__ out) {
+  const int e = blockIdx.y;
+  const double2* pl = planes + (long long)e * N;
+  int nz = 0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    const double2 v = pl[i];
+    nz |= (v.x != 0.0 || v.y != 0.0);
+  }
+  nz = __syncthreads_or(nz);
+  if (nz && threadIdx.x == 0) atomicOr(out + e, 1ull);
 }
 
 // ------------------------------------------------------------------ casts
@@ -466,11 +517,36 @@ static void invert_dense(Ctx& c, Level& L, cudaStream_t s) {
   if (hsing) throw Error(HZ_ERR_INVALID_ARG, "coarsest-level operator is singular");
 }
 
+// Both phases over slabs of the slow axis, with at most kSlabBytes of patch
+// inverses alive at a time.
+constexpr size_t kSlabBytes = 256u << 20;
 template <int NP>
 static void launch_vanka(Level& L, const PatchDesc& pd, const StencilLut& Mfull, double2* Mp, int* sing,
                          cudaStream_t s) {
-  k_vanka_assemble<NP><<<nblk(L.g.N, 128), 128, 0, s>>>(L.g, L.A, L.A64, pd, Mfull, Mp, sing);
-  HZ_LAUNCHED();
+  const GridDev& g = L.g;
+  const int ns = g.dim == 3 ? g.nz : g.ny;                    // slow-axis extent
+  const long long per = g.dim == 3 ? (long long)g.nx * g.ny : g.nx;
+  const int ax = g.dim == 3 ? 2 : 1;
+  int dmin = 0, dmax = 0;                                      // patch extent along the slow axis
+  for (int k = 0; k < pd.np; ++k) {
+    dmin = std::min(dmin, (int)pd.d[k][ax]);
+    dmax = std::max(dmax, (int)pd.d[k][ax]);
+  }
+  const size_t per_plane = (size_t)per * NP * NP * sizeof(double2);
+  const int chunk = (int)std::max<size_t>(1, kSlabBytes / per_plane);     // node planes per slab
+  const int span = std::min(ns, chunk + dmax - dmin);
+  double2* Hinv = nullptr;
+  HZ_CUDA(cudaMallocAsync(&Hinv, per_plane * span, s));
+  for (int n0 = 0; n0 < ns; n0 += chunk) {
+    const int n1 = std::min(ns, n0 + chunk);
+    // anchors of the patches of nodes n0..n1-1: node - d
+    const int s0 = std::max(0, n0 - dmax), s1 = std::min(ns, n1 - dmin);
+    k_patch_inverse<NP><<<nblk(per * (s1 - s0), 128), 128, 0, s>>>(g, L.A, L.A64, pd, s0, s1, Hinv, sing);
+    HZ_LAUNCHED();
+    k_vanka_gather<NP><<<nblk(per * (n1 - n0), 128), 128, 0, s>>>(g, pd, Mfull, Hinv, s0, n0, n1, Mp);
+    HZ_LAUNCHED();
+  }
+  HZ_CUDA(cudaFreeAsync(Hinv, s));
 }
 
 static void assemble_smoother(Ctx& c, Level& L, cudaStream_t s) {
@@ -505,7 +581,7 @@ static void assemble_smoother(Ctx& c, Level& L, cudaStream_t s) {
     case 27: launch_vanka<27>(L, pd, Mfull, Mp, sing, s); break;
     default: throw Error(HZ_ERR_INVALID_ARG, "unsupported patch size");
   }
-  k_plane_absmax<<<nblk(N * Mfull.off.n, 256), 256, 0, s>>>(Mp, N, Mfull.off.n, amax);
+  k_plane_nonzero<<<dim3((unsigned)std::min<long long>(nblk(N, 256 * 8), 1216), Mfull.off.n), 256, 0, s>>>(Mp, N, amax);
   HZ_LAUNCHED();
   std::vector<unsigned long long> hmax(Mfull.off.n);
   int hsing = 0;

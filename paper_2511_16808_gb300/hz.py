@@ -59,7 +59,8 @@ class hz_level_desc(C.Structure):
 
 
 class hz_server_opts(C.Structure):
-    _fields_ = [("hbm_budget", C.c_size_t), ("max_active", C.c_int), ("device", C.c_int)]
+    _fields_ = [("hbm_budget", C.c_size_t), ("max_active", C.c_int), ("device", C.c_int),
+                ("setup_threads", C.c_int)]
 
 
 class hz_request(C.Structure):
@@ -80,7 +81,8 @@ class hz_ticket_info(C.Structure):
 class hz_server_counters(C.Structure):
     _fields_ = [("queued", C.c_int), ("setting_up", C.c_int), ("solving", C.c_int), ("done", C.c_int),
                 ("failed", C.c_int), ("bytes_in_use", C.c_size_t), ("peak_bytes", C.c_size_t),
-                ("budget", C.c_size_t), ("max_active", C.c_int), ("elapsed_s", C.c_double)]
+                ("budget", C.c_size_t), ("max_active", C.c_int), ("elapsed_s", C.c_double),
+                ("kernel_launches", C.c_int64)]
 
 
 class HzError(RuntimeError):
@@ -344,8 +346,8 @@ def hz_coarse_solve(ctx, f, u, stream=None):
 
 # ------------------------------------------------------------------ serving
 
-def hz_server_create(hbm_budget: int = 0, max_active: int = 0, device: int = -1):
-    o = hz_server_opts(int(hbm_budget), int(max_active), int(device))
+def hz_server_create(hbm_budget: int = 0, max_active: int = 0, device: int = -1, setup_threads: int = 0):
+    o = hz_server_opts(int(hbm_budget), int(max_active), int(device), int(setup_threads))
     out = C.c_void_p()
     _check(lib.hz_server_create(C.byref(o), C.byref(out)), "hz_server_create")
     return out.value

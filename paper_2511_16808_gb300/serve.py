@@ -13,10 +13,11 @@ from .solver import make_opts
 
 class Server:
     """hbm_budget: device bytes the admitted requests may hold (0: 80% of free
-    memory); max_active: requests set up or solving at once (0: 32)."""
+    memory); max_active: requests set up or solving at once (0: 32);
+    setup_threads: hierarchies built concurrently (0: 2)."""
 
-    def __init__(self, hbm_budget: int = 0, max_active: int = 0, device: int = -1):
-        self.srv = hz.hz_server_create(hbm_budget, max_active, device)
+    def __init__(self, hbm_budget: int = 0, max_active: int = 0, device: int = -1, setup_threads: int = 0):
+        self.srv = hz.hz_server_create(hbm_budget, max_active, device, setup_threads)
         self._keep = {}
 
     def submit(self, dim, n, kappa, omega, q, gamma=None, alpha=0.25, levels=4, gamma0=0.0, **solver_opts):

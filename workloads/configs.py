@@ -132,8 +132,11 @@ def config4(n: int = 513, levels: int = 5, nsrc: int = 64, seed: int = 1,
     return out
 
 
-# Levels per grid side: coarsest side <= 33 (2D) or <= 17 (3D) nodes.
-SERVE_LEVELS = {2: {257: 4, 513: 5, 1025: 6, 2049: 7}, 3: {65: 3, 129: 4, 193: 5}}
+# Levels per grid side for served requests: coarsest side <= 33 nodes in 2D
+# and <= 9 in 3D (65 -> 9^3, 129 -> 9^3, 193 -> 7^3 unknowns).  Setup is on a
+# request's latency path and the dense coarsest inverse costs O(N_c^3); deep
+# V-cycles with the additive Vanka smoother keep their convergence (Section 5).
+SERVE_LEVELS = {2: {257: 4, 513: 5, 1025: 6, 2049: 7}, 3: {65: 4, 129: 5, 193: 6}}
 
 
 @dataclass
