@@ -1,4 +1,5 @@
 // C ABI of libhz (declarations and contracts in include/hz.h).
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -21,17 +22,66 @@ void set_last_error(const char* msg) {
 // library holds these 4 MiB until the process exits.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[(size_t)HZ_NOALLOC_MAX_NODES * 16];
 
-void* ctx_alloc(Ctx& c, size_t bytes) {
+// Device memory of a context comes from the device's stream-ordered pool
+// (cudaMallocAsync on the context's allocation stream), so that building and
+// freeing hierarchies while other contexts solve does not synchronize the
+// device; freed blocks stay in the pool for the next context.
+static void keep_pool_memory(int dev) {
+  static std::mutex mu;
+  static std::vector<int> done;
+  std::lock_guard<std::mutex> lk(mu);
+  if (std::find(done.begin(), done.end(), dev) != done.end()) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t keep = ~0ull;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  (void)cudaGetLastError();
+  done.push_back(dev);
+}
+
+void* ctx_alloc(Ctx& c, size_t bytes, cudaStream_t s) {
   void* p = nullptr;
   if (bytes == 0) bytes = 16;
-  cudaError_t e = cudaMalloc(&p, bytes);
+  keep_pool_memory(c.dev);
+  cudaError_t e = cudaMallocAsync(&p, bytes, s);
   if (e != cudaSuccess) {
     (void)cudaGetLastError();
     throw Error(e == cudaErrorMemoryAllocation ? HZ_ERR_OOM : HZ_ERR_CUDA,
-                std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+                std::string("cudaMallocAsync(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
   }
   c.allocations.push_back(p);
   return p;
+}
+
+void* ctx_alloc(Ctx& c, size_t bytes) { return ctx_alloc(c, bytes, c.alloc_stream); }
+
+// Small pinned host blocks (the per-context status copies) from a shared
+// arena: pinned allocations are slow and synchronizing, and a served request
+// needs one per context.
+namespace {
+constexpr size_t kPinBlock = 4096, kPinChunk = 256;
+std::mutex g_pin_mu;
+std::vector<void*> g_pin_free;
+}  // namespace
+
+void* pinned_small_alloc(size_t bytes) {
+  require(bytes <= kPinBlock, "pinned status block too large");
+  std::lock_guard<std::mutex> lk(g_pin_mu);
+  if (g_pin_free.empty()) {
+    void* chunk = nullptr;
+    HZ_CUDA(cudaMallocHost(&chunk, kPinBlock * kPinChunk));
+    for (size_t i = 0; i < kPinChunk; ++i) g_pin_free.push_back((char*)chunk + i * kPinBlock);
+  }
+  void* p = g_pin_free.back();
+  g_pin_free.pop_back();
+  return p;
+}
+
+void pinned_small_free(void* p) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lk(g_pin_mu);
+  g_pin_free.push_back(p);
 }
 
 void ctx_free_all(Ctx& c) {
@@ -44,14 +94,17 @@ void ctx_free_all(Ctx& c) {
   if (c.ev_in) cudaEventDestroy(c.ev_in);
   if (c.ev_out) cudaEventDestroy(c.ev_out);
   if (c.ev_status) cudaEventDestroy(c.ev_status);
-  c.ev_status = nullptr;
-  if (c.graph_stream) cudaStreamDestroy(c.graph_stream);
-  c.ev_in = c.ev_out = nullptr;
-  c.graph_stream = nullptr;
-  for (void* p : c.allocations) cudaFree(p);
+  c.ev_in = c.ev_out = c.ev_status = nullptr;
+  // frees are ordered after the context's own stream; the caller has
+  // synchronized every stream that used the context
+  cudaStream_t fs = c.graph_stream ? c.graph_stream : c.alloc_stream;
+  for (void* p : c.allocations) cudaFreeAsync(p, fs);
   c.allocations.clear();
-  if (c.ks_host) cudaFreeHost(c.ks_host);
+  if (c.graph_stream) cudaStreamDestroy(c.graph_stream);
+  c.graph_stream = nullptr;
+  pinned_small_free(c.ks_host);
   c.ks_host = nullptr;
+  (void)cudaGetLastError();
 }
 
 namespace {
@@ -236,6 +289,7 @@ hz_status hz_setup(const hz_grid* g, const double* kappa, double omega, const do
     c.alpha = shift_alpha;
     c.h = g->h;
     c.mixed = opts->precision == HZ_PREC_MIXED;
+    c.alloc_stream = s;
     HZ_CUDA(cudaGetDevice(&c.dev));
     const long long N = grid_nodes(c.grid);
     // stage kappa / gamma on the device and check kappa
@@ -286,7 +340,7 @@ hz_status hz_solve(hz_ctx* ctx, const void* q, void* p, int nrhs, hz_info* info,
     double2* pd = (double2*)p;
     const bool q_host = !is_device_ptr(q), p_host = !is_device_ptr(p);
     if (q_host) {
-      if (!c.qstage) c.qstage = (double2*)ctx_alloc(c, sizeof(double2) * c.L[0].g.N * c.opts.nrhs_max);
+      if (!c.qstage) c.qstage = (double2*)ctx_alloc(c, sizeof(double2) * c.L[0].g.N * c.opts.nrhs_max, s);
       HZ_CUDA(cudaMemcpyAsync(c.qstage, q, sizeof(double2) * N, cudaMemcpyHostToDevice, s));
       qd = c.qstage;
     }
@@ -310,7 +364,7 @@ hz_status hz_solve_begin(hz_ctx* ctx, const void* q, void* cuda_stream) {
     cudaStream_t s = (cudaStream_t)cuda_stream;
     const double2* qd = (const double2*)q;
     if (!is_device_ptr(q)) {
-      if (!c.qstage) c.qstage = (double2*)ctx_alloc(c, sizeof(double2) * c.L[0].g.N * c.opts.nrhs_max);
+      if (!c.qstage) c.qstage = (double2*)ctx_alloc(c, sizeof(double2) * c.L[0].g.N * c.opts.nrhs_max, s);
       HZ_CUDA(cudaMemcpyAsync(c.qstage, q, sizeof(double2) * c.L[0].g.N, cudaMemcpyHostToDevice, s));
       qd = c.qstage;
     }

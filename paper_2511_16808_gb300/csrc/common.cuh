@@ -362,6 +362,7 @@ struct Ctx {
   void* ks_host = nullptr;      // pinned host copy of the status
   int red_blocks = 0;
   std::vector<void*> allocations;
+  cudaStream_t alloc_stream = nullptr;   // stream of hz_setup: orders the context's allocations
   std::atomic<int> busy{0};
   cudaGraphExec_t cycle_graph = nullptr;
   cudaGraphExec_t batch_graph = nullptr;   // restart cycle for nrhs > 1
@@ -387,7 +388,10 @@ struct Ctx {
 };
 
 // allocation helpers (all device memory of a context goes through these)
-void* ctx_alloc(Ctx& c, size_t bytes);
+void* ctx_alloc(Ctx& c, size_t bytes);          // stream-ordered, on c.alloc_stream
+void* ctx_alloc(Ctx& c, size_t bytes, cudaStream_t s);
+void* pinned_small_alloc(size_t bytes);         // <= 4 KB pinned host block (shared arena)
+void pinned_small_free(void* p);
 void ctx_free_all(Ctx& c);
 
 // setup.cu

@@ -513,9 +513,9 @@ void krylov_alloc(Ctx& c) {
   const long long nbR = R > 1 ? R * (nblk(N * R, kRedBlock * 8) + grid_blocks(g) * R) : 0;
   c.partials = (double2*)ctx_alloc(c, sizeof(double2) * std::max(nb1, nbR));
   c.ks = (KrylovState*)ctx_alloc(c, sizeof(KrylovState) * R);
-  HZ_CUDA(cudaMemset(c.ks, 0, sizeof(KrylovState) * R));
+  HZ_CUDA(cudaMemsetAsync(c.ks, 0, sizeof(KrylovState) * R, c.alloc_stream));
   c.n_active = (int*)ctx_alloc(c, sizeof(int));
-  HZ_CUDA(cudaMallocHost(&c.ks_host, sizeof(KrylovStatus) * R));
+  c.ks_host = pinned_small_alloc(sizeof(KrylovStatus) * R);
   HZ_CUDA(cudaStreamCreateWithFlags(&c.graph_stream, cudaStreamNonBlocking));
   HZ_CUDA(cudaEventCreateWithFlags(&c.ev_in, cudaEventDisableTiming));
   HZ_CUDA(cudaEventCreateWithFlags(&c.ev_out, cudaEventDisableTiming));

@@ -156,7 +156,11 @@ class ServeRequest:
         levels = SERVE_LEVELS[dim][n]
         layer = max(4, (20 * (n - 1)) // 1024) if dim == 2 else max(3, (16 * (n - 1)) // 256)
         if self.generator == "homogeneous" and dim == 2:
-            w = config1(n=n, levels=levels, tol=1e-6, precision="mixed")
+            # config 1's medium; with deeper cycles than config 1's 4 levels the
+            # plus patch at alpha 0.25 stalls on near-resonant frequencies of the
+            # closed box, RB at 0.25 (config 2's patch; the layered medium's 0.1
+            # scaled by its kappa_max^2 = 0.44) converges
+            w = config1(n=n, levels=levels, tol=1e-6, precision="mixed", patch="rb", alpha=0.25)
             v_min = 1.0
         elif dim == 2:
             w = config2(n=n, levels=levels, seed=self.seed, layer_cells=layer)
