@@ -291,8 +291,8 @@ hz_status hz_kernel_launches(const hz_ctx* ctx, int64_t* count);
 
 /* Measurement hooks.  hz_profile_select makes every later hz_solve on this
  * context record CUDA events around each launch of one kernel class:
- *   0 none, 1 the Gram-Schmidt update passes, 2 the first Gram-Schmidt pass
- *   (FP64 operator apply + inner product), 3 the whole V-cycle.
+ *   0 none, 1 the Gram-Schmidt update passes, 2 the Gram-Schmidt pass with the
+ *   FP64 operator apply and the inner products, 3 the whole V-cycle.
  * Only launches of inner iterations that did work are counted.  The restart
  * cycle graph is re-captured with the events; the overhead is two event
  * records per bracketed launch.  hz_profile_read returns the accumulated

@@ -1,27 +1,26 @@
 // Flexible GMRES(m) in FP64 around the multigrid V-cycle (Section 2.3; m = 5
 // in Section 5.2), right preconditioned, zero initial guess (Section 5).
 //
-// Per inner iteration j (one preconditioner application):
-//   f0 = cast(v_j)                 c128 -> working precision
-//   z_j = V-cycle(f0)              stored in the working precision (the
-//                                  Arnoldi relation A Z = V H holds for the
-//                                  stored z_j, so FP32 storage loses nothing)
-//   modified Gram-Schmidt, one pass per basis vector with each update fused
-//   with the next inner product:
-//     pass 0      w = A z_j,           h_0j = v_0^H w
-//     pass i      w -= h_{i-1,j} v_{i-1}, h_ij = v_i^H w      (i = 1..j)
-//     pass j+1    w -= h_jj v_j,       ||w||^2
-//   (half the FP64 operations of classical Gram-Schmidt applied twice,
-//   whose second pass was needed at every iteration here)
-//   H(:, j), H(j+1, j) = ||w||, complex Givens update of H and g,
-//   residual estimate |g_{j+1}| / ||q_hat|| and the stop flag: all on the
-//   device.
-// v_{j+1} is stored unnormalised with its scale 1/||w|| (deferred
-// normalisation).  At the end of a cycle: y = H^{-1} g (back substitution),
-// p += Z y, true residual q_hat - A p in FP64, restart.  One restart cycle is
-// captured once as a CUDA graph and replayed; the host reads one small status
-// record per cycle.  GB300's FP64 rate is 1/64 of FP32, so the FP64 passes
-// are organised to minimise FP64 operations per node, not just bytes.
+// Per inner iteration j (one preconditioner application), two FP64 passes of
+// classical Gram-Schmidt:
+//   z'_j = V-cycle(f)      f = V_j cast to the working precision, V_j stored
+//                          unnormalised with v_j = scale_j V_j, so z_j =
+//                          scale_j z'_j (the cycle is linear); z'_j is stored
+//                          in the working precision (the Arnoldi relation
+//                          A Z = V H holds for the stored vectors)
+//   pass A   w = A z'_j -> V_{j+1};  d_i = V_i^H w, i = 0..j (one sweep)
+//   pass B   w -= sum_i scale_i^2 d_i V_i;  ||w||^2;  f = cast(w) for the
+//            next cycle;  then (last block) H(i, j) = scale_j scale_i d_i,
+//            H(j+1, j) = scale_j ||w||, complex Givens update of H and g,
+//            residual estimate |g_{j+1}| / ||q_hat|| and the stop flag.
+// Two passes and two reductions per iteration whatever j (modified
+// Gram-Schmidt needs j + 2 dependent ones) with the same FP64 operation count;
+// in FP64 with m = 5 the orthogonality lost by one classical pass stays at
+// rounding level.  At the end of a cycle: y = H^{-1} g, p += sum y_i scale_i
+// z'_i, true residual q_hat - A p in FP64 (also cast into f), restart.  One
+// restart cycle is captured once as a CUDA graph and replayed; the host reads
+// one small status record per cycle.  GB300's FP64 rate is 1/64 of FP32, so
+// the passes are organised to minimise FP64 operations and launches.
 //
 // Reductions are two-stage and deterministic: each pass kernel writes one
 // partial per block, a second kernel sums the partials in a fixed order.
@@ -91,15 +90,63 @@ __device__ __forceinline__ bool reduce_last(double2 acc, double2* __restrict__ p
 __device__ __forceinline__ int block_linear() { return (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x; }
 
 
-// pass 0: w = A z_j -> V[j+1]; h_0j (raw) = conj(V_0) . w
-template <typename TZ>
-__global__ void __launch_bounds__(kRedBlock) k_mgs_first(Geo g, double invh2, const double2* __restrict__ diag,
-                                                         const TZ* __restrict__ z, double2* __restrict__ V, int j,
-                                                         double2* __restrict__ partials, KrylovState* st) {
+// Per-block partials of NV complex accumulators, then (last block to arrive)
+// NV deterministic sums: warp w sums vectors w, w+8, ... over the blocks in
+// index order.  Returns true in the last block.
+template <int NV>
+__device__ __forceinline__ bool reduce_last_multi(const double2 (&acc)[NV], double2* __restrict__ partials, int nb,
+                                                  int block, unsigned* counter, double2* out) {
+  __shared__ double2 sm[kRedBlock / 32][NV];
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int lane = tid & 31, wid = tid >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    double2 a = acc[i];
+    for (int o = 16; o > 0; o >>= 1) {
+      a.x += __shfl_xor_sync(0xffffffffu, a.x, o);
+      a.y += __shfl_xor_sync(0xffffffffu, a.y, o);
+    }
+    if (lane == 0) sm[wid][i] = a;
+  }
+  __syncthreads();
+  if (tid < NV) {
+    double2 t = make_double2(0, 0);
+    for (int w = 0; w < kRedBlock / 32; ++w) t = t + sm[w][tid];
+    partials[tid * nb + block] = t;
+  }
+  __threadfence();
+  __syncthreads();
+  __shared__ int is_last;
+  if (tid == 0) is_last = atomicAdd(counter, 1u) == (unsigned)(nb - 1);
+  __syncthreads();
+  if (!is_last) return false;
+  __threadfence();
+  for (int i = wid; i < NV; i += kRedBlock / 32) {
+    const double2* pi = partials + (long long)i * nb;
+    double2 t = make_double2(0, 0);
+    for (int b = lane; b < nb; b += 32) t = t + __ldcg(pi + b);
+    for (int o = 16; o > 0; o >>= 1) {
+      t.x += __shfl_xor_sync(0xffffffffu, t.x, o);
+      t.y += __shfl_xor_sync(0xffffffffu, t.y, o);
+    }
+    if (lane == 0) out[i] = t;
+  }
+  __syncthreads();
+  if (tid == 0) *counter = 0u;
+  return true;
+}
+
+// pass A: w = A z'_j -> V[j+1]; d_i = conj(V_i) . w for i < NV = j + 1
+template <typename TZ, int NV>
+__global__ void __launch_bounds__(kRedBlock) k_gs_dots(Geo g, double invh2, const double2* __restrict__ diag,
+                                                       const TZ* __restrict__ z, double2* __restrict__ V,
+                                                       double2* __restrict__ partials, KrylovState* st) {
   if (!st->active) return;
-  double2 acc = make_double2(0, 0);
+  double2 acc[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) acc[i] = make_double2(0, 0);
   const int x = blockIdx.x * BX + threadIdx.x;
-  double2* w = V + (j + 1) * g.N;
+  double2* w = V + (long long)NV * g.N;
   if (x < g.nx) {
     for (int zz = blockIdx.z; zz < g.nz; zz += gridDim.z) {
 #pragma unroll
@@ -109,52 +156,56 @@ __global__ void __launch_bounds__(kRedBlock) k_mgs_first(Geo g, double invh2, co
         const int p = (zz * g.ny + y) * g.nx + x;
         const double2 a = apply_A(g, invh2, diag, z, p, x, y, zz);
         w[p] = a;
-        acc = dot_acc(acc, V[p], a);
+#pragma unroll
+        for (int i = 0; i < NV; ++i) acc[i] = dot_acc(acc[i], V[(long long)i * g.N + p], a);
       }
     }
   }
-  reduce_last(acc, partials, gridDim.x * gridDim.y * gridDim.z, block_linear(), &st->counter, &st->h1[0]);
+  reduce_last_multi<NV>(acc, partials, gridDim.x * gridDim.y * gridDim.z, block_linear(), &st->counter, st->h1);
 }
 
-// pass i (1..j): w -= h_{i-1} v_{i-1}; h_ij (raw) = conj(V_i) . w
-// pass j+1 (LAST): w -= h_j v_j; ||w||^2, then (last block) the Arnoldi column
-template <bool LAST>
-__global__ void __launch_bounds__(kRedBlock) k_mgs_step(int N, double2* __restrict__ V, int j, int i,
-                                                        double2* __restrict__ partials, KrylovState* st) {
+// pass B: w -= sum_{i < NV} scale_i^2 d_i V_i; ||w||^2; f = w in the working
+// precision; then (last block) the Arnoldi column of j = NV - 1
+template <typename TF, int NV>
+__global__ void __launch_bounds__(kRedBlock) k_gs_update(int N, double2* __restrict__ V, TF* __restrict__ f,
+                                                         double2* __restrict__ partials, KrylovState* st) {
   if (!st->active) return;
-  const double s = st->scale[i - 1];
-  const double2 c = (s * s) * st->h1[i - 1];          // h_{i-1,j} * scale_{i-1}
-  const double2* vp = V + (i - 1) * N;
-  const double2* vi = V + i * N;
-  double2* w = V + (j + 1) * N;
-  double2 acc = make_double2(0, 0);
+  double2 c[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    const double s = st->scale[i];
+    c[i] = (s * s) * st->h1[i];
+  }
+  double2* w = V + (long long)NV * N;
+  double acc = 0.0;
   const int base = blockIdx.x * (kRedBlock * kPerThread) + threadIdx.x;
 #pragma unroll
   for (int k = 0; k < kPerThread; ++k) {
     const int p = base + k * kRedBlock;
     if (p < N) {
-      const double2 ww = axmy(w[p], c, vp[p]);
+      double2 ww = w[p];
+#pragma unroll
+      for (int i = 0; i < NV; ++i) ww = axmy(ww, c[i], V[(long long)i * N + p]);
       w[p] = ww;
-      if (LAST) acc.x = nrm_acc(acc.x, ww);
-      else acc = dot_acc(acc, vi[p], ww);
+      if constexpr (std::is_same<TF, float2>::value) f[p] = make_float2(d2f_rn(ww.x), d2f_rn(ww.y));
+      else f[p] = ww;
+      acc = nrm_acc(acc, ww);
     }
   }
-  const bool last = reduce_last(acc, partials, gridDim.x, blockIdx.x, &st->counter, LAST ? &st->nrm2 : &st->h1[i]);
-  if (LAST && last && threadIdx.x == 0) arnoldi_update(st, j);
+  const bool last = reduce_last(make_double2(acc, 0.0), partials, gridDim.x, blockIdx.x, &st->counter, &st->nrm2);
+  if (last && threadIdx.x == 0) arnoldi_update(st, NV - 1, nullptr, st->scale[NV - 1]);
 }
 
-template <typename V>
-__global__ void k_cast_in(int N, const double2* __restrict__ v, const KrylovState* __restrict__ st, int j,
-                          V* __restrict__ f) {
-  if (!st->active) return;
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= N) return;
-  const double2 a = v[p];
-  if constexpr (std::is_same<V, float2>::value) {
-    const float sc = d2f_rn(st->scale[j]);
-    f[p] = make_float2(d2f_rn(a.x) * sc, d2f_rn(a.y) * sc);
-  } else {
-    f[p] = st->scale[j] * a;
+// NV = 1..kMaxM as a compile-time constant
+template <typename F>
+void with_nv(int nv, F&& f) {
+  switch (nv) {
+#define HZ_NV(K) \
+  case K: f(std::integral_constant<int, K>{}); return;
+    HZ_NV(1) HZ_NV(2) HZ_NV(3) HZ_NV(4) HZ_NV(5) HZ_NV(6) HZ_NV(7) HZ_NV(8)
+    HZ_NV(9) HZ_NV(10) HZ_NV(11) HZ_NV(12) HZ_NV(13) HZ_NV(14) HZ_NV(15) HZ_NV(16)
+#undef HZ_NV
+    default: throw Error(HZ_ERR_INVALID_ARG, "restart_m must be in 1..16");
   }
 }
 
@@ -177,18 +228,21 @@ __global__ void k_update_p(int N, const TZ* __restrict__ Z, const KrylovState* _
   const int k = st->kcyc;
   double2 acc = p[q];
   for (int i = 0; i < k; ++i) {
-    const double2 yi = st->y[i], zi = ld64(Z, i * N + q);
+    const double2 yi = st->scale[i] * st->y[i], zi = ld64(Z, i * N + q);
     acc = make_double2(fma(yi.x, zi.x, fma(-yi.y, zi.y, acc.x)), fma(yi.x, zi.y, fma(yi.y, zi.x, acc.y)));
   }
   p[q] = acc;
 }
 
 
-// r = q_hat - A p -> V_0; ||r||^2, then (last block) the restart decision
+// r = q_hat - A p -> V_0 and f (working precision, the next cycle's first
+// V-cycle input); ||r||^2, then (last block) the restart decision
+template <typename TF>
 __global__ void __launch_bounds__(kRedBlock) k_true_residual(Geo g, double invh2, const double2* __restrict__ diag,
                                                              const double2* __restrict__ p,
                                                              const double2* __restrict__ qhat, double2* __restrict__ r,
-                                                             double2* __restrict__ partials, KrylovState* st) {
+                                                             TF* __restrict__ f, double2* __restrict__ partials,
+                                                             KrylovState* st) {
   if (st->st.done) return;
   double2 acc = make_double2(0, 0);
   const int x = blockIdx.x * BX + threadIdx.x;
@@ -201,6 +255,8 @@ __global__ void __launch_bounds__(kRedBlock) k_true_residual(Geo g, double invh2
         const int q = (zz * g.ny + y) * g.nx + x;
         const double2 v = qhat[q] - apply_A(g, invh2, diag, p, q, x, y, zz);
         r[q] = v;
+        if constexpr (std::is_same<TF, float2>::value) f[q] = make_float2(d2f_rn(v.x), d2f_rn(v.y));
+        else f[q] = v;
         acc.x = nrm_acc(acc.x, v);
       }
     }
@@ -264,30 +320,29 @@ void run_cycle(Ctx& c, cudaStream_t s) {
   const int* active = &st->active;
   TZ* Z = (TZ*)c.Z;
   for (int j = 0; j < m; ++j) {
-    k_cast_in<TZ><<<nblk(N, 256), 256, 0, s>>>(N, c.V + (long long)j * N, st, j, (TZ*)L0.f);
+    const int nv = j + 1;
     int pk = prof_begin(c, 3, j, vcycle_bytes(c), 0.0, s);
     vcycle(c, L0.f, Z + (long long)j * N, active, s);
     prof_end(c, pk, s);
-    // k_mgs_first: z (b), diag, v_0 read, w written; 24 flops (A z: 16, dot: 8)
-    pk = prof_begin(c, 2, j, (double)N * (sizeof(TZ) + 48), 24.0 * N, s);
-    k_mgs_first<TZ><<<grid_xy(g), dim3(BX, BY), 0, s>>>(g, invh2, c.diagA64, Z + (long long)j * N, c.V, j,
-                                                         c.partials, st);
+    // pass A: z (b) and diag read, w written, nv vectors read; A z 16 flops + 8 per dot
+    pk = prof_begin(c, 2, j, (double)N * (sizeof(TZ) + 32 + 16.0 * nv), (16.0 + 8.0 * nv) * N, s);
+    with_nv(nv, [&](auto NV) {
+      k_gs_dots<TZ, decltype(NV)::value><<<grid_xy(g), dim3(BX, BY), 0, s>>>(g, invh2, c.diagA64, Z + (long long)j * N, c.V,
+                                                             c.partials, st);
+    });
     prof_end(c, pk, s);
-    for (int i = 1; i <= j; ++i) {
-      // w, v_{i-1}, v_i read, w written; 8 flops update + 8 flops dot
-      pk = prof_begin(c, 1, j, 64.0 * N, 16.0 * N, s);
-      k_mgs_step<false><<<grid_1d(N), kRedBlock, 0, s>>>(N, c.V, j, i, c.partials, st);
-      prof_end(c, pk, s);
-    }
-    // w, v_j read, w written; 8 flops update + 4 flops norm
-    pk = prof_begin(c, 1, j, 48.0 * N, 12.0 * N, s);
-    k_mgs_step<true><<<grid_1d(N), kRedBlock, 0, s>>>(N, c.V, j, j + 1, c.partials, st);
+    // pass B: w and nv vectors read, w and f written; 8 flops per vector + 4 for the norm
+    pk = prof_begin(c, 1, j, (double)N * (32 + 16.0 * nv + sizeof(TZ)), (8.0 * nv + 4.0) * N, s);
+    with_nv(nv, [&](auto NV) {
+      k_gs_update<TZ, decltype(NV)::value><<<grid_1d(N), kRedBlock, 0, s>>>(N, c.V, (TZ*)L0.f, c.partials, st);
+    });
     prof_end(c, pk, s);
   }
   HZ_LAUNCHED();
   k_solve_y<<<1, 1, 0, s>>>(st);
   k_update_p<TZ><<<nblk(N, 256), 256, 0, s>>>(N, Z, st, c.p);
-  k_true_residual<<<grid_xy(g), dim3(BX, BY), 0, s>>>(g, invh2, c.diagA64, c.p, c.qhat, c.V, c.partials, st);
+  k_true_residual<TZ><<<grid_xy(g), dim3(BX, BY), 0, s>>>(g, invh2, c.diagA64, c.p, c.qhat, c.V, (TZ*)L0.f,
+                                                          c.partials, st);
   HZ_LAUNCHED();
 }
 
@@ -349,7 +404,8 @@ void solve_begin_t(Ctx& c, const double2* q, cudaStream_t user) {
   k_scale_rhs<<<nblk(N, kRedBlock), kRedBlock, 0, s>>>(N, c.wmass, q, c.qhat, c.partials, st, c.opts.tol,
                                                        c.opts.max_iter, c.opts.restart_m);
   HZ_CUDA(cudaMemsetAsync(c.p, 0, sizeof(double2) * N, s));
-  k_true_residual<<<grid_xy(g), dim3(BX, BY), 0, s>>>(g, invh2, c.diagA64, c.p, c.qhat, c.V, c.partials, st);
+  k_true_residual<TZ><<<grid_xy(g), dim3(BX, BY), 0, s>>>(g, invh2, c.diagA64, c.p, c.qhat, c.V, (TZ*)c.L[0].f,
+                                                          c.partials, st);
   HZ_LAUNCHED();
   c.launches += 2;
   HZ_CUDA(cudaMemcpyAsync(hs, &st->st, sizeof(KrylovStatus), cudaMemcpyDeviceToHost, s));
@@ -412,8 +468,8 @@ namespace {
 }  // namespace
 
 // ---- measurement hooks: events around the launches of the selected class
-// (1 = Gram-Schmidt update passes k_mgs_step, 2 = first pass k_mgs_first with
-// the FP64 operator, 3 = whole V-cycle preconditioner application)
+// (1 = Gram-Schmidt update passes, 2 = the pass with the FP64 operator and the
+// inner products, 3 = whole V-cycle preconditioner application)
 int prof_begin(Ctx& c, int cls, int j, double bytes, double flops, cudaStream_t s) {
   if (c.prof_class != cls) return -1;
   const int k = (int)c.prof_j.size();
@@ -491,8 +547,8 @@ size_t krylov_bytes(const hz_grid& g, const hz_opts& o) {
   const size_t vb = o.precision == HZ_PREC_MIXED ? 8 : 16;
   const int m = o.restart_m;
   const long long R = std::max(1, o.nrhs_max);
-  const long long nb = nblk(N * R, kRedBlock) * 2;
-  return (16ull * N * (m + 1) + vb * N * m + 16ull * N * 4) * R + 16ull * nb * R + sizeof(KrylovState) * R;
+  const long long nb = nblk(N * R, kRedBlock) * 2 * R + (long long)m * (nblk(N, BX * BY * kRows) + 1024);
+  return (16ull * N * (m + 1) + vb * N * m + 16ull * N * 4) * R + 16ull * nb + sizeof(KrylovState) * R;
 }
 
 void krylov_alloc(Ctx& c) {
@@ -507,9 +563,10 @@ void krylov_alloc(Ctx& c) {
   c.qhat = (double2*)ctx_alloc(c, sizeof(double2) * N * R);
   c.p = (double2*)ctx_alloc(c, sizeof(double2) * N * R);
   const Geo g = geo(c.L[0].g);
-  // single RHS: one partial per block; batched: one per block and RHS (blocks of
-  // at least 8 values per thread, see krylov_batch.cu)
-  const long long nb1 = std::max<long long>(grid_blocks(g), nblk(N, kRedBlock));
+  // single RHS: the operator pass keeps up to m partials per block (one per
+  // inner product), the 1D passes one per block; batched: one per block and
+  // RHS (blocks of at least 8 values per thread, see krylov_batch.cu)
+  const long long nb1 = std::max<long long>((long long)grid_blocks(g) * m, nblk(N, kRedBlock));
   const long long nbR = R > 1 ? R * (nblk(N * R, kRedBlock * 8) + grid_blocks(g) * R) : 0;
   c.partials = (double2*)ctx_alloc(c, sizeof(double2) * std::max(nb1, nbR));
   c.ks = (KrylovState*)ctx_alloc(c, sizeof(KrylovState) * R);

@@ -130,10 +130,13 @@ __device__ inline void givens(double2 a, double2 b, double& c, double2& s) {
 
 // Column j of the Hessenberg matrix, Givens rotations, residual estimate
 // (one thread, in the last block of the final Gram-Schmidt pass).
-__device__ inline void arnoldi_update(KrylovState* st, int j, int* n_active = nullptr) {
-  for (int i = 0; i <= j; ++i) st->H[i][j] = st->scale[i] * st->h1[i];
+// sj: scale of the preconditioned vector when z_j = sj * (V-cycle of the
+// unnormalised V_j) was used (the Gram-Schmidt dots and norm are then those
+// of A z_j / sj), 1 when z_j came from the normalised v_j.
+__device__ inline void arnoldi_update(KrylovState* st, int j, int* n_active = nullptr, double sj = 1.0) {
+  for (int i = 0; i <= j; ++i) st->H[i][j] = (sj * st->scale[i]) * st->h1[i];
   const double hn = sqrt(st->nrm2.x);
-  st->H[j + 1][j] = make_double2(hn, 0.0);
+  st->H[j + 1][j] = make_double2(sj * hn, 0.0);
   for (int i = 0; i < j; ++i) {
     const double2 a = st->H[i][j], b = st->H[i + 1][j];
     const double c = st->cs[i];
