@@ -25,6 +25,8 @@
 // Reductions are two-stage and deterministic: each pass kernel writes one
 // partial per block, a second kernel sums the partials in a fixed order.
 #include <cstddef>
+#include <map>
+#include <mutex>
 #include <type_traits>
 
 #include "krylov_impl.cuh"
@@ -136,6 +138,28 @@ __device__ __forceinline__ bool reduce_last_multi(const double2 (&acc)[NV], doub
   return true;
 }
 
+// Persistent stride over the tiles (32 x 8 threads, one node each, one z
+// plane per tile): f(p, x, y, z) for every node of the block's tiles.
+template <typename F>
+__device__ __forceinline__ void for_tiles(const Geo& g, F&& f) {
+  const int tnx = (g.nx + BX - 1) / BX, tny = (g.ny + BY - 1) / BY;
+  const int tiles = tnx * tny * g.nz;
+  for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const int tz = t / (tnx * tny), r = t - tz * (tnx * tny);
+    const int tyi = r / tnx, txi = r - tyi * tnx;
+    const int x = txi * BX + threadIdx.x, y = tyi * BY + threadIdx.y;
+    if (x < g.nx && y < g.ny) f((tz * g.ny + y) * g.nx + x, x, y, tz);
+  }
+}
+
+// Contiguous, equal share [b0, b1) of N elements for this block of a
+// persistent 1D pass.
+__device__ __forceinline__ void block_range(int N, int& b0, int& b1) {
+  const long long per = ((long long)N + gridDim.x - 1) / gridDim.x;
+  b0 = (int)std::min<long long>((long long)blockIdx.x * per, N);
+  b1 = (int)std::min<long long>(b0 + per, N);
+}
+
 // pass A: w = A z'_j -> V[j+1]; d_i = conj(V_i) . w for i < NV = j + 1
 template <typename TZ, int NV>
 __global__ void __launch_bounds__(kRedBlock) k_gs_dots(Geo g, double invh2, const double2* __restrict__ diag,
@@ -145,23 +169,14 @@ __global__ void __launch_bounds__(kRedBlock) k_gs_dots(Geo g, double invh2, cons
   double2 acc[NV];
 #pragma unroll
   for (int i = 0; i < NV; ++i) acc[i] = make_double2(0, 0);
-  const int x = blockIdx.x * BX + threadIdx.x;
   double2* w = V + (long long)NV * g.N;
-  if (x < g.nx) {
-    for (int zz = blockIdx.z; zz < g.nz; zz += gridDim.z) {
+  for_tiles(g, [&](int p, int x, int y, int zz) {
+    const double2 a = apply_A(g, invh2, diag, z, p, x, y, zz);
+    w[p] = a;
 #pragma unroll
-      for (int k = 0; k < kRows; ++k) {
-        const int y = (blockIdx.y * kRows + k) * BY + threadIdx.y;
-        if (y >= g.ny) break;
-        const int p = (zz * g.ny + y) * g.nx + x;
-        const double2 a = apply_A(g, invh2, diag, z, p, x, y, zz);
-        w[p] = a;
-#pragma unroll
-        for (int i = 0; i < NV; ++i) acc[i] = dot_acc(acc[i], V[(long long)i * g.N + p], a);
-      }
-    }
-  }
-  reduce_last_multi<NV>(acc, partials, gridDim.x * gridDim.y * gridDim.z, block_linear(), &st->counter, st->h1);
+    for (int i = 0; i < NV; ++i) acc[i] = dot_acc(acc[i], V[(long long)i * g.N + p], a);
+  });
+  reduce_last_multi<NV>(acc, partials, gridDim.x, blockIdx.x, &st->counter, st->h1);
 }
 
 // pass B: w -= sum_{i < NV} scale_i^2 d_i V_i; ||w||^2; f = w in the working
@@ -178,19 +193,16 @@ __global__ void __launch_bounds__(kRedBlock) k_gs_update(int N, double2* __restr
   }
   double2* w = V + (long long)NV * N;
   double acc = 0.0;
-  const int base = blockIdx.x * (kRedBlock * kPerThread) + threadIdx.x;
+  int b0, b1;
+  block_range(N, b0, b1);
+  for (int p = b0 + threadIdx.x; p < b1; p += kRedBlock) {
+    double2 ww = w[p];
 #pragma unroll
-  for (int k = 0; k < kPerThread; ++k) {
-    const int p = base + k * kRedBlock;
-    if (p < N) {
-      double2 ww = w[p];
-#pragma unroll
-      for (int i = 0; i < NV; ++i) ww = axmy(ww, c[i], V[(long long)i * N + p]);
-      w[p] = ww;
-      if constexpr (std::is_same<TF, float2>::value) f[p] = make_float2(d2f_rn(ww.x), d2f_rn(ww.y));
-      else f[p] = ww;
-      acc = nrm_acc(acc, ww);
-    }
+    for (int i = 0; i < NV; ++i) ww = axmy(ww, c[i], V[(long long)i * N + p]);
+    w[p] = ww;
+    if constexpr (std::is_same<TF, float2>::value) f[p] = make_float2(d2f_rn(ww.x), d2f_rn(ww.y));
+    else f[p] = ww;
+    acc = nrm_acc(acc, ww);
   }
   const bool last = reduce_last(make_double2(acc, 0.0), partials, gridDim.x, blockIdx.x, &st->counter, &st->nrm2);
   if (last && threadIdx.x == 0) arnoldi_update(st, NV - 1, nullptr, st->scale[NV - 1]);
@@ -245,24 +257,14 @@ __global__ void __launch_bounds__(kRedBlock) k_true_residual(Geo g, double invh2
                                                              KrylovState* st) {
   if (st->st.done) return;
   double2 acc = make_double2(0, 0);
-  const int x = blockIdx.x * BX + threadIdx.x;
-  if (x < g.nx) {
-    for (int zz = blockIdx.z; zz < g.nz; zz += gridDim.z) {
-#pragma unroll
-      for (int k = 0; k < kRows; ++k) {
-        const int y = (blockIdx.y * kRows + k) * BY + threadIdx.y;
-        if (y >= g.ny) break;
-        const int q = (zz * g.ny + y) * g.nx + x;
-        const double2 v = qhat[q] - apply_A(g, invh2, diag, p, q, x, y, zz);
-        r[q] = v;
-        if constexpr (std::is_same<TF, float2>::value) f[q] = make_float2(d2f_rn(v.x), d2f_rn(v.y));
-        else f[q] = v;
-        acc.x = nrm_acc(acc.x, v);
-      }
-    }
-  }
-  const bool last = reduce_last(acc, partials, gridDim.x * gridDim.y * gridDim.z, block_linear(), &st->counter,
-                                &st->nrm2);
+  for_tiles(g, [&](int q, int x, int y, int zz) {
+    const double2 v = qhat[q] - apply_A(g, invh2, diag, p, q, x, y, zz);
+    r[q] = v;
+    if constexpr (std::is_same<TF, float2>::value) f[q] = make_float2(d2f_rn(v.x), d2f_rn(v.y));
+    else f[q] = v;
+    acc.x = nrm_acc(acc.x, v);
+  });
+  const bool last = reduce_last(acc, partials, gridDim.x, blockIdx.x, &st->counter, &st->nrm2);
   if (last && threadIdx.x == 0 && threadIdx.y == 0) restart_update(st);
 }
 
@@ -324,25 +326,32 @@ void run_cycle(Ctx& c, cudaStream_t s) {
     int pk = prof_begin(c, 3, j, vcycle_bytes(c), 0.0, s);
     vcycle(c, L0.f, Z + (long long)j * N, active, s);
     prof_end(c, pk, s);
-    // pass A: z (b) and diag read, w written, nv vectors read; A z 16 flops + 8 per dot
-    pk = prof_begin(c, 2, j, (double)N * (sizeof(TZ) + 32 + 16.0 * nv), (16.0 + 8.0 * nv) * N, s);
+    // pass A: z (b) and diag read, w written, nv vectors read; A z 16 flops
+    // (2D; 20 in 3D: two more neighbour sums) + 8 per dot
+    pk = prof_begin(c, 2, j, (double)N * (sizeof(TZ) + 32 + 16.0 * nv), ((g.dim == 3 ? 20.0 : 16.0) + 8.0 * nv) * N, s);
     with_nv(nv, [&](auto NV) {
-      k_gs_dots<TZ, decltype(NV)::value><<<grid_xy(g), dim3(BX, BY), 0, s>>>(g, invh2, c.diagA64, Z + (long long)j * N, c.V,
-                                                             c.partials, st);
+      auto kern = k_gs_dots<TZ, decltype(NV)::value>;
+      const unsigned G = (unsigned)std::min<long long>(tiles_xy(g), resident_slots((const void*)kern, kRedBlock));
+      kern<<<G, dim3(BX, BY), 0, s>>>(g, invh2, c.diagA64, Z + (long long)j * N, c.V, c.partials, st);
     });
     prof_end(c, pk, s);
     // pass B: w and nv vectors read, w and f written; 8 flops per vector + 4 for the norm
     pk = prof_begin(c, 1, j, (double)N * (32 + 16.0 * nv + sizeof(TZ)), (8.0 * nv + 4.0) * N, s);
     with_nv(nv, [&](auto NV) {
-      k_gs_update<TZ, decltype(NV)::value><<<grid_1d(N), kRedBlock, 0, s>>>(N, c.V, (TZ*)L0.f, c.partials, st);
+      auto kern = k_gs_update<TZ, decltype(NV)::value>;
+      const unsigned G = (unsigned)std::min<long long>(grid_1d(N), resident_slots((const void*)kern, kRedBlock));
+      kern<<<G, kRedBlock, 0, s>>>(N, c.V, (TZ*)L0.f, c.partials, st);
     });
     prof_end(c, pk, s);
   }
   HZ_LAUNCHED();
   k_solve_y<<<1, 1, 0, s>>>(st);
   k_update_p<TZ><<<nblk(N, 256), 256, 0, s>>>(N, Z, st, c.p);
-  k_true_residual<TZ><<<grid_xy(g), dim3(BX, BY), 0, s>>>(g, invh2, c.diagA64, c.p, c.qhat, c.V, (TZ*)L0.f,
-                                                          c.partials, st);
+  {
+    auto kern = k_true_residual<TZ>;
+    const unsigned G = (unsigned)std::min<long long>(tiles_xy(g), resident_slots((const void*)kern, kRedBlock));
+    kern<<<G, dim3(BX, BY), 0, s>>>(g, invh2, c.diagA64, c.p, c.qhat, c.V, (TZ*)L0.f, c.partials, st);
+  }
   HZ_LAUNCHED();
 }
 
@@ -404,8 +413,11 @@ void solve_begin_t(Ctx& c, const double2* q, cudaStream_t user) {
   k_scale_rhs<<<nblk(N, kRedBlock), kRedBlock, 0, s>>>(N, c.wmass, q, c.qhat, c.partials, st, c.opts.tol,
                                                        c.opts.max_iter, c.opts.restart_m);
   HZ_CUDA(cudaMemsetAsync(c.p, 0, sizeof(double2) * N, s));
-  k_true_residual<TZ><<<grid_xy(g), dim3(BX, BY), 0, s>>>(g, invh2, c.diagA64, c.p, c.qhat, c.V, (TZ*)c.L[0].f,
-                                                          c.partials, st);
+  {
+    auto kern = k_true_residual<TZ>;
+    const unsigned G = (unsigned)std::min<long long>(tiles_xy(g), resident_slots((const void*)kern, kRedBlock));
+    kern<<<G, dim3(BX, BY), 0, s>>>(g, invh2, c.diagA64, c.p, c.qhat, c.V, (TZ*)c.L[0].f, c.partials, st);
+  }
   HZ_LAUNCHED();
   c.launches += 2;
   HZ_CUDA(cudaMemcpyAsync(hs, &st->st, sizeof(KrylovStatus), cudaMemcpyDeviceToHost, s));
@@ -466,6 +478,31 @@ void solve_end(Ctx& c, double2* p, hz_info* info, cudaStream_t user) {
 namespace {
 
 }  // namespace
+
+int max_slots() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  (void)cudaGetLastError();
+  return std::max(1, sms) * 8;
+}
+
+int resident_slots(const void* kernel, int threads) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, int> cache;
+  int dev = 0;
+  HZ_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  const auto key = std::make_pair(kernel, dev * 4096 + threads);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  int per_sm = 0, sms = 0;
+  HZ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0));
+  HZ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int slots = std::max(1, std::min(per_sm, 2048 / threads)) * sms;
+  cache[key] = slots;
+  return slots;
+}
 
 // ---- measurement hooks: events around the launches of the selected class
 // (1 = Gram-Schmidt update passes, 2 = the pass with the FP64 operator and the
@@ -547,7 +584,7 @@ size_t krylov_bytes(const hz_grid& g, const hz_opts& o) {
   const size_t vb = o.precision == HZ_PREC_MIXED ? 8 : 16;
   const int m = o.restart_m;
   const long long R = std::max(1, o.nrhs_max);
-  const long long nb = nblk(N * R, kRedBlock) * 2 * R + (long long)m * (nblk(N, BX * BY * kRows) + 1024);
+  const long long nb = nblk(N * R, kRedBlock) * 2 * R + (long long)m * (nblk(N, BX * BY * kRows) + 2048);
   return (16ull * N * (m + 1) + vb * N * m + 16ull * N * 4) * R + 16ull * nb + sizeof(KrylovState) * R;
 }
 
@@ -566,7 +603,7 @@ void krylov_alloc(Ctx& c) {
   // single RHS: the operator pass keeps up to m partials per block (one per
   // inner product), the 1D passes one per block; batched: one per block and
   // RHS (blocks of at least 8 values per thread, see krylov_batch.cu)
-  const long long nb1 = std::max<long long>((long long)grid_blocks(g) * m, nblk(N, kRedBlock));
+  const long long nb1 = std::max<long long>((long long)max_slots() * m, nblk(N, kRedBlock));
   const long long nbR = R > 1 ? R * (nblk(N * R, kRedBlock * 8) + grid_blocks(g) * R) : 0;
   c.partials = (double2*)ctx_alloc(c, sizeof(double2) * std::max(nb1, nbR));
   c.ks = (KrylovState*)ctx_alloc(c, sizeof(KrylovState) * R);

@@ -52,6 +52,20 @@ inline dim3 grid_xy(const Geo& g) {
   return dim3((g.nx + BX - 1) / BX, (g.ny + BY * kRows - 1) / (BY * kRows), g.nz < 8 ? g.nz : 8);
 }
 inline unsigned grid_1d(long long N) { return nblk(N, kRedBlock * kPerThread); }
+
+// Tiles of the persistent stencil passes: 32 x 8 nodes of one z plane (one
+// node per thread), small enough that striding blocks end within one tile of
+// each other.
+inline long long tiles_xy(const Geo& g) {
+  return (long long)((g.nx + BX - 1) / BX) * ((g.ny + BY - 1) / BY) * g.nz;
+}
+// Resident blocks of `threads` threads of `kernel` on the whole device (SMs x
+// blocks per SM, cached per kernel): persistent passes launch at most this
+// many blocks and stride over their tiles, so no partial last wave idles SMs.
+int resident_slots(const void* kernel, int threads);
+// At most this many blocks are launched by a persistent pass (8 blocks of 256
+// threads per SM), which bounds the reduction partials.
+int max_slots();
 inline int grid_blocks(const Geo& g) {
   const dim3 d = grid_xy(g);
   return (int)(d.x * d.y * d.z);
