@@ -40,14 +40,108 @@ struct Geo {
   int nx, ny, nz, sxy, N;     // nodes
   int R, lr;                  // right-hand sides (R = 1 << lr)
   int nxR, sxyR;              // field strides in y and z
+  int lv, nxV;                // each thread handles VR = 1 << lv consecutive RHS; threads per row
 };
-inline Geo geo(const GridDev& g, int R = 1) {
-  int lr = 0;
+inline Geo geo(const GridDev& g, int R = 1, int VR = 1) {
+  int lr = 0, lv = 0;
   while ((1 << lr) < R) ++lr;
+  while ((1 << lv) < VR) ++lv;
   require((1 << lr) == R && R <= 64, "nrhs must be a power of two <= 64");
-  return Geo{g.nx, g.ny, g.nz, g.nx * g.ny, (int)g.N, R, lr, g.nx * R, g.nx * g.ny * R};
+  require((1 << lv) == VR && VR <= R, "bad RHS pack");
+  return Geo{g.nx, g.ny, g.nz, g.nx * g.ny, (int)g.N, R, lr, g.nx * R, g.nx * g.ny * R, lv, (g.nx * R) >> lv};
 }
-inline dim3 grid_of(const Geo& g) { return dim3((g.nxR + BX - 1) / BX, (g.ny + BY - 1) / BY, g.nz); }
+inline dim3 grid_of(const Geo& g) { return dim3((g.nxV + BX - 1) / BX, (g.ny + BY - 1) / BY, g.nz); }
+
+// RHS pack per thread: with many right-hand sides each thread handles VR
+// consecutive ones (32 bytes: 4 complex floats or 2 complex doubles), so a
+// stencil coefficient is loaded once for VR values and the fields move in
+// 16-byte vector accesses.  VR = 1 is the plain complex value.
+template <typename T, int VR>
+struct PkS {
+  c_t<T> v[VR];
+};
+template <typename T, int VR>
+using pk_t = std::conditional_t<VR == 1, c_t<T>, PkS<T, VR>>;
+template <typename T> constexpr int kVRMax = 32 / (int)sizeof(c_t<T>);
+inline int vr_for(int R, int vmax) { return R >= vmax ? vmax : 1; }
+
+// the complex-value versions from namespace hz stay visible beside the pack ones
+using ::hz::cfma;
+using ::hz::cmul;
+using ::hz::operator+;
+using ::hz::operator-;
+using ::hz::operator*;
+
+template <typename T, int VR>
+__device__ __forceinline__ PkS<T, VR> operator+(PkS<T, VR> a, const PkS<T, VR>& b) {
+#pragma unroll
+  for (int i = 0; i < VR; ++i) a.v[i] = a.v[i] + b.v[i];
+  return a;
+}
+template <typename T, int VR>
+__device__ __forceinline__ PkS<T, VR> operator-(PkS<T, VR> a, const PkS<T, VR>& b) {
+#pragma unroll
+  for (int i = 0; i < VR; ++i) a.v[i] = a.v[i] - b.v[i];
+  return a;
+}
+template <typename T, int VR>
+__device__ __forceinline__ PkS<T, VR> operator*(T s, PkS<T, VR> a) {
+#pragma unroll
+  for (int i = 0; i < VR; ++i) a.v[i] = s * a.v[i];
+  return a;
+}
+template <typename T, int VR>
+__device__ __forceinline__ PkS<T, VR> cmul(c_t<T> c, PkS<T, VR> a) {
+#pragma unroll
+  for (int i = 0; i < VR; ++i) a.v[i] = cmul(c, a.v[i]);
+  return a;
+}
+template <typename T, int VR>
+__device__ __forceinline__ PkS<T, VR> cfma(c_t<T> c, const PkS<T, VR>& a, PkS<T, VR> acc) {
+#pragma unroll
+  for (int i = 0; i < VR; ++i) acc.v[i] = cfma(c, a.v[i], acc.v[i]);
+  return acc;
+}
+template <typename V>
+__device__ __forceinline__ V pk_zero() {
+  V z;
+  if constexpr (std::is_same<V, float2>::value || std::is_same<V, double2>::value) {
+    z.x = 0;
+    z.y = 0;
+  } else {
+#pragma unroll
+    for (int i = 0; i < (int)(sizeof(V) / sizeof(z.v[0])); ++i) {
+      z.v[i].x = 0;
+      z.v[i].y = 0;
+    }
+  }
+  return z;
+}
+// pack load / store at field index q (q a multiple of VR: 16-byte aligned chunks)
+template <typename T, int VR>
+__device__ __forceinline__ pk_t<T, VR> ldp(const c_t<T>* a, int q) {
+  if constexpr (VR == 1) {
+    return a[q];
+  } else {
+    PkS<T, VR> r;
+    const uint4* src = reinterpret_cast<const uint4*>(a + q);
+    uint4* dst = reinterpret_cast<uint4*>(&r);
+#pragma unroll
+    for (int i = 0; i < (int)(sizeof(r) / 16); ++i) dst[i] = src[i];
+    return r;
+  }
+}
+template <typename T, int VR>
+__device__ __forceinline__ void stp(c_t<T>* a, int q, const pk_t<T, VR>& v) {
+  if constexpr (VR == 1) {
+    a[q] = v;
+  } else {
+    uint4* dst = reinterpret_cast<uint4*>(a + q);
+    const uint4* src = reinterpret_cast<const uint4*>(&v);
+#pragma unroll
+    for (int i = 0; i < (int)(sizeof(v) / 16); ++i) dst[i] = src[i];
+  }
+}
 inline unsigned nblk(long long n, int b) { return (unsigned)((n + b - 1) / b); }
 
 // Offsets of an assembled Vanka sum with their flat index offsets on one level.
@@ -74,18 +168,19 @@ __device__ __forceinline__ bool node_xyz(const Geo& g, int& x, int& y, int& z, i
   const int X = blockIdx.x * BX + threadIdx.x;
   y = blockIdx.y * BY + threadIdx.y;
   z = blockIdx.z;
-  if (X >= g.nxR || y >= g.ny) return false;
-  x = X >> g.lr;
+  if (X >= g.nxV || y >= g.ny) return false;
+  x = X >> (g.lr - g.lv);
   const int row = z * g.ny + y;
   p = row * g.nx + x;
-  q = row * g.nxR + X;
+  q = row * g.nxR + (X << g.lv);
   return true;
 }
 
 // true when every node of this block and its neighbours within r lie in the grid
 template <int DIM>
 __device__ __forceinline__ bool interior_block(const Geo& g, int r) {
-  const int x0 = (blockIdx.x * BX) >> g.lr, x1 = (blockIdx.x * BX + BX - 1) >> g.lr, y0 = blockIdx.y * BY;
+  const int x0 = (blockIdx.x * BX) >> (g.lr - g.lv), x1 = (blockIdx.x * BX + BX - 1) >> (g.lr - g.lv);
+  const int y0 = blockIdx.y * BY;
   bool ok = x0 >= r && x1 + r < g.nx && y0 >= r && y0 + BY - 1 + r < g.ny;
   if (DIM == 3) ok = ok && (int)blockIdx.z >= r && (int)blockIdx.z + r < g.nz;
   return ok;
@@ -98,47 +193,45 @@ __device__ __forceinline__ V scale(V a, decltype(a.x) s) {
   return a;
 }
 
+// The stencil helpers work on the value type of `ld` (a complex value, or a
+// pack of VR right-hand sides sharing the node's coefficients).
+
 // A u at node p for the fine 5-/7-point operator (diag d at p).
 template <typename T, int DIM, bool CHECK, typename LD>
-__device__ __forceinline__ c_t<T> fine_Au(const Geo& g, T invh2, c_t<T> d, const LD& ld, int q, int x, int y,
-                                          int z) {
-  using V = c_t<T>;
+__device__ __forceinline__ auto fine_Au(const Geo& g, T invh2, c_t<T> d, const LD& ld, int q, int x, int y, int z) {
+  using V = decltype(ld(0));
   V acc = cmul(d, ld(q));
   if (!CHECK) {
     V s = ld(q - g.R) + ld(q + g.R) + ld(q - g.nxR) + ld(q + g.nxR);
     if (DIM == 3) s = s + ld(q - g.sxyR) + ld(q + g.sxyR);
-    acc.x -= invh2 * s.x;
-    acc.y -= invh2 * s.y;
-    return acc;
+    return acc - invh2 * s;
   }
   const T wx = (x == 0 || x == g.nx - 1) ? T(0.5) : T(1);
   const T wy = (y == 0 || y == g.ny - 1) ? T(0.5) : T(1);
   const T wz = (DIM == 3 && (z == 0 || z == g.nz - 1)) ? T(0.5) : T(1);
-  V sx = cmk<V>(0, 0), sy = cmk<V>(0, 0);
+  V sx = pk_zero<V>(), sy = pk_zero<V>();
   if (x > 0) sx = sx + ld(q - g.R);
   if (x < g.nx - 1) sx = sx + ld(q + g.R);
   if (y > 0) sy = sy + ld(q - g.nxR);
   if (y < g.ny - 1) sy = sy + ld(q + g.nxR);
   const T cx = wy * wz * invh2, cy = wx * wz * invh2;
-  acc.x -= cx * sx.x + cy * sy.x;
-  acc.y -= cx * sx.y + cy * sy.y;
+  acc = acc - (cx * sx + cy * sy);
   if (DIM == 3) {
-    V sz = cmk<V>(0, 0);
+    V sz = pk_zero<V>();
     if (z > 0) sz = sz + ld(q - g.sxyR);
     if (z < g.nz - 1) sz = sz + ld(q + g.sxyR);
     const T cz = wx * wy * invh2;
-    acc.x -= cz * sz.x;
-    acc.y -= cz * sz.y;
+    acc = acc - cz * sz;
   }
   return acc;
 }
 
 // A u at node p for a stored box stencil of radius RHO (planes [s][N]).
 template <typename T, int DIM, int RHO, bool CHECK, typename LD>
-__device__ __forceinline__ c_t<T> box_Au(const Geo& g, const c_t<T>* __restrict__ P, const LD& ld, int p, int q,
-                                         int x, int y, int z) {
-  using V = c_t<T>;
-  V acc = cmk<V>(0, 0);
+__device__ __forceinline__ auto box_Au(const Geo& g, const c_t<T>* __restrict__ P, const LD& ld, int p, int q, int x,
+                                       int y, int z) {
+  using V = decltype(ld(0));
+  V acc = pk_zero<V>();
   constexpr int RZ = DIM == 3 ? RHO : 0;
   constexpr int W = 2 * RHO + 1;
 #pragma unroll
@@ -159,8 +252,8 @@ __device__ __forceinline__ c_t<T> box_Au(const Geo& g, const c_t<T>* __restrict_
 
 // AK = 0: fine analytic operator; AK = rho > 0: stored box stencil.
 template <typename T, int DIM, int AK, bool CHECK, typename LD>
-__device__ __forceinline__ c_t<T> apply_A(const Geo& g, T invh2, const c_t<T>* __restrict__ A, const LD& ld, int p,
-                                          int q, int x, int y, int z) {
+__device__ __forceinline__ auto apply_A(const Geo& g, T invh2, const c_t<T>* __restrict__ A, const LD& ld, int p, int q,
+                                        int x, int y, int z) {
   if constexpr (AK == 0)
     return fine_Au<T, DIM, CHECK>(g, invh2, A[p], ld, q, x, y, z);
   else
@@ -168,10 +261,10 @@ __device__ __forceinline__ c_t<T> apply_A(const Geo& g, T invh2, const c_t<T>* _
 }
 
 template <typename T, int DIM, bool CHECK, typename LD>
-__device__ __forceinline__ c_t<T> list_Au(const Geo& g, const MList& m, const c_t<T>* __restrict__ P, const LD& ld,
-                                          int p, int q, int x, int y, int z) {
-  using V = c_t<T>;
-  V acc = cmk<V>(0, 0);
+__device__ __forceinline__ auto list_Au(const Geo& g, const MList& m, const c_t<T>* __restrict__ P, const LD& ld, int p,
+                                        int q, int x, int y, int z) {
+  using V = decltype(ld(0));
+  V acc = pk_zero<V>();
   for (int s = 0; s < m.n; ++s) {
     if (CHECK) {
       const int xx = x + m.d[s][0], yy = y + m.d[s][1], zz = z + m.d[s][2];
@@ -186,7 +279,7 @@ __device__ __forceinline__ c_t<T> list_Au(const Geo& g, const MList& m, const c_
 // ------------------------------------------------------------------ kernels
 
 // r = f - A u
-template <typename T, int DIM, int AK>
+template <typename T, int DIM, int AK, int VR>
 __global__ void __launch_bounds__(BX* BY) k_resid(Geo g, T invh2, const c_t<T>* __restrict__ A,
                                                   const c_t<T>* __restrict__ u, const c_t<T>* __restrict__ f,
                                                   c_t<T>* __restrict__ r, const int* active) {
@@ -195,14 +288,14 @@ __global__ void __launch_bounds__(BX* BY) k_resid(Geo g, T invh2, const c_t<T>* 
   const bool in = interior_block<DIM>(g, RA);
   int x, y, z, p, q;
   if (!node_xyz(g, x, y, z, p, q)) return;
-  auto ld = [u](int i) { return u[i]; };
-  const c_t<T> a = in ? apply_A<T, DIM, AK, false>(g, invh2, A, ld, p, q, x, y, z)
-                      : apply_A<T, DIM, AK, true>(g, invh2, A, ld, p, q, x, y, z);
-  r[q] = f[q] - a;
+  auto ld = [u](int i) { return ldp<T, VR>(u, i); };
+  const pk_t<T, VR> a = in ? apply_A<T, DIM, AK, false>(g, invh2, A, ld, p, q, x, y, z)
+                           : apply_A<T, DIM, AK, true>(g, invh2, A, ld, p, q, x, y, z);
+  stp<T, VR>(r, q, ldp<T, VR>(f, q) - a);
 }
 
 // u = w M f  (first sweep from u = 0)
-template <typename T, int DIM>
+template <typename T, int DIM, int VR>
 __global__ void __launch_bounds__(BX* BY) k_sweep0(Geo g, MList m, const c_t<T>* __restrict__ M, T w,
                                                    const c_t<T>* __restrict__ f, c_t<T>* __restrict__ u,
                                                    const int* active) {
@@ -210,14 +303,14 @@ __global__ void __launch_bounds__(BX* BY) k_sweep0(Geo g, MList m, const c_t<T>*
   const bool in = interior_block<DIM>(g, m.rho);
   int x, y, z, p, q;
   if (!node_xyz(g, x, y, z, p, q)) return;
-  auto ld = [f](int i) { return f[i]; };
-  const c_t<T> v = in ? list_Au<T, DIM, false>(g, m, M, ld, p, q, x, y, z)
-                      : list_Au<T, DIM, true>(g, m, M, ld, p, q, x, y, z);
-  u[q] = scale(v, w);
+  auto ld = [f](int i) { return ldp<T, VR>(f, i); };
+  const pk_t<T, VR> v = in ? list_Au<T, DIM, false>(g, m, M, ld, p, q, x, y, z)
+                           : list_Au<T, DIM, true>(g, m, M, ld, p, q, x, y, z);
+  stp<T, VR>(u, q, w * v);
 }
 
 // diagonal M: u = w m0 f and r = f - A u in one pass
-template <typename T, int DIM, int AK>
+template <typename T, int DIM, int AK, int VR>
 __global__ void __launch_bounds__(BX* BY) k_sweep0_resid_diag(Geo g, T invh2, const c_t<T>* __restrict__ A,
                                                               const c_t<T>* __restrict__ m0, T w,
                                                               const c_t<T>* __restrict__ f, c_t<T>* __restrict__ u,
@@ -228,16 +321,16 @@ __global__ void __launch_bounds__(BX* BY) k_sweep0_resid_diag(Geo g, T invh2, co
   int x, y, z, p, q;
   if (!node_xyz(g, x, y, z, p, q)) return;
   const int lr = g.lr;
-  auto ld = [m0, f, w, lr](int i) { return scale(cmul(m0[i >> lr], f[i]), w); };
-  const c_t<T> a = in ? apply_A<T, DIM, AK, false>(g, invh2, A, ld, p, q, x, y, z)
-                      : apply_A<T, DIM, AK, true>(g, invh2, A, ld, p, q, x, y, z);
-  const c_t<T> fp = f[q];
-  u[q] = scale(cmul(m0[p], fp), w);
-  r[q] = fp - a;
+  auto ld = [m0, f, w, lr](int i) { return w * cmul(m0[i >> lr], ldp<T, VR>(f, i)); };
+  const pk_t<T, VR> a = in ? apply_A<T, DIM, AK, false>(g, invh2, A, ld, p, q, x, y, z)
+                           : apply_A<T, DIM, AK, true>(g, invh2, A, ld, p, q, x, y, z);
+  const pk_t<T, VR> fp = ldp<T, VR>(f, q);
+  stp<T, VR>(u, q, w * cmul(m0[p], fp));
+  stp<T, VR>(r, q, fp - a);
 }
 
 // out = in + w M r  (out may alias in)
-template <typename T, int DIM>
+template <typename T, int DIM, int VR>
 __global__ void __launch_bounds__(BX* BY) k_sweep_out(Geo g, MList m, const c_t<T>* __restrict__ M, T w,
                                                       const c_t<T>* __restrict__ r, const c_t<T>* in, c_t<T>* out,
                                                       const int* active) {
@@ -245,14 +338,14 @@ __global__ void __launch_bounds__(BX* BY) k_sweep_out(Geo g, MList m, const c_t<
   const bool inb = interior_block<DIM>(g, m.rho);
   int x, y, z, p, q;
   if (!node_xyz(g, x, y, z, p, q)) return;
-  auto ld = [r](int i) { return r[i]; };
-  const c_t<T> v = inb ? list_Au<T, DIM, false>(g, m, M, ld, p, q, x, y, z)
-                       : list_Au<T, DIM, true>(g, m, M, ld, p, q, x, y, z);
-  out[q] = in[q] + scale(v, w);
+  auto ld = [r](int i) { return ldp<T, VR>(r, i); };
+  const pk_t<T, VR> v = inb ? list_Au<T, DIM, false>(g, m, M, ld, p, q, x, y, z)
+                            : list_Au<T, DIM, true>(g, m, M, ld, p, q, x, y, z);
+  stp<T, VR>(out, q, ldp<T, VR>(in, q) + w * v);
 }
 
 // diagonal M: out = in + w m0 (f - A in)   (out != in)
-template <typename T, int DIM, int AK>
+template <typename T, int DIM, int AK, int VR>
 __global__ void __launch_bounds__(BX* BY) k_resid_sweep_diag(Geo g, T invh2, const c_t<T>* __restrict__ A,
                                                              const c_t<T>* __restrict__ m0, T w,
                                                              const c_t<T>* __restrict__ f, const c_t<T>* __restrict__ in,
@@ -262,10 +355,10 @@ __global__ void __launch_bounds__(BX* BY) k_resid_sweep_diag(Geo g, T invh2, con
   const bool inb = interior_block<DIM>(g, RA);
   int x, y, z, p, q;
   if (!node_xyz(g, x, y, z, p, q)) return;
-  auto ld = [in](int i) { return in[i]; };
-  const c_t<T> a = inb ? apply_A<T, DIM, AK, false>(g, invh2, A, ld, p, q, x, y, z)
-                       : apply_A<T, DIM, AK, true>(g, invh2, A, ld, p, q, x, y, z);
-  out[q] = in[q] + scale(cmul(m0[p], f[q] - a), w);
+  auto ld = [in](int i) { return ldp<T, VR>(in, i); };
+  const pk_t<T, VR> a = inb ? apply_A<T, DIM, AK, false>(g, invh2, A, ld, p, q, x, y, z)
+                            : apply_A<T, DIM, AK, true>(g, invh2, A, ld, p, q, x, y, z);
+  stp<T, VR>(out, q, ldp<T, VR>(in, q) + w * cmul(m0[p], ldp<T, VR>(f, q) - a));
 }
 
 // 1D prolongation weight P(j, J) in single precision (the same exact dyadic
@@ -281,8 +374,8 @@ __device__ __forceinline__ float p1f(int kind, int nf, int nc, int j, int J) {
   return w;
 }
 
-// f_c = R r, one thread per coarse node
-template <typename T, int DIM, int KIND>
+// f_c = R r, one thread per coarse node (and RHS pack)
+template <typename T, int DIM, int KIND, int VR>
 __global__ void __launch_bounds__(BX* BY) k_restrict(Geo gf, Geo gc, const c_t<T>* __restrict__ r,
                                                      c_t<T>* __restrict__ fc, const int* active) {
   if (active && !*active) return;
@@ -303,7 +396,7 @@ __global__ void __launch_bounds__(BX* BY) k_restrict(Geo gf, Geo gc, const c_t<T
     const int iz = 2 * Z - RZ + k;
     wz[k] = DIM == 3 ? ((iz >= 0 && iz < gf.nz) ? (T)(0.5f * p1f(KIND, gf.nz, gc.nz, iz, Z)) : T(0)) : T(1);
   }
-  c_t<T> acc = cmk<c_t<T>>(0, 0);
+  pk_t<T, VR> acc = pk_zero<pk_t<T, VR>>();
 #pragma unroll
   for (int kz = 0; kz <= 2 * RZ; ++kz) {
     if (wz[kz] == T(0)) continue;
@@ -316,14 +409,11 @@ __global__ void __launch_bounds__(BX* BY) k_restrict(Geo gf, Geo gc, const c_t<T
 #pragma unroll
       for (int kx = 0; kx <= 2 * RAD; ++kx) {
         if (wx[kx] == T(0)) continue;
-        const c_t<T> v = r[row + kx * gf.R];
-        const T ww = wyz * wx[kx];
-        acc.x += ww * v.x;
-        acc.y += ww * v.y;
+        acc = acc + (wyz * wx[kx]) * ldp<T, VR>(r, row + kx * gf.R);
       }
     }
   }
-  fc[qc] = acc;
+  stp<T, VR>(fc, qc, acc);
 }
 
 // 1D prolongation stencil of fine index j: coarse nodes J0, J0+1, J0+2 with
@@ -353,15 +443,15 @@ __device__ __forceinline__ int p1_stencil(int j, int nf, int nc, float (&w)[3]) 
   return J - 1;
 }
 
-// (P e_c) at fine node (x, y, z)
-template <typename T, int DIM, int KIND>
-__device__ __forceinline__ c_t<T> prolong_at(const Geo& gf, const Geo& gc, const c_t<T>* __restrict__ ec, int x, int y,
-                                             int z, int rr = 0) {
+// (P e_c) at fine node (x, y, z), RHS pack starting at rr
+template <typename T, int DIM, int KIND, int VR = 1>
+__device__ __forceinline__ pk_t<T, VR> prolong_at(const Geo& gf, const Geo& gc, const c_t<T>* __restrict__ ec, int x,
+                                                  int y, int z, int rr = 0) {
   float wx[3], wy[3], wz[3] = {1.0f, 0.0f, 0.0f};
   const int X0 = p1_stencil<KIND>(x, gf.nx, gc.nx, wx);
   const int Y0 = p1_stencil<KIND>(y, gf.ny, gc.ny, wy);
   const int Z0 = DIM == 3 ? p1_stencil<KIND>(z, gf.nz, gc.nz, wz) : 0;
-  c_t<T> acc = cmk<c_t<T>>(0, 0);
+  pk_t<T, VR> acc = pk_zero<pk_t<T, VR>>();
 #pragma unroll
   for (int c = 0; c < (DIM == 3 ? 3 : 1); ++c) {
     if (wz[c] == 0.0f) continue;
@@ -373,10 +463,7 @@ __device__ __forceinline__ c_t<T> prolong_at(const Geo& gf, const Geo& gc, const
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         if (wx[a] == 0.0f) continue;
-        const T w3 = (T)(wyz * wx[a]);
-        const c_t<T> v = ec[row + a * gc.R];
-        acc.x += w3 * v.x;
-        acc.y += w3 * v.y;
+        acc = acc + (T)(wyz * wx[a]) * ldp<T, VR>(ec, row + a * gc.R);
       }
     }
   }
@@ -384,13 +471,13 @@ __device__ __forceinline__ c_t<T> prolong_at(const Geo& gf, const Geo& gc, const
 }
 
 // out = in + P e_c (pointwise; out may alias in)
-template <typename T, int DIM, int KIND>
+template <typename T, int DIM, int KIND, int VR>
 __global__ void __launch_bounds__(BX* BY) k_prolong(Geo gf, Geo gc, const c_t<T>* __restrict__ ec, const c_t<T>* in,
                                                     c_t<T>* out, const int* active) {
   if (active && !*active) return;
   int x, y, z, p, q;
   if (!node_xyz(gf, x, y, z, p, q)) return;
-  out[q] = in[q] + prolong_at<T, DIM, KIND>(gf, gc, ec, x, y, z, q & (gf.R - 1));
+  stp<T, VR>(out, q, ldp<T, VR>(in, q) + prolong_at<T, DIM, KIND, VR>(gf, gc, ec, x, y, z, q & (gf.R - 1)));
 }
 
 // 2D: u' = t + P e_c on a tile with halo RA in shared memory, then
@@ -468,24 +555,57 @@ __global__ void k_dense_gemv(int n, const c_t<T>* __restrict__ A, const c_t<T>* 
   if (lane == 0) u[warp] = acc;
 }
 
-// u[i][r] = sum_j Ainv[i][j] f[j][r] for R right-hand sides: one block per row,
-// one thread per right-hand side, the row staged through shared memory
+// u[i][r] = sum_j Ainv[i][j] f[j][r] for R >= 8 right-hand sides (a plain
+// complex GEMM): 256 threads per block, each computing rows i0, i0+1 of one
+// RHS; a block covers TM = 512/R <= 64 rows x all R right-hand sides.  K is
+// walked in chunks (32 complex floats / 16 complex doubles): the chunk of the
+// block's Ainv rows and of f are staged in shared memory, then every thread
+// does two complex FMAs per staged column, in a fixed order.
 template <typename T>
-__global__ void k_dense_gemm_rhs(int n, int R, const c_t<T>* __restrict__ A, const c_t<T>* __restrict__ f,
-                                 c_t<T>* __restrict__ u, const int* active) {
+__global__ void __launch_bounds__(256) k_dense_gemm_rhs(int n, int R, const c_t<T>* __restrict__ A,
+                                                        const c_t<T>* __restrict__ f, c_t<T>* __restrict__ u,
+                                                        const int* active) {
   if (active && !*active) return;
-  __shared__ c_t<T> row[256];
-  const int i = blockIdx.x, r = threadIdx.x;
-  c_t<T> acc = cmk<c_t<T>>(0, 0);
-  for (int j0 = 0; j0 < n; j0 += 256) {
+  constexpr int KC = sizeof(T) == 4 ? 32 : 16;
+  __shared__ c_t<T> As[64][KC + 1];
+  __shared__ c_t<T> Fs[KC * 64];
+  const int TM = 512 / R;
+  const int tid = threadIdx.x;
+  const int rhs = tid & (R - 1), rg = tid / R;
+  const int row0 = blockIdx.x * TM;
+  const int i0 = row0 + 2 * rg, i1 = i0 + 1;
+  c_t<T> acc0 = cmk<c_t<T>>(0, 0), acc1 = cmk<c_t<T>>(0, 0);
+  for (int k0 = 0; k0 < n; k0 += KC) {
+    const int kc = min(KC, n - k0);
     __syncthreads();
-    for (int k = threadIdx.x; k < 256 && j0 + k < n; k += blockDim.x) row[k] = A[(long long)i * n + j0 + k];
+    for (int e = tid; e < TM * KC; e += 256) {
+      const int r = e / KC, k = e - r * KC;
+      As[r][k] = (row0 + r < n && k < kc) ? A[(long long)(row0 + r) * n + k0 + k] : cmk<c_t<T>>(0, 0);
+    }
+    for (int e = tid; e < KC * R; e += 256) Fs[e] = (e / R < kc) ? f[(long long)k0 * R + e] : cmk<c_t<T>>(0, 0);
     __syncthreads();
-    const int jn = min(256, n - j0);
-    if (r < R)
-      for (int k = 0; k < jn; ++k) acc = cfma(row[k], f[(j0 + k) * R + r], acc);
+#pragma unroll 8
+    for (int k = 0; k < KC; ++k) {
+      const c_t<T> fv = Fs[k * R + rhs];
+      acc0 = cfma(As[2 * rg][k], fv, acc0);
+      acc1 = cfma(As[2 * rg + 1][k], fv, acc1);
+    }
   }
-  if (r < R) u[i * R + r] = acc;
+  if (i0 < n) u[(long long)i0 * R + rhs] = acc0;
+  if (i1 < n) u[(long long)i1 * R + rhs] = acc1;
+}
+
+// the same product for R = 2 or 4: one block per row, one thread per RHS
+template <typename T>
+__global__ void k_dense_gemm_rhs_small(int n, int R, const c_t<T>* __restrict__ A, const c_t<T>* __restrict__ f,
+                                       c_t<T>* __restrict__ u, const int* active) {
+  if (active && !*active) return;
+  const int i = blockIdx.x, r = threadIdx.x;
+  if (r >= R) return;
+  c_t<T> acc = cmk<c_t<T>>(0, 0);
+  const c_t<T>* row = A + (long long)i * n;
+  for (int j = 0; j < n; ++j) acc = cfma(row[j], f[(long long)j * R + r], acc);
+  u[(long long)i * R + r] = acc;
 }
 
 // ------------------------------------------------------------------ dispatch
@@ -500,14 +620,25 @@ void with_dim_ak(int dim, int ak, F&& f) {
 
 inline int akind(const Level& L) { return L.fine ? 0 : L.A.off.rho; }
 
+// RHS pack width for nrhs right-hand sides: 32 bytes per thread once there
+// are enough of them, else one value
+template <typename T, typename F>
+void with_vr(int nrhs, F&& f) {
+  if (vr_for(nrhs, kVRMax<T>) == kVRMax<T>) f(std::integral_constant<int, kVRMax<T>>{});
+  else f(std::integral_constant<int, 1>{});
+}
+
 template <typename T>
 void resid(Ctx& c, int l, const void* u, const void* f, void* r, const int* active, cudaStream_t s) {
   Level& L = c.L[l];
-  const Geo g = geo(L.g, c.nrhs);
   const T invh2 = (T)(1.0 / (c.h * c.h));
-  with_dim_ak(L.g.dim, akind(L), [&](auto D, auto K) {
-    k_resid<T, D, K><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, invh2, (const c_t<T>*)L.Aw, (const c_t<T>*)u,
-                                                         (const c_t<T>*)f, (c_t<T>*)r, active);
+  with_vr<T>(c.nrhs, [&](auto V) {
+    constexpr int VR = decltype(V)::value;
+    const Geo g = geo(L.g, c.nrhs, VR);
+    with_dim_ak(L.g.dim, akind(L), [&](auto D, auto K) {
+      k_resid<T, D, K, VR><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, invh2, (const c_t<T>*)L.Aw, (const c_t<T>*)u,
+                                                               (const c_t<T>*)f, (c_t<T>*)r, active);
+    });
   });
   HZ_LAUNCHED();
 }
@@ -515,40 +646,51 @@ void resid(Ctx& c, int l, const void* u, const void* f, void* r, const int* acti
 template <typename T>
 void sweep_out(Ctx& c, int l, const void* r, const void* in, void* out, const int* active, cudaStream_t s) {
   Level& L = c.L[l];
-  const Geo g = geo(L.g, c.nrhs);
   const MList m = mlist(L, c.nrhs);
-  if (L.g.dim == 2)
-    k_sweep_out<T, 2><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, m, (const c_t<T>*)L.Mw, (T)L.damping,
-                                                          (const c_t<T>*)r, (const c_t<T>*)in, (c_t<T>*)out, active);
-  else
-    k_sweep_out<T, 3><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, m, (const c_t<T>*)L.Mw, (T)L.damping,
-                                                          (const c_t<T>*)r, (const c_t<T>*)in, (c_t<T>*)out, active);
+  with_vr<T>(c.nrhs, [&](auto V) {
+    constexpr int VR = decltype(V)::value;
+    const Geo g = geo(L.g, c.nrhs, VR);
+    if (L.g.dim == 2)
+      k_sweep_out<T, 2, VR><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, m, (const c_t<T>*)L.Mw, (T)L.damping,
+                                                                (const c_t<T>*)r, (const c_t<T>*)in, (c_t<T>*)out,
+                                                                active);
+    else
+      k_sweep_out<T, 3, VR><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, m, (const c_t<T>*)L.Mw, (T)L.damping,
+                                                                (const c_t<T>*)r, (const c_t<T>*)in, (c_t<T>*)out,
+                                                                active);
+  });
   HZ_LAUNCHED();
 }
 
 template <typename T>
 void sweep0(Ctx& c, int l, const void* f, void* u, const int* active, cudaStream_t s) {
   Level& L = c.L[l];
-  const Geo g = geo(L.g, c.nrhs);
   const MList m = mlist(L, c.nrhs);
-  if (L.g.dim == 2)
-    k_sweep0<T, 2><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, m, (const c_t<T>*)L.Mw, (T)L.damping, (const c_t<T>*)f,
-                                                       (c_t<T>*)u, active);
-  else
-    k_sweep0<T, 3><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, m, (const c_t<T>*)L.Mw, (T)L.damping, (const c_t<T>*)f,
-                                                       (c_t<T>*)u, active);
+  with_vr<T>(c.nrhs, [&](auto V) {
+    constexpr int VR = decltype(V)::value;
+    const Geo g = geo(L.g, c.nrhs, VR);
+    if (L.g.dim == 2)
+      k_sweep0<T, 2, VR><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, m, (const c_t<T>*)L.Mw, (T)L.damping,
+                                                             (const c_t<T>*)f, (c_t<T>*)u, active);
+    else
+      k_sweep0<T, 3, VR><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, m, (const c_t<T>*)L.Mw, (T)L.damping,
+                                                             (const c_t<T>*)f, (c_t<T>*)u, active);
+  });
   HZ_LAUNCHED();
 }
 
 template <typename T>
 void sweep0_resid_diag(Ctx& c, int l, const void* f, void* u, void* r, const int* active, cudaStream_t s) {
   Level& L = c.L[l];
-  const Geo g = geo(L.g, c.nrhs);
   const T invh2 = (T)(1.0 / (c.h * c.h));
-  with_dim_ak(L.g.dim, akind(L), [&](auto D, auto K) {
-    k_sweep0_resid_diag<T, D, K><<<grid_of(g), dim3(BX, BY), 0, s>>>(
-        g, invh2, (const c_t<T>*)L.Aw, (const c_t<T>*)L.Mw, (T)L.damping, (const c_t<T>*)f, (c_t<T>*)u, (c_t<T>*)r,
-        active);
+  with_vr<T>(c.nrhs, [&](auto V) {
+    constexpr int VR = decltype(V)::value;
+    const Geo g = geo(L.g, c.nrhs, VR);
+    with_dim_ak(L.g.dim, akind(L), [&](auto D, auto K) {
+      k_sweep0_resid_diag<T, D, K, VR><<<grid_of(g), dim3(BX, BY), 0, s>>>(
+          g, invh2, (const c_t<T>*)L.Aw, (const c_t<T>*)L.Mw, (T)L.damping, (const c_t<T>*)f, (c_t<T>*)u,
+          (c_t<T>*)r, active);
+    });
   });
   HZ_LAUNCHED();
 }
@@ -556,12 +698,15 @@ void sweep0_resid_diag(Ctx& c, int l, const void* f, void* u, void* r, const int
 template <typename T>
 void resid_sweep_diag(Ctx& c, int l, const void* f, const void* in, void* out, const int* active, cudaStream_t s) {
   Level& L = c.L[l];
-  const Geo g = geo(L.g, c.nrhs);
   const T invh2 = (T)(1.0 / (c.h * c.h));
-  with_dim_ak(L.g.dim, akind(L), [&](auto D, auto K) {
-    k_resid_sweep_diag<T, D, K><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, invh2, (const c_t<T>*)L.Aw,
-                                                                    (const c_t<T>*)L.Mw, (T)L.damping, (const c_t<T>*)f,
-                                                                    (const c_t<T>*)in, (c_t<T>*)out, active);
+  with_vr<T>(c.nrhs, [&](auto V) {
+    constexpr int VR = decltype(V)::value;
+    const Geo g = geo(L.g, c.nrhs, VR);
+    with_dim_ak(L.g.dim, akind(L), [&](auto D, auto K) {
+      k_resid_sweep_diag<T, D, K, VR><<<grid_of(g), dim3(BX, BY), 0, s>>>(
+          g, invh2, (const c_t<T>*)L.Aw, (const c_t<T>*)L.Mw, (T)L.damping, (const c_t<T>*)f, (const c_t<T>*)in,
+          (c_t<T>*)out, active);
+    });
   });
   HZ_LAUNCHED();
 }
@@ -570,16 +715,20 @@ template <typename T>
 void restrict_t(Ctx& c, int l, const void* r, void* fc, const int* active, cudaStream_t s) {
   Level& L = c.L[l];
   Level& C = c.L[l + 1];
-  const Geo gf = geo(L.g, c.nrhs), gc = geo(C.g, c.nrhs);
-  auto go = [&](auto D, auto KIND) {
-    k_restrict<T, D, KIND><<<grid_of(gc), dim3(BX, BY), 0, s>>>(gf, gc, (const c_t<T>*)r, (c_t<T>*)fc, active);
-  };
-  using I2 = std::integral_constant<int, 2>;
-  using I3 = std::integral_constant<int, 3>;
-  using K0 = std::integral_constant<int, 0>;
-  using K1 = std::integral_constant<int, 1>;
-  if (L.g.dim == 2) L.rkind ? go(I2{}, K1{}) : go(I2{}, K0{});
-  else L.rkind ? go(I3{}, K1{}) : go(I3{}, K0{});
+  with_vr<T>(c.nrhs, [&](auto V) {
+    constexpr int VR = decltype(V)::value;
+    const Geo gf = geo(L.g, c.nrhs, VR), gc = geo(C.g, c.nrhs, VR);
+    auto go = [&](auto D, auto KIND) {
+      k_restrict<T, D, KIND, VR><<<grid_of(gc), dim3(BX, BY), 0, s>>>(gf, gc, (const c_t<T>*)r, (c_t<T>*)fc,
+                                                                      active);
+    };
+    using I2 = std::integral_constant<int, 2>;
+    using I3 = std::integral_constant<int, 3>;
+    using K0 = std::integral_constant<int, 0>;
+    using K1 = std::integral_constant<int, 1>;
+    if (L.g.dim == 2) L.rkind ? go(I2{}, K1{}) : go(I2{}, K0{});
+    else L.rkind ? go(I3{}, K1{}) : go(I3{}, K0{});
+  });
   HZ_LAUNCHED();
 }
 
@@ -587,17 +736,20 @@ template <typename T>
 void prolong_t(Ctx& c, int l, const void* ec, const void* in, void* out, const int* active, cudaStream_t s) {
   Level& L = c.L[l];
   Level& C = c.L[l + 1];
-  const Geo gf = geo(L.g, c.nrhs), gc = geo(C.g, c.nrhs);
-  auto go = [&](auto D, auto KIND) {
-    k_prolong<T, D, KIND><<<grid_of(gf), dim3(BX, BY), 0, s>>>(gf, gc, (const c_t<T>*)ec, (const c_t<T>*)in,
-                                                              (c_t<T>*)out, active);
-  };
-  using I2 = std::integral_constant<int, 2>;
-  using I3 = std::integral_constant<int, 3>;
-  using K0 = std::integral_constant<int, 0>;
-  using K1 = std::integral_constant<int, 1>;
-  if (L.g.dim == 2) L.pkind ? go(I2{}, K1{}) : go(I2{}, K0{});
-  else L.pkind ? go(I3{}, K1{}) : go(I3{}, K0{});
+  with_vr<T>(c.nrhs, [&](auto V) {
+    constexpr int VR = decltype(V)::value;
+    const Geo gf = geo(L.g, c.nrhs, VR), gc = geo(C.g, c.nrhs, VR);
+    auto go = [&](auto D, auto KIND) {
+      k_prolong<T, D, KIND, VR><<<grid_of(gf), dim3(BX, BY), 0, s>>>(gf, gc, (const c_t<T>*)ec, (const c_t<T>*)in,
+                                                                     (c_t<T>*)out, active);
+    };
+    using I2 = std::integral_constant<int, 2>;
+    using I3 = std::integral_constant<int, 3>;
+    using K0 = std::integral_constant<int, 0>;
+    using K1 = std::integral_constant<int, 1>;
+    if (L.g.dim == 2) L.pkind ? go(I2{}, K1{}) : go(I2{}, K0{});
+    else L.pkind ? go(I3{}, K1{}) : go(I3{}, K0{});
+  });
   HZ_LAUNCHED();
 }
 
@@ -635,8 +787,12 @@ void coarse_t(Ctx& c, const void* f, void* u, const int* active, cudaStream_t s)
   if (c.nrhs == 1)
     k_dense_gemv<T><<<nblk((long long)n * 32, 256), 256, 0, s>>>(n, (const c_t<T>*)L.Ainvw, (const c_t<T>*)f,
                                                                 (c_t<T>*)u, active);
+  else if (c.nrhs >= 8)
+    k_dense_gemm_rhs<T><<<nblk(n, 512 / c.nrhs), 256, 0, s>>>(n, c.nrhs, (const c_t<T>*)L.Ainvw, (const c_t<T>*)f,
+                                                               (c_t<T>*)u, active);
   else
-    k_dense_gemm_rhs<T><<<n, 64, 0, s>>>(n, c.nrhs, (const c_t<T>*)L.Ainvw, (const c_t<T>*)f, (c_t<T>*)u, active);
+    k_dense_gemm_rhs_small<T><<<n, 32, 0, s>>>(n, c.nrhs, (const c_t<T>*)L.Ainvw, (const c_t<T>*)f, (c_t<T>*)u,
+                                               active);
   HZ_LAUNCHED();
 }
 

@@ -208,18 +208,6 @@ __global__ void __launch_bounds__(kRedBlock) k_gs_update(int N, double2* __restr
   if (last && threadIdx.x == 0) arnoldi_update(st, NV - 1, nullptr, st->scale[NV - 1]);
 }
 
-// NV = 1..kMaxM as a compile-time constant
-template <typename F>
-void with_nv(int nv, F&& f) {
-  switch (nv) {
-#define HZ_NV(K) \
-  case K: f(std::integral_constant<int, K>{}); return;
-    HZ_NV(1) HZ_NV(2) HZ_NV(3) HZ_NV(4) HZ_NV(5) HZ_NV(6) HZ_NV(7) HZ_NV(8)
-    HZ_NV(9) HZ_NV(10) HZ_NV(11) HZ_NV(12) HZ_NV(13) HZ_NV(14) HZ_NV(15) HZ_NV(16)
-#undef HZ_NV
-    default: throw Error(HZ_ERR_INVALID_ARG, "restart_m must be in 1..16");
-  }
-}
 
 __global__ void k_solve_y(KrylovState* __restrict__ st) {
   if (st->st.done) return;
@@ -584,7 +572,8 @@ size_t krylov_bytes(const hz_grid& g, const hz_opts& o) {
   const size_t vb = o.precision == HZ_PREC_MIXED ? 8 : 16;
   const int m = o.restart_m;
   const long long R = std::max(1, o.nrhs_max);
-  const long long nb = nblk(N * R, kRedBlock) * 2 * R + (long long)m * (nblk(N, BX * BY * kRows) + 2048);
+  const long long nb = nblk(N * R, kRedBlock) * 2 * R + (long long)m * (nblk(N, BX * BY * kRows) + 2048) +
+                       (R > 1 ? (long long)m * R * 2048 : 0);
   return (16ull * N * (m + 1) + vb * N * m + 16ull * N * 4) * R + 16ull * nb + sizeof(KrylovState) * R;
 }
 
@@ -604,7 +593,7 @@ void krylov_alloc(Ctx& c) {
   // inner product), the 1D passes one per block; batched: one per block and
   // RHS (blocks of at least 8 values per thread, see krylov_batch.cu)
   const long long nb1 = std::max<long long>((long long)max_slots() * m, nblk(N, kRedBlock));
-  const long long nbR = R > 1 ? R * (nblk(N * R, kRedBlock * 8) + grid_blocks(g) * R) : 0;
+  const long long nbR = R > 1 ? std::max<long long>(R * nblk(N * R, kRedBlock * 8), (long long)m * R * max_slots()) : 0;
   c.partials = (double2*)ctx_alloc(c, sizeof(double2) * std::max(nb1, nbR));
   c.ks = (KrylovState*)ctx_alloc(c, sizeof(KrylovState) * R);
   HZ_CUDA(cudaMemsetAsync(c.ks, 0, sizeof(KrylovState) * R, c.alloc_stream));

@@ -1,7 +1,10 @@
 // FGMRES(m) for R right-hand sides at once (R a power of two <= 64) sharing one
-// hierarchy: the same algorithm as krylov.cu, per right-hand side, with the
-// V-cycle applied to all R right-hand sides in one batched pass (RHS index
-// innermost, field index node*R + r).
+// hierarchy: the same algorithm as krylov.cu (two-pass classical Gram-Schmidt,
+// unnormalised V-cycle inputs with the scales folded into H and the update),
+// per right-hand side, with the V-cycle applied to all R right-hand sides in
+// one batched pass (RHS index innermost, field index node*R + r).  The FP64
+// passes are persistent 1D sweeps over the fields in block ranges that are
+// multiples of 256, so a thread always serves the same right-hand side.
 //
 // Every right-hand side has its own Krylov state (basis scales, Hessenberg
 // column, Givens rotations, residual estimate, convergence): a right-hand side
@@ -21,7 +24,6 @@ namespace hz {
 namespace {
 
 constexpr int kB = 256;            // threads per block
-constexpr int kRowsB = 8;          // y rows per thread in the 2D passes
 constexpr int kPerB = 8;           // values per thread in the 1D passes
 
 struct GeoB {
@@ -32,9 +34,6 @@ GeoB geob(const GridDev& g, int R) {
   int lr = 0;
   while ((1 << lr) < R) ++lr;
   return GeoB{g.nx, g.ny, g.nz, (int)g.N, g.dim, R, lr, g.nx * R, g.nx * g.ny * R, (int)g.N * R};
-}
-dim3 grid2(const GeoB& g) {
-  return dim3((g.nxR + BX - 1) / BX, (g.ny + BY * kRowsB - 1) / (BY * kRowsB), g.nz < 8 ? g.nz : 8);
 }
 unsigned grid1(const GeoB& g) { return nblk(g.NR, kB * kPerB); }
 
@@ -72,7 +71,6 @@ __device__ __forceinline__ double2 apply_A_b(const GeoB& g, double invh2, const 
   return acc;
 }
 
-__device__ __forceinline__ int block_lin() { return (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x; }
 
 // Per-RHS block partials: thread t holds (acc, r); partials[r*nb + block] =
 // the sum over the block's threads with that r (zero if none), in a fixed
@@ -84,6 +82,7 @@ __device__ __forceinline__ void block_store_r(double2 acc, int r, int R, double2
                                               int block) {
   __shared__ double2 sv[kB / 32][32];
   __shared__ int sr0[kB / 32];
+  __syncthreads();                          // the arrays may still be read by a previous call
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
   for (int off = 16; off >= R; off >>= 1) {
@@ -124,24 +123,32 @@ __global__ void __launch_bounds__(kB) k_scale_rhs_b(GeoB g, const double* __rest
   block_store_r(acc, r, g.R, partials, gridDim.x, blockIdx.x);
 }
 
-enum { kInit = 0, kH1 = 1, kArnoldi = 2, kRestart = 3 };
+enum { kInit = 0, kDots = 1, kArnoldi = 2, kRestart = 3 };
 
 // One block per RHS: sum its partials, then the RHS's state update.
-__global__ void k_reduce_b(const double2* __restrict__ partials, int nb, int mode, int idx, KrylovState* st,
+// kDots: idx inner products (partials [(i*R + r)*nb + b]) -> h1[i];
+// kArnoldi: the squared norm -> the Arnoldi column of iteration idx.
+__global__ void k_reduce_b(const double2* __restrict__ partials, int nb, int R, int mode, int idx, KrylovState* st,
                            int* n_active, double tol, int max_iter, int m) {
-  if ((mode == kH1 || mode == kArnoldi) && *n_active == 0) return;
+  if ((mode == kDots || mode == kArnoldi) && *n_active == 0) return;
   const int r = blockIdx.x;
   KrylovState* s = st + r;
   __shared__ double2 sm[kB];
-  double2 acc = make_double2(0, 0);
-  for (int b = threadIdx.x; b < nb; b += kB) acc = acc + partials[r * nb + b];
-  sm[threadIdx.x] = acc;
-  __syncthreads();
-  for (int k = kB / 2; k > 0; k >>= 1) {
-    if (threadIdx.x < k) sm[threadIdx.x] = sm[threadIdx.x] + sm[threadIdx.x + k];
+  const int nsum = mode == kDots ? idx : 1;
+  for (int i = 0; i < nsum; ++i) {
+    const double2* pp = partials + ((long long)i * R + r) * nb;
+    double2 acc = make_double2(0, 0);
+    for (int b = threadIdx.x; b < nb; b += kB) acc = acc + pp[b];
     __syncthreads();
+    sm[threadIdx.x] = acc;
+    __syncthreads();
+    for (int k = kB / 2; k > 0; k >>= 1) {
+      if (threadIdx.x < k) sm[threadIdx.x] = sm[threadIdx.x] + sm[threadIdx.x + k];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0 && mode == kDots && s->active) s->h1[i] = sm[0];
   }
-  if (threadIdx.x != 0) return;
+  if (threadIdx.x != 0 || mode == kDots) return;
   const double2 sum = sm[0];
   switch (mode) {
     case kInit: {
@@ -160,13 +167,10 @@ __global__ void k_reduce_b(const double2* __restrict__ partials, int nb, int mod
       s->kcyc = 0;
       break;
     }
-    case kH1:
-      if (s->active) s->h1[idx] = sum;
-      break;
     case kArnoldi:
       if (s->active) {
         s->nrm2 = sum;
-        arnoldi_update(s, idx, n_active);
+        arnoldi_update(s, idx, n_active, s->scale[idx]);
       }
       break;
     case kRestart:
@@ -178,81 +182,84 @@ __global__ void k_reduce_b(const double2* __restrict__ partials, int nb, int mod
   }
 }
 
-template <typename V>
-__global__ void k_cast_in_b(GeoB g, const double2* __restrict__ v, const KrylovState* __restrict__ st, int j,
-                            V* __restrict__ f, const int* n_active) {
-  if (*n_active == 0) return;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= g.NR) return;
-  const KrylovState* s = st + (i & (g.R - 1));
-  if (!s->active) return;
-  const double2 a = v[i];
-  if constexpr (std::is_same<V, float2>::value) {
-    const float sc = d2f_rn(s->scale[j]);
-    f[i] = make_float2(d2f_rn(a.x) * sc, d2f_rn(a.y) * sc);
-  } else {
-    f[i] = s->scale[j] * a;
-  }
+// Persistent 1D sweep: this block's share of the NR field elements, in a
+// range starting at a multiple of kB so that thread t always sees RHS t mod R.
+__device__ __forceinline__ void block_range_b(int NR, int& e0, int& e1) {
+  const int chunks = (NR + kB - 1) / kB;
+  const int per = (chunks + gridDim.x - 1) / gridDim.x;
+  e0 = min(NR, blockIdx.x * per * kB);
+  e1 = min(NR, e0 + per * kB);
 }
 
-// pass 0: w = A z_j -> V[j+1]; partial conj(V_0) . w per RHS
-template <typename TZ>
-__global__ void __launch_bounds__(kB) k_mgs_first_b(GeoB g, double invh2, const double2* __restrict__ diag,
-                                                    const TZ* __restrict__ z, double2* __restrict__ V, int j,
-                                                    double2* __restrict__ partials, const KrylovState* __restrict__ st,
-                                                    const int* n_active) {
+// node coordinates of field element e
+__device__ __forceinline__ void coords_b(const GeoB& g, int e, int& p, int& x, int& y, int& z) {
+  p = e >> g.lr;
+  const int row = p / g.nx;
+  x = p - row * g.nx;
+  z = row / g.ny;
+  y = row - z * g.ny;
+}
+
+// pass A: w = A z'_j -> V[j+1]; d_i = conj(V_i) . w per RHS, i < NV = j + 1
+template <typename TZ, int NV>
+__global__ void __launch_bounds__(kB) k_gs_dots_b(GeoB g, double invh2, const double2* __restrict__ diag,
+                                                  const TZ* __restrict__ z, double2* __restrict__ V,
+                                                  double2* __restrict__ partials, const KrylovState* __restrict__ st,
+                                                  const int* n_active) {
   if (*n_active == 0) return;
-  const int X = blockIdx.x * BX + threadIdx.x;
-  const int r = X & (g.R - 1);
-  const bool act = X < g.nxR && st[r].active;
-  double2 acc = make_double2(0, 0);
-  double2* w = V + (long long)(j + 1) * g.NR;
-  if (act) {
-    const int x = X >> g.lr;
-    for (int zz = blockIdx.z; zz < g.nz; zz += gridDim.z) {
+  const int r = threadIdx.x & (g.R - 1);
+  double2 acc[NV];
 #pragma unroll
-      for (int k = 0; k < kRowsB; ++k) {
-        const int y = (blockIdx.y * kRowsB + k) * BY + threadIdx.y;
-        if (y >= g.ny) break;
-        const int row = zz * g.ny + y;
-        const int p = row * g.nx + x, q = row * g.nxR + X;
-        const double2 a = apply_A_b(g, invh2, diag, z, p, q, x, y, zz);
-        w[q] = a;
-        acc = dot_acc(acc, V[q], a);
-      }
+  for (int i = 0; i < NV; ++i) acc[i] = make_double2(0, 0);
+  if (st[r].active) {
+    double2* w = V + (long long)NV * g.NR;
+    int e0, e1;
+    block_range_b(g.NR, e0, e1);
+    for (int e = e0 + threadIdx.x; e < e1; e += kB) {
+      int p, x, y, zz;
+      coords_b(g, e, p, x, y, zz);
+      const double2 a = apply_A_b(g, invh2, diag, z, p, e, x, y, zz);
+      w[e] = a;
+#pragma unroll
+      for (int i = 0; i < NV; ++i) acc[i] = dot_acc(acc[i], V[(long long)i * g.NR + e], a);
     }
   }
-  block_store_r(acc, r, g.R, partials, gridDim.x * gridDim.y * gridDim.z, block_lin());
+#pragma unroll
+  for (int i = 0; i < NV; ++i) block_store_r(acc[i], r, g.R, partials + (long long)i * g.R * gridDim.x, gridDim.x,
+                                             blockIdx.x);
 }
 
-// pass i: w -= h_{i-1} v_{i-1}; partial conj(V_i) . w (LAST: ||w||^2) per RHS
-template <bool LAST>
-__global__ void __launch_bounds__(kB) k_mgs_step_b(GeoB g, double2* __restrict__ V, int j, int i,
-                                                   double2* __restrict__ partials,
-                                                   const KrylovState* __restrict__ st, const int* n_active) {
+// pass B: w -= sum_{i < NV} scale_i^2 d_i V_i; ||w||^2 per RHS; f = w in the
+// working precision (the next V-cycle input)
+template <typename TF, int NV>
+__global__ void __launch_bounds__(kB) k_gs_update_b(GeoB g, double2* __restrict__ V, TF* __restrict__ f,
+                                                    double2* __restrict__ partials,
+                                                    const KrylovState* __restrict__ st, const int* n_active) {
   if (*n_active == 0) return;
   const int r = threadIdx.x & (g.R - 1);
   const KrylovState* s = st + r;
-  double2 acc = make_double2(0, 0);
+  double acc = 0.0;
   if (s->active) {
-    const double sc = s->scale[i - 1];
-    const double2 c = (sc * sc) * s->h1[i - 1];
-    const double2* vp = V + (long long)(i - 1) * g.NR;
-    const double2* vi = V + (long long)i * g.NR;
-    double2* w = V + (long long)(j + 1) * g.NR;
-    const int base = blockIdx.x * (kB * kPerB) + threadIdx.x;
+    double2 c[NV];
 #pragma unroll
-    for (int k = 0; k < kPerB; ++k) {
-      const int p = base + k * kB;
-      if (p < g.NR) {
-        const double2 ww = axmy(w[p], c, vp[p]);
-        w[p] = ww;
-        if (LAST) acc.x = nrm_acc(acc.x, ww);
-        else acc = dot_acc(acc, vi[p], ww);
-      }
+    for (int i = 0; i < NV; ++i) {
+      const double sc = s->scale[i];
+      c[i] = (sc * sc) * s->h1[i];
+    }
+    double2* w = V + (long long)NV * g.NR;
+    int e0, e1;
+    block_range_b(g.NR, e0, e1);
+    for (int e = e0 + threadIdx.x; e < e1; e += kB) {
+      double2 ww = w[e];
+#pragma unroll
+      for (int i = 0; i < NV; ++i) ww = axmy(ww, c[i], V[(long long)i * g.NR + e]);
+      w[e] = ww;
+      if constexpr (std::is_same<TF, float2>::value) f[e] = make_float2(d2f_rn(ww.x), d2f_rn(ww.y));
+      else f[e] = ww;
+      acc = nrm_acc(acc, ww);
     }
   }
-  block_store_r(acc, r, g.R, partials, gridDim.x, blockIdx.x);
+  block_store_r(make_double2(acc, 0.0), r, g.R, partials, gridDim.x, blockIdx.x);
 }
 
 __global__ void k_solve_y_b(KrylovState* st, int R) {
@@ -268,6 +275,7 @@ __global__ void k_solve_y_b(KrylovState* st, int R) {
   }
 }
 
+// p += sum_i y_i scale_i z'_i
 template <typename TZ>
 __global__ void k_update_p_b(GeoB g, const TZ* __restrict__ Z, const KrylovState* __restrict__ st,
                              double2* __restrict__ p) {
@@ -278,43 +286,40 @@ __global__ void k_update_p_b(GeoB g, const TZ* __restrict__ Z, const KrylovState
   const int k = s->kcyc;
   double2 acc = p[q];
   for (int i = 0; i < k; ++i) {
-    const double2 yi = s->y[i], zi = ld64(Z, i * g.NR + q);
+    const double2 yi = s->scale[i] * s->y[i], zi = ld64(Z, i * g.NR + q);
     acc = make_double2(fma(yi.x, zi.x, fma(-yi.y, zi.y, acc.x)), fma(yi.x, zi.y, fma(yi.y, zi.x, acc.y)));
   }
   p[q] = acc;
 }
 
-// r = q_hat - A p -> V_0; partial ||r||^2 per RHS (RHS already done: skipped)
+// r = q_hat - A p -> V_0 and f; partial ||r||^2 per RHS (RHS already done: skipped)
+template <typename TF>
 __global__ void __launch_bounds__(kB) k_true_residual_b(GeoB g, double invh2, const double2* __restrict__ diag,
                                                         const double2* __restrict__ pv,
                                                         const double2* __restrict__ qhat, double2* __restrict__ rv,
-                                                        double2* __restrict__ partials,
+                                                        TF* __restrict__ f, double2* __restrict__ partials,
                                                         const KrylovState* __restrict__ st) {
-  const int X = blockIdx.x * BX + threadIdx.x;
-  const int r = X & (g.R - 1);
-  const bool act = X < g.nxR && !st[r].st.done;
+  const int r = threadIdx.x & (g.R - 1);
   double2 acc = make_double2(0, 0);
-  if (act) {
-    const int x = X >> g.lr;
-    for (int zz = blockIdx.z; zz < g.nz; zz += gridDim.z) {
-#pragma unroll
-      for (int k = 0; k < kRowsB; ++k) {
-        const int y = (blockIdx.y * kRowsB + k) * BY + threadIdx.y;
-        if (y >= g.ny) break;
-        const int row = zz * g.ny + y;
-        const int p = row * g.nx + x, q = row * g.nxR + X;
-        const double2 v = qhat[q] - apply_A_b(g, invh2, diag, pv, p, q, x, y, zz);
-        rv[q] = v;
-        acc.x = nrm_acc(acc.x, v);
-      }
+  if (!st[r].st.done) {
+    int e0, e1;
+    block_range_b(g.NR, e0, e1);
+    for (int e = e0 + threadIdx.x; e < e1; e += kB) {
+      int p, x, y, zz;
+      coords_b(g, e, p, x, y, zz);
+      const double2 v = qhat[e] - apply_A_b(g, invh2, diag, pv, p, e, x, y, zz);
+      rv[e] = v;
+      if constexpr (std::is_same<TF, float2>::value) f[e] = make_float2(d2f_rn(v.x), d2f_rn(v.y));
+      else f[e] = v;
+      acc.x = nrm_acc(acc.x, v);
     }
   }
-  block_store_r(acc, r, g.R, partials, gridDim.x * gridDim.y * gridDim.z, block_lin());
+  block_store_r(acc, r, g.R, partials, gridDim.x, blockIdx.x);
 }
 
-int nb2(const GeoB& g) {
-  const dim3 d = grid2(g);
-  return (int)(d.x * d.y * d.z);
+template <typename K>
+unsigned persistent_grid(K kern, const GeoB& g) {
+  return (unsigned)std::max(1, std::min<int>(nblk(g.NR, kB), resident_slots((const void*)kern, kB)));
 }
 
 template <typename TZ>
@@ -325,39 +330,41 @@ void run_cycle_b(Ctx& c, const GeoB& g, cudaStream_t s) {
   KrylovState* st = c.ks;
   int* na = c.n_active;
   TZ* Z = (TZ*)c.Z;
-  const int n2 = nb2(g), n1 = (int)grid1(g);
   const double tol = c.opts.tol;
   const int mi = c.opts.max_iter;
   const double NR = g.NR;
   for (int j = 0; j < m; ++j) {
-    k_cast_in_b<TZ><<<nblk(g.NR, 256), 256, 0, s>>>(g, c.V + (long long)j * g.NR, st, j, (TZ*)L0.f, na);
+    const int nv = j + 1;
     int pk = prof_begin(c, 3, j, vcycle_bytes(c), 0.0, s);
     vcycle(c, L0.f, Z + (long long)j * g.NR, na, s);
     prof_end(c, pk, s);
-    // z (sizeof TZ), v_0 read, w written; diag once; 24 flops (A z: 16, dot: 8)
-    pk = prof_begin(c, 2, j, NR * (sizeof(TZ) + 32) + 16.0 * g.N, 24.0 * NR, s);
-    k_mgs_first_b<TZ><<<grid2(g), dim3(BX, BY), 0, s>>>(g, invh2, c.diagA64, Z + (long long)j * g.NR, c.V, j,
-                                                         c.partials, st, na);
+    // pass A: z and diag read, w written, nv vectors read; A z 16 (3D: 20) flops + 8 per dot
+    pk = prof_begin(c, 2, j, NR * (sizeof(TZ) + 16 + 16.0 * nv) + 16.0 * g.N,
+                    ((g.dim == 3 ? 20.0 : 16.0) + 8.0 * nv) * NR, s);
+    unsigned G = 0;
+    with_nv(nv, [&](auto NV) {
+      auto kern = k_gs_dots_b<TZ, decltype(NV)::value>;
+      G = persistent_grid(kern, g);
+      kern<<<G, kB, 0, s>>>(g, invh2, c.diagA64, Z + (long long)j * g.NR, c.V, c.partials, st, na);
+    });
     prof_end(c, pk, s);
-    k_reduce_b<<<R, kB, 0, s>>>(c.partials, n2, kH1, 0, st, na, tol, mi, m);
-    for (int i = 1; i <= j; ++i) {
-      // w, v_{i-1}, v_i read, w written; 8 flops update + 8 flops dot
-      pk = prof_begin(c, 1, j, 64.0 * NR, 16.0 * NR, s);
-      k_mgs_step_b<false><<<n1, kB, 0, s>>>(g, c.V, j, i, c.partials, st, na);
-      prof_end(c, pk, s);
-      k_reduce_b<<<R, kB, 0, s>>>(c.partials, n1, kH1, i, st, na, tol, mi, m);
-    }
-    // w, v_j read, w written; 8 flops update + 4 flops norm
-    pk = prof_begin(c, 1, j, 48.0 * NR, 12.0 * NR, s);
-    k_mgs_step_b<true><<<n1, kB, 0, s>>>(g, c.V, j, j + 1, c.partials, st, na);
+    k_reduce_b<<<R, kB, 0, s>>>(c.partials, G, R, kDots, nv, st, na, tol, mi, m);
+    // pass B: w and nv vectors read, w and f written; 8 flops per vector + 4 for the norm
+    pk = prof_begin(c, 1, j, NR * (32 + 16.0 * nv + sizeof(TZ)), (8.0 * nv + 4.0) * NR, s);
+    with_nv(nv, [&](auto NV) {
+      auto kern = k_gs_update_b<TZ, decltype(NV)::value>;
+      G = persistent_grid(kern, g);
+      kern<<<G, kB, 0, s>>>(g, c.V, (TZ*)L0.f, c.partials, st, na);
+    });
     prof_end(c, pk, s);
-    k_reduce_b<<<R, kB, 0, s>>>(c.partials, n1, kArnoldi, j, st, na, tol, mi, m);
+    k_reduce_b<<<R, kB, 0, s>>>(c.partials, G, R, kArnoldi, j, st, na, tol, mi, m);
   }
   HZ_LAUNCHED();
   k_solve_y_b<<<1, 64, 0, s>>>(st, R);
   k_update_p_b<TZ><<<nblk(g.NR, 256), 256, 0, s>>>(g, Z, st, c.p);
-  k_true_residual_b<<<grid2(g), dim3(BX, BY), 0, s>>>(g, invh2, c.diagA64, c.p, c.qhat, c.V, c.partials, st);
-  k_reduce_b<<<R, kB, 0, s>>>(c.partials, n2, kRestart, 0, st, na, tol, mi, m);
+  const unsigned Gt = persistent_grid(k_true_residual_b<TZ>, g);
+  k_true_residual_b<TZ><<<Gt, kB, 0, s>>>(g, invh2, c.diagA64, c.p, c.qhat, c.V, (TZ*)L0.f, c.partials, st);
+  k_reduce_b<<<R, kB, 0, s>>>(c.partials, Gt, R, kRestart, 0, st, na, tol, mi, m);
   HZ_LAUNCHED();
 }
 
@@ -407,17 +414,18 @@ void solve_b(Ctx& c, const double2* q, double2* p, int R, hz_info* info, cudaStr
   ensure_graph_b<TZ>(c, g);
   cudaStream_t s = c.graph_stream;
   KrylovState* st = c.ks;
-  const int n1 = (int)grid1(g), n2 = nb2(g);
+  const int n1 = (int)grid1(g);
   const double invh2 = 1.0 / (c.h * c.h);
   HZ_CUDA(cudaEventRecord(c.ev_in, user));
   HZ_CUDA(cudaStreamWaitEvent(s, c.ev_in, 0));
   HZ_CUDA(cudaMemsetAsync(c.n_active, 0, sizeof(int), s));
   k_scale_rhs_b<<<n1, kB, 0, s>>>(g, c.wmass, q, c.qhat, c.partials);
-  k_reduce_b<<<R, kB, 0, s>>>(c.partials, n1, kInit, 0, st, c.n_active, c.opts.tol, c.opts.max_iter,
+  k_reduce_b<<<R, kB, 0, s>>>(c.partials, n1, R, kInit, 0, st, c.n_active, c.opts.tol, c.opts.max_iter,
                               c.opts.restart_m);
   HZ_CUDA(cudaMemsetAsync(c.p, 0, sizeof(double2) * g.NR, s));
-  k_true_residual_b<<<grid2(g), dim3(BX, BY), 0, s>>>(g, invh2, c.diagA64, c.p, c.qhat, c.V, c.partials, st);
-  k_reduce_b<<<R, kB, 0, s>>>(c.partials, n2, kRestart, 0, st, c.n_active, c.opts.tol, c.opts.max_iter,
+  const unsigned Gt = persistent_grid(k_true_residual_b<TZ>, g);
+  k_true_residual_b<TZ><<<Gt, kB, 0, s>>>(g, invh2, c.diagA64, c.p, c.qhat, c.V, (TZ*)c.L[0].f, c.partials, st);
+  k_reduce_b<<<R, kB, 0, s>>>(c.partials, Gt, R, kRestart, 0, st, c.n_active, c.opts.tol, c.opts.max_iter,
                               c.opts.restart_m);
   HZ_LAUNCHED();
   c.launches += 4;

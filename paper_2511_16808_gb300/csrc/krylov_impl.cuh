@@ -205,6 +205,19 @@ __device__ inline void restart_update(KrylovState* st, int* n_active = nullptr) 
   if (n_active) atomicAdd(n_active, 1);
 }
 
+// NV = 1..kMaxM as a compile-time constant
+template <typename F>
+void with_nv(int nv, F&& f) {
+  switch (nv) {
+#define HZ_NV(K) \
+  case K: f(std::integral_constant<int, K>{}); return;
+    HZ_NV(1) HZ_NV(2) HZ_NV(3) HZ_NV(4) HZ_NV(5) HZ_NV(6) HZ_NV(7) HZ_NV(8)
+    HZ_NV(9) HZ_NV(10) HZ_NV(11) HZ_NV(12) HZ_NV(13) HZ_NV(14) HZ_NV(15) HZ_NV(16)
+#undef HZ_NV
+    default: throw Error(HZ_ERR_INVALID_ARG, "restart_m must be in 1..16");
+  }
+}
+
 // Measurement hooks (krylov.cu): CUDA events around the launches of the
 // selected class (1 = Gram-Schmidt update passes, 2 = first pass with the FP64
 // operator, 3 = whole V-cycle), recorded inside the captured restart cycle.
