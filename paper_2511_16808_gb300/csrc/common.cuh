@@ -15,6 +15,7 @@
 //                      (Eq. smoother); a sweep is a gather, conflict-free
 #pragma once
 #include <cstring>
+#include <utility>
 #include <new>
 #include <stdexcept>
 
@@ -284,6 +285,34 @@ std::vector<std::array<int, 3>> fine_offsets(int dim);
 std::vector<std::array<int, 3>> box_offsets(int dim, int rho);
 std::vector<std::array<int, 3>> patch_offsets(int dim, hz_patch kind);
 std::vector<std::array<int, 3>> patch_difference_offsets(int dim, hz_patch kind);
+
+// ---------------------------------------------------------------- dependent launch
+// Programmatic dependent launch (Blackwell / Hopper): the kernels of the
+// solver's chains (V-cycle steps, Gram-Schmidt passes) are launched with
+// programmatic stream serialization, so the next kernel is launched and its
+// blocks become resident while the previous one drains; every such kernel
+// first waits for its predecessor's completion and memory (griddepcontrol.wait,
+// a hardware dependency, returning at once when there is none), then allows
+// its own successor to start launching.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  HZ_CUDA(cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...));
+}
 
 // ---------------------------------------------------------------- errors at the ABI
 // The message of the calling thread's last failed call (api.cu).

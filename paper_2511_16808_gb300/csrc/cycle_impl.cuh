@@ -283,6 +283,7 @@ template <typename T, int DIM, int AK, int VR>
 __global__ void __launch_bounds__(BX* BY) k_resid(Geo g, T invh2, const c_t<T>* __restrict__ A,
                                                   const c_t<T>* __restrict__ u, const c_t<T>* __restrict__ f,
                                                   c_t<T>* __restrict__ r, const int* active) {
+  pdl_enter();
   if (active && !*active) return;
   constexpr int RA = AK == 0 ? 1 : AK;
   const bool in = interior_block<DIM>(g, RA);
@@ -299,6 +300,7 @@ template <typename T, int DIM, int VR>
 __global__ void __launch_bounds__(BX* BY) k_sweep0(Geo g, MList m, const c_t<T>* __restrict__ M, T w,
                                                    const c_t<T>* __restrict__ f, c_t<T>* __restrict__ u,
                                                    const int* active) {
+  pdl_enter();
   if (active && !*active) return;
   const bool in = interior_block<DIM>(g, m.rho);
   int x, y, z, p, q;
@@ -315,6 +317,7 @@ __global__ void __launch_bounds__(BX* BY) k_sweep0_resid_diag(Geo g, T invh2, co
                                                               const c_t<T>* __restrict__ m0, T w,
                                                               const c_t<T>* __restrict__ f, c_t<T>* __restrict__ u,
                                                               c_t<T>* __restrict__ r, const int* active) {
+  pdl_enter();
   if (active && !*active) return;
   constexpr int RA = AK == 0 ? 1 : AK;
   const bool in = interior_block<DIM>(g, RA);
@@ -334,6 +337,7 @@ template <typename T, int DIM, int VR>
 __global__ void __launch_bounds__(BX* BY) k_sweep_out(Geo g, MList m, const c_t<T>* __restrict__ M, T w,
                                                       const c_t<T>* __restrict__ r, const c_t<T>* in, c_t<T>* out,
                                                       const int* active) {
+  pdl_enter();
   if (active && !*active) return;
   const bool inb = interior_block<DIM>(g, m.rho);
   int x, y, z, p, q;
@@ -350,6 +354,7 @@ __global__ void __launch_bounds__(BX* BY) k_resid_sweep_diag(Geo g, T invh2, con
                                                              const c_t<T>* __restrict__ m0, T w,
                                                              const c_t<T>* __restrict__ f, const c_t<T>* __restrict__ in,
                                                              c_t<T>* __restrict__ out, const int* active) {
+  pdl_enter();
   if (active && !*active) return;
   constexpr int RA = AK == 0 ? 1 : AK;
   const bool inb = interior_block<DIM>(g, RA);
@@ -378,6 +383,7 @@ __device__ __forceinline__ float p1f(int kind, int nf, int nc, int j, int J) {
 template <typename T, int DIM, int KIND, int VR>
 __global__ void __launch_bounds__(BX* BY) k_restrict(Geo gf, Geo gc, const c_t<T>* __restrict__ r,
                                                      c_t<T>* __restrict__ fc, const int* active) {
+  pdl_enter();
   if (active && !*active) return;
   int X, Y, Z, pc, qc;
   if (!node_xyz(gc, X, Y, Z, pc, qc)) return;
@@ -474,6 +480,7 @@ __device__ __forceinline__ pk_t<T, VR> prolong_at(const Geo& gf, const Geo& gc, 
 template <typename T, int DIM, int KIND, int VR>
 __global__ void __launch_bounds__(BX* BY) k_prolong(Geo gf, Geo gc, const c_t<T>* __restrict__ ec, const c_t<T>* in,
                                                     c_t<T>* out, const int* active) {
+  pdl_enter();
   if (active && !*active) return;
   int x, y, z, p, q;
   if (!node_xyz(gf, x, y, z, p, q)) return;
@@ -489,6 +496,7 @@ __global__ void __launch_bounds__(BX* BY) k_prolong_fused_2d(Geo gf, Geo gc, T i
                                                              const c_t<T>* __restrict__ f, const c_t<T>* __restrict__ m0,
                                                              T w, c_t<T>* __restrict__ out, c_t<T>* __restrict__ r,
                                                              const int* active) {
+  pdl_enter();
   if (active && !*active) return;
   constexpr int RA = AK == 0 ? 1 : AK;
   constexpr int TX = BX + 2 * RA, TY = BY + 2 * RA;
@@ -541,6 +549,7 @@ __global__ void __launch_bounds__(BX* BY) k_prolong_fused_2d(Geo gf, Geo gc, T i
 template <typename T>
 __global__ void k_dense_gemv(int n, const c_t<T>* __restrict__ A, const c_t<T>* __restrict__ f, c_t<T>* __restrict__ u,
                              const int* active) {
+  pdl_enter();
   if (active && !*active) return;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -565,6 +574,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_dense_gemm_rhs(int n, int R, const c_t<T>* __restrict__ A,
                                                         const c_t<T>* __restrict__ f, c_t<T>* __restrict__ u,
                                                         const int* active) {
+  pdl_enter();
   if (active && !*active) return;
   constexpr int KC = sizeof(T) == 4 ? 32 : 16;
   __shared__ c_t<T> As[64][KC + 1];
@@ -599,6 +609,7 @@ __global__ void __launch_bounds__(256) k_dense_gemm_rhs(int n, int R, const c_t<
 template <typename T>
 __global__ void k_dense_gemm_rhs_small(int n, int R, const c_t<T>* __restrict__ A, const c_t<T>* __restrict__ f,
                                        c_t<T>* __restrict__ u, const int* active) {
+  pdl_enter();
   if (active && !*active) return;
   const int i = blockIdx.x, r = threadIdx.x;
   if (r >= R) return;
@@ -636,7 +647,7 @@ void resid(Ctx& c, int l, const void* u, const void* f, void* r, const int* acti
     constexpr int VR = decltype(V)::value;
     const Geo g = geo(L.g, c.nrhs, VR);
     with_dim_ak(L.g.dim, akind(L), [&](auto D, auto K) {
-      k_resid<T, D, K, VR><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, invh2, (const c_t<T>*)L.Aw, (const c_t<T>*)u,
+      launch_pdl(k_resid<T, D, K, VR>, grid_of(g), dim3(BX, BY), s, g, invh2, (const c_t<T>*)L.Aw, (const c_t<T>*)u,
                                                                (const c_t<T>*)f, (c_t<T>*)r, active);
     });
   });
@@ -651,11 +662,11 @@ void sweep_out(Ctx& c, int l, const void* r, const void* in, void* out, const in
     constexpr int VR = decltype(V)::value;
     const Geo g = geo(L.g, c.nrhs, VR);
     if (L.g.dim == 2)
-      k_sweep_out<T, 2, VR><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, m, (const c_t<T>*)L.Mw, (T)L.damping,
+      launch_pdl(k_sweep_out<T, 2, VR>, grid_of(g), dim3(BX, BY), s, g, m, (const c_t<T>*)L.Mw, (T)L.damping,
                                                                 (const c_t<T>*)r, (const c_t<T>*)in, (c_t<T>*)out,
                                                                 active);
     else
-      k_sweep_out<T, 3, VR><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, m, (const c_t<T>*)L.Mw, (T)L.damping,
+      launch_pdl(k_sweep_out<T, 3, VR>, grid_of(g), dim3(BX, BY), s, g, m, (const c_t<T>*)L.Mw, (T)L.damping,
                                                                 (const c_t<T>*)r, (const c_t<T>*)in, (c_t<T>*)out,
                                                                 active);
   });
@@ -670,10 +681,10 @@ void sweep0(Ctx& c, int l, const void* f, void* u, const int* active, cudaStream
     constexpr int VR = decltype(V)::value;
     const Geo g = geo(L.g, c.nrhs, VR);
     if (L.g.dim == 2)
-      k_sweep0<T, 2, VR><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, m, (const c_t<T>*)L.Mw, (T)L.damping,
+      launch_pdl(k_sweep0<T, 2, VR>, grid_of(g), dim3(BX, BY), s, g, m, (const c_t<T>*)L.Mw, (T)L.damping,
                                                              (const c_t<T>*)f, (c_t<T>*)u, active);
     else
-      k_sweep0<T, 3, VR><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, m, (const c_t<T>*)L.Mw, (T)L.damping,
+      launch_pdl(k_sweep0<T, 3, VR>, grid_of(g), dim3(BX, BY), s, g, m, (const c_t<T>*)L.Mw, (T)L.damping,
                                                              (const c_t<T>*)f, (c_t<T>*)u, active);
   });
   HZ_LAUNCHED();
@@ -687,8 +698,7 @@ void sweep0_resid_diag(Ctx& c, int l, const void* f, void* u, void* r, const int
     constexpr int VR = decltype(V)::value;
     const Geo g = geo(L.g, c.nrhs, VR);
     with_dim_ak(L.g.dim, akind(L), [&](auto D, auto K) {
-      k_sweep0_resid_diag<T, D, K, VR><<<grid_of(g), dim3(BX, BY), 0, s>>>(
-          g, invh2, (const c_t<T>*)L.Aw, (const c_t<T>*)L.Mw, (T)L.damping, (const c_t<T>*)f, (c_t<T>*)u,
+      launch_pdl(k_sweep0_resid_diag<T, D, K, VR>, grid_of(g), dim3(BX, BY), s, g, invh2, (const c_t<T>*)L.Aw, (const c_t<T>*)L.Mw, (T)L.damping, (const c_t<T>*)f, (c_t<T>*)u,
           (c_t<T>*)r, active);
     });
   });
@@ -703,8 +713,7 @@ void resid_sweep_diag(Ctx& c, int l, const void* f, const void* in, void* out, c
     constexpr int VR = decltype(V)::value;
     const Geo g = geo(L.g, c.nrhs, VR);
     with_dim_ak(L.g.dim, akind(L), [&](auto D, auto K) {
-      k_resid_sweep_diag<T, D, K, VR><<<grid_of(g), dim3(BX, BY), 0, s>>>(
-          g, invh2, (const c_t<T>*)L.Aw, (const c_t<T>*)L.Mw, (T)L.damping, (const c_t<T>*)f, (const c_t<T>*)in,
+      launch_pdl(k_resid_sweep_diag<T, D, K, VR>, grid_of(g), dim3(BX, BY), s, g, invh2, (const c_t<T>*)L.Aw, (const c_t<T>*)L.Mw, (T)L.damping, (const c_t<T>*)f, (const c_t<T>*)in,
           (c_t<T>*)out, active);
     });
   });
@@ -719,7 +728,7 @@ void restrict_t(Ctx& c, int l, const void* r, void* fc, const int* active, cudaS
     constexpr int VR = decltype(V)::value;
     const Geo gf = geo(L.g, c.nrhs, VR), gc = geo(C.g, c.nrhs, VR);
     auto go = [&](auto D, auto KIND) {
-      k_restrict<T, D, KIND, VR><<<grid_of(gc), dim3(BX, BY), 0, s>>>(gf, gc, (const c_t<T>*)r, (c_t<T>*)fc,
+      launch_pdl(k_restrict<T, D, KIND, VR>, grid_of(gc), dim3(BX, BY), s, gf, gc, (const c_t<T>*)r, (c_t<T>*)fc,
                                                                       active);
     };
     using I2 = std::integral_constant<int, 2>;
@@ -740,7 +749,7 @@ void prolong_t(Ctx& c, int l, const void* ec, const void* in, void* out, const i
     constexpr int VR = decltype(V)::value;
     const Geo gf = geo(L.g, c.nrhs, VR), gc = geo(C.g, c.nrhs, VR);
     auto go = [&](auto D, auto KIND) {
-      k_prolong<T, D, KIND, VR><<<grid_of(gf), dim3(BX, BY), 0, s>>>(gf, gc, (const c_t<T>*)ec, (const c_t<T>*)in,
+      launch_pdl(k_prolong<T, D, KIND, VR>, grid_of(gf), dim3(BX, BY), s, gf, gc, (const c_t<T>*)ec, (const c_t<T>*)in,
                                                                      (c_t<T>*)out, active);
     };
     using I2 = std::integral_constant<int, 2>;
@@ -763,8 +772,7 @@ void prolong_fused_2d(Ctx& c, int l, const void* ec, const void* t, const void* 
   const Geo gf = geo(L.g), gc = geo(C.g);
   const T invh2 = (T)(1.0 / (c.h * c.h));
   auto go = [&](auto K, auto KIND) {
-    k_prolong_fused_2d<T, K, KIND, DIAG><<<grid_of(gf), dim3(BX, BY), 0, s>>>(
-        gf, gc, invh2, (const c_t<T>*)L.Aw, (const c_t<T>*)ec, (const c_t<T>*)t, (const c_t<T>*)f,
+    launch_pdl(k_prolong_fused_2d<T, K, KIND, DIAG>, grid_of(gf), dim3(BX, BY), s, gf, gc, invh2, (const c_t<T>*)L.Aw, (const c_t<T>*)ec, (const c_t<T>*)t, (const c_t<T>*)f,
         (const c_t<T>*)L.Mw, (T)L.damping, (c_t<T>*)out, (c_t<T>*)r, active);
   };
   using K0 = std::integral_constant<int, 0>;
@@ -785,13 +793,13 @@ void coarse_t(Ctx& c, const void* f, void* u, const int* active, cudaStream_t s)
   Level& L = c.L.back();
   const int n = (int)L.g.N;
   if (c.nrhs == 1)
-    k_dense_gemv<T><<<nblk((long long)n * 32, 256), 256, 0, s>>>(n, (const c_t<T>*)L.Ainvw, (const c_t<T>*)f,
+    launch_pdl(k_dense_gemv<T>, nblk((long long)n * 32, 256), 256, s, n, (const c_t<T>*)L.Ainvw, (const c_t<T>*)f,
                                                                 (c_t<T>*)u, active);
   else if (c.nrhs >= 8)
-    k_dense_gemm_rhs<T><<<nblk(n, 512 / c.nrhs), 256, 0, s>>>(n, c.nrhs, (const c_t<T>*)L.Ainvw, (const c_t<T>*)f,
+    launch_pdl(k_dense_gemm_rhs<T>, nblk(n, 512 / c.nrhs), 256, s, n, c.nrhs, (const c_t<T>*)L.Ainvw, (const c_t<T>*)f,
                                                                (c_t<T>*)u, active);
   else
-    k_dense_gemm_rhs_small<T><<<n, 32, 0, s>>>(n, c.nrhs, (const c_t<T>*)L.Ainvw, (const c_t<T>*)f, (c_t<T>*)u,
+    launch_pdl(k_dense_gemm_rhs_small<T>, n, 32, s, n, c.nrhs, (const c_t<T>*)L.Ainvw, (const c_t<T>*)f, (c_t<T>*)u,
                                                active);
   HZ_LAUNCHED();
 }

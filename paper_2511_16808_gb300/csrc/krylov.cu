@@ -165,6 +165,7 @@ template <typename TZ, int NV>
 __global__ void __launch_bounds__(kRedBlock) k_gs_dots(Geo g, double invh2, const double2* __restrict__ diag,
                                                        const TZ* __restrict__ z, double2* __restrict__ V,
                                                        double2* __restrict__ partials, KrylovState* st) {
+  pdl_enter();
   if (!st->active) return;
   double2 acc[NV];
 #pragma unroll
@@ -184,6 +185,7 @@ __global__ void __launch_bounds__(kRedBlock) k_gs_dots(Geo g, double invh2, cons
 template <typename TF, int NV>
 __global__ void __launch_bounds__(kRedBlock) k_gs_update(int N, double2* __restrict__ V, TF* __restrict__ f,
                                                          double2* __restrict__ partials, KrylovState* st) {
+  pdl_enter();
   if (!st->active) return;
   double2 c[NV];
 #pragma unroll
@@ -210,6 +212,7 @@ __global__ void __launch_bounds__(kRedBlock) k_gs_update(int N, double2* __restr
 
 
 __global__ void k_solve_y(KrylovState* __restrict__ st) {
+  pdl_enter();
   if (st->st.done) return;
   const int k = st->kcyc;
   for (int i = k - 1; i >= 0; --i) {
@@ -222,6 +225,7 @@ __global__ void k_solve_y(KrylovState* __restrict__ st) {
 template <typename TZ>
 __global__ void k_update_p(int N, const TZ* __restrict__ Z, const KrylovState* __restrict__ st,
                            double2* __restrict__ p) {
+  pdl_enter();
   if (st->st.done) return;
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= N) return;
@@ -243,6 +247,7 @@ __global__ void __launch_bounds__(kRedBlock) k_true_residual(Geo g, double invh2
                                                              const double2* __restrict__ qhat, double2* __restrict__ r,
                                                              TF* __restrict__ f, double2* __restrict__ partials,
                                                              KrylovState* st) {
+  pdl_enter();
   if (st->st.done) return;
   double2 acc = make_double2(0, 0);
   for_tiles(g, [&](int q, int x, int y, int zz) {
@@ -261,6 +266,7 @@ __global__ void __launch_bounds__(kRedBlock) k_scale_rhs(int N, const double* __
                                                          const double2* __restrict__ q, double2* __restrict__ qhat,
                                                          double2* __restrict__ partials, KrylovState* st, double tol,
                                                          int max_iter, int m) {
+  pdl_enter();
   double2 acc = make_double2(0, 0);
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p < N) {
@@ -288,11 +294,13 @@ __global__ void __launch_bounds__(kRedBlock) k_scale_rhs(int N, const double* __
 
 template <typename V>
 __global__ void k_cast_vec(int N, const double2* __restrict__ in, V* __restrict__ out) {
+  pdl_enter();
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p < N) out[p] = from_c128<V>(in[p]);
 }
 template <typename V>
 __global__ void k_widen_vec(int N, const V* __restrict__ in, double2* __restrict__ out) {
+  pdl_enter();
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p < N) out[p] = ld64(in, p);
 }
@@ -320,7 +328,7 @@ void run_cycle(Ctx& c, cudaStream_t s) {
     with_nv(nv, [&](auto NV) {
       auto kern = k_gs_dots<TZ, decltype(NV)::value>;
       const unsigned G = (unsigned)std::min<long long>(tiles_xy(g), resident_slots((const void*)kern, kRedBlock));
-      kern<<<G, dim3(BX, BY), 0, s>>>(g, invh2, c.diagA64, Z + (long long)j * N, c.V, c.partials, st);
+      launch_pdl(kern, G, dim3(BX, BY), s, g, invh2, c.diagA64, Z + (long long)j * N, c.V, c.partials, st);
     });
     prof_end(c, pk, s);
     // pass B: w and nv vectors read, w and f written; 8 flops per vector + 4 for the norm
@@ -328,17 +336,17 @@ void run_cycle(Ctx& c, cudaStream_t s) {
     with_nv(nv, [&](auto NV) {
       auto kern = k_gs_update<TZ, decltype(NV)::value>;
       const unsigned G = (unsigned)std::min<long long>(grid_1d(N), resident_slots((const void*)kern, kRedBlock));
-      kern<<<G, kRedBlock, 0, s>>>(N, c.V, (TZ*)L0.f, c.partials, st);
+      launch_pdl(kern, G, kRedBlock, s, N, c.V, (TZ*)L0.f, c.partials, st);
     });
     prof_end(c, pk, s);
   }
   HZ_LAUNCHED();
-  k_solve_y<<<1, 1, 0, s>>>(st);
-  k_update_p<TZ><<<nblk(N, 256), 256, 0, s>>>(N, Z, st, c.p);
+  launch_pdl(k_solve_y, 1, 1, s, st);
+  launch_pdl(k_update_p<TZ>, nblk(N, 256), 256, s, N, Z, st, c.p);
   {
     auto kern = k_true_residual<TZ>;
     const unsigned G = (unsigned)std::min<long long>(tiles_xy(g), resident_slots((const void*)kern, kRedBlock));
-    kern<<<G, dim3(BX, BY), 0, s>>>(g, invh2, c.diagA64, c.p, c.qhat, c.V, (TZ*)L0.f, c.partials, st);
+    launch_pdl(kern, G, dim3(BX, BY), s, g, invh2, c.diagA64, c.p, c.qhat, c.V, (TZ*)L0.f, c.partials, st);
   }
   HZ_LAUNCHED();
 }
@@ -398,13 +406,13 @@ void solve_begin_t(Ctx& c, const double2* q, cudaStream_t user) {
   HZ_CUDA(cudaEventRecord(c.ev_in, user));
   HZ_CUDA(cudaStreamWaitEvent(s, c.ev_in, 0));
   HZ_CUDA(cudaMemsetAsync(&st->counter, 0, sizeof(unsigned), s));
-  k_scale_rhs<<<nblk(N, kRedBlock), kRedBlock, 0, s>>>(N, c.wmass, q, c.qhat, c.partials, st, c.opts.tol,
+  launch_pdl(k_scale_rhs, nblk(N, kRedBlock), kRedBlock, s, N, c.wmass, q, c.qhat, c.partials, st, c.opts.tol,
                                                        c.opts.max_iter, c.opts.restart_m);
   HZ_CUDA(cudaMemsetAsync(c.p, 0, sizeof(double2) * N, s));
   {
     auto kern = k_true_residual<TZ>;
     const unsigned G = (unsigned)std::min<long long>(tiles_xy(g), resident_slots((const void*)kern, kRedBlock));
-    kern<<<G, dim3(BX, BY), 0, s>>>(g, invh2, c.diagA64, c.p, c.qhat, c.V, (TZ*)c.L[0].f, c.partials, st);
+    launch_pdl(kern, G, dim3(BX, BY), s, g, invh2, c.diagA64, c.p, c.qhat, c.V, (TZ*)c.L[0].f, c.partials, st);
   }
   HZ_LAUNCHED();
   c.launches += 2;
@@ -627,9 +635,9 @@ void precond_apply_c128(Ctx& c, const double2* r, double2* z, int nrhs, cudaStre
   const int NR = (int)L0.g.N * nrhs;
   c.nrhs = nrhs;
   if (c.mixed) {
-    k_cast_vec<float2><<<nblk(NR, 256), 256, 0, s>>>(NR, r, (float2*)L0.f);
+    launch_pdl(k_cast_vec<float2>, nblk(NR, 256), 256, s, NR, r, (float2*)L0.f);
     vcycle(c, L0.f, L0.u, nullptr, s);
-    k_widen_vec<float2><<<nblk(NR, 256), 256, 0, s>>>(NR, (const float2*)L0.u, z);
+    launch_pdl(k_widen_vec<float2>, nblk(NR, 256), 256, s, NR, (const float2*)L0.u, z);
   } else {
     HZ_CUDA(cudaMemcpyAsync(L0.f, r, sizeof(double2) * NR, cudaMemcpyDeviceToDevice, s));
     vcycle(c, L0.f, L0.u, nullptr, s);

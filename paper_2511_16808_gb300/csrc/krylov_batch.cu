@@ -108,6 +108,7 @@ __device__ __forceinline__ void block_store_r(double2 acc, int r, int R, double2
 __global__ void __launch_bounds__(kB) k_scale_rhs_b(GeoB g, const double* __restrict__ wmass,
                                                     const double2* __restrict__ q, double2* __restrict__ qhat,
                                                     double2* __restrict__ partials) {
+  pdl_enter();
   const int r = threadIdx.x & (g.R - 1);
   double2 acc = make_double2(0, 0);
   const int base = blockIdx.x * (kB * kPerB) + threadIdx.x;
@@ -130,6 +131,7 @@ enum { kInit = 0, kDots = 1, kArnoldi = 2, kRestart = 3 };
 // kArnoldi: the squared norm -> the Arnoldi column of iteration idx.
 __global__ void k_reduce_b(const double2* __restrict__ partials, int nb, int R, int mode, int idx, KrylovState* st,
                            int* n_active, double tol, int max_iter, int m) {
+  pdl_enter();
   if ((mode == kDots || mode == kArnoldi) && *n_active == 0) return;
   const int r = blockIdx.x;
   KrylovState* s = st + r;
@@ -206,6 +208,7 @@ __global__ void __launch_bounds__(kB) k_gs_dots_b(GeoB g, double invh2, const do
                                                   const TZ* __restrict__ z, double2* __restrict__ V,
                                                   double2* __restrict__ partials, const KrylovState* __restrict__ st,
                                                   const int* n_active) {
+  pdl_enter();
   if (*n_active == 0) return;
   const int r = threadIdx.x & (g.R - 1);
   double2 acc[NV];
@@ -235,6 +238,7 @@ template <typename TF, int NV>
 __global__ void __launch_bounds__(kB) k_gs_update_b(GeoB g, double2* __restrict__ V, TF* __restrict__ f,
                                                     double2* __restrict__ partials,
                                                     const KrylovState* __restrict__ st, const int* n_active) {
+  pdl_enter();
   if (*n_active == 0) return;
   const int r = threadIdx.x & (g.R - 1);
   const KrylovState* s = st + r;
@@ -263,6 +267,7 @@ __global__ void __launch_bounds__(kB) k_gs_update_b(GeoB g, double2* __restrict_
 }
 
 __global__ void k_solve_y_b(KrylovState* st, int R) {
+  pdl_enter();
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= R) return;
   KrylovState* s = st + r;
@@ -279,6 +284,7 @@ __global__ void k_solve_y_b(KrylovState* st, int R) {
 template <typename TZ>
 __global__ void k_update_p_b(GeoB g, const TZ* __restrict__ Z, const KrylovState* __restrict__ st,
                              double2* __restrict__ p) {
+  pdl_enter();
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= g.NR) return;
   const KrylovState* s = st + (q & (g.R - 1));
@@ -299,6 +305,7 @@ __global__ void __launch_bounds__(kB) k_true_residual_b(GeoB g, double invh2, co
                                                         const double2* __restrict__ qhat, double2* __restrict__ rv,
                                                         TF* __restrict__ f, double2* __restrict__ partials,
                                                         const KrylovState* __restrict__ st) {
+  pdl_enter();
   const int r = threadIdx.x & (g.R - 1);
   double2 acc = make_double2(0, 0);
   if (!st[r].st.done) {
@@ -345,26 +352,26 @@ void run_cycle_b(Ctx& c, const GeoB& g, cudaStream_t s) {
     with_nv(nv, [&](auto NV) {
       auto kern = k_gs_dots_b<TZ, decltype(NV)::value>;
       G = persistent_grid(kern, g);
-      kern<<<G, kB, 0, s>>>(g, invh2, c.diagA64, Z + (long long)j * g.NR, c.V, c.partials, st, na);
+      launch_pdl(kern, G, kB, s, g, invh2, c.diagA64, Z + (long long)j * g.NR, c.V, c.partials, st, na);
     });
     prof_end(c, pk, s);
-    k_reduce_b<<<R, kB, 0, s>>>(c.partials, G, R, kDots, nv, st, na, tol, mi, m);
+    launch_pdl(k_reduce_b, R, kB, s, c.partials, G, R, kDots, nv, st, na, tol, mi, m);
     // pass B: w and nv vectors read, w and f written; 8 flops per vector + 4 for the norm
     pk = prof_begin(c, 1, j, NR * (32 + 16.0 * nv + sizeof(TZ)), (8.0 * nv + 4.0) * NR, s);
     with_nv(nv, [&](auto NV) {
       auto kern = k_gs_update_b<TZ, decltype(NV)::value>;
       G = persistent_grid(kern, g);
-      kern<<<G, kB, 0, s>>>(g, c.V, (TZ*)L0.f, c.partials, st, na);
+      launch_pdl(kern, G, kB, s, g, c.V, (TZ*)L0.f, c.partials, st, na);
     });
     prof_end(c, pk, s);
-    k_reduce_b<<<R, kB, 0, s>>>(c.partials, G, R, kArnoldi, j, st, na, tol, mi, m);
+    launch_pdl(k_reduce_b, R, kB, s, c.partials, G, R, kArnoldi, j, st, na, tol, mi, m);
   }
   HZ_LAUNCHED();
-  k_solve_y_b<<<1, 64, 0, s>>>(st, R);
-  k_update_p_b<TZ><<<nblk(g.NR, 256), 256, 0, s>>>(g, Z, st, c.p);
+  launch_pdl(k_solve_y_b, 1, 64, s, st, R);
+  launch_pdl(k_update_p_b<TZ>, nblk(g.NR, 256), 256, s, g, Z, st, c.p);
   const unsigned Gt = persistent_grid(k_true_residual_b<TZ>, g);
-  k_true_residual_b<TZ><<<Gt, kB, 0, s>>>(g, invh2, c.diagA64, c.p, c.qhat, c.V, (TZ*)L0.f, c.partials, st);
-  k_reduce_b<<<R, kB, 0, s>>>(c.partials, Gt, R, kRestart, 0, st, na, tol, mi, m);
+  launch_pdl(k_true_residual_b<TZ>, Gt, kB, s, g, invh2, c.diagA64, c.p, c.qhat, c.V, (TZ*)L0.f, c.partials, st);
+  launch_pdl(k_reduce_b, R, kB, s, c.partials, Gt, R, kRestart, 0, st, na, tol, mi, m);
   HZ_LAUNCHED();
 }
 
@@ -419,13 +426,13 @@ void solve_b(Ctx& c, const double2* q, double2* p, int R, hz_info* info, cudaStr
   HZ_CUDA(cudaEventRecord(c.ev_in, user));
   HZ_CUDA(cudaStreamWaitEvent(s, c.ev_in, 0));
   HZ_CUDA(cudaMemsetAsync(c.n_active, 0, sizeof(int), s));
-  k_scale_rhs_b<<<n1, kB, 0, s>>>(g, c.wmass, q, c.qhat, c.partials);
-  k_reduce_b<<<R, kB, 0, s>>>(c.partials, n1, R, kInit, 0, st, c.n_active, c.opts.tol, c.opts.max_iter,
+  launch_pdl(k_scale_rhs_b, n1, kB, s, g, c.wmass, q, c.qhat, c.partials);
+  launch_pdl(k_reduce_b, R, kB, s, c.partials, n1, R, kInit, 0, st, c.n_active, c.opts.tol, c.opts.max_iter,
                               c.opts.restart_m);
   HZ_CUDA(cudaMemsetAsync(c.p, 0, sizeof(double2) * g.NR, s));
   const unsigned Gt = persistent_grid(k_true_residual_b<TZ>, g);
-  k_true_residual_b<TZ><<<Gt, kB, 0, s>>>(g, invh2, c.diagA64, c.p, c.qhat, c.V, (TZ*)c.L[0].f, c.partials, st);
-  k_reduce_b<<<R, kB, 0, s>>>(c.partials, Gt, R, kRestart, 0, st, c.n_active, c.opts.tol, c.opts.max_iter,
+  launch_pdl(k_true_residual_b<TZ>, Gt, kB, s, g, invh2, c.diagA64, c.p, c.qhat, c.V, (TZ*)c.L[0].f, c.partials, st);
+  launch_pdl(k_reduce_b, R, kB, s, c.partials, Gt, R, kRestart, 0, st, c.n_active, c.opts.tol, c.opts.max_iter,
                               c.opts.restart_m);
   HZ_LAUNCHED();
   c.launches += 4;
