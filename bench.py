@@ -441,8 +441,8 @@ def run_batched(args):
     out = None
     if rank == 0:
         run = lambda: step()  # noqa: E731
-        prof = _profile_class(torch, hz, solvers, run, "mgs_step")
-        first = _profile_class(torch, hz, solvers, run, "mgs_first")
+        prof = _profile_class(torch, hz, solvers, run, "gs_update")
+        first = _profile_class(torch, hz, solvers, run, "gs_apply")
         vprof = _profile_class(torch, hz, solvers, run, "vcycle")
         smoothed = 0
         for l in range(hz.hz_level_count(solvers[0].ctx) - 1):
@@ -475,20 +475,20 @@ def run_batched(args):
             it1 = iters[1]
             cpu = cpu_baseline_sample(args.config, args.cpu_iters, sum(it1) / len(it1))
         peak, src = _peaks()
-        avg_ms = prof["ms"] / max(prof["launches"], 1)
-        achieved = prof["flops"] / max(prof["launches"], 1) / (avg_ms / 1e3) / 1e12
-        roofline = {"kernel": "k_mgs_step_b (FP64 modified Gram-Schmidt update + per-RHS inner products)",
-                    "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": _traffic("k_mgs_step_b", ws[0].name.rsplit("-ppw", 1)[0] + f"-x{R}"),
-                    "launches": prof["launches"], "avg_launch_us": avg_ms * 1e3,
-                    "hbm_achieved_gbs": prof["bytes"] / (prof["ms"] / 1e3) / 1e9 if prof["ms"] else None,
+        wname = ws[0].name.rsplit("-ppw", 1)[0] + f"-x{R}"
+
+        def roof(pr, kernel, label):
+            avg_ms = pr["ms"] / max(pr["launches"], 1)
+            ach = pr["flops"] / max(pr["launches"], 1) / (avg_ms / 1e3) / 1e12 if avg_ms > 0 else None
+            return {"kernel": label, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": ach / FP64_PEAK_TFLOPS if ach else None, "traffic": _traffic(kernel, wname),
+                    "launches": pr["launches"], "avg_launch_us": avg_ms * 1e3, "total_ms": pr["ms"],
+                    "hbm_achieved_gbs": pr["bytes"] / (pr["ms"] / 1e3) / 1e9 if pr["ms"] else None,
                     "peak_note": "FP64 peak derived from DFMA rate x SMs x max clock"}
-        f_ms = first["ms"] / max(first["launches"], 1)
-        first_roof = {"kernel": "k_mgs_first_b (FP64 operator on z + per-RHS inner products)", "bound": "alu",
-                      "achieved": first["flops"] / max(first["launches"], 1) / (f_ms / 1e3) / 1e12 if f_ms else None,
-                      "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "avg_launch_us": f_ms * 1e3,
-                      "launches": first["launches"]}
-        first_roof["frac"] = first_roof["achieved"] / FP64_PEAK_TFLOPS if first_roof["achieved"] else None
+        r_upd = roof(prof, "k_gs_update_b",
+                     "k_gs_update_b (FP64 Gram-Schmidt update + per-RHS norms + cast of the next V-cycle input)")
+        r_dot = roof(first, "k_gs_dots_b", "k_gs_dots_b (FP64 operator on z + the cycle's per-RHS inner products)")
+        roofline, first_roof = (r_dot, r_upd) if first["ms"] >= prof["ms"] else (r_upd, r_dot)
         v_gbs = vprof["bytes"] / (vprof["ms"] / 1e3) / 1e9 if vprof["ms"] else None
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -512,7 +512,7 @@ def run_batched(args):
             "plain_fp64": fp64,
             "clocks": clk.summary(),
             "roofline": roofline,
-            "mgs_first_roofline": first_roof,
+            "roofline_second": first_roof,
             "vcycle_roofline": {"bound": "hbm", "achieved": v_gbs, "peak": peak, "unit": "GB/s",
                                 "frac": v_gbs / peak if v_gbs else None, "peak_source": src,
                                 "avg_vcycle_us": vprof["ms"] * 1e3 / max(vprof["launches"], 1)},
