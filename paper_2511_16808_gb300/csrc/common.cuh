@@ -345,6 +345,7 @@ struct Level {
   GridDev g;
   bool fine = false;
   bool coarsest = false;
+  bool a_sym = false;           // A_s of this level is complex symmetric
   // operator A_s at this level
   StencilLut A;                 // fine: the 2d+1 point offsets; coarse: box of radius rho
   double2* A64 = nullptr;       // FP64 planes [A.n][N] (setup; kept for export when asked)
@@ -354,7 +355,17 @@ struct Level {
   double damping = 1.0;
   StencilLut M;                 // offsets of the assembled Vanka sum (zero planes dropped)
   double2* M64 = nullptr;       // FP64 planes [M.n][N]
-  void* Mw = nullptr;           // working precision planes
+  void* Mw = nullptr;           // working precision planes (diagonal M only)
+  // M in half form: every patch weight is 1/count of its node, so M = D^{-1} M'
+  // with M' = sum_i V_i^T H_i^{-1} V_i, complex symmetric where A_s is (then
+  // H_i = H_i^T; Section 3.2).  Stored: 1/count per node and the planes of M'
+  // at the offsets s >= 0 (lexicographic, z then y then x), M'(p, p - s) being
+  // read as M'(p - s, p) at node p - s; on levels whose operator is not
+  // symmetric the planes of M itself are kept (no weights, nothing mirrored).
+  StencilLut Mh;                // offsets of the stored half
+  unsigned char mh_mirror[HZ_MAX_STENCIL] = {};   // 1: offset -s is stored as s
+  void* Mhw = nullptr;          // working precision planes [Mh.n][N]
+  void* wcw = nullptr;          // working precision 1/count per node [N] (real); null: Mhw holds M
   // transfers to the next coarser level (0 = linear, 1 = cubic)
   int rkind = 0, pkind = 0;
   // work vectors, working precision, N * nrhs_max

@@ -3,8 +3,9 @@
 //
 //   residual    r = f - A_s u          fine: diagonal + index weights (5/7-point);
 //                                      coarse: stored Galerkin planes (box radius rho)
-//   sweep       u += w M r             M = assembled Vanka sum (Eq. smoother); the
-//                                      first sweep from u = 0 is u = w M f
+//   sweep       u += w M r             M = assembled Vanka sum (Eq. smoother) in its
+//                                      symmetric half form; the first sweep from
+//                                      u = 0 is u = w M f
 //   restrict    f_c = R r              Eqs. biliniearIntergrid / bicubicIntergrid (gather)
 //   prolong     u += P e_c             P = 2^d R^T of the same kind (gather)
 //   coarse      u = A_L^{-1} f         dense inverse from setup, one warp per row
@@ -144,7 +145,9 @@ __device__ __forceinline__ void stp(c_t<T>* a, int q, const pk_t<T, VR>& v) {
 }
 inline unsigned nblk(long long n, int b) { return (unsigned)((n + b - 1) / b); }
 
-// Offsets of an assembled Vanka sum with their flat index offsets on one level.
+// Offsets of a stored Vanka sum that is applied as it is (no mirroring), with
+// their flat field index offsets (kept small: the list travels in the kernel
+// parameters of every sweep launch).
 struct MList {
   int n, rho;
   int flat[kMaxM];
@@ -152,13 +155,37 @@ struct MList {
 };
 
 inline MList mlist(const Level& L, int R = 1) {
-  require(L.M.off.n <= kMaxM, "Vanka stencil too large");
+  require(L.Mh.off.n <= kMaxM, "Vanka stencil too large");
   MList m;
-  m.n = L.M.off.n;
-  m.rho = L.M.off.rho;
+  m.n = L.Mh.off.n;
+  m.rho = L.Mh.off.rho;
   for (int s = 0; s < m.n; ++s) {
-    for (int a = 0; a < 3; ++a) m.d[s][a] = L.M.off.d[s][a];
-    m.flat[s] = (L.M.off.d[s][0] + L.M.off.d[s][1] * L.g.nx + L.M.off.d[s][2] * L.g.nx * L.g.ny) * R;
+    for (int a = 0; a < 3; ++a) m.d[s][a] = L.Mh.off.d[s][a];
+    m.flat[s] = (L.Mh.off.d[s][0] + L.Mh.off.d[s][1] * L.g.nx + L.Mh.off.d[s][2] * L.g.nx * L.g.ny) * R;
+  }
+  return m;
+}
+
+// The stored half of a symmetric Vanka sum (setup: L.Mh, L.mh_mirror):
+// offsets with node and field index offsets, and whether -s is applied too.
+struct SList {
+  int n, rho;
+  int flat[kMaxM];              // field index offset (node offset x R)
+  int nflat[kMaxM];             // node index offset
+  signed char d[kMaxM][3];
+  unsigned char mirror[kMaxM];
+};
+
+inline SList slist(const Level& L, int R = 1) {
+  require(L.Mh.off.n <= kMaxM, "Vanka stencil too large");
+  SList m;
+  m.n = L.Mh.off.n;
+  m.rho = L.Mh.off.rho;
+  for (int s = 0; s < m.n; ++s) {
+    for (int a = 0; a < 3; ++a) m.d[s][a] = L.Mh.off.d[s][a];
+    m.nflat[s] = L.Mh.off.d[s][0] + L.Mh.off.d[s][1] * L.g.nx + L.Mh.off.d[s][2] * L.g.nx * L.g.ny;
+    m.flat[s] = m.nflat[s] * R;
+    m.mirror[s] = L.mh_mirror[s];
   }
   return m;
 }
@@ -276,6 +303,35 @@ __device__ __forceinline__ auto list_Au(const Geo& g, const MList& m, const c_t<
   return acc;
 }
 
+// (M v)_p from the stored form: symmetric half (M = D^{-1} M', M'(p, p+s)
+// stored at node p for the half offsets, M'(p, p-s) = M'(p-s, p) read at node
+// p-s, then the weight 1/count_p), or all planes of M itself (wc null).
+template <typename T, int DIM, bool CHECK, bool SYM, typename LST, typename LD>
+__device__ __forceinline__ auto sym_Au(const Geo& g, const LST& m, const c_t<T>* __restrict__ P,
+                                       const T* __restrict__ wc, const LD& ld, int p, int q, int x, int y, int z) {
+  using V = decltype(ld(0));
+  V acc = pk_zero<V>();
+  for (int s = 0; s < m.n; ++s) {
+    if (CHECK) {
+      const int dx = m.d[s][0], dy = m.d[s][1], dz = m.d[s][2];
+      const bool okp = x + dx >= 0 && x + dx < g.nx && y + dy >= 0 && y + dy < g.ny &&
+                       (DIM == 2 || (z + dz >= 0 && z + dz < g.nz));
+      if (okp) acc = cfma(P[s * g.N + p], ld(q + m.flat[s]), acc);
+      if constexpr (SYM) {
+        const bool okm = x - dx >= 0 && x - dx < g.nx && y - dy >= 0 && y - dy < g.ny &&
+                         (DIM == 2 || (z - dz >= 0 && z - dz < g.nz));
+        if (m.mirror[s] && okm) acc = cfma(P[s * g.N + p - m.nflat[s]], ld(q - m.flat[s]), acc);
+      }
+    } else {
+      acc = cfma(P[s * g.N + p], ld(q + m.flat[s]), acc);
+      if constexpr (SYM)
+        if (m.mirror[s]) acc = cfma(P[s * g.N + p - m.nflat[s]], ld(q - m.flat[s]), acc);
+    }
+  }
+  if constexpr (SYM) return wc[p] * acc;
+  else return acc;                           // the planes hold M itself
+}
+
 // ------------------------------------------------------------------ kernels
 
 // r = f - A u
@@ -308,6 +364,22 @@ __global__ void __launch_bounds__(BX* BY) k_sweep0(Geo g, MList m, const c_t<T>*
   auto ld = [f](int i) { return ldp<T, VR>(f, i); };
   const pk_t<T, VR> v = in ? list_Au<T, DIM, false>(g, m, M, ld, p, q, x, y, z)
                            : list_Au<T, DIM, true>(g, m, M, ld, p, q, x, y, z);
+  stp<T, VR>(u, q, w * v);
+}
+
+// symmetric half form: u = w D^{-1} M' f
+template <typename T, int DIM, int VR>
+__global__ void __launch_bounds__(BX* BY) k_sweep0_sym(Geo g, SList m, const c_t<T>* __restrict__ M,
+                                                   const T* __restrict__ wc, T w, const c_t<T>* __restrict__ f,
+                                                   c_t<T>* __restrict__ u, const int* active) {
+  pdl_enter();
+  if (active && !*active) return;
+  const bool in = interior_block<DIM>(g, m.rho);
+  int x, y, z, p, q;
+  if (!node_xyz(g, x, y, z, p, q)) return;
+  auto ld = [f](int i) { return ldp<T, VR>(f, i); };
+  const pk_t<T, VR> v = in ? sym_Au<T, DIM, false, true>(g, m, M, wc, ld, p, q, x, y, z)
+                           : sym_Au<T, DIM, true, true>(g, m, M, wc, ld, p, q, x, y, z);
   stp<T, VR>(u, q, w * v);
 }
 
@@ -345,6 +417,22 @@ __global__ void __launch_bounds__(BX* BY) k_sweep_out(Geo g, MList m, const c_t<
   auto ld = [r](int i) { return ldp<T, VR>(r, i); };
   const pk_t<T, VR> v = inb ? list_Au<T, DIM, false>(g, m, M, ld, p, q, x, y, z)
                             : list_Au<T, DIM, true>(g, m, M, ld, p, q, x, y, z);
+  stp<T, VR>(out, q, ldp<T, VR>(in, q) + w * v);
+}
+
+// symmetric half form: out = in + w D^{-1} M' r
+template <typename T, int DIM, int VR>
+__global__ void __launch_bounds__(BX* BY) k_sweep_out_sym(Geo g, SList m, const c_t<T>* __restrict__ M,
+                                                      const T* __restrict__ wc, T w, const c_t<T>* __restrict__ r,
+                                                      const c_t<T>* in, c_t<T>* out, const int* active) {
+  pdl_enter();
+  if (active && !*active) return;
+  const bool inb = interior_block<DIM>(g, m.rho);
+  int x, y, z, p, q;
+  if (!node_xyz(g, x, y, z, p, q)) return;
+  auto ld = [r](int i) { return ldp<T, VR>(r, i); };
+  const pk_t<T, VR> v = inb ? sym_Au<T, DIM, false, true>(g, m, M, wc, ld, p, q, x, y, z)
+                            : sym_Au<T, DIM, true, true>(g, m, M, wc, ld, p, q, x, y, z);
   stp<T, VR>(out, q, ldp<T, VR>(in, q) + w * v);
 }
 
@@ -631,6 +719,18 @@ void with_dim_ak(int dim, int ak, F&& f) {
 
 inline int akind(const Level& L) { return L.fine ? 0 : L.A.off.rho; }
 
+// dimension and stored form of a level's smoother (symmetric half or M itself)
+template <typename F>
+void dispatch_dim_sym(const Level& L, F&& f) {
+  using I2 = std::integral_constant<int, 2>;
+  using I3 = std::integral_constant<int, 3>;
+  using ST = std::integral_constant<bool, true>;
+  using SF = std::integral_constant<bool, false>;
+  const bool sym = L.wcw != nullptr;
+  if (L.g.dim == 2) sym ? f(I2{}, ST{}) : f(I2{}, SF{});
+  else sym ? f(I3{}, ST{}) : f(I3{}, SF{});
+}
+
 // RHS pack width for nrhs right-hand sides: 32 bytes per thread once there
 // are enough of them, else one value
 template <typename T, typename F>
@@ -657,18 +757,20 @@ void resid(Ctx& c, int l, const void* u, const void* f, void* r, const int* acti
 template <typename T>
 void sweep_out(Ctx& c, int l, const void* r, const void* in, void* out, const int* active, cudaStream_t s) {
   Level& L = c.L[l];
-  const MList m = mlist(L, c.nrhs);
   with_vr<T>(c.nrhs, [&](auto V) {
     constexpr int VR = decltype(V)::value;
     const Geo g = geo(L.g, c.nrhs, VR);
-    if (L.g.dim == 2)
-      launch_pdl(k_sweep_out<T, 2, VR>, grid_of(g), dim3(BX, BY), s, g, m, (const c_t<T>*)L.Mw, (T)L.damping,
-                                                                (const c_t<T>*)r, (const c_t<T>*)in, (c_t<T>*)out,
-                                                                active);
-    else
-      launch_pdl(k_sweep_out<T, 3, VR>, grid_of(g), dim3(BX, BY), s, g, m, (const c_t<T>*)L.Mw, (T)L.damping,
-                                                                (const c_t<T>*)r, (const c_t<T>*)in, (c_t<T>*)out,
-                                                                active);
+    auto go = [&](auto D, auto S) {
+      constexpr int DIM = decltype(D)::value;
+      if constexpr (decltype(S)::value)
+        launch_pdl(k_sweep_out_sym<T, DIM, VR>, grid_of(g), dim3(BX, BY), s, g, slist(L, c.nrhs),
+                   (const c_t<T>*)L.Mhw, (const T*)L.wcw, (T)L.damping, (const c_t<T>*)r, (const c_t<T>*)in,
+                   (c_t<T>*)out, active);
+      else
+        launch_pdl(k_sweep_out<T, DIM, VR>, grid_of(g), dim3(BX, BY), s, g, mlist(L, c.nrhs),
+                   (const c_t<T>*)L.Mhw, (T)L.damping, (const c_t<T>*)r, (const c_t<T>*)in, (c_t<T>*)out, active);
+    };
+    dispatch_dim_sym(L, go);
   });
   HZ_LAUNCHED();
 }
@@ -676,16 +778,19 @@ void sweep_out(Ctx& c, int l, const void* r, const void* in, void* out, const in
 template <typename T>
 void sweep0(Ctx& c, int l, const void* f, void* u, const int* active, cudaStream_t s) {
   Level& L = c.L[l];
-  const MList m = mlist(L, c.nrhs);
   with_vr<T>(c.nrhs, [&](auto V) {
     constexpr int VR = decltype(V)::value;
     const Geo g = geo(L.g, c.nrhs, VR);
-    if (L.g.dim == 2)
-      launch_pdl(k_sweep0<T, 2, VR>, grid_of(g), dim3(BX, BY), s, g, m, (const c_t<T>*)L.Mw, (T)L.damping,
-                                                             (const c_t<T>*)f, (c_t<T>*)u, active);
-    else
-      launch_pdl(k_sweep0<T, 3, VR>, grid_of(g), dim3(BX, BY), s, g, m, (const c_t<T>*)L.Mw, (T)L.damping,
-                                                             (const c_t<T>*)f, (c_t<T>*)u, active);
+    auto go = [&](auto D, auto S) {
+      constexpr int DIM = decltype(D)::value;
+      if constexpr (decltype(S)::value)
+        launch_pdl(k_sweep0_sym<T, DIM, VR>, grid_of(g), dim3(BX, BY), s, g, slist(L, c.nrhs),
+                   (const c_t<T>*)L.Mhw, (const T*)L.wcw, (T)L.damping, (const c_t<T>*)f, (c_t<T>*)u, active);
+      else
+        launch_pdl(k_sweep0<T, DIM, VR>, grid_of(g), dim3(BX, BY), s, g, mlist(L, c.nrhs), (const c_t<T>*)L.Mhw,
+                   (T)L.damping, (const c_t<T>*)f, (c_t<T>*)u, active);
+    };
+    dispatch_dim_sym(L, go);
   });
   HZ_LAUNCHED();
 }

@@ -357,6 +357,22 @@ __global__ void k_vanka_gather(GridDev g, PatchDesc pd, StencilLut Ml, const dou
   }
 }
 
+// M' planes at the stored half offsets and 1/count per node: M'[s](p) =
+// count_p M[s](p) (count_p = patches containing p, the inverse of the weight
+// the gather applied), wc(p) = 1/count_p (0 where no patch contains p).
+__global__ void k_sym_half(GridDev g, PatchDesc pd, const double2* __restrict__ M64, int nh,
+                           const short* __restrict__ src, double2* __restrict__ Mh, double* __restrict__ wc) {
+  const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= g.N) return;
+  int x, y, z;
+  node_coords(g, j, x, y, z);
+  int count = 0;
+  for (int k = 0; k < pd.np; ++k)
+    if (anchor_ok(g, pd, x - pd.d[k][0], y - pd.d[k][1], z - pd.d[k][2])) ++count;
+  wc[j] = count ? 1.0 / count : 0.0;
+  for (int h = 0; h < nh; ++h) Mh[(long long)h * g.N + j] = (double)count * M64[(long long)src[h] * g.N + j];
+}
+
 // 1 in out[e] when plane e of `planes` has a non-zero entry (block-wide OR,
 // one atomic per block)
 __global__ void k_plane_nonzero(const double2* __restrict__ planes, long long N, unsigned long long* __restrict__ out) {
@@ -549,6 +565,28 @@ static void launch_vanka(Level& L, const PatchDesc& pd, const StencilLut& Mfull,
   HZ_CUDA(cudaFreeAsync(Hinv, s));
 }
 
+template <typename V>
+__global__ void k_cast_real(const double* __restrict__ in, V* __restrict__ out, long long n) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) out[t] = (V)in[t];
+}
+
+static void* working_copy_real(Ctx& c, const double* src, long long n, cudaStream_t s) {
+  if (!c.mixed) return (void*)src;
+  float* dst = (float*)ctx_alloc(c, sizeof(float) * n);
+  k_cast_real<float><<<nblk(n, 256), 256, 0, s>>>(src, dst, n);
+  HZ_LAUNCHED();
+  return dst;
+}
+
+static void* working_copy(Ctx& c, const double2* src, long long n, cudaStream_t s) {
+  if (!c.mixed) return (void*)src;             // FP64 path works on the setup arrays
+  float2* dst = (float2*)ctx_alloc(c, sizeof(float2) * n);
+  k_cast<float2><<<nblk(n, 256), 256, 0, s>>>(src, dst, n);
+  HZ_LAUNCHED();
+  return dst;
+}
+
 static void assemble_smoother(Ctx& c, Level& L, cudaStream_t s) {
   const int dim = c.grid.dim;
   auto po = patch_offsets(dim, L.patch);
@@ -608,18 +646,46 @@ static void assemble_smoother(Ctx& c, Level& L, cudaStream_t s) {
   for (size_t k = 0; k < src.size(); ++k)
     HZ_CUDA(cudaMemcpyAsync(L.M64 + (long long)k * N, Mp + (long long)src[k] * N, sizeof(double2) * N,
                             cudaMemcpyDeviceToDevice, s));
+  if (!L.a_sym) {
+    // operator not symmetric: the weighted planes of M as they are (working
+    // copy made by the caller)
+    L.Mh = L.M;
+    L.wcw = nullptr;
+  } else {
+    // half set: s >= 0 lexicographically (z, y, x), mirrored when -s is in the set too
+    std::vector<std::array<int, 3>> half;
+    std::vector<short> hsrc;
+    std::vector<unsigned char> mirror;
+    for (size_t k = 0; k < keep.size(); ++k) {
+      const auto& d = keep[k];
+      const bool pos = d[2] > 0 || (d[2] == 0 && (d[1] > 0 || (d[1] == 0 && d[0] >= 0)));
+      const bool has_neg = L.M.lut[lut_index(-d[0], -d[1], -d[2])] >= 0;
+      const bool zero = d[0] == 0 && d[1] == 0 && d[2] == 0;
+      if (pos || !has_neg) {            // a negative offset without its mirror is stored as it is
+        half.push_back(d);
+        hsrc.push_back((short)k);
+        mirror.push_back((unsigned char)(pos && has_neg && !zero));
+      }
+    }
+    L.Mh = make_lut(half);
+    for (size_t k = 0; k < half.size(); ++k) L.mh_mirror[k] = mirror[k];
+    short* dsrc = nullptr;
+    HZ_CUDA(cudaMallocAsync(&dsrc, sizeof(short) * hsrc.size(), s));
+    HZ_CUDA(cudaMemcpyAsync(dsrc, hsrc.data(), sizeof(short) * hsrc.size(), cudaMemcpyHostToDevice, s));
+    double2* Mh64 = (double2*)ctx_alloc(c, sizeof(double2) * N * half.size());
+    double* wc64 = (double*)ctx_alloc(c, sizeof(double) * N);
+    k_sym_half<<<nblk(N, 256), 256, 0, s>>>(L.g, pd, L.M64, (int)half.size(), dsrc, Mh64, wc64);
+    HZ_LAUNCHED();
+    HZ_CUDA(cudaStreamSynchronize(s));  // hsrc (host) and dsrc are released below
+    HZ_CUDA(cudaFreeAsync(dsrc, s));
+    L.Mhw = working_copy(c, Mh64, N * (long long)half.size(), s);
+    L.wcw = working_copy_real(c, wc64, N, s);
+  }
   cudaFreeAsync(Mp, s);
   cudaFreeAsync(sing, s);
   cudaFreeAsync(amax, s);
 }
 
-static void* working_copy(Ctx& c, const double2* src, long long n, cudaStream_t s) {
-  if (!c.mixed) return (void*)src;             // FP64 path works on the setup arrays
-  float2* dst = (float2*)ctx_alloc(c, sizeof(float2) * n);
-  k_cast<float2><<<nblk(n, 256), 256, 0, s>>>(src, dst, n);
-  HZ_LAUNCHED();
-  return dst;
-}
 
 static int rkind_of(hz_intergrid ig, int level) {
   switch (ig) {
@@ -651,6 +717,9 @@ void build_hierarchy(Ctx& c, const double* kappa, const double* gamma, double ga
     L.damping = c.opts.damping[l];
     L.rkind = rkind_of(c.opts.intergrid, l);
     L.pkind = pkind_of(c.opts.intergrid, l);
+    // A_s is complex symmetric on the fine level; R A P keeps that when R is a
+    // scaled P^T (same kind of both transfers), not for linear R / cubic P
+    L.a_sym = l == 0 || (c.L[l - 1].a_sym && c.L[l - 1].rkind == c.L[l - 1].pkind);
     for (int a = 0; a < dim; ++a) n[a] = (n[a] - 1) / 2 + 1;
   }
   // a1: fine coefficients
@@ -681,7 +750,8 @@ void build_hierarchy(Ctx& c, const double* kappa, const double* gamma, double ga
       const long long T = C.g.N * C.A.off.n;
       k_galerkin<<<nblk(T, 128), 128, 0, s>>>(L.g, L.A.off, L.A64, C.g, C.A.off, C.A64, L.rkind, L.pkind);
       HZ_LAUNCHED();
-      L.Mw = working_copy(c, L.M64, N * L.M.off.n, s);
+      if (L.m_diag) L.Mw = working_copy(c, L.M64, N, s);
+      if (!L.a_sym) L.Mhw = working_copy(c, L.M64, N * (long long)L.M.off.n, s);
     }
     // working operator: fine = diagonal of A_s (plane 0), coarse = all planes
     L.Aw = working_copy(c, L.A64, L.fine ? N : N * L.A.off.n, s);
