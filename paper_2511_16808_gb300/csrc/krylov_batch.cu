@@ -45,8 +45,19 @@ __device__ __forceinline__ double2 apply_A_b(const GeoB& g, double invh2, const 
   const bool inx = x > 0 && x < g.nx - 1, iny = y > 0 && y < g.ny - 1;
   const bool inz = g.dim == 2 || (z > 0 && z < g.nz - 1);
   if (inx && iny && inz) {
-    double2 s = ld64(v, q - g.R) + ld64(v, q + g.R) + ld64(v, q - g.nxR) + ld64(v, q + g.nxR);
-    if (g.dim == 3) s = s + ld64(v, q - g.sxyR) + ld64(v, q + g.sxyR);
+    double2 s;
+    if constexpr (std::is_same<U, float2>::value) {
+      if (g.dim == 3) {
+        const float2 n[6] = {v[q - g.R], v[q + g.R], v[q - g.nxR], v[q + g.nxR], v[q - g.sxyR], v[q + g.sxyR]};
+        s = nbr_sum<6>(n);
+      } else {
+        const float2 n[4] = {v[q - g.R], v[q + g.R], v[q - g.nxR], v[q + g.nxR]};
+        s = nbr_sum<4>(n);
+      }
+    } else {
+      s = ld64(v, q - g.R) + ld64(v, q + g.R) + ld64(v, q - g.nxR) + ld64(v, q + g.nxR);
+      if (g.dim == 3) s = s + ld64(v, q - g.sxyR) + ld64(v, q + g.sxyR);
+    }
     return make_double2(fma(d.x, vp.x, fma(-d.y, vp.y, -invh2 * s.x)), fma(d.x, vp.y, fma(d.y, vp.x, -invh2 * s.y)));
   }
   double2 acc = cmul(d, vp);

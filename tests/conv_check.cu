@@ -2,12 +2,36 @@
 // path (test infrastructure): reads raw float32 / float64 bit patterns, writes
 // f2d_exact / d2f_rn of each, for a bit-for-bit comparison with numpy.
 // usage: conv_check <f32 in> <f64 out> <f64 in> <f32 out>
+//        conv_check --sum <f32 in, groups of 6> <f64 out: fsum_wide of the first 4 and of all 6>
 #include <cstdio>
+#include <cstring>
 #include <vector>
 
-#include "common.cuh"
+#include "krylov_impl.cuh"
+
+static int sums(const char* in, const char* out) {
+  FILE* f = fopen(in, "rb");
+  if (!f) return 3;
+  std::vector<float> v;
+  float x;
+  while (fread(&x, 4, 1, f) == 1) v.push_back(x);
+  fclose(f);
+  std::vector<double> r;
+  for (size_t i = 0; i + 6 <= v.size(); i += 6) {
+    const float a4[4] = {v[i], v[i + 1], v[i + 2], v[i + 3]};
+    const float a6[6] = {v[i], v[i + 1], v[i + 2], v[i + 3], v[i + 4], v[i + 5]};
+    r.push_back(hz::fsum_wide<4>(a4));
+    r.push_back(hz::fsum_wide<6>(a6));
+  }
+  FILE* o = fopen(out, "wb");
+  if (!o) return 4;
+  fwrite(r.data(), 8, r.size(), o);
+  fclose(o);
+  return 0;
+}
 
 int main(int argc, char** argv) {
+  if (argc == 4 && strcmp(argv[1], "--sum") == 0) return sums(argv[2], argv[3]);
   if (argc != 5) return 2;
   auto rd = [](const char* p, size_t el, std::vector<unsigned char>& b) {
     FILE* f = fopen(p, "rb");

@@ -1,4 +1,5 @@
-"""The CUDA path's integer-pipe float <-> double conversions, bit for bit.
+"""The CUDA path's integer-pipe float <-> double conversions, bit for bit, and
+its error-free FP32 neighbour sums against exactly rounded sums.
 
 The FP64 Krylov passes widen FP32 vectors and the mixed V-cycle narrows FP64
 ones with integer operations only (the hardware conversion runs on the slow
@@ -101,3 +102,27 @@ def test_narrowing_rounds_to_nearest_even(conv_bin, tmp_path):
     assert np.all(np.isnan(narrow[nan]))
     # signed zeros / infinities / subnormal results are all present in the sample
     assert np.any(ref[~nan] == 0) and np.any(np.isinf(ref)) and np.any((ref != 0) & (np.abs(ref) < 1.1754944e-38))
+
+
+def test_neighbour_sums_within_bound(conv_bin, tmp_path):
+    """fsum_wide (FP32 two-sums + one FP64 add) against math.fsum of the same
+    values: |error| <= (n-1)^2 2^-48 max partial sum, on random values of
+    mixed magnitudes and on sets built to cancel."""
+    import math
+    rng = np.random.default_rng(7)
+    m = 20000
+    g = rng.standard_normal((m, 6)) * 10.0 ** rng.integers(-6, 7, size=(m, 6))
+    g[: m // 4, 1] = -g[: m // 4, 0] * (1 + 1e-7 * rng.standard_normal(m // 4))   # near cancellation
+    g[m // 4: m // 2, 5] = -g[m // 4: m // 2, :5].sum(axis=1)
+    f = g.astype(np.float32)
+    inp = os.path.join(str(tmp_path), "s.bin")
+    out = os.path.join(str(tmp_path), "r.bin")
+    f.tofile(inp)
+    subprocess.run([conv_bin, "--sum", inp, out], check=True)
+    r = np.fromfile(out, dtype=np.float64).reshape(m, 2)
+    for k, n in ((0, 4), (1, 6)):
+        vals = f[:, :n].astype(np.float64)
+        exact = np.array([math.fsum(row) for row in vals])
+        partial = np.max(np.abs(np.cumsum(vals, axis=1)), axis=1)
+        bound = (n - 1) ** 2 * 2.0 ** -48 * partial
+        assert np.all(np.abs(r[:, k] - exact) <= bound), np.max(np.abs(r[:, k] - exact) / np.maximum(bound, 1e-300))
