@@ -268,11 +268,15 @@ __device__ __forceinline__ auto box_Au(const Geo& g, const c_t<T>* __restrict__ 
 #pragma unroll
       for (int dx = -RHO; dx <= RHO; ++dx) {
         const int s = ((dz + RZ) * W + (dy + RHO)) * W + (dx + RHO);
+        int qq = q + dx * g.R + dy * g.nxR + dz * g.sxyR;
         if (CHECK) {
-          if (x + dx < 0 || x + dx >= g.nx || y + dy < 0 || y + dy >= g.ny) continue;
-          if (DIM == 3 && (z + dz < 0 || z + dz >= g.nz)) continue;
+          // branch-free: a neighbour outside the grid has a zero plane entry,
+          // so it is read at the node itself (a valid address) and adds 0
+          const bool ok = x + dx >= 0 && x + dx < g.nx && y + dy >= 0 && y + dy < g.ny &&
+                          (DIM == 2 || (z + dz >= 0 && z + dz < g.nz));
+          qq = ok ? qq : q;
         }
-        acc = cfma(P[s * g.N + p], ld(q + dx * g.R + dy * g.nxR + dz * g.sxyR), acc);
+        acc = cfma(P[s * g.N + p], ld(qq), acc);
       }
   return acc;
 }
@@ -293,12 +297,14 @@ __device__ __forceinline__ auto list_Au(const Geo& g, const MList& m, const c_t<
   using V = decltype(ld(0));
   V acc = pk_zero<V>();
   for (int s = 0; s < m.n; ++s) {
+    int qq = q + m.flat[s];
     if (CHECK) {
+      // branch-free: the plane entry of a neighbour outside the grid is zero
       const int xx = x + m.d[s][0], yy = y + m.d[s][1], zz = z + m.d[s][2];
-      if (xx < 0 || xx >= g.nx || yy < 0 || yy >= g.ny) continue;
-      if (DIM == 3 && (zz < 0 || zz >= g.nz)) continue;
+      const bool ok = xx >= 0 && xx < g.nx && yy >= 0 && yy < g.ny && (DIM == 2 || (zz >= 0 && zz < g.nz));
+      qq = ok ? qq : q;
     }
-    acc = cfma(P[s * g.N + p], ld(q + m.flat[s]), acc);
+    acc = cfma(P[s * g.N + p], ld(qq), acc);
   }
   return acc;
 }
@@ -313,14 +319,17 @@ __device__ __forceinline__ auto sym_Au(const Geo& g, const LST& m, const c_t<T>*
   V acc = pk_zero<V>();
   for (int s = 0; s < m.n; ++s) {
     if (CHECK) {
+      // branch-free: out-of-grid terms read valid addresses and add 0 (the
+      // + entry is stored as zero; the mirrored coefficient is selected to 0)
       const int dx = m.d[s][0], dy = m.d[s][1], dz = m.d[s][2];
       const bool okp = x + dx >= 0 && x + dx < g.nx && y + dy >= 0 && y + dy < g.ny &&
                        (DIM == 2 || (z + dz >= 0 && z + dz < g.nz));
-      if (okp) acc = cfma(P[s * g.N + p], ld(q + m.flat[s]), acc);
+      acc = cfma(P[s * g.N + p], ld(okp ? q + m.flat[s] : q), acc);
       if constexpr (SYM) {
-        const bool okm = x - dx >= 0 && x - dx < g.nx && y - dy >= 0 && y - dy < g.ny &&
+        const bool okm = m.mirror[s] && x - dx >= 0 && x - dx < g.nx && y - dy >= 0 && y - dy < g.ny &&
                          (DIM == 2 || (z - dz >= 0 && z - dz < g.nz));
-        if (m.mirror[s] && okm) acc = cfma(P[s * g.N + p - m.nflat[s]], ld(q - m.flat[s]), acc);
+        const c_t<T> cm = P[s * g.N + (okm ? p - m.nflat[s] : p)];
+        acc = cfma(okm ? cm : cmk<c_t<T>>(0, 0), ld(okm ? q - m.flat[s] : q), acc);
       }
     } else {
       acc = cfma(P[s * g.N + p], ld(q + m.flat[s]), acc);
@@ -478,33 +487,36 @@ __global__ void __launch_bounds__(BX* BY) k_restrict(Geo gf, Geo gc, const c_t<T
   const int rr = qc & (gc.R - 1);
   constexpr int RAD = KIND ? 2 : 1;
   constexpr int RZ = DIM == 3 ? RAD : 0;
+  // weights are zero outside the fine grid; those terms read a clamped (valid)
+  // index, so the loops carry no branches and the loads issue together
   T wx[2 * RAD + 1], wy[2 * RAD + 1], wz[2 * RZ + 1];
+  int ix[2 * RAD + 1], iy[2 * RAD + 1], iz[2 * RZ + 1];
 #pragma unroll
   for (int k = 0; k <= 2 * RAD; ++k) {
-    const int ix = 2 * X - RAD + k, iy = 2 * Y - RAD + k;
-    wx[k] = (ix >= 0 && ix < gf.nx) ? (T)(0.5f * p1f(KIND, gf.nx, gc.nx, ix, X)) : T(0);
-    wy[k] = (iy >= 0 && iy < gf.ny) ? (T)(0.5f * p1f(KIND, gf.ny, gc.ny, iy, Y)) : T(0);
+    const int jx = 2 * X - RAD + k, jy = 2 * Y - RAD + k;
+    const bool okx = jx >= 0 && jx < gf.nx, oky = jy >= 0 && jy < gf.ny;
+    wx[k] = okx ? (T)(0.5f * p1f(KIND, gf.nx, gc.nx, jx, X)) : T(0);
+    wy[k] = oky ? (T)(0.5f * p1f(KIND, gf.ny, gc.ny, jy, Y)) : T(0);
+    ix[k] = okx ? jx : 2 * X;
+    iy[k] = oky ? jy : 2 * Y;
   }
 #pragma unroll
   for (int k = 0; k <= 2 * RZ; ++k) {
-    const int iz = 2 * Z - RZ + k;
-    wz[k] = DIM == 3 ? ((iz >= 0 && iz < gf.nz) ? (T)(0.5f * p1f(KIND, gf.nz, gc.nz, iz, Z)) : T(0)) : T(1);
+    const int jz = 2 * Z - RZ + k;
+    const bool okz = DIM == 2 || (jz >= 0 && jz < gf.nz);
+    wz[k] = DIM == 3 ? (okz ? (T)(0.5f * p1f(KIND, gf.nz, gc.nz, jz, Z)) : T(0)) : T(1);
+    iz[k] = okz ? jz : 2 * Z;
   }
   pk_t<T, VR> acc = pk_zero<pk_t<T, VR>>();
 #pragma unroll
   for (int kz = 0; kz <= 2 * RZ; ++kz) {
-    if (wz[kz] == T(0)) continue;
-    const int iz = 2 * Z - RZ + kz;
 #pragma unroll
     for (int ky = 0; ky <= 2 * RAD; ++ky) {
       const T wyz = wy[ky] * wz[kz];
-      if (wyz == T(0)) continue;
-      const int row = ((iz * gf.ny + (2 * Y - RAD + ky)) * gf.nx + 2 * X - RAD) * gf.R + rr;
+      const int row = (iz[kz] * gf.ny + iy[ky]) * gf.nx;
 #pragma unroll
-      for (int kx = 0; kx <= 2 * RAD; ++kx) {
-        if (wx[kx] == T(0)) continue;
-        acc = acc + (wyz * wx[kx]) * ldp<T, VR>(r, row + kx * gf.R);
-      }
+      for (int kx = 0; kx <= 2 * RAD; ++kx)
+        acc = acc + (wyz * wx[kx]) * ldp<T, VR>(r, (row + ix[kx]) * gf.R + rr);
     }
   }
   stp<T, VR>(fc, qc, acc);
