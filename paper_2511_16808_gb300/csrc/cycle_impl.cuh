@@ -668,35 +668,63 @@ __global__ void k_dense_gemv(int n, const c_t<T>* __restrict__ A, const c_t<T>* 
 // complex GEMM): 256 threads per block, each computing rows i0, i0+1 of one
 // RHS; a block covers TM = 512/R <= 64 rows x all R right-hand sides.  K is
 // walked in chunks (32 complex floats / 16 complex doubles): the chunk of the
-// block's Ainv rows and of f are staged in shared memory, then every thread
-// does two complex FMAs per staged column, in a fixed order.
+// block's Ainv rows and of f are staged in shared memory (the next one already
+// loading into registers), then every thread does two complex FMAs per staged
+// column, in a fixed order.
 template <typename T>
 __global__ void __launch_bounds__(256) k_dense_gemm_rhs(int n, int R, const c_t<T>* __restrict__ A,
                                                         const c_t<T>* __restrict__ f, c_t<T>* __restrict__ u,
                                                         const int* active) {
   pdl_enter();
   if (active && !*active) return;
+  using V = c_t<T>;
   constexpr int KC = sizeof(T) == 4 ? 32 : 16;
-  __shared__ c_t<T> As[64][KC + 1];
-  __shared__ c_t<T> Fs[KC * 64];
+  constexpr int PA = 2 * KC / 8, PF = KC * 64 / 256;   // staged values per thread at most (R >= 8)
+  __shared__ V As[64][KC + 1];
+  __shared__ V Fs[KC * 64];
   const int TM = 512 / R;
   const int tid = threadIdx.x;
   const int rhs = tid & (R - 1), rg = tid / R;
   const int row0 = blockIdx.x * TM;
   const int i0 = row0 + 2 * rg, i1 = i0 + 1;
-  c_t<T> acc0 = cmk<c_t<T>>(0, 0), acc1 = cmk<c_t<T>>(0, 0);
-  for (int k0 = 0; k0 < n; k0 += KC) {
+  const int na = TM * KC, nf = KC * R;                 // staged values per chunk
+  V ra[PA], rf[PF];
+  // the next chunk is read into registers while the current one is multiplied
+  auto fetch = [&](int k0) {
     const int kc = min(KC, n - k0);
-    __syncthreads();
-    for (int e = tid; e < TM * KC; e += 256) {
-      const int r = e / KC, k = e - r * KC;
-      As[r][k] = (row0 + r < n && k < kc) ? A[(long long)(row0 + r) * n + k0 + k] : cmk<c_t<T>>(0, 0);
+#pragma unroll
+    for (int t = 0; t < PA; ++t) {
+      const int e = tid + t * 256;
+      if (e < na) {
+        const int r = e / KC, k = e - r * KC;
+        ra[t] = (row0 + r < n && k < kc) ? A[(long long)(row0 + r) * n + k0 + k] : cmk<V>(0, 0);
+      }
     }
-    for (int e = tid; e < KC * R; e += 256) Fs[e] = (e / R < kc) ? f[(long long)k0 * R + e] : cmk<c_t<T>>(0, 0);
+#pragma unroll
+    for (int t = 0; t < PF; ++t) {
+      const int e = tid + t * 256;
+      if (e < nf) rf[t] = (e / R < kc) ? f[(long long)k0 * R + e] : cmk<V>(0, 0);
+    }
+  };
+  V acc0 = cmk<V>(0, 0), acc1 = cmk<V>(0, 0);
+  fetch(0);
+  for (int k0 = 0; k0 < n; k0 += KC) {
     __syncthreads();
+#pragma unroll
+    for (int t = 0; t < PA; ++t) {
+      const int e = tid + t * 256;
+      if (e < na) As[e / KC][e % KC] = ra[t];
+    }
+#pragma unroll
+    for (int t = 0; t < PF; ++t) {
+      const int e = tid + t * 256;
+      if (e < nf) Fs[e] = rf[t];
+    }
+    __syncthreads();
+    if (k0 + KC < n) fetch(k0 + KC);
 #pragma unroll 8
     for (int k = 0; k < KC; ++k) {
-      const c_t<T> fv = Fs[k * R + rhs];
+      const V fv = Fs[k * R + rhs];
       acc0 = cfma(As[2 * rg][k], fv, acc0);
       acc1 = cfma(As[2 * rg + 1][k], fv, acc1);
     }
