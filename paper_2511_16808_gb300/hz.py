@@ -279,7 +279,7 @@ def hz_kernel_launches(ctx) -> int:
 
 # 1: Gram-Schmidt update pass(es); 2: the pass with the FP64 operator and the
 # inner products; 3: the whole V-cycle
-PROFILE = {"none": 0, "gs_update": 1, "gs_apply": 2, "vcycle": 3, "mgs_step": 1, "mgs_first": 2}
+PROFILE = {"none": 0, "gs_update": 1, "gs_apply": 2, "vcycle": 3}
 
 
 def hz_profile_select(ctx, kernel_class) -> None:
