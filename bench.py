@@ -37,6 +37,22 @@ METRIC = "solves/s @ rel-res 1e-6 (mixed vs plain FP64); Vanka DOF/s; p50/p99 la
 UNIT = "solves/s"
 
 
+def replica_throughput(dist, units_local, ms_local, device):
+    """Whole-job throughput of independent replicas (one per rank, no data-path
+    collective): every rank processed units_local units in ms_local ms; the
+    value is all ranks' units over the slowest rank's time.  Returns (value,
+    max ms)."""
+    if dist is None:
+        return units_local / (ms_local / 1e3), ms_local
+    import torch
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([float(units_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    ms_max = float(t.item())
+    return float(u.item()) / (ms_max / 1e3), ms_max
+
+
 def _env_rank():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
@@ -243,13 +259,10 @@ def run_ours(args):
             ms_prof[cls], _ = time_solves(torch, solver, q, p, args.steps, stream)
             profs[cls] = _hz.hz_profile_read(solver.ctx)
         _hz.hz_profile_select(solver.ctx, "none")
+    value, ms = replica_throughput(dist, args.steps, ms, "cuda")
     if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
     iters = infos[-1].iters
-    value = world * args.steps / (ms / 1e3)
 
     # e2e through the C ABI with host buffers (pinned source, host solution)
     from paper_2511_16808_gb300 import hz
@@ -415,12 +428,9 @@ def run_batched(args):
         t1.synchronize()
     ms = t0.elapsed_time(t1)
     launches = sum(hz.hz_kernel_launches(sv.ctx) for sv in solvers) - launches0
+    value, ms = replica_throughput(dist, args.steps * nsolve, ms, "cuda")
     if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
-    value = world * args.steps * nsolve / (ms / 1e3)
     iters = [[i.iters for i in inf] for inf in infos]
     conv = all(i.converged for inf in infos for i in inf)
     relres = max(i.relres_true for inf in infos for i in inf)

@@ -138,3 +138,37 @@ def test_async_solve_matches_blocking():
     with pytest.raises(hz.HzError):
         hz.hz_solve_step(s.ctx)                      # nothing in flight any more
     s.close()
+
+
+def test_async_solve_host_buffers():
+    from paper_2511_16808_gb300 import hz
+    from paper_2511_16808_gb300.solver import HelmholtzSolver
+    r = REQS[1]
+    kappa, gamma, omega, q, opts = _problem(r)
+    s = HelmholtzSolver(r["dim"], [r["n"]] * r["dim"], kappa, omega, gamma, r["alpha"], r["levels"], **opts)
+    p_block, info = s.solve(q, np.zeros_like(q))
+    hz.hz_solve_begin(s.ctx, q)                       # host source, staged by the library
+    while not hz.hz_solve_step(s.ctx, block=True):
+        pass
+    p_async = np.zeros_like(q)
+    ok, info2 = hz.hz_solve_end(s.ctx, p_async)      # host output
+    assert ok and info2.iters == info.iters and np.array_equal(p_async, p_block)
+    s.close()
+
+
+def test_many_small_requests():
+    """A burst of small 2D / 3D requests through few slots: all finish, the
+    slots and bytes are all returned, and sampled results equal solo solves."""
+    from paper_2511_16808_gb300.serve import Server
+    small = [REQS[1], REQS[3], REQS[4], REQS[6]]
+    reqs = [dict(small[i % 4], seed=10 + i) for i in range(24)]
+    with Server(max_active=6, setup_threads=3) as srv:
+        tickets = [_submit(srv, r) for r in reqs]
+        res = [srv.wait(t, timeout=300) for t in tickets]
+        st = srv.stats()
+    assert st["done"] == len(reqs) and st["failed"] == 0 and st["bytes_in_use"] == 0
+    assert st["kernel_launches"] > 0
+    for i in (0, 7, 13, 22):
+        p, d = res[i]
+        p1, info1 = _solo(reqs[i])
+        assert d["status"] == "HZ_OK" and d["iters"] == info1.iters and np.array_equal(p, p1)
