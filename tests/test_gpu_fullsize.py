@@ -1,6 +1,6 @@
 """Full-size parity of the benchmark workloads against stored oracle results.
 
-tests/golden/oracle_config{1,2}.json were written by oracle/make_golden.py
+tests/golden/oracle_config{1,2,3_129}.json were written by oracle/make_golden.py
 (which runs only the FP64 oracle): the FGMRES iteration count at the
 workload's tolerance and the solution of a 1e-10 solve at seeded sampled
 nodes.  Here the CUDA path solves the same full-size problem and is checked
@@ -29,14 +29,21 @@ def _gold(name):
         return json.load(f)
 
 
-@pytest.mark.parametrize("name,precision,bound", [("config1", "fp64", 1e-6), ("config1", "mixed", 1e-5),
-                                                   ("config2", "mixed", 1e-5), ("config2", "fp64", 1e-6)])
-def test_full_size_solve_matches_oracle(name, precision, bound):
+def _workload(name):
     import workloads
+    if name == "config3_129":             # the 3D generator at 129^3, 4 levels (the oracle's reach)
+        return workloads.small_variant("config3", 129, 4)
+    return getattr(workloads, name)()
+
+
+@pytest.mark.parametrize("name,precision,bound", [("config1", "fp64", 1e-6), ("config1", "mixed", 1e-5),
+                                                   ("config2", "mixed", 1e-5), ("config2", "fp64", 1e-6),
+                                                   ("config3_129", "mixed", 1e-5)])
+def test_full_size_solve_matches_oracle(name, precision, bound):
     from oracle import operator
     from paper_2511_16808_gb300.solver import HelmholtzSolver
     g = _gold(name)
-    w = getattr(workloads, name)()
+    w = _workload(name)
     s = HelmholtzSolver(w.dim, [w.n] * w.dim, w.kappa.ravel(), w.omega, w.gamma.ravel(), w.alpha, w.levels,
                         patch=w.patch, intergrid=w.intergrid, precision=precision, tol=w.tol,
                         restart=w.restart, max_iter=w.max_iter)
