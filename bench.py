@@ -224,6 +224,16 @@ print(json.dumps({{"s_per_iter": dt / info.iters, "iters": info.iters}}))
                       f"{ref_iters:g} iterations a full solve takes" + note}
 
 
+def _with_overrides(w, args):
+    """The workload with the smoother / intergrid / depth options of the command
+    line (the smoother comparisons of the 3D heterogeneous experiments)."""
+    from dataclasses import replace
+    kw = {k: v for k, v in (("levels", args.levels), ("patch", args.patch),
+                            ("patch_coarse", args.patch_coarse), ("intergrid", args.intergrid))
+          if v is not None}
+    return replace(w, **kw) if kw else w
+
+
 def run_ours(args):
     import torch
     import workloads
@@ -234,7 +244,8 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    w = getattr(workloads, args.config)()
+    w0 = getattr(workloads, args.config)()
+    w = _with_overrides(w0, args)
     stream = torch.cuda.current_stream()
     solver = make_solver(w, "mixed", stream)
     q = torch.tensor(w.rhs(0), device="cuda")
@@ -306,7 +317,7 @@ def run_ours(args):
             s64.close()
         vdofs = smoothed * vprof["launches"] / (vprof["ms"] / 1e3) if vprof["ms"] > 0 else None
         cpu = None
-        if not args.no_cpu_baseline:
+        if not args.no_cpu_baseline and w is w0:           # the oracle sample is of the stock workload
             cpu = cpu_baseline_sample(args.config, args.cpu_iters, iters)
         peak, src = _peaks()
         names = {"gs_apply": "k_gs_dots (FP64 operator on z + the cycle's inner products, one pass)",
@@ -339,7 +350,7 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "c64 V-cycle / c128 FGMRES",
             "data": "synthetic (seeded layered medium)",
             "config": {"workload": w.name, "nodes": w.nodes, "levels": w.levels, "patch": w.patch,
-                       "intergrid": w.intergrid, "alpha": w.alpha, "tol": w.tol, "restart": w.restart,
+                       "patch_coarse": w.patch_coarse or w.patch, "intergrid": w.intergrid, "alpha": w.alpha, "tol": w.tol, "restart": w.restart,
                        "omega": w.omega, "layer_cells": w.layer_cells,
                        "l2": "working set per solve > 129 MB L2 (no flush)",
                        "parallelism": f"replicas x{world}"},
@@ -715,6 +726,10 @@ def main():
     ap.add_argument("--one-at-a-time", type=int, default=24,
                     help="config5: requests timed one at a time on the plain FP64 path")
     ap.add_argument("--setup-threads", type=int, default=2, help="config5: hierarchies built concurrently")
+    ap.add_argument("--levels", type=int, default=None, help="override the workload's cycle depth")
+    ap.add_argument("--patch", default=None, help="override the fine-level Vanka patch")
+    ap.add_argument("--patch-coarse", default=None, help="patch on the coarse levels (default: the fine one)")
+    ap.add_argument("--intergrid", default=None, help="override the intergrid scheme")
     args = ap.parse_args()
     if args.impl == "reference":
         out = run_reference(args)

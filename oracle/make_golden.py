@@ -56,7 +56,8 @@ def run(name: str, out_dir: str = os.path.join(ROOT, "tests", "golden")) -> dict
     idx = np.sort(rng.choice(w.nodes, size=min(SAMPLES, w.nodes), replace=False))
     rec = {
         "workload": w.name, "nodes": w.nodes, "levels": w.levels, "alpha": w.alpha,
-        "patch": w.patch, "intergrid": w.intergrid, "tol": w.tol,
+        "patch": w.patch, "patch_coarse": w.patch_coarse or w.patch, "intergrid": w.intergrid,
+        "tol": w.tol,
         "iters": info.iters, "relres_true": info.relres_true,
         "iters_tight": info_ref.iters, "relres_tight": info_ref.relres_true,
         "setup_s": t_setup, "solve_s": t_solve, "s_per_iter": t_solve / max(info.iters, 1),

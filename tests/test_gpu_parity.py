@@ -30,12 +30,17 @@ CASES_3D = [
     dict(dim=3, n=17, levels=3, patch="element", scheme="linear", layer=3),
     dict(dim=3, n=9, levels=2, patch="plus", scheme="leveldep"),
     dict(dim=3, n=9, levels=2, patch="rb", scheme="cubic"),
+    # the heterogeneous 3D smoother choices of Section 5.5: Jacobi on the fine level
+    # with element Vanka below it, and plain damped Jacobi with trilinear intergrid
+    dict(dim=3, n=17, levels=3, patch="jacobi", scheme="linear", layer=3, patch_coarse="element"),
+    dict(dim=3, n=17, levels=4, patch="jacobi", scheme="linear", layer=3),
 ]
 ALL = CASES_2D + CASES_3D
 
 
 def _ids(cases):
-    return [f"{c['dim']}d-n{c['n']}-L{c['levels']}-{c['patch']}-{c['scheme']}" for c in cases]
+    return [f"{c['dim']}d-n{c['n']}-L{c['levels']}-{c['patch']}"
+            + (f"+{c['patch_coarse']}" if c.get("patch_coarse") else "") + f"-{c['scheme']}" for c in cases]
 
 
 def _pair(case, precision="fp64"):

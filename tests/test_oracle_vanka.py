@@ -125,6 +125,25 @@ def test_rb_patch_on_second_order_stencil_is_jacobi(shape):
     assert np.allclose(J.diagonal(), 1.0 / A.diagonal(), rtol=1e-14)
 
 
+def test_jacobi_fine_element_coarse_hierarchy():
+    """The combined smoother of the heterogeneous 3D experiments (Section 5.5):
+    damped Jacobi on the finest level only, element Vanka on every coarser
+    smoothed level.  The Galerkin operators do not depend on the smoother, so
+    each level must match the single-smoother hierarchy it takes its patch from."""
+    from oracle import defaults, multigrid
+    shape = (9, 9, 9)
+    A = _problem(shape)
+    mix = multigrid.build_hierarchy(A, shape, 3, ["jacobi", "element"], "linear")
+    jac = multigrid.build_hierarchy(A, shape, 3, "jacobi", "linear")
+    ele = multigrid.build_hierarchy(A, shape, 3, "element", "linear")
+    assert abs(mix[0].M - jac[0].M).max() == 0 and mix[0].w == defaults.damping(3, "jacobi", 0)
+    assert np.allclose(mix[0].M.diagonal(), 1.0 / A.diagonal(), rtol=1e-14) and mix[0].M.nnz == A.shape[0]
+    assert abs(mix[1].M - ele[1].M).max() == 0 and mix[1].w == defaults.damping(3, "element", 1)
+    assert mix[1].M.nnz > 8 * mix[1].A.shape[0]                    # true patches, not a diagonal
+    for a, b in zip(mix, ele):
+        assert abs(a.A - b.A).max() == 0
+
+
 def test_whole_domain_patch_gives_one_minus_w():
     shape = (5, 4)
     A = _problem(shape)

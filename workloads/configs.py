@@ -99,7 +99,10 @@ def config2(n: int = 1025, levels: int = 6, seed: int = 0, layer_cells: int = 20
 
 def config3(n: int = 257, levels: int = 5, seed: int = 0, layer_cells: int = 16, **kw) -> Workload:
     """3D geophysical-like medium (seeded), 8 ppw at v_min = 1.5,
-    gamma/omega = 0.01, absorbing layer + ABC, source just below the top layer."""
+    gamma/omega = 0.01, absorbing layer + ABC, source just below the top layer.
+    Smoother: damped Jacobi on the finest level and element-patch Vanka on the
+    coarser ones, trilinear intergrid (the combination Section 5.5 finds best
+    for large heterogeneous 3D media)."""
     h = 1.0 / (n - 1)
     omega = media.omega_for_ppw(8.0, h, v_min=1.5)
     kappa = media.geophysical_kappa_3d(n, seed)
@@ -107,7 +110,7 @@ def config3(n: int = 257, levels: int = 5, seed: int = 0, layer_cells: int = 16,
     c = (n - 1) // 2
     src = (c, c, min(layer_cells + 1, n - 1))
     w = Workload(name=f"3d-geophysical-{n}", dim=3, n=n, omega=omega, kappa=kappa, gamma=gamma,
-                 sources=[src], levels=levels, alpha=0.5, patch="element",
+                 sources=[src], levels=levels, alpha=0.5, patch="jacobi", patch_coarse="element",
                  intergrid="linear", tol=1e-6, precision="mixed", layer_cells=layer_cells,
                  meta={"seed": seed})
     return replace(w, **kw)
