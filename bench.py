@@ -152,7 +152,7 @@ def make_solver(w, precision, stream=None, nrhs_max=1):
     return HelmholtzSolver(w.dim, [w.n] * w.dim, w.kappa.ravel(), w.omega, w.gamma.ravel(), w.alpha,
                            w.levels, patch=w.patch, intergrid=w.intergrid, precision=precision,
                            tol=w.tol, restart=w.restart, nu1=w.nu1, nu2=w.nu2, max_iter=w.max_iter,
-                           patch_coarse=w.patch_coarse, nrhs_max=nrhs_max, stream=stream)
+                           patch_coarse=w.patch_coarse, nrhs_max=nrhs_max, stream=stream, cycle=w.cycle)
 
 
 def _workload(name):

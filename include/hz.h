@@ -102,6 +102,10 @@ typedef struct {
   double tol;                        /* relative residual ||q_hat - A p|| / ||q_hat|| */
   int max_iter;                      /* max preconditioner applications    */
   int nrhs_max;                      /* largest nrhs any call will pass    */
+  int cycle_visits;                  /* cycles on the next level per visit of a
+                                        level, Section 2.2: 1 = V-cycle,
+                                        2 = W-cycle (the coarsest level, solved
+                                        exactly, is solved once); 0 means 1  */
 } hz_opts;
 
 typedef struct hz_ctx hz_ctx;        /* opaque, owned by the library */

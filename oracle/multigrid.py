@@ -4,7 +4,8 @@ Section 2.3 / 3.1: the preconditioner is multigrid applied to the shifted
 operator H_s (Eq. shift); coarse operators are Galerkin products
 A_{l+1} = R_l A_l P_l (Section 3.1) with the intergrid scheme of
 `transfer.scheme_kinds`.  Algorithm 1 (two-grid cycle) with step 3 replaced by
-a recursive call gives the V-cycle (Section 2.2); the coarsest level is
+a recursive call gives the V-cycle, by two recursive calls the W-cycle
+(Section 2.2); the coarsest level is
 solved exactly by LU with partial pivoting (SuperLU; an exact direct solve).
 Coarse initial guesses are zero.
 """
@@ -62,8 +63,12 @@ def build_hierarchy(A_s: sp.csr_matrix, shape_xyz, levels: int, patches, scheme:
 
 
 def vcycle(hier, f: np.ndarray, level: int = 0, nu1: int = 1, nu2: int = 1,
-           u: np.ndarray | None = None) -> np.ndarray:
-    """One V(nu1, nu2) cycle for A_level u = f (Algorithm 1, applied recursively)."""
+           u: np.ndarray | None = None, cycle: str = "V") -> np.ndarray:
+    """One V(nu1, nu2) or W(nu1, nu2) cycle for A_level u = f (Algorithm 1,
+    applied recursively).  V: step 3 is one cycle on the coarser level; W: step
+    3 is two cycles on the coarser level, the second starting from the first
+    one's result (Section 2.2).  On the coarsest level a cycle is the exact
+    solve, whatever the initial guess."""
     L = hier[level]
     if L.lu is not None:
         return L.lu.solve(np.asarray(f, dtype=np.complex128))
@@ -71,7 +76,11 @@ def vcycle(hier, f: np.ndarray, level: int = 0, nu1: int = 1, nu2: int = 1,
     for _ in range(nu1):                                   # step 1: pre-relaxation
         u = vanka.sweep(L.A, L.M, L.w, u, f)
     r_c = L.R @ (f - L.A @ u)                              # step 2: restrict residual
-    e_c = vcycle(hier, r_c, level + 1, nu1, nu2)           # step 3: coarse problem (recursive)
+    e_c = vcycle(hier, r_c, level + 1, nu1, nu2, cycle=cycle)   # step 3: coarse problem (recursive)
+    if cycle == "W":
+        e_c = vcycle(hier, r_c, level + 1, nu1, nu2, u=e_c, cycle=cycle)
+    elif cycle != "V":
+        raise ValueError(cycle)
     u = u + L.P @ e_c                                      # step 4: coarse-grid correction
     for _ in range(nu2):                                   # step 5: post-relaxation
         u = vanka.sweep(L.A, L.M, L.w, u, f)

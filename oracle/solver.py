@@ -3,7 +3,7 @@
 Puts the pieces together as the paper's method: the Helmholtz operator A of
 Eq. (1), the shifted operator A_s of Eq. (shift), the Galerkin multigrid
 hierarchy of A_s with additive Vanka smoothing (Sections 3.1-3.3), one
-V(nu1, nu2) cycle (Algorithm 1, recursive) as the preconditioner, and
+V(nu1, nu2) (or W) cycle (Algorithm 1, recursive) as the preconditioner, and
 FGMRES(m) on the row-scaled system A p = q_hat (Section 2.3, m = 5 in
 Section 5.2), zero initial guess (Section 5).
 """
@@ -17,11 +17,12 @@ from . import multigrid, operator
 
 class Problem:
     def __init__(self, shape_xyz, h, kappa, omega, gamma, alpha, levels, patch, scheme,
-                 patch_coarse=None, nu1=1, nu2=1, damping=None, periodic=False):
+                 patch_coarse=None, nu1=1, nu2=1, damping=None, periodic=False, cycle="V"):
         self.shape = tuple(shape_xyz)
         self.h = h
         self.omega = omega
         self.nu1, self.nu2 = nu1, nu2
+        self.cycle = cycle
         self.periodic = periodic
         self.A = operator.helmholtz(self.shape, h, kappa, omega, gamma, periodic)
         self.A_s = operator.shifted(self.A, self.shape, omega, alpha, periodic)
@@ -30,8 +31,9 @@ class Problem:
                                               scheme, damping, periodic)
 
     def precond(self, r: np.ndarray) -> np.ndarray:
-        """z = V-cycle(r) with zero initial guess."""
-        return multigrid.vcycle(self.hier, np.asarray(r, dtype=np.complex128), 0, self.nu1, self.nu2)
+        """z = V- (or W-) cycle(r) with zero initial guess."""
+        return multigrid.vcycle(self.hier, np.asarray(r, dtype=np.complex128), 0, self.nu1, self.nu2,
+                                cycle=self.cycle)
 
     def rhs(self, q: np.ndarray) -> np.ndarray:
         return operator.scaled_rhs(q, self.shape, self.periodic)
@@ -45,6 +47,6 @@ def from_workload(w, **overrides) -> Problem:
     """Problem for a `workloads.Workload`."""
     kw = dict(shape_xyz=w.shape, h=w.h, kappa=w.kappa, omega=w.omega, gamma=w.gamma,
               alpha=w.alpha, levels=w.levels, patch=w.patch, scheme=w.intergrid,
-              patch_coarse=w.patch_coarse, nu1=w.nu1, nu2=w.nu2)
+              patch_coarse=w.patch_coarse, nu1=w.nu1, nu2=w.nu2, cycle=w.cycle)
     kw.update(overrides)
     return Problem(**kw)

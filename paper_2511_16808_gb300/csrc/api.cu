@@ -146,6 +146,7 @@ void validate(const hz_grid* g, const hz_opts* o) {
   require(o->restart_m >= 1 && o->restart_m <= 16, "restart_m out of range");
   require(o->tol > 0 && o->max_iter >= 1, "tol/max_iter out of range");
   require(o->nrhs_max >= 1 && o->nrhs_max <= 64, "nrhs_max must be in 1..64");
+  require(o->cycle_visits >= 0 && o->cycle_visits <= 2, "cycle_visits must be 0, 1 (V) or 2 (W)");
   require(o->precision == HZ_PREC_FP64 || o->precision == HZ_PREC_MIXED, "bad precision");
   require(o->intergrid >= HZ_IG_LINEAR && o->intergrid <= HZ_IG_LEVELDEP, "bad intergrid");
   require(!(g->dim == 3 && o->intergrid == HZ_IG_CUBIC && o->levels >= 3),
@@ -249,6 +250,7 @@ hz_status hz_opts_default(int dim, hz_opts* out) {
     out->tol = 1e-6;
     out->max_iter = 2000;
     out->nrhs_max = 1;
+    out->cycle_visits = 1;
   });
 }
 

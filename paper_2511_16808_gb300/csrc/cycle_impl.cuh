@@ -949,9 +949,11 @@ void coarse_t(Ctx& c, const void* f, void* u, const int* active, cudaStream_t s)
   HZ_LAUNCHED();
 }
 
-// One V(nu1, nu2) cycle at level l for A_l u = f from u = 0; result in `out`.
+// One V(nu1, nu2) cycle at level l for A_l u = f from u = u0 (0 when u0 is
+// null); result in `out`.  Step 3 of Algorithm 1 is opts.cycle_visits cycles
+// on the next level (1: V-cycle, 2: W-cycle, Section 2.2).
 template <typename T>
-void vcycle_t(Ctx& c, int l, const void* f, void* out, const int* active, cudaStream_t s) {
+void cycle_rec(Ctx& c, int l, const void* f, const void* u0, void* out, const int* active, cudaStream_t s) {
   Level& L = c.L[l];
   if (L.coarsest) {
     coarse_t<T>(c, f, out, active, s);
@@ -961,7 +963,23 @@ void vcycle_t(Ctx& c, int l, const void* f, void* out, const int* active, cudaSt
   const bool d2 = L.g.dim == 2 && c.nrhs == 1;     // shared-memory tile kernels: one RHS
   // steps 1-2: pre-relaxation into t, residual into r
   const void* rr = L.r;
-  if (nu1 == 0) {
+  if (u0) {
+    // from the initial guess u0 (the second coarse-level cycle of a W-cycle);
+    // u0 may be `out`, which is written only by the post-relaxation
+    if (nu1 == 0) {
+      HZ_CUDA(cudaMemcpyAsync(L.t, u0, sizeof(c_t<T>) * L.g.N * c.nrhs, cudaMemcpyDeviceToDevice, s));
+    } else if (L.m_diag) {
+      resid_sweep_diag<T>(c, l, f, u0, L.t, active, s);
+    } else {
+      resid<T>(c, l, u0, f, L.r, active, s);
+      sweep_out<T>(c, l, L.r, u0, L.t, active, s);
+    }
+    for (int i = 1; i < nu1; ++i) {
+      resid<T>(c, l, L.t, f, L.r, active, s);
+      sweep_out<T>(c, l, L.r, L.t, L.t, active, s);
+    }
+    resid<T>(c, l, L.t, f, L.r, active, s);
+  } else if (nu1 == 0) {
     HZ_CUDA(cudaMemsetAsync(L.t, 0, sizeof(c_t<T>) * L.g.N * c.nrhs, s));
     rr = f;
   } else if (L.m_diag && nu1 == 1) {
@@ -976,7 +994,11 @@ void vcycle_t(Ctx& c, int l, const void* f, void* out, const int* active, cudaSt
   }
   Level& C = c.L[l + 1];
   restrict_t<T>(c, l, rr, C.f, active, s);
-  vcycle_t<T>(c, l + 1, C.f, C.u, active, s);                   // step 3 (recursive)
+  cycle_rec<T>(c, l + 1, C.f, nullptr, C.u, active, s);         // step 3 (recursive)
+  // W-cycle: a second coarse-level cycle from the first one's result; on the
+  // coarsest level a cycle is the exact solve, so it would repeat the first
+  for (int v = 1; v < c.opts.cycle_visits && !C.coarsest; ++v)
+    cycle_rec<T>(c, l + 1, C.f, C.u, C.u, active, s);
   // steps 4-5: coarse-grid correction and post-relaxation into out
   if (nu2 == 0) {
     prolong_t<T>(c, l, C.u, L.t, out, active, s);
@@ -1002,6 +1024,11 @@ void vcycle_t(Ctx& c, int l, const void* f, void* out, const int* active, cudaSt
     resid<T>(c, l, out, f, L.r, active, s);
     sweep_out<T>(c, l, L.r, out, out, active, s);
   }
+}
+
+template <typename T>
+void vcycle_t(Ctx& c, int l, const void* f, void* out, const int* active, cudaStream_t s) {
+  cycle_rec<T>(c, l, f, nullptr, out, active, s);
 }
 
 }  // namespace cyc

@@ -554,11 +554,18 @@ double vcycle_bytes(const Ctx& c) {
   const double b = c.mixed ? 8.0 : 16.0;
   const double R = c.nrhs;
   double tot = 0;
+  // visits of each level per cycle: 1 for a V-cycle; a W-cycle visits level
+  // l >= 1 twice per visit of level l-1 (the coarsest once per visit of its
+  // parent).  Every visit is counted like a first one (zero initial guess).
+  double vis = 1.0;
+  const double per = std::max(1, c.opts.cycle_visits);
   for (size_t l = 0; l < c.L.size(); ++l) {
     const Level& L = c.L[l];
     const double N = (double)L.g.N;
+    const double t0 = tot;
+    if (l > 0 && !L.coarsest) vis *= per;
     if (L.coarsest) {
-      tot += N * N * b + 2 * N * b * R;
+      tot += vis * (N * N * b + 2 * N * b * R);
       continue;
     }
     // stored smoother planes: the diagonal, or the half / full planes (+ a real weight per node)
@@ -567,12 +574,13 @@ double vcycle_bytes(const Ctx& c) {
       const double sA = L.fine ? 1.0 : L.A.off.n, sM = sMst;
       const double rc = L.g.dim == 3 ? 0.125 : 0.25;
       tot += N * b * R * (14 + 2 * rc) + N * b * 2 * (sA + sM);
-      continue;
+    } else {
+      const double sA = L.fine ? 1.0 : L.A.off.n, sM = sMst;
+      const double rc = L.g.dim == 3 ? 0.125 : 0.25;
+      if (L.m_diag) tot += N * b * (5 + (1 + rc) + (5 + rc)) + (sA - 1) * 2 * N * b;   // sweep0+resid, restrict, prolong+sweep
+      else tot += N * b * (2 * sM + 2 * sA + 13 + 2 * rc);
     }
-    const double sA = L.fine ? 1.0 : L.A.off.n, sM = sMst;
-    const double rc = L.g.dim == 3 ? 0.125 : 0.25;
-    if (L.m_diag) tot += N * b * (5 + (1 + rc) + (5 + rc)) + (sA - 1) * 2 * N * b;   // sweep0+resid, restrict, prolong+sweep
-    else tot += N * b * (2 * sM + 2 * sA + 13 + 2 * rc);
+    tot = t0 + vis * (tot - t0);
   }
   return tot;
 }

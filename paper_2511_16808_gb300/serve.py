@@ -49,7 +49,7 @@ class Server:
         """Submit source k of a workloads.Workload."""
         opts = dict(patch=w.patch, intergrid=w.intergrid, precision=w.precision, tol=w.tol,
                     restart=w.restart, nu1=w.nu1, nu2=w.nu2, max_iter=w.max_iter,
-                    patch_coarse=w.patch_coarse)
+                    patch_coarse=w.patch_coarse, cycle=w.cycle)
         opts.update(overrides)
         return self.submit(w.dim, w.n, w.kappa, w.omega, w.rhs(k), gamma=w.gamma, alpha=w.alpha,
                            levels=w.levels, **opts)

@@ -15,11 +15,12 @@ class HelmholtzSolver:
     kappa, gamma: per-node float64 arrays (numpy or torch, any device),
     flattened x-fastest.  patch: fine-level patch; patch_coarse: patch on the
     coarser levels (default: the same).  damping: per-level list, default the
-    paper's table for each level's patch."""
+    paper's table for each level's patch.  cycle: "V" or "W" (two cycles on
+    the next level per visit, Section 2.2)."""
 
     def __init__(self, dim, n, kappa, omega, gamma, alpha, levels, patch="rb", intergrid="leveldep",
                  precision="mixed", tol=1e-6, restart=5, nu1=1, nu2=1, max_iter=2000,
-                 patch_coarse=None, damping=None, nrhs_max=1, stream=None):
+                 patch_coarse=None, damping=None, nrhs_max=1, stream=None, cycle="V"):
         n = list(n) if hasattr(n, "__len__") else [n] * dim
         self.dim = dim
         self.n = n + [1] * (3 - len(n))
@@ -28,7 +29,7 @@ class HelmholtzSolver:
         self.grid = hz.make_grid(dim, n, self.h)
         o = make_opts(dim, levels, patch=patch, intergrid=intergrid, precision=precision, tol=tol,
                       restart=restart, nu1=nu1, nu2=nu2, max_iter=max_iter, patch_coarse=patch_coarse,
-                      damping=damping, nrhs_max=nrhs_max)
+                      damping=damping, nrhs_max=nrhs_max, cycle=cycle)
         self.opts = o
         self.mixed = precision == "mixed"
         self.stream = stream
@@ -78,7 +79,7 @@ class HelmholtzSolver:
 
 
 def make_opts(dim, levels, patch="rb", intergrid="leveldep", precision="mixed", tol=1e-6, restart=5, nu1=1,
-              nu2=1, max_iter=2000, patch_coarse=None, damping=None, nrhs_max=1) -> hz.hz_opts:
+              nu2=1, max_iter=2000, patch_coarse=None, damping=None, nrhs_max=1, cycle="V") -> hz.hz_opts:
     """hz_opts from solver settings; damping defaults to the paper's table per
     level and patch."""
     o = hz.hz_opts_default(dim)
@@ -95,6 +96,7 @@ def make_opts(dim, levels, patch="rb", intergrid="leveldep", precision="mixed", 
     o.tol = tol
     o.max_iter = max_iter
     o.nrhs_max = nrhs_max
+    o.cycle_visits = {"V": 1, "W": 2}[cycle]
     return o
 
 

@@ -42,7 +42,7 @@ def test_oracle_damping_matches_printed_table():
 
 def test_opts_default_and_setup_bytes():
     o = hz.hz_opts_default(2)
-    assert o.levels == 4 and o.restart_m == 5 and o.nu1 == 1 and o.nu2 == 1
+    assert o.levels == 4 and o.restart_m == 5 and o.nu1 == 1 and o.nu2 == 1 and o.cycle_visits == 1
     g = hz.make_grid(2, [129, 129], 1 / 128)
     b = hz.hz_setup_bytes(g, o)
     assert 129 * 129 * 16 * 6 < b < 1 << 31
@@ -63,7 +63,8 @@ def test_invalid_grid_rejected(n, levels):
 
 def test_invalid_options_rejected():
     g = hz.make_grid(2, [33, 33], 1 / 32)
-    for field, value in [("restart_m", 0), ("restart_m", 17), ("tol", 0.0), ("nrhs_max", 0)]:
+    for field, value in [("restart_m", 0), ("restart_m", 17), ("tol", 0.0), ("nrhs_max", 0),
+                         ("cycle_visits", 3), ("cycle_visits", -1)]:
         o = hz.hz_opts_default(2)
         setattr(o, field, value)
         with pytest.raises(hz.HzError) as e:

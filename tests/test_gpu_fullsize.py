@@ -46,7 +46,7 @@ def test_full_size_solve_matches_oracle(name, precision, bound):
     w = _workload(name)
     s = HelmholtzSolver(w.dim, [w.n] * w.dim, w.kappa.ravel(), w.omega, w.gamma.ravel(), w.alpha, w.levels,
                         patch=w.patch, intergrid=w.intergrid, precision=precision, tol=w.tol,
-                        restart=w.restart, max_iter=w.max_iter)
+                        restart=w.restart, max_iter=w.max_iter, patch_coarse=w.patch_coarse, cycle=w.cycle)
     q = w.rhs(0)
     p, info = s.solve(torch.tensor(q, device="cuda"))
     p = p.cpu().numpy()
@@ -80,7 +80,8 @@ def test_config4_batched_sources_match_oracle(fi):
     R = len(w.sources)
     s = HelmholtzSolver(w.dim, [w.n] * w.dim, w.kappa.ravel(), w.omega, w.gamma.ravel(), w.alpha, w.levels,
                         patch=w.patch, intergrid=w.intergrid, precision="mixed", tol=w.tol,
-                        restart=w.restart, max_iter=w.max_iter, nrhs_max=R)
+                        restart=w.restart, max_iter=w.max_iter, nrhs_max=R, patch_coarse=w.patch_coarse,
+                        cycle=w.cycle)
     Q = w.rhs_block()
     P, infos = s.solve_batch(torch.tensor(Q, device="cuda"))
     P = P.cpu().numpy()

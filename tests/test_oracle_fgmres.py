@@ -13,6 +13,11 @@ V-cycle
   S^nu2 (I - P A_c^{-1} R A) S^nu1 with S = I - w M A, built from dense
   matrices (Eq. 2G); the coarse-grid correction is a projection.
 - The cycle is linear in its right-hand side.
+- V- and W-cycles over 3 and 4 levels: the error propagation equals the
+  textbook recursion E_l = S^nu2 (I - P (I - E_{l+1}^g) A_{l+1}^{-1} R A) S^nu1
+  with E_coarsest = 0 and g = 1 (V) or 2 (W) cycles on the coarser level
+  (Section 2.2; Trottenberg, Oosterlee & Schueller, Multigrid, Sec. 2.4),
+  built from dense matrices; a two-level W-cycle equals the V-cycle.
 """
 import numpy as np
 import pytest
@@ -106,3 +111,46 @@ def test_vcycle_is_linear():
     f, g = (rng.standard_normal((2, N)) + 1j * rng.standard_normal((2, N)))
     a, b = 0.3 - 1.1j, 2.0 + 0.5j
     assert np.allclose(pr.precond(a * f + b * g), a * pr.precond(f) + b * pr.precond(g), atol=1e-10)
+
+
+def _dense_cycle_error(hier, level, nu, g):
+    L = hier[level]
+    A = L.A.toarray()
+    N = A.shape[0]
+    if L.lu is not None:
+        return np.zeros((N, N), dtype=complex)
+    S = np.eye(N) - L.w * L.M.toarray() @ A
+    P, R = L.P.toarray(), L.R.toarray()
+    Ac = hier[level + 1].A.toarray()
+    Ec = _dense_cycle_error(hier, level + 1, nu, g)
+    inner = np.eye(Ac.shape[0]) - np.linalg.matrix_power(Ec, g)
+    CGC = np.eye(N) - P @ inner @ np.linalg.solve(Ac, R @ A)
+    return np.linalg.matrix_power(S, nu[1]) @ CGC @ np.linalg.matrix_power(S, nu[0])
+
+
+@pytest.mark.parametrize("levels", [3, 4])
+@pytest.mark.parametrize("cycle,g", [("V", 1), ("W", 2)])
+@pytest.mark.parametrize("nu", [(1, 1), (2, 1)])
+def test_multilevel_error_propagation_recursion(levels, cycle, g, nu):
+    pr = _small_problem(levels, "rb", n=17)
+    pr.nu1, pr.nu2 = nu
+    pr.cycle = cycle
+    A = pr.hier[0].A.toarray()
+    N = A.shape[0]
+    B = np.column_stack([pr.precond(np.eye(N)[:, j].astype(complex)) for j in range(N)])
+    E = _dense_cycle_error(pr.hier, 0, nu, g)
+    assert np.allclose(np.eye(N) - B @ A, E, atol=1e-9)
+
+
+def test_two_level_w_cycle_is_v_cycle():
+    pr = _small_problem(2, "plus")
+    rng = np.random.default_rng(3)
+    f = rng.standard_normal(81) + 1j * rng.standard_normal(81)
+    zv = pr.precond(f)
+    pr.cycle = "W"
+    assert np.array_equal(pr.precond(f), zv)
+    pr3 = _small_problem(3, "plus", n=17)
+    f3 = rng.standard_normal(289) + 1j * rng.standard_normal(289)
+    zv3 = pr3.precond(f3)
+    pr3.cycle = "W"
+    assert np.linalg.norm(pr3.precond(f3) - zv3) > 1e-6 * np.linalg.norm(zv3)   # a real difference

@@ -41,6 +41,7 @@ class Workload:
     restart: int = 5
     nu1: int = 1
     nu2: int = 1
+    cycle: str = "V"                  # "V" or "W" (two coarse-level cycles per visit)
     max_iter: int = 2000
     layer_cells: int = 0
     meta: dict = field(default_factory=dict)
