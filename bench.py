@@ -30,6 +30,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -222,6 +224,87 @@ print(json.dumps({{"s_per_iter": dt / info.iters, "iters": info.iters}}))
             "sample": f"{workload}: setup untimed, then {d['iters']} FGMRES iterations of the same "
                       f"solve timed ({d['s_per_iter'] * 1e3:.1f} ms/iteration) and scaled by the "
                       f"{ref_iters:g} iterations a full solve takes" + note}
+
+
+LFA_SWEEPS = (  # (dim, patch, samples per axis, dampings, transfer kinds, grid side)
+    (2, "rb", 256, 64, ("cubic", "cubic"), 513),
+    (3, "element", 48, 32, ("linear", "linear"), 129),
+)
+
+
+def _lfa_stencil(dim, n, alpha=0.2, ppw=10.0):
+    """Constant 5-/7-point shifted stencil (offset tuple -> value) at 10 ppw."""
+    h = 1.0 / (n - 1)
+    omega = 2 * np.pi / (ppw * h)
+    sigma = omega ** 2 * (1 - 0.01j) - 1j * alpha * omega ** 2
+    st = {tuple([0] * dim): 2.0 * dim / h ** 2 - sigma}
+    for a in range(dim):
+        for sgn in (-1, 1):
+            off = [0] * dim
+            off[a] = sgn
+            st[tuple(off)] = -1.0 / h ** 2
+    return st
+
+
+def run_lfa(args):
+    """The LFA damping sweep of Section 5.2 (mu_loc and rho_loc for many
+    dampings at once) on the GPU; cpu_baseline: the oracle's LFA on two of the
+    dampings of each sweep, scaled per (damping, frequency) evaluation."""
+    import torch
+    from paper_2511_16808_gb300 import hz
+    rank, world, local = _env_rank()
+    if rank != 0:
+        return None
+    torch.cuda.set_device(local)
+    total_evals, total_s, lines = 0, 0.0, []
+    with ClockSampler(local) as clk:
+        for dim, patch, samples, nw, kinds, n in LFA_SWEEPS:
+            st = _lfa_stencil(dim, n)
+            ws = np.linspace(0.3, 1.3, nw)
+            for _ in range(args.warmup):
+                hz.hz_lfa_factors(dim, st, patch, ws, kinds[0], kinds[1], 1, 1, samples)
+            t = time.perf_counter()
+            for _ in range(args.steps):
+                mu, rho = hz.hz_lfa_factors(dim, st, patch, ws, kinds[0], kinds[1], 1, 1, samples)
+            dt = (time.perf_counter() - t) / args.steps
+            ev = nw * samples ** dim
+            total_evals += ev
+            total_s += dt
+            lines.append({"dim": dim, "patch": patch, "samples": samples, "dampings": nw, "ms": dt * 1e3,
+                          "best_w_rho": float(ws[int(np.nanargmin(rho))]), "rho_min": float(np.nanmin(rho))})
+    cpu = None
+    if not args.no_cpu_baseline:
+        code = f"""
+import sys, time, json
+import numpy as np
+sys.path.insert(0, {ROOT!r})
+import bench
+from oracle import lfa
+t_eval = 0.0
+for dim, patch, samples, nw, kinds, n in bench.LFA_SWEEPS:
+    st = bench._lfa_stencil(dim, n)
+    t = time.perf_counter()
+    for w in (0.7, 1.0):
+        lfa.mu_loc(st, patch, w, samples=samples)
+        lfa.rho_loc(st, patch, w, kinds[0], kinds[1], samples=samples)
+    t_eval += (time.perf_counter() - t) / (2 * samples ** dim)
+print(json.dumps({{"s_per_eval": t_eval / len(bench.LFA_SWEEPS)}}))
+"""
+        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+        if r.returncode == 0:
+            d = json.loads(r.stdout.strip().splitlines()[-1])
+            cpu = {"value": 1.0 / d["s_per_eval"], "unit": "evaluations/s", "cores": 1, "kind": "oracle",
+                   "sample": "oracle mu_loc + rho_loc for 2 dampings of each sweep (same meshes), "
+                             "time per (damping, frequency) evaluation averaged over the sweeps"}
+    return {"metric": "LFA (damping, frequency) evaluations/s (mu_loc and rho_loc)", "value": total_evals / total_s,
+            "unit": "evaluations/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_s * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c128", "data": "synthetic (constant shifted stencils at 10 ppw, alpha 0.2)",
+            "config": {"workload": "lfa-damping-sweeps", "sweeps": lines,
+                       "timing": "wall clock around the synchronous call (allocation, launch, read-back)"},
+            "clocks": clk.summary(), "cpu_baseline": cpu, "gpu_launches": 3 * args.steps * len(LFA_SWEEPS),
+            "roofline": None}
 
 
 def _with_overrides(w, args):
@@ -737,6 +820,8 @@ def main():
         out = run_batched(args)
     elif args.config == "config5":
         out = run_serving(args)
+    elif args.config == "lfa":
+        out = run_lfa(args)
     else:
         out = run_ours(args)
     if out is not None:

@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define HZ_ABI_VERSION 1
+#define HZ_ABI_VERSION 2
 #define HZ_MAX_LEVELS 10
 #define HZ_MAX_STENCIL 343   /* 7^3: cubic Galerkin stencils in 3D */
 
@@ -350,6 +350,48 @@ hz_status hz_level_restrict(hz_ctx* ctx, int level, const void* r, void* fc, voi
 hz_status hz_level_prolong_add(hz_ctx* ctx, int level, const void* ec, void* u, void* cuda_stream);
 /* u = (A_s^L)^{-1} f on the coarsest level L (dense inverse from setup). */
 hz_status hz_coarse_solve(hz_ctx* ctx, const void* f, void* u, void* cuda_stream);
+
+/* ---- tuning tools (Section 5.2) ---------------------------------------- */
+
+/* Convergence factor of Eq. cf (Section 5.1) of the context's cycle used as a
+ * stationary solver for the shifted fine operator, u <- u + B(f - A_s u):
+ * after `warmup` iterations, iterate until ||r_k|| / ||r_init|| <= target or
+ * max_iter iterations; factor = (||r_k|| / ||r_warmup||)^(1/k), 0 if k = 0.
+ *   f, u     device, complex128, one value per fine node; u holds the initial
+ *            guess on entry and the last iterate on return
+ *   iters    out: k
+ * The residual norm is read back after every iteration (synchronous on the
+ * stream).  In a mixed-precision context the cycle runs in complex FP32, so
+ * the residual stalls near FP32 rounding: use HZ_PREC_FP64 for targets below
+ * about 1e-6.  Uses the context's Krylov buffers as scratch: no solve may be in
+ * flight on the context.  Errors: HZ_ERR_INVALID_ARG (null pointers,
+ * warmup < 0, max_iter < 1, target not in (0, 1)), HZ_ERR_BUSY. */
+hz_status hz_cycle_factor(hz_ctx* ctx, const void* f, void* u, int warmup, double target, int max_iter,
+                          double* factor, int* iters, void* cuda_stream);
+
+/* Local Fourier analysis of additive Vanka for a constant stencil (Section 4),
+ * for nw damping values in one sweep on the current device:
+ *   stencil  host, 3^dim complex values (re, im interleaved) of the stencil on
+ *            the box {-1,0,1}^dim, entry (dx, dy[, dz]) at
+ *            (dz+1)*9 + (dy+1)*3 + (dx+1) (no dz term in 2D); its symbol is
+ *            H~(θ) = Σ_d s_d e^{iθ·d}
+ *   patch    the Vanka patch (Section 3.2), equal weights 1/N (Eq. smoother_symbol)
+ *   w, nw    host, damping values, 1 <= nw <= 1024
+ *   rk, pk   HZ_IG_LINEAR ((1 + cos t)/2 per axis) or HZ_IG_CUBIC
+ *            ((3 + 4 cos t + cos 2t)/8 per axis) restriction / prolongation
+ *            symbols (Section 4.2); the coarse symbol is Galerkin
+ *   nu1, nu2 relaxations in the two-grid symbol (Eq. symbolTG)
+ *   samples  points per axis: mu is the max of |S~| over the mesh
+ *            θ_a = -π/2 + 2π i/samples restricted to high frequencies (some
+ *            θ_a >= π/2), Definition 2.1; rho the max spectral radius of TG~
+ *            over the mesh θ_a = -π/2 + π i/samples (low frequencies),
+ *            Definition 2.2; 2 <= samples <= 4096 (2D) / 256 (3D)
+ *   mu, rho  host out, nw values each; either may be NULL; rho is NaN where
+ *            the eigenvalue iteration did not converge
+ * Synchronous.  Errors: HZ_ERR_INVALID_ARG (sizes, kinds, non-finite input,
+ * singular patch matrix), HZ_ERR_NO_DEVICE, HZ_ERR_CUDA. */
+hz_status hz_lfa_factors(int dim, const double* stencil, hz_patch patch, const double* w, int nw, hz_intergrid rk,
+                         hz_intergrid pk, int nu1, int nu2, int samples, double* mu, double* rho);
 
 #ifdef __cplusplus
 }

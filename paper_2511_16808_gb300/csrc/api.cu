@@ -572,4 +572,17 @@ hz_status hz_coarse_solve(hz_ctx* ctx, const void* f, void* u, void* cuda_stream
   });
 }
 
+hz_status hz_cycle_factor(hz_ctx* ctx, const void* f, void* u, int warmup, double target, int max_iter,
+                          double* factor, int* iters, void* cuda_stream) {
+  return guarded([&] {
+    require(ctx && f && u && factor && iters, "null argument");
+    require(warmup >= 0 && max_iter >= 1, "warmup >= 0 and max_iter >= 1 required");
+    require(target > 0.0 && target < 1.0, "target must be in (0, 1)");
+    BusyGuard bg(&ctx->c);
+    ctx->c.nrhs = 1;
+    cycle_factor(ctx->c, (const double2*)f, (double2*)u, warmup, target, max_iter, factor, iters,
+                 (cudaStream_t)cuda_stream);
+  });
+}
+
 }  // extern "C"

@@ -459,6 +459,9 @@ int solve_step(Ctx& c, bool block);
 void solve_end(Ctx& c, double2* p_dev, hz_info* info, cudaStream_t s);
 void fgmres_solve_batch(Ctx& c, const double2* q_dev, double2* p_dev, int nrhs, hz_info* info, cudaStream_t s);
 void precond_apply_c128(Ctx& c, const double2* r, double2* z, int nrhs, cudaStream_t s);
+// Eq. cf convergence factor of the cycle as a stationary solver (tune.cu)
+void cycle_factor(Ctx& c, const double2* f, double2* u, int warmup, double target, int max_iter, double* factor,
+                  int* iters, cudaStream_t s);
 void profile_select(Ctx& c, int cls);
 
 }  // namespace hz

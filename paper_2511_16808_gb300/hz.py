@@ -120,6 +120,10 @@ _SIGS = {
     "hz_level_restrict": ([_P, C.c_int, _P, _P, _P], C.c_int),
     "hz_level_prolong_add": ([_P, C.c_int, _P, _P, _P], C.c_int),
     "hz_coarse_solve": ([_P, _P, _P, _P], C.c_int),
+    "hz_cycle_factor": ([_P, _P, _P, C.c_int, C.c_double, C.c_int, C.POINTER(C.c_double),
+                         C.POINTER(C.c_int), _P], C.c_int),
+    "hz_lfa_factors": ([C.c_int, _P, C.c_int, _P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                        _P, _P], C.c_int),
     "hz_solve_begin": ([_P, _P, _P], C.c_int),
     "hz_solve_step": ([_P, C.c_int, C.POINTER(C.c_int)], C.c_int),
     "hz_solve_end": ([_P, _P, C.POINTER(hz_info), _P], C.c_int),
@@ -345,6 +349,34 @@ def hz_level_prolong_add(ctx, level, ec, u, stream=None):
 
 def hz_coarse_solve(ctx, f, u, stream=None):
     _check(lib.hz_coarse_solve(ctx, _ptr(f), _ptr(u), _stream(stream)), "hz_coarse_solve")
+
+
+def hz_cycle_factor(ctx, f, u, warmup: int = 5, target: float = 1e-9, max_iter: int = 300, stream=None):
+    """(factor, iterations) of Eq. cf; u (device complex128) is updated in place."""
+    fac, its = C.c_double(), C.c_int()
+    _check(lib.hz_cycle_factor(ctx, _ptr(f), _ptr(u), int(warmup), float(target), int(max_iter),
+                               C.byref(fac), C.byref(its), _stream(stream)), "hz_cycle_factor")
+    return fac.value, its.value
+
+
+def hz_lfa_factors(dim: int, stencil, patch: str, w, rk: str = "cubic", pk: str = "cubic", nu1: int = 1,
+                   nu2: int = 1, samples: int = 128, want_mu: bool = True, want_rho: bool = True):
+    """(mu_loc[w], rho_loc[w]) for a constant stencil given as 3^dim complex
+    values in (dz, dy, dx) order (or a dict {offset: value})."""
+    if isinstance(stencil, dict):
+        arr = np.zeros((3,) * dim, dtype=np.complex128)
+        for off, v in stencil.items():
+            arr[tuple(o + 1 for o in reversed(off))] = v
+        stencil = arr
+    st = np.ascontiguousarray(np.asarray(stencil, dtype=np.complex128).reshape(-1))
+    if st.size != 3 ** dim:
+        raise ValueError("stencil needs 3^dim values")
+    ws = np.ascontiguousarray(np.atleast_1d(np.asarray(w, dtype=np.float64)))
+    mu = np.zeros(ws.size) if want_mu else None
+    rho = np.zeros(ws.size) if want_rho else None
+    _check(lib.hz_lfa_factors(dim, st.ctypes.data, PATCH[patch], ws.ctypes.data, ws.size, INTERGRID[rk],
+                              INTERGRID[pk], nu1, nu2, samples, _ptr(mu), _ptr(rho)), "hz_lfa_factors")
+    return mu, rho
 
 
 # ------------------------------------------------------------------ serving
