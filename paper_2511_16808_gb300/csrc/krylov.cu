@@ -35,22 +35,47 @@ namespace hz {
 
 namespace {
 
-// Block-reduce one double2 accumulator per thread; thread 0 writes partials[block].
-__device__ __forceinline__ void block_store(double2 acc, double2* __restrict__ partials, int block) {
-  __shared__ double2 sm[kRedBlock / 32];
-  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-  const int lane = tid & 31, wid = tid >> 5;
-  for (int o = 16; o > 0; o >>= 1) {
-    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
-    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
-  }
-  if (lane == 0) sm[wid] = acc;
+// Block sums of C double2 values per thread by a shared-memory tree (256 ->
+// 32 values, then the shuffles of one warp).  The Krylov passes are bound by
+// the FP64 pipe, and this takes 7 + 5 FP64 add steps per component against 5
+// in every one of the 8 warps for a shuffle tree alone.  CPLX = false sums the
+// real parts only.  The result is in v of thread 0 (all of warp 0).
+template <int C, bool CPLX>
+__device__ __forceinline__ void block_sums(double2 (&v)[C], double2 (&sm)[C][kRedBlock], int tid) {
+#pragma unroll
+  for (int c = 0; c < C; ++c) sm[c][tid] = v[c];
   __syncthreads();
-  if (tid == 0) {
-    double2 s = make_double2(0, 0);
-    for (int w = 0; w < kRedBlock / 32; ++w) s = s + sm[w];
-    partials[block] = s;
+#pragma unroll
+  for (int k = kRedBlock / 2; k >= 32; k >>= 1) {
+    if (tid < k) {
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        sm[c][tid].x += sm[c][tid + k].x;
+        if (CPLX) sm[c][tid].y += sm[c][tid + k].y;
+      }
+    }
+    __syncthreads();
   }
+  if (tid < 32) {
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      double2 a = sm[c][tid];
+      for (int o = 16; o > 0; o >>= 1) {
+        a.x += __shfl_xor_sync(0xffffffffu, a.x, o);
+        if (CPLX) a.y += __shfl_xor_sync(0xffffffffu, a.y, o);
+      }
+      v[c] = a;
+    }
+  }
+}
+
+// Block-reduce the real accumulator of each thread; thread 0 writes partials[block].
+__device__ __forceinline__ void block_store(double2 acc, double2* __restrict__ partials, int block) {
+  __shared__ double2 sm[1][kRedBlock];
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  double2 v[1] = {make_double2(acc.x, 0.0)};
+  block_sums<1, false>(v, sm, tid);
+  if (tid == 0) partials[block] = make_double2(v[0].x, 0.0);
 }
 
 // Two-stage deterministic reduction finished by the last block to arrive:
@@ -67,23 +92,19 @@ __device__ __forceinline__ bool reduce_last(double2 acc, double2* __restrict__ p
   __syncthreads();
   if (!is_last) return false;
   __threadfence();
-  __shared__ double2 red[kRedBlock];
-  double2 s = make_double2(0, 0);
+  __shared__ double2 red[1][kRedBlock];
+  double s = 0.0;
   int b = tid;
   for (; b + 3 * kRedBlock < nb; b += 4 * kRedBlock) {
-    const double2 a0 = __ldcg(partials + b), a1 = __ldcg(partials + b + kRedBlock);
-    const double2 a2 = __ldcg(partials + b + 2 * kRedBlock), a3 = __ldcg(partials + b + 3 * kRedBlock);
+    const double a0 = __ldcg(partials + b).x, a1 = __ldcg(partials + b + kRedBlock).x;
+    const double a2 = __ldcg(partials + b + 2 * kRedBlock).x, a3 = __ldcg(partials + b + 3 * kRedBlock).x;
     s = s + ((a0 + a1) + (a2 + a3));
   }
-  for (; b < nb; b += kRedBlock) s = s + __ldcg(partials + b);
-  red[tid] = s;
-  __syncthreads();
-  for (int k = kRedBlock / 2; k > 0; k >>= 1) {
-    if (tid < k) red[tid] = red[tid] + red[tid + k];
-    __syncthreads();
-  }
+  for (; b < nb; b += kRedBlock) s = s + __ldcg(partials + b).x;
+  double2 v[1] = {make_double2(s, 0.0)};
+  block_sums<1, false>(v, red, tid);
   if (tid == 0) {
-    *out = red[0];
+    *out = make_double2(v[0].x, 0.0);
     *counter = 0u;
   }
   return true;
@@ -92,29 +113,29 @@ __device__ __forceinline__ bool reduce_last(double2 acc, double2* __restrict__ p
 __device__ __forceinline__ int block_linear() { return (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x; }
 
 
-// Per-block partials of NV complex accumulators, then (last block to arrive)
-// NV deterministic sums: warp w sums vectors w, w+8, ... over the blocks in
-// index order.  Returns true in the last block.
+// Per-block partials of NV complex accumulators (block_sums, up to 4 vectors
+// per round), then (last block to arrive) NV deterministic sums: warp w sums
+// vectors w, w+8, ... over the blocks in index order.  Returns true in the
+// last block.
 template <int NV>
 __device__ __forceinline__ bool reduce_last_multi(const double2 (&acc)[NV], double2* __restrict__ partials, int nb,
                                                   int block, unsigned* counter, double2* out) {
-  __shared__ double2 sm[kRedBlock / 32][NV];
+  constexpr int CH = NV < 4 ? NV : 4;            // vectors per shared-memory round
+  __shared__ double2 sm[CH][kRedBlock];
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   const int lane = tid & 31, wid = tid >> 5;
 #pragma unroll
-  for (int i = 0; i < NV; ++i) {
-    double2 a = acc[i];
-    for (int o = 16; o > 0; o >>= 1) {
-      a.x += __shfl_xor_sync(0xffffffffu, a.x, o);
-      a.y += __shfl_xor_sync(0xffffffffu, a.y, o);
+  for (int i0 = 0; i0 < NV; i0 += CH) {
+    double2 v[CH];
+#pragma unroll
+    for (int c = 0; c < CH; ++c) v[c] = i0 + c < NV ? acc[i0 + c < NV ? i0 + c : NV - 1] : make_double2(0, 0);
+    block_sums<CH, true>(v, sm, tid);
+    if (tid == 0) {
+#pragma unroll
+      for (int c = 0; c < CH; ++c)
+        if (i0 + c < NV) partials[(i0 + c) * nb + block] = v[c];
     }
-    if (lane == 0) sm[wid][i] = a;
-  }
-  __syncthreads();
-  if (tid < NV) {
-    double2 t = make_double2(0, 0);
-    for (int w = 0; w < kRedBlock / 32; ++w) t = t + sm[w][tid];
-    partials[tid * nb + block] = t;
+    __syncthreads();                               // sm is restaged by the next round
   }
   __threadfence();
   __syncthreads();
@@ -219,6 +240,7 @@ __global__ void k_solve_y(KrylovState* __restrict__ st) {
     double2 acc = st->g[i];
     for (int l = i + 1; l < k; ++l) acc = acc - cmul(st->H[i][l], st->y[l]);
     st->y[i] = cdiv(acc, st->H[i][i]);
+    st->c[i] = st->scale[i] * st->y[i];          // once here instead of at every node
   }
 }
 
@@ -232,7 +254,7 @@ __global__ void k_update_p(int N, const TZ* __restrict__ Z, const KrylovState* _
   const int k = st->kcyc;
   double2 acc = p[q];
   for (int i = 0; i < k; ++i) {
-    const double2 yi = st->scale[i] * st->y[i], zi = ld64(Z, i * N + q);
+    const double2 yi = st->c[i], zi = ld64(Z, i * N + q);
     acc = make_double2(fma(yi.x, zi.x, fma(-yi.y, zi.y, acc.x)), fma(yi.x, zi.y, fma(yi.y, zi.x, acc.y)));
   }
   p[q] = acc;

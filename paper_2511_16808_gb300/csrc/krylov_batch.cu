@@ -288,6 +288,7 @@ __global__ void k_solve_y_b(KrylovState* st, int R) {
     double2 acc = s->g[i];
     for (int l = i + 1; l < k; ++l) acc = acc - cmul(s->H[i][l], s->y[l]);
     s->y[i] = cdiv(acc, s->H[i][i]);
+    s->c[i] = s->scale[i] * s->y[i];
   }
 }
 
@@ -303,7 +304,7 @@ __global__ void k_update_p_b(GeoB g, const TZ* __restrict__ Z, const KrylovState
   const int k = s->kcyc;
   double2 acc = p[q];
   for (int i = 0; i < k; ++i) {
-    const double2 yi = s->scale[i] * s->y[i], zi = ld64(Z, i * g.NR + q);
+    const double2 yi = s->c[i], zi = ld64(Z, i * g.NR + q);
     acc = make_double2(fma(yi.x, zi.x, fma(-yi.y, zi.y, acc.x)), fma(yi.x, zi.y, fma(yi.y, zi.x, acc.y)));
   }
   p[q] = acc;

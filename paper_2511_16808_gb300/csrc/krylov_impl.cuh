@@ -35,6 +35,7 @@ struct KrylovState {
   double2 g[kMaxM + 1];
   double scale[kMaxM + 1];  // v_i = scale[i] * V[i]
   double2 y[kMaxM];
+  double2 c[kMaxM];         // scale[i] * y[i]: the update coefficients of z'_i
   double2 h1[kMaxM + 2];    // raw dots conj(V_i) . w of the Gram-Schmidt passes
   double2 nrm2;             // .x = ||w||^2 after orthogonalisation
   unsigned counter;         // blocks finished in the current reduction (last block resets it)
