@@ -645,23 +645,43 @@ __global__ void __launch_bounds__(BX* BY) k_prolong_fused_2d(Geo gf, Geo gc, T i
   }
 }
 
-// u = Ainv f, one warp per row
-template <typename T>
-__global__ void k_dense_gemv(int n, const c_t<T>* __restrict__ A, const c_t<T>* __restrict__ f, c_t<T>* __restrict__ u,
-                             const int* active) {
+// u = Ainv f: TPR threads per row (256 / TPR rows per block of 256), four
+// independent accumulators per thread so that several row loads are in flight
+// (the matrix is streamed once per cycle); warp shuffles, then the row's warps
+// added in a fixed order through shared memory (deterministic).
+template <typename T, int TPR>
+__global__ void __launch_bounds__(256) k_dense_gemv(int n, const c_t<T>* __restrict__ A, const c_t<T>* __restrict__ f,
+                                                    c_t<T>* __restrict__ u, const int* active) {
   pdl_enter();
   if (active && !*active) return;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (warp >= n) return;
-  c_t<T> acc = cmk<c_t<T>>(0, 0);
-  const c_t<T>* row = A + (long long)warp * n;
-  for (int j = lane; j < n; j += 32) acc = cfma(row[j], f[j], acc);
-  for (int o = 16; o > 0; o >>= 1) {
-    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
-    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+  using V = c_t<T>;
+  constexpr int RPB = 256 / TPR, WPR = TPR / 32;
+  __shared__ V part[RPB][WPR];
+  const int tr = threadIdx.x % TPR, rb = threadIdx.x / TPR;
+  const int row = blockIdx.x * RPB + rb;
+  V acc[4] = {cmk<V>(0, 0), cmk<V>(0, 0), cmk<V>(0, 0), cmk<V>(0, 0)};
+  if (row < n) {
+    const V* a = A + (long long)row * n;
+    int j = tr;
+    for (; j + 3 * TPR < n; j += 4 * TPR) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) acc[k] = cfma(a[j + k * TPR], f[j + k * TPR], acc[k]);
+    }
+    for (int k = 0; j < n; j += TPR, ++k) acc[k] = cfma(a[j], f[j], acc[k]);
   }
-  if (lane == 0) u[warp] = acc;
+  V t = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+  for (int o = 16; o > 0; o >>= 1) {
+    t.x += __shfl_xor_sync(0xffffffffu, t.x, o);
+    t.y += __shfl_xor_sync(0xffffffffu, t.y, o);
+  }
+  if ((tr & 31) == 0) part[rb][tr >> 5] = t;
+  __syncthreads();
+  if (tr == 0 && row < n) {
+    V s = part[rb][0];
+#pragma unroll
+    for (int w = 1; w < WPR; ++w) s = s + part[rb][w];
+    u[row] = s;
+  }
 }
 
 // u[i][r] = sum_j Ainv[i][j] f[j][r] for R >= 8 right-hand sides (a plain
@@ -937,9 +957,14 @@ template <typename T>
 void coarse_t(Ctx& c, const void* f, void* u, const int* active, cudaStream_t s) {
   Level& L = c.L.back();
   const int n = (int)L.g.N;
-  if (c.nrhs == 1)
-    launch_pdl(k_dense_gemv<T>, nblk((long long)n * 32, 256), 256, s, n, (const c_t<T>*)L.Ainvw, (const c_t<T>*)f,
-                                                                (c_t<T>*)u, active);
+  if (c.nrhs == 1) {
+    if (n <= 512)
+      launch_pdl(k_dense_gemv<T, 32>, nblk(n, 8), 256, s, n, (const c_t<T>*)L.Ainvw, (const c_t<T>*)f, (c_t<T>*)u,
+                 active);
+    else
+      launch_pdl(k_dense_gemv<T, 128>, nblk(n, 2), 256, s, n, (const c_t<T>*)L.Ainvw, (const c_t<T>*)f, (c_t<T>*)u,
+                 active);
+  }
   else if (c.nrhs >= 8)
     launch_pdl(k_dense_gemm_rhs<T>, nblk(n, 512 / c.nrhs), 256, s, n, c.nrhs, (const c_t<T>*)L.Ainvw, (const c_t<T>*)f,
                                                                (c_t<T>*)u, active);
