@@ -98,7 +98,10 @@ typedef struct {
   int nu1, nu2;                      /* pre- / post-relaxations            */
   hz_intergrid intergrid;
   hz_precision precision;
-  int restart_m;                     /* FGMRES restart length, 1..16       */
+  int restart_m;                     /* FGMRES restart length, 1..128 (1..16
+                                        when nrhs_max > 1); a length at
+                                        least the iteration count gives
+                                        non-restarted FGMRES (§5.2)        */
   double tol;                        /* relative residual ||q_hat - A p|| / ||q_hat|| */
   int max_iter;                      /* max preconditioner applications    */
   int nrhs_max;                      /* largest nrhs any call will pass    */

@@ -143,7 +143,8 @@ void validate(const hz_grid* g, const hz_opts* o) {
     require((g->n[a] - 1) / div >= 2, "coarsest grid needs at least 3 nodes per axis");
   }
   require(o->nu1 >= 0 && o->nu2 >= 0 && o->nu1 + o->nu2 <= 16, "nu1/nu2 out of range");
-  require(o->restart_m >= 1 && o->restart_m <= 16, "restart_m out of range");
+  require(o->restart_m >= 1 && o->restart_m <= 128, "restart_m out of range (1..128)");
+  require(o->nrhs_max <= 1 || o->restart_m <= 16, "restart_m must be <= 16 when nrhs_max > 1");
   require(o->tol > 0 && o->max_iter >= 1, "tol/max_iter out of range");
   require(o->nrhs_max >= 1 && o->nrhs_max <= 64, "nrhs_max must be in 1..64");
   require(o->cycle_visits >= 0 && o->cycle_visits <= 2, "cycle_visits must be 0, 1 (V) or 2 (W)");

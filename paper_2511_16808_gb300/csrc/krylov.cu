@@ -181,17 +181,18 @@ __device__ __forceinline__ void block_range(int N, int& b0, int& b1) {
   b1 = (int)std::min<long long>(b0 + per, N);
 }
 
-// pass A: w = A z'_j -> V[j+1]; d_i = conj(V_i) . w for i < NV = j + 1
+// pass A: w = A z'_j (w = V[j+1]); d_i = conj(V_i) . w for i < NV (the first
+// chunk of the j + 1 inner products, all of them when j < kMaxNV)
 template <typename TZ, int NV>
 __global__ void __launch_bounds__(kRedBlock) k_gs_dots(Geo g, double invh2, const double2* __restrict__ diag,
-                                                       const TZ* __restrict__ z, double2* __restrict__ V,
-                                                       double2* __restrict__ partials, KrylovState* st) {
+                                                       const TZ* __restrict__ z, const double2* __restrict__ V,
+                                                       double2* __restrict__ w, double2* __restrict__ partials,
+                                                       KrylovState* st) {
   pdl_enter();
   if (!st->active) return;
   double2 acc[NV];
 #pragma unroll
   for (int i = 0; i < NV; ++i) acc[i] = make_double2(0, 0);
-  double2* w = V + (long long)NV * g.N;
   for_tiles(g, [&](int p, int x, int y, int zz) {
     const double2 a = apply_A(g, invh2, diag, z, p, x, y, zz);
     w[p] = a;
@@ -201,34 +202,61 @@ __global__ void __launch_bounds__(kRedBlock) k_gs_dots(Geo g, double invh2, cons
   reduce_last_multi<NV>(acc, partials, gridDim.x, blockIdx.x, &st->counter, st->h1);
 }
 
-// pass B: w -= sum_{i < NV} scale_i^2 d_i V_i; ||w||^2; f = w in the working
-// precision; then (last block) the Arnoldi column of j = NV - 1
-template <typename TF, int NV>
-__global__ void __launch_bounds__(kRedBlock) k_gs_update(int N, double2* __restrict__ V, TF* __restrict__ f,
-                                                         double2* __restrict__ partials, KrylovState* st) {
+// pass A, further chunks: d_{base+i} = conj(V_{base+i}) . w for i < NV
+template <int NV>
+__global__ void __launch_bounds__(kRedBlock) k_gs_dots_more(int N, const double2* __restrict__ Vb,
+                                                            const double2* __restrict__ w,
+                                                            double2* __restrict__ partials, KrylovState* st,
+                                                            int base) {
+  pdl_enter();
+  if (!st->active) return;
+  double2 acc[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) acc[i] = make_double2(0, 0);
+  int b0, b1;
+  block_range(N, b0, b1);
+  for (int p = b0 + threadIdx.x; p < b1; p += kRedBlock) {
+    const double2 a = w[p];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) acc[i] = dot_acc(acc[i], Vb[(long long)i * N + p], a);
+  }
+  reduce_last_multi<NV>(acc, partials, gridDim.x, blockIdx.x, &st->counter, st->h1 + base);
+}
+
+// pass B: w -= sum_{i < NV} scale_{base+i}^2 d_{base+i} V_{base+i}.  The last
+// chunk also forms ||w||^2 and f = w in the working precision, then (last
+// block) the Arnoldi column j.
+template <typename TF, int NV, bool LAST>
+__global__ void __launch_bounds__(kRedBlock) k_gs_update(int N, const double2* __restrict__ Vb,
+                                                         double2* __restrict__ w, TF* __restrict__ f,
+                                                         double2* __restrict__ partials, KrylovState* st, int base,
+                                                         int j) {
   pdl_enter();
   if (!st->active) return;
   double2 c[NV];
 #pragma unroll
   for (int i = 0; i < NV; ++i) {
-    const double s = st->scale[i];
-    c[i] = (s * s) * st->h1[i];
+    const double s = st->scale[base + i];
+    c[i] = (s * s) * st->h1[base + i];
   }
-  double2* w = V + (long long)NV * N;
   double acc = 0.0;
   int b0, b1;
   block_range(N, b0, b1);
   for (int p = b0 + threadIdx.x; p < b1; p += kRedBlock) {
     double2 ww = w[p];
 #pragma unroll
-    for (int i = 0; i < NV; ++i) ww = axmy(ww, c[i], V[(long long)i * N + p]);
+    for (int i = 0; i < NV; ++i) ww = axmy(ww, c[i], Vb[(long long)i * N + p]);
     w[p] = ww;
-    if constexpr (std::is_same<TF, float2>::value) f[p] = make_float2(d2f_rn(ww.x), d2f_rn(ww.y));
-    else f[p] = ww;
-    acc = nrm_acc(acc, ww);
+    if constexpr (LAST) {
+      if constexpr (std::is_same<TF, float2>::value) f[p] = make_float2(d2f_rn(ww.x), d2f_rn(ww.y));
+      else f[p] = ww;
+      acc = nrm_acc(acc, ww);
+    }
   }
-  const bool last = reduce_last(make_double2(acc, 0.0), partials, gridDim.x, blockIdx.x, &st->counter, &st->nrm2);
-  if (last && threadIdx.x == 0) arnoldi_update(st, NV - 1, nullptr, st->scale[NV - 1]);
+  if constexpr (LAST) {
+    const bool last = reduce_last(make_double2(acc, 0.0), partials, gridDim.x, blockIdx.x, &st->counter, &st->nrm2);
+    if (last && threadIdx.x == 0) arnoldi_update(st, j, nullptr, st->scale[j]);
+  }
 }
 
 
@@ -347,19 +375,38 @@ void run_cycle(Ctx& c, cudaStream_t s) {
     // pass A: z (b) and diag read, w written, nv vectors read; A z 16 flops
     // (2D; 20 in 3D: two more neighbour sums) + 8 per dot
     pk = prof_begin(c, 2, j, (double)N * (sizeof(TZ) + 32 + 16.0 * nv), ((g.dim == 3 ? 20.0 : 16.0) + 8.0 * nv) * N, s);
-    with_nv(nv, [&](auto NV) {
-      auto kern = k_gs_dots<TZ, decltype(NV)::value>;
-      const unsigned G = (unsigned)std::min<long long>(tiles_xy(g), resident_slots((const void*)kern, kRedBlock));
-      launch_pdl(kern, G, dim3(BX, BY), s, g, invh2, c.diagA64, Z + (long long)j * N, c.V, c.partials, st);
-    });
+    double2* w = c.V + (long long)nv * N;
+    // more than kMaxNV inner products (restarts longer than 16) run in chunks
+    for (int b = 0; b < nv; b += kMaxNV) {
+      with_nv(std::min(kMaxNV, nv - b), [&](auto NV) {
+        if (b == 0) {
+          auto kern = k_gs_dots<TZ, decltype(NV)::value>;
+          const unsigned G = (unsigned)std::min<long long>(tiles_xy(g), resident_slots((const void*)kern, kRedBlock));
+          launch_pdl(kern, G, dim3(BX, BY), s, g, invh2, c.diagA64, Z + (long long)j * N, (const double2*)c.V, w,
+                     c.partials, st);
+        } else {
+          auto kern = k_gs_dots_more<decltype(NV)::value>;
+          const unsigned G = (unsigned)std::min<long long>(grid_1d(N), resident_slots((const void*)kern, kRedBlock));
+          launch_pdl(kern, G, kRedBlock, s, N, (const double2*)(c.V + (long long)b * N), (const double2*)w,
+                     c.partials, st, b);
+        }
+      });
+    }
     prof_end(c, pk, s);
     // pass B: w and nv vectors read, w and f written; 8 flops per vector + 4 for the norm
     pk = prof_begin(c, 1, j, (double)N * (32 + 16.0 * nv + sizeof(TZ)), (8.0 * nv + 4.0) * N, s);
-    with_nv(nv, [&](auto NV) {
-      auto kern = k_gs_update<TZ, decltype(NV)::value>;
-      const unsigned G = (unsigned)std::min<long long>(grid_1d(N), resident_slots((const void*)kern, kRedBlock));
-      launch_pdl(kern, G, kRedBlock, s, N, c.V, (TZ*)L0.f, c.partials, st);
-    });
+    for (int b = 0; b < nv; b += kMaxNV) {
+      const int cnt = std::min(kMaxNV, nv - b);
+      with_nv(cnt, [&](auto NV) {
+        auto go = [&](auto kern) {
+          const unsigned G = (unsigned)std::min<long long>(grid_1d(N), resident_slots((const void*)kern, kRedBlock));
+          launch_pdl(kern, G, kRedBlock, s, N, (const double2*)(c.V + (long long)b * N), w, (TZ*)L0.f, c.partials,
+                     st, b, j);
+        };
+        if (b + cnt >= nv) go(k_gs_update<TZ, decltype(NV)::value, true>);
+        else go(k_gs_update<TZ, decltype(NV)::value, false>);
+      });
+    }
     prof_end(c, pk, s);
   }
   HZ_LAUNCHED();
@@ -622,7 +669,8 @@ void krylov_alloc(Ctx& c) {
   const int m = c.opts.restart_m;
   const long long R = std::max(1, c.opts.nrhs_max);
   const size_t vb = c.mixed ? sizeof(float2) : sizeof(double2);
-  require(m >= 1 && m <= kMaxM, "restart_m must be in 1..16");
+  require(m >= 1 && m <= kMaxM, "restart_m must be in 1..128");
+  require(R == 1 || m <= kMaxNV, "restart_m must be in 1..16 with several right-hand sides");
   require(N * R * (m + 1) < (1ll << 31), "grid too large for 32-bit Krylov indexing");
   c.V = (double2*)ctx_alloc(c, sizeof(double2) * N * R * (m + 1));
   c.Z = ctx_alloc(c, vb * N * R * m);

@@ -8,7 +8,8 @@
 
 namespace hz {
 
-constexpr int kMaxM = 16;
+constexpr int kMaxM = 128;      // longest restart cycle (one RHS; kMaxNV with several)
+constexpr int kMaxNV = 16;      // vectors per Gram-Schmidt launch: longer passes run in chunks
 constexpr int kRedBlock = 256;
 constexpr int BX = 32, BY = 8;
 constexpr int kRows = 4;        // y rows per thread in the 2D passes
@@ -259,7 +260,7 @@ __device__ inline void restart_update(KrylovState* st, int* n_active = nullptr) 
   if (n_active) atomicAdd(n_active, 1);
 }
 
-// NV = 1..kMaxM as a compile-time constant
+// NV = 1..kMaxNV as a compile-time constant
 template <typename F>
 void with_nv(int nv, F&& f) {
   switch (nv) {
@@ -268,7 +269,7 @@ void with_nv(int nv, F&& f) {
     HZ_NV(1) HZ_NV(2) HZ_NV(3) HZ_NV(4) HZ_NV(5) HZ_NV(6) HZ_NV(7) HZ_NV(8)
     HZ_NV(9) HZ_NV(10) HZ_NV(11) HZ_NV(12) HZ_NV(13) HZ_NV(14) HZ_NV(15) HZ_NV(16)
 #undef HZ_NV
-    default: throw Error(HZ_ERR_INVALID_ARG, "restart_m must be in 1..16");
+    default: throw Error(HZ_ERR_INVALID_ARG, "more than 16 vectors in one Gram-Schmidt launch");
   }
 }
 

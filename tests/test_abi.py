@@ -63,10 +63,21 @@ def test_invalid_grid_rejected(n, levels):
 
 def test_invalid_options_rejected():
     g = hz.make_grid(2, [33, 33], 1 / 32)
-    for field, value in [("restart_m", 0), ("restart_m", 17), ("tol", 0.0), ("nrhs_max", 0),
+    for field, value in [("restart_m", 0), ("restart_m", 129), ("tol", 0.0), ("nrhs_max", 0),
                          ("cycle_visits", 3), ("cycle_visits", -1)]:
         o = hz.hz_opts_default(2)
         setattr(o, field, value)
         with pytest.raises(hz.HzError) as e:
             hz.hz_setup_bytes(g, o)
         assert e.value.status == 1
+
+
+def test_long_restart_needs_one_rhs():
+    g = hz.make_grid(2, [33, 33], 1 / 32)
+    o = hz.hz_opts_default(2)
+    o.restart_m = 128
+    hz.hz_setup_bytes(g, o)                          # one right-hand side: up to 128
+    o.nrhs_max = 2
+    with pytest.raises(hz.HzError) as e:
+        hz.hz_setup_bytes(g, o)
+    assert e.value.status == 1

@@ -187,3 +187,63 @@ def test_solve_host_buffers_match_device():
     assert ok and infos[0].iters == info_d.iters
     assert np.array_equal(p_host, p_dev.cpu().numpy())
     gpu.close()
+
+
+LONG = [CASES_2D[0], CASES_3D[0]]
+
+
+@pytest.mark.parametrize("m", [20, 40])
+@pytest.mark.parametrize("precision,err_tol", [("fp64", 1e-6), ("mixed", 1e-5)])
+@pytest.mark.parametrize("case", LONG, ids=_ids(LONG))
+def test_fgmres_long_restart(case, m, precision, err_tol):
+    """FGMRES(m) with m > 16: the Gram-Schmidt passes of the later inner steps
+    run in chunks of 16 vectors; counts +-1 and solutions as for m = 5."""
+    from paper_2511_16808_gb300.solver import HelmholtzSolver
+    from pairs import medium
+    import workloads
+    c = dict(case)
+    dim, n = c["dim"], c["n"]
+    h, omega, kappa, gamma = medium(dim, n, 0, c.get("layer", 0))
+    from oracle import solver as osolver
+    orc = osolver.Problem((n,) * dim, h, kappa, omega, gamma, 0.25, c["levels"], c["patch"], c["scheme"])
+    gpu = HelmholtzSolver(dim, [n] * dim, kappa, omega, gamma, 0.25, c["levels"], patch=c["patch"],
+                          intergrid=c["scheme"], precision=precision, tol=1e-7, restart=m)
+    q = workloads.point_source((n,) * dim, tuple([(n - 1) // 2] * dim), h).ravel()
+    p_o, info_o = orc.solve(q, tol=1e-7, m=m)
+    p_ref, _ = orc.solve(q, tol=1e-10)
+    p, info = gpu.solve(torch.tensor(q, device="cuda"))
+    p = p.cpu().numpy()
+    gpu.close()
+    assert info.converged == 1 and abs(info.iters - info_o.iters) <= 1, (info.iters, info_o.iters)
+    qh = orc.rhs(q)
+    assert np.linalg.norm(qh - orc.A @ p) / np.linalg.norm(qh) < 1e-7
+    err = np.linalg.norm(p - p_ref) / np.linalg.norm(p_ref)
+    err_o = np.linalg.norm(p_o - p_ref) / np.linalg.norm(p_ref)
+    assert err < max(err_tol, 2 * err_o), (err, err_o)
+
+
+def test_non_restarted_fgmres_w_cycle():
+    """Non-restarted FGMRES (m = 128 > iterations) with 4-level W(1,1) cycles on
+    the 2D homogeneous medium of Table const2D: the oracle's count +-1, and no
+    more iterations than GMRES(5)."""
+    from paper_2511_16808_gb300.solver import HelmholtzSolver
+    from oracle import solver as osolver
+    import workloads
+    n = 129
+    h = 1.0 / (n - 1)
+    omega = workloads.omega_for_ppw(10.0, h, 1.0)
+    kappa = np.ones(n * n)
+    gamma = workloads.absorbing_gamma((n, n), omega, 0.0, 20).ravel()
+    q = workloads.point_source((n, n), (64, 64), h).ravel()
+    orc = osolver.Problem((n, n), h, kappa, omega, gamma, 0.25, 4, "element", "leveldep", cycle="W")
+    _, info_o = orc.solve(q, tol=1e-6, m=128)
+    its = {}
+    for m in (128, 5):
+        s = HelmholtzSolver(2, [n, n], kappa, omega, gamma, 0.25, 4, patch="element", intergrid="leveldep",
+                            precision="fp64", tol=1e-6, restart=m, cycle="W")
+        _, info = s.solve(torch.tensor(q, device="cuda"))
+        s.close()
+        assert info.converged == 1
+        its[m] = info.iters
+    assert abs(its[128] - info_o.iters) <= 1 and its[128] < 128, (its, info_o.iters)
+    assert its[128] <= its[5]
