@@ -354,6 +354,23 @@ hz_status hz_level_prolong_add(hz_ctx* ctx, int level, const void* ec, void* u, 
 /* u = (A_s^L)^{-1} f on the coarsest level L (dense inverse from setup). */
 hz_status hz_coarse_solve(hz_ctx* ctx, const void* f, void* u, void* cuda_stream);
 
+/* ---- per-solve metrics -------------------------------------------------- */
+
+/* Wall time of hz_setup for this context, seconds (host clock around the whole
+ * call, device work included). */
+hz_status hz_setup_seconds(const hz_ctx* ctx, double* seconds);
+
+/* Convergence history of the last single-RHS solve on the context (hz_solve
+ * with nrhs = 1, or hz_solve_begin/step/end): one entry per status read, that
+ * is the start and the end of every restart cycle, each with the iteration
+ * count so far, the true relative residual ||q_hat - A p|| / ||q_hat|| (FP64,
+ * formed at restarts) and the Arnoldi estimate.  A batched solve clears it.
+ *   cap        capacity of the output arrays (host); entries beyond it are dropped
+ *   iters, relres_true, relres_est   host arrays of cap values, each may be NULL
+ *   n          out: entries recorded (may exceed cap) */
+hz_status hz_solve_history(const hz_ctx* ctx, int cap, int* iters, double* relres_true, double* relres_est,
+                           int* n);
+
 /* ---- tuning tools (Section 5.2) ---------------------------------------- */
 
 /* Convergence factor of Eq. cf (Section 5.1) of the context's cycle used as a

@@ -7,6 +7,8 @@
 
 #include "common.cuh"
 
+#include <chrono>
+
 namespace hz {
 
 static thread_local std::string g_last_error;
@@ -283,6 +285,8 @@ hz_status hz_setup(const hz_grid* g, const double* kappa, double omega, const do
       throw Error(HZ_ERR_NO_DEVICE, "no CUDA device");
     }
     cudaStream_t s = (cudaStream_t)cuda_stream;
+    NvtxRange range("hz_setup");
+    const auto t0 = std::chrono::steady_clock::now();
     h = new hz_ctx();
     Ctx& c = h->c;
     c.grid = *g;
@@ -307,6 +311,7 @@ hz_status hz_setup(const hz_grid* g, const double* kappa, double omega, const do
     build_hierarchy(c, dk, dg, gamma0, s);
     krylov_alloc(c);
     HZ_CUDA(cudaStreamSynchronize(s));
+    c.setup_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   });
   if (st != HZ_OK) {
     if (h) {
@@ -570,6 +575,27 @@ hz_status hz_coarse_solve(hz_ctx* ctx, const void* f, void* u, void* cuda_stream
     BusyGuard bg(&ctx->c);
     ctx->c.nrhs = 1;
     coarse_solve(ctx->c, f, u, nullptr, (cudaStream_t)cuda_stream);
+  });
+}
+
+hz_status hz_setup_seconds(const hz_ctx* ctx, double* seconds) {
+  return guarded([&] {
+    require(ctx && seconds, "null argument");
+    *seconds = ctx->c.setup_seconds;
+  });
+}
+
+hz_status hz_solve_history(const hz_ctx* ctx, int cap, int* iters, double* relres_true, double* relres_est,
+                           int* n) {
+  return guarded([&] {
+    require(ctx && n && cap >= 0, "null argument or negative capacity");
+    const auto& hst = ctx->c.history;
+    *n = (int)hst.size();
+    for (int i = 0; i < cap && i < (int)hst.size(); ++i) {
+      if (iters) iters[i] = (int)hst[i][0];
+      if (relres_true) relres_true[i] = hst[i][1];
+      if (relres_est) relres_est[i] = hst[i][2];
+    }
   });
 }
 

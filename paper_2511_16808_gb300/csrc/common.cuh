@@ -20,6 +20,7 @@
 #include <stdexcept>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <array>
 #include <atomic>
@@ -381,9 +382,22 @@ struct Level {
 
 struct KrylovState;              // device-side FGMRES state, krylov.cu
 
+// NVTX range for the life of a scope (setup levels, solves, restart cycles);
+// header-only NVTX3, a no-op unless a tool (nsys, ncu --nvtx) is attached
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 struct Ctx {
   hz_grid grid;
   hz_opts opts;
+  double setup_seconds = 0;     // wall time of hz_setup (host, including the device work)
+  // per status read of the last single-RHS solve (start, then every restart
+  // cycle): iterations so far, true relative residual, Arnoldi estimate
+  std::vector<std::array<double, 3>> history;
   double omega = 0, alpha = 0, h = 0;
   int dev = 0;
   bool mixed = true;

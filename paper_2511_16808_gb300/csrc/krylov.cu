@@ -487,6 +487,7 @@ void solve_begin_t(Ctx& c, const double2* q, cudaStream_t user) {
   c.launches += 2;
   HZ_CUDA(cudaMemcpyAsync(hs, &st->st, sizeof(KrylovStatus), cudaMemcpyDeviceToHost, s));
   HZ_CUDA(cudaEventRecord(c.ev_status, s));
+  c.history.clear();
   c.as_before = 0;
   c.as_replayed = false;
   c.as_state = 1;
@@ -505,12 +506,14 @@ int solve_step(Ctx& c, bool block) {
   }
   KrylovStatus* hs = (KrylovStatus*)c.ks_host;
   if (c.as_replayed && c.prof_class) prof_collect(c, hs->iters - c.as_before, nullptr, 1);
+  c.history.push_back({(double)hs->iters, hs->relres_true, hs->relres_est});
   if (hs->done) {
     c.as_state = 2;
     return 1;
   }
   c.as_before = hs->iters;
   cudaStream_t s = c.graph_stream;
+  NvtxRange range("hz restart cycle");
   HZ_CUDA(cudaGraphLaunch(c.cycle_graph, s));
   c.as_replayed = true;
   c.launches += c.graph_kernels;
@@ -704,6 +707,7 @@ void profile_select(Ctx& c, int cls) {
 }
 
 void fgmres_solve(Ctx& c, const double2* q, double2* p, hz_info* info, cudaStream_t s) {
+  NvtxRange range("hz solve");
   solve_begin(c, q, s);
   while (!solve_step(c, true)) {
   }

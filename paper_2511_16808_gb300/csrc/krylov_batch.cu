@@ -488,6 +488,8 @@ void solve_b(Ctx& c, const double2* q, double2* p, int R, hz_info* info, cudaStr
 }  // namespace
 
 void fgmres_solve_batch(Ctx& c, const double2* q, double2* p, int nrhs, hz_info* info, cudaStream_t s) {
+  NvtxRange range("hz batched solve");
+  c.history.clear();
   if (c.mixed) solve_b<float2>(c, q, p, nrhs, info, s);
   else solve_b<double2>(c, q, p, nrhs, info, s);
 }

@@ -734,9 +734,14 @@ void build_hierarchy(Ctx& c, const double* kappa, const double* gamma, double ga
                                                 c.diagA64, c.wmass, L.A.off, L.A64);
     HZ_LAUNCHED();
   }
+  static const char* kLevelRange[] = {"hz setup level 0", "hz setup level 1", "hz setup level 2",
+                                      "hz setup level 3", "hz setup level 4", "hz setup level 5",
+                                      "hz setup level 6", "hz setup level 7", "hz setup level 8",
+                                      "hz setup level 9", "hz setup level 10", "hz setup level 11"};
   for (int l = 0; l < levels; ++l) {
     Level& L = c.L[l];
     const long long N = L.g.N;
+    NvtxRange range(kLevelRange[l < 12 ? l : 11]);
     if (L.coarsest) {
       invert_dense(c, L, s);
       L.Ainvw = working_copy(c, L.Ainv64, N * N, s);

@@ -120,6 +120,8 @@ _SIGS = {
     "hz_level_restrict": ([_P, C.c_int, _P, _P, _P], C.c_int),
     "hz_level_prolong_add": ([_P, C.c_int, _P, _P, _P], C.c_int),
     "hz_coarse_solve": ([_P, _P, _P, _P], C.c_int),
+    "hz_setup_seconds": ([_P, C.POINTER(C.c_double)], C.c_int),
+    "hz_solve_history": ([_P, C.c_int, _P, _P, _P, C.POINTER(C.c_int)], C.c_int),
     "hz_cycle_factor": ([_P, _P, _P, C.c_int, C.c_double, C.c_int, C.POINTER(C.c_double),
                          C.POINTER(C.c_int), _P], C.c_int),
     "hz_lfa_factors": ([C.c_int, _P, C.c_int, _P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
@@ -349,6 +351,26 @@ def hz_level_prolong_add(ctx, level, ec, u, stream=None):
 
 def hz_coarse_solve(ctx, f, u, stream=None):
     _check(lib.hz_coarse_solve(ctx, _ptr(f), _ptr(u), _stream(stream)), "hz_coarse_solve")
+
+
+def hz_setup_seconds(ctx) -> float:
+    out = C.c_double()
+    _check(lib.hz_setup_seconds(ctx, C.byref(out)), "hz_setup_seconds")
+    return out.value
+
+
+def hz_solve_history(ctx) -> dict:
+    """{"iters", "relres_true", "relres_est"} lists of the last single-RHS solve."""
+    n = C.c_int()
+    _check(lib.hz_solve_history(ctx, 0, None, None, None, C.byref(n)), "hz_solve_history")
+    k = n.value
+    its = np.zeros(k, dtype=np.int32)
+    rt = np.zeros(k)
+    re = np.zeros(k)
+    if k:
+        _check(lib.hz_solve_history(ctx, k, its.ctypes.data, rt.ctypes.data, re.ctypes.data, C.byref(n)),
+               "hz_solve_history")
+    return {"iters": its.tolist(), "relres_true": rt.tolist(), "relres_est": re.tolist()}
 
 
 def hz_cycle_factor(ctx, f, u, warmup: int = 5, target: float = 1e-9, max_iter: int = 300, stream=None):

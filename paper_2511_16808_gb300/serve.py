@@ -7,18 +7,25 @@ from __future__ import annotations
 
 import numpy as np
 
+import time
+
 from . import hz
-from .solver import make_opts
+from .solver import JsonLines, make_opts
 
 
 class Server:
     """hbm_budget: device bytes the admitted requests may hold (0: 80% of free
     memory); max_active: requests set up or solving at once (0: 32);
-    setup_threads: hierarchies built concurrently (0: 2)."""
+    setup_threads: hierarchies built concurrently (0: 2); log: a path or text
+    file receiving one JSON line per finished request (latency, queue delay,
+    setup and solve spans, iterations, bytes) and one with the server's
+    counters when it closes."""
 
-    def __init__(self, hbm_budget: int = 0, max_active: int = 0, device: int = -1, setup_threads: int = 0):
+    def __init__(self, hbm_budget: int = 0, max_active: int = 0, device: int = -1, setup_threads: int = 0,
+                 log=None):
         self.srv = hz.hz_server_create(hbm_budget, max_active, device, setup_threads)
         self._keep = {}
+        self.log = JsonLines(log) if log is not None else None
 
     def submit(self, dim, n, kappa, omega, q, gamma=None, alpha=0.25, levels=4, gamma0=0.0, **solver_opts):
         """kappa, gamma, q: host arrays of n^dim values (float64, float64,
@@ -60,6 +67,8 @@ class Server:
     def wait(self, ticket, timeout: float = -1.0):
         """(solution, info dict) once the request has finished or failed."""
         d = _info(hz.hz_server_wait(self.srv, ticket, timeout))
+        if self.log is not None and d["state"] in ("done", "failed"):
+            self.log.write(request_record(ticket, d))
         return self._keep.pop(ticket), d
 
     def stats(self) -> dict:
@@ -67,8 +76,13 @@ class Server:
 
     def close(self):
         if getattr(self, "srv", None):
+            if getattr(self, "log", None) is not None:
+                self.log.write(dict(self.stats(), event="server_stats", t=time.time()))
             hz.hz_server_destroy(self.srv)
             self.srv = None
+        if getattr(self, "log", None) is not None:
+            self.log.close()
+            self.log = None
 
     def __enter__(self):
         return self
@@ -88,3 +102,21 @@ def _info(t: hz.hz_ticket_info) -> dict:
             "iters": t.info.iters, "converged": bool(t.info.converged), "relres_true": t.info.relres_true,
             "t_submit": t.t_submit, "t_admit": t.t_admit, "t_start": t.t_start, "t_done": t.t_done,
             "bytes": t.bytes, "message": t.message.decode(errors="replace")}
+
+
+def request_record(ticket, d: dict) -> dict:
+    """The per-request metrics line: end-to-end latency, queueing delay
+    (submission to admission), setup span (admission to first restart cycle),
+    solve span, iterations, status and device bytes held."""
+    rec = {"event": "request", "t": time.time(), "ticket": int(ticket), "state": d["state"], "status": d["status"],
+           "iters": d["iters"], "converged": d["converged"], "relres_true": d["relres_true"], "bytes": d["bytes"],
+           "latency_s": d["t_done"] - d["t_submit"]}
+
+    def span(a, b):                  # a stage the request never reached has no span
+        return d[b] - d[a] if d[b] >= d[a] > 0 or (a == "t_submit" and d[b] >= d[a]) else None
+    rec["queue_s"] = span("t_submit", "t_admit")
+    rec["setup_s"] = span("t_admit", "t_start")
+    rec["solve_s"] = span("t_start", "t_done")
+    if d["message"]:
+        rec["message"] = d["message"]
+    return rec
