@@ -10,8 +10,9 @@
 // 2. The convergence factor of Eq. cf of the cycle used as a stationary solver
 //    u <- u + B(f - A_s u) on a set-up hierarchy (the shift and per-level
 //    damping searches run it once per candidate).
-#include "common.cuh"
+#include "krylov_impl.cuh"
 
+#include <algorithm>
 #include <array>
 #include <cmath>
 #include <cstring>
@@ -346,7 +347,7 @@ void cycle_factor(Ctx& c, const double2* f, double2* u, int warmup, double targe
   // reduction partials
   double2* r = c.V;
   double2* w = c.V + N;
-  const int G = 152 * 4;
+  const int G = std::max(1, max_slots() / 2);      // 4 blocks of 256 per SM (max_slots = 8 per SM)
   double* part = (double*)c.partials;
   double* norm = part + G;
   unsigned* count = (unsigned*)(norm + 1);
