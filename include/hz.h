@@ -101,7 +101,7 @@ typedef struct {
   int restart_m;                     /* FGMRES restart length, 1..128 (1..16
                                         when nrhs_max > 1); a length at
                                         least the iteration count gives
-                                        non-restarted FGMRES (§5.2)        */
+                                        non-restarted FGMRES (Section 5.2) */
   double tol;                        /* relative residual ||q_hat - A p|| / ||q_hat|| */
   int max_iter;                      /* max preconditioner applications    */
   int nrhs_max;                      /* largest nrhs any call will pass    */
