@@ -347,6 +347,7 @@ struct Level {
   bool fine = false;
   bool coarsest = false;
   bool a_sym = false;           // A_s of this level is complex symmetric
+  bool a_half = false;          // working copy Aw holds the planes s >= 0 only (symmetric box)
   // operator A_s at this level
   StencilLut A;                 // fine: the 2d+1 point offsets; coarse: box of radius rho
   double2* A64 = nullptr;       // FP64 planes [A.n][N] (setup; kept for export when asked)

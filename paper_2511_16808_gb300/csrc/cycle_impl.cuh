@@ -281,12 +281,63 @@ __device__ __forceinline__ auto box_Au(const Geo& g, const c_t<T>* __restrict__ 
   return acc;
 }
 
-// AK = 0: fine analytic operator; AK = rho > 0: stored box stencil.
+// A u at node p for a symmetric stored box stencil of radius RHO kept as its
+// half: planes of the offsets s >= 0 (the upper half of the box's (z, y, x)
+// order, centre first), A(p, p+s) at node p; A(p, p-s) = A(p-s, p) is read at
+// node p-s.  Half the coefficient bytes of box_Au; the mirrored loads are the
+// neighbouring nodes' own entries.
+template <typename T, int DIM, int RHO, bool CHECK, typename LD>
+__device__ __forceinline__ auto box_Au_half(const Geo& g, const c_t<T>* __restrict__ P, const LD& ld, int p, int q,
+                                            int x, int y, int z) {
+  using V = decltype(ld(0));
+  V acc = pk_zero<V>();
+  constexpr int RZ = DIM == 3 ? RHO : 0;
+  constexpr int W = 2 * RHO + 1;
+  constexpr int C = ((2 * RZ + 1) * W * W - 1) / 2;             // box index of the centre
+#pragma unroll
+  for (int dz = -RZ; dz <= RZ; ++dz)
+#pragma unroll
+    for (int dy = -RHO; dy <= RHO; ++dy)
+#pragma unroll
+      for (int dx = -RHO; dx <= RHO; ++dx) {
+        const int s = ((dz + RZ) * W + (dy + RHO)) * W + (dx + RHO);
+        if (s < C) continue;
+        const int k = s - C;
+        const int fo = dx * g.R + dy * g.nxR + dz * g.sxyR;
+        const int no = dx + dy * g.nx + dz * g.sxy;
+        int qp = q + fo;
+        if (CHECK) {
+          // branch-free: an out-of-grid + neighbour has a zero stored entry (read at q)
+          const bool ok = x + dx >= 0 && x + dx < g.nx && y + dy >= 0 && y + dy < g.ny &&
+                          (DIM == 2 || (z + dz >= 0 && z + dz < g.nz));
+          qp = ok ? qp : q;
+        }
+        acc = cfma(P[k * g.N + p], ld(qp), acc);
+        if (s == C) continue;
+        if (CHECK) {
+          // the mirrored entry lives at node p - s: outside the grid the address
+          // is replaced by p and the coefficient by 0
+          const bool ok = x - dx >= 0 && x - dx < g.nx && y - dy >= 0 && y - dy < g.ny &&
+                          (DIM == 2 || (z - dz >= 0 && z - dz < g.nz));
+          c_t<T> cm = P[k * g.N + (ok ? p - no : p)];
+          cm = ok ? cm : cmk<c_t<T>>(0, 0);
+          acc = cfma(cm, ld(ok ? q - fo : q), acc);
+        } else {
+          acc = cfma(P[k * g.N + p - no], ld(q - fo), acc);
+        }
+      }
+  return acc;
+}
+
+// AK = 0: fine analytic operator; AK = rho > 0: stored box stencil;
+// AK = 10 + rho: symmetric box stencil stored as its half (box_Au_half).
 template <typename T, int DIM, int AK, bool CHECK, typename LD>
 __device__ __forceinline__ auto apply_A(const Geo& g, T invh2, const c_t<T>* __restrict__ A, const LD& ld, int p, int q,
                                         int x, int y, int z) {
   if constexpr (AK == 0)
     return fine_Au<T, DIM, CHECK>(g, invh2, A[p], ld, q, x, y, z);
+  else if constexpr (AK > 10)
+    return box_Au_half<T, DIM, AK - 10, CHECK>(g, A, ld, p, q, x, y, z);
   else
     return box_Au<T, DIM, AK, CHECK>(g, A, ld, p, q, x, y, z);
 }
@@ -350,7 +401,7 @@ __global__ void __launch_bounds__(BX* BY) k_resid(Geo g, T invh2, const c_t<T>* 
                                                   c_t<T>* __restrict__ r, const int* active) {
   pdl_enter();
   if (active && !*active) return;
-  constexpr int RA = AK == 0 ? 1 : AK;
+  constexpr int RA = AK == 0 ? 1 : AK % 10;
   const bool in = interior_block<DIM>(g, RA);
   int x, y, z, p, q;
   if (!node_xyz(g, x, y, z, p, q)) return;
@@ -400,7 +451,7 @@ __global__ void __launch_bounds__(BX* BY) k_sweep0_resid_diag(Geo g, T invh2, co
                                                               c_t<T>* __restrict__ r, const int* active) {
   pdl_enter();
   if (active && !*active) return;
-  constexpr int RA = AK == 0 ? 1 : AK;
+  constexpr int RA = AK == 0 ? 1 : AK % 10;
   const bool in = interior_block<DIM>(g, RA);
   int x, y, z, p, q;
   if (!node_xyz(g, x, y, z, p, q)) return;
@@ -453,7 +504,7 @@ __global__ void __launch_bounds__(BX* BY) k_resid_sweep_diag(Geo g, T invh2, con
                                                              c_t<T>* __restrict__ out, const int* active) {
   pdl_enter();
   if (active && !*active) return;
-  constexpr int RA = AK == 0 ? 1 : AK;
+  constexpr int RA = AK == 0 ? 1 : AK % 10;
   const bool inb = interior_block<DIM>(g, RA);
   int x, y, z, p, q;
   if (!node_xyz(g, x, y, z, p, q)) return;
@@ -598,7 +649,7 @@ __global__ void __launch_bounds__(BX* BY) k_prolong_fused_2d(Geo gf, Geo gc, T i
                                                              const int* active) {
   pdl_enter();
   if (active && !*active) return;
-  constexpr int RA = AK == 0 ? 1 : AK;
+  constexpr int RA = AK == 0 ? 1 : AK % 10;
   constexpr int TX = BX + 2 * RA, TY = BY + 2 * RA;
   __shared__ c_t<T> sm[TY][TX];
   const int x0 = blockIdx.x * BX - RA, y0 = blockIdx.y * BY - RA;
@@ -626,6 +677,22 @@ __global__ void __launch_bounds__(BX* BY) k_prolong_fused_2d(Geo gf, Geo gc, T i
     a = cmul(A[p], up);
     a.x -= invh2 * (wy * sx.x + wx * sy.x);
     a.y -= invh2 * (wy * sx.y + wx * sy.y);
+  } else if constexpr (AK > 10) {
+    // symmetric half (box_Au_half): the tile holds zeros outside the grid, and
+    // a mirrored entry whose node p - s is outside is read at p instead
+    a = cmk<c_t<T>>(0, 0);
+    constexpr int R0 = AK - 10, W = 2 * R0 + 1, C = (W * W - 1) / 2;
+#pragma unroll
+    for (int dy = -R0; dy <= R0; ++dy)
+#pragma unroll
+      for (int dx = -R0; dx <= R0; ++dx) {
+        const int s = (dy + R0) * W + (dx + R0);
+        if (s < C) continue;
+        a = cfma(A[(s - C) * gf.N + p], sm[ly + dy][lx + dx], a);
+        if (s == C) continue;
+        const bool ok = x - dx >= 0 && x - dx < gf.nx && y - dy >= 0 && y - dy < gf.ny;
+        a = cfma(A[(s - C) * gf.N + (ok ? p - dx - dy * gf.nx : p)], sm[ly - dy][lx - dx], a);
+      }
   } else {
     // coefficients reaching outside the grid are stored as zeros
     a = cmk<c_t<T>>(0, 0);
@@ -773,11 +840,12 @@ void with_dim_ak(int dim, int ak, F&& f) {
 #define HZ_DA(D, K) \
   if (dim == D && ak == K) return f(std::integral_constant<int, D>{}, std::integral_constant<int, K>{});
   HZ_DA(2, 0) HZ_DA(2, 1) HZ_DA(2, 2) HZ_DA(2, 3) HZ_DA(3, 0) HZ_DA(3, 1) HZ_DA(3, 2)
+  HZ_DA(2, 11) HZ_DA(2, 12) HZ_DA(3, 11)
 #undef HZ_DA
   throw Error(HZ_ERR_INVALID_ARG, "unsupported stencil radius");
 }
 
-inline int akind(const Level& L) { return L.fine ? 0 : L.A.off.rho; }
+inline int akind(const Level& L) { return L.fine ? 0 : (L.a_half ? 10 : 0) + L.A.off.rho; }
 
 // dimension and stored form of a level's smoother (symmetric half or M itself)
 template <typename F>
@@ -948,6 +1016,8 @@ void prolong_fused_2d(Ctx& c, int l, const void* ec, const void* t, const void* 
     case 1: kind(std::integral_constant<int, 1>{}); break;
     case 2: kind(std::integral_constant<int, 2>{}); break;
     case 3: kind(std::integral_constant<int, 3>{}); break;
+    case 11: kind(std::integral_constant<int, 11>{}); break;
+    case 12: kind(std::integral_constant<int, 12>{}); break;
     default: throw Error(HZ_ERR_INVALID_ARG, "unsupported stencil radius");
   }
   HZ_LAUNCHED();

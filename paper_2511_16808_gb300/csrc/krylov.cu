@@ -643,11 +643,11 @@ double vcycle_bytes(const Ctx& c) {
     // stored smoother planes: the diagonal, or the half / full planes (+ a real weight per node)
     const double sMst = L.m_diag ? 1.0 : L.Mh.off.n + (L.wcw ? 0.5 : 0.0);
     if (c.nrhs > 1) {
-      const double sA = L.fine ? 1.0 : L.A.off.n, sM = sMst;
+      const double sA = L.fine ? 1.0 : (L.a_half ? (L.A.off.n + 1) / 2 : L.A.off.n), sM = sMst;
       const double rc = L.g.dim == 3 ? 0.125 : 0.25;
       tot += N * b * R * (14 + 2 * rc) + N * b * 2 * (sA + sM);
     } else {
-      const double sA = L.fine ? 1.0 : L.A.off.n, sM = sMst;
+      const double sA = L.fine ? 1.0 : (L.a_half ? (L.A.off.n + 1) / 2 : L.A.off.n), sM = sMst;
       const double rc = L.g.dim == 3 ? 0.125 : 0.25;
       if (L.m_diag) tot += N * b * (5 + (1 + rc) + (5 + rc)) + (sA - 1) * 2 * N * b;   // sweep0+resid, restrict, prolong+sweep
       else tot += N * b * (2 * sM + 2 * sA + 13 + 2 * rc);

@@ -758,8 +758,19 @@ void build_hierarchy(Ctx& c, const double* kappa, const double* gamma, double ga
       if (L.m_diag) L.Mw = working_copy(c, L.M64, N, s);
       if (!L.a_sym) L.Mhw = working_copy(c, L.M64, N * (long long)L.M.off.n, s);
     }
-    // working operator: fine = diagonal of A_s (plane 0), coarse = all planes
-    L.Aw = working_copy(c, L.A64, L.fine ? N : N * L.A.off.n, s);
+    // working operator: fine = diagonal of A_s (plane 0), coarse = all planes;
+    // a symmetric full box of radius 1 or 2 (2D) / 1 (3D) keeps only the
+    // planes s >= 0, the second half of the box order (centre first)
+    const int rho = L.A.off.rho, W = 2 * rho + 1;
+    const int box = dim == 3 ? W * W * W : W * W;
+    L.a_half = !L.fine && !L.coarsest && L.a_sym && L.A.off.n == box &&
+               ((dim == 2 && (rho == 1 || rho == 2)) || (dim == 3 && rho == 1));
+    if (L.a_half) {
+      const int c0 = (box - 1) / 2;
+      L.Aw = working_copy(c, L.A64 + (long long)c0 * N, N * (long long)(box - c0), s);
+    } else {
+      L.Aw = working_copy(c, L.A64, L.fine ? N : N * L.A.off.n, s);
+    }
     L.u = ctx_alloc(c, vb * N * R);
     L.f = ctx_alloc(c, vb * N * R);
     L.r = ctx_alloc(c, vb * N * R);
