@@ -9,6 +9,10 @@
   kind), boundaries included.
 - Galerkin stencil widths as stated in Section 3.1 (3x3 linear; 5x5 then 7x7
   cubic; <= 5x5 mixed / level-dependent; <= 5x5x5 in 3D).
+- Galerkin values: interior rows of R A P for a constant complex 5-point
+  stencil equal the tensor formula built from numpy.convolve of the 1D taps of
+  the printed restriction stencils (linear, cubic, mixed), and for bilinear
+  transfers on the Laplacian the textbook (1/16h^2)[-1 -2 -1; -2 12 -2; -1 -2 -1].
 - The operator complexity of Table opcomplexity (golden fixture), computed
   from the sparsity of the Galerkin products of the compact 3D stencil on
   64^3 cells.
@@ -161,3 +165,57 @@ def test_operator_complexity_table():
                 assert 1.202 <= round(c, 3) <= 1.206
             else:
                 assert abs(c - gold[scheme][j]) <= 0.0006, (scheme, levels, c)
+
+
+# 1D prolongation taps about a coarse node: twice the 1D factor of the printed
+# restriction stencils (Eq. biliniearIntergrid: (1/4)(1, 2, 1) per axis;
+# Eq. bicubicIntergrid: (1/16)(1, 4, 6, 4, 1) per axis), since R = P^T / 2 per axis
+_TAPS = {"linear": 2 * np.array([1.0, 2.0, 1.0]) / 4,
+         "cubic": 2 * np.array([1.0, 4.0, 6.0, 4.0, 1.0]) / 16}
+
+
+def _galerkin_1d(a, rk, pk):
+    """Coarse 1D stencil of R a P with R = P_rk^T / 2 and P = P_pk: half the
+    convolution of the taps with the fine stencil, at even offsets."""
+    c = 0.5 * np.convolve(np.convolve(_TAPS[rk], a), _TAPS[pk])
+    mid = len(c) // 2
+    return c[mid % 2::2], mid // 2                  # values at even offsets, index of offset 0
+
+
+@pytest.mark.parametrize("rk,pk", [("linear", "linear"), ("cubic", "cubic"), ("linear", "cubic")])
+def test_galerkin_values_are_tap_convolutions(rk, pk):
+    """Interior rows of R A P for a constant 5-point stencil equal the tensor
+    formula c0 G(d) x G(d) + e (G(s) x G(d) + G(d) x G(s)) with the 1D
+    factors G from numpy.convolve of the interpolation taps (d = [1], s =
+    [1, 0, 1]); for bilinear transfers on the Laplacian this is the textbook
+    (1/16h^2) [-1 -2 -1; -2 12 -2; -1 -2 -1]."""
+    n = 65
+    h = 1.0 / (n - 1)
+    sigma = 900.0 * (1 - 0.05j)
+    st = operator.five_point_stencil(h, sigma, 2)
+    shape = (n, n)
+    A = operator.stencil_matrix(shape, st)
+    sc = transfer.coarse_shape(shape)
+    Ac = (transfer.restriction(sc, rk) @ A @ transfer.prolongation(sc, pk)).tocsr()
+    c0, e = st[(0, 0)], st[(1, 0)]
+    gd, md = _galerkin_1d(np.array([1.0]), rk, pk)
+    gs, ms = _galerkin_1d(np.array([1.0, 0.0, 1.0]), rk, pk)
+    # centre the two 1D factors on a common offset range
+    r = max(md, ms)
+    pad = lambda g, m: np.pad(g, (r - m, r - m))
+    gd, gs = pad(gd, md), pad(gs, ms)
+    expect = c0 * np.outer(gd, gd) + e * (np.outer(gd, gs) + np.outer(gs, gd))   # [dy, dx]
+    nc = sc[0]
+    for J in [(12, 12), (15, 17), (20, 9)]:
+        row = J[1] * nc + J[0]
+        for dy in range(-r, r + 1):
+            for dx in range(-r, r + 1):
+                got = Ac[row, (J[1] + dy) * nc + J[0] + dx]
+                assert abs(got - expect[dy + r, dx + r]) <= 1e-12 * abs(c0), (rk, pk, dx, dy, got)
+    if rk == pk == "linear":
+        lap = operator.five_point_stencil(h, 0.0, 2)
+        Al = (transfer.restriction(sc, rk) @ operator.stencil_matrix(shape, lap) @ transfer.prolongation(sc, pk))
+        row = 16 * nc + 16
+        block = np.array([[Al[row, (16 + dy) * nc + 16 + dx] for dx in (-1, 0, 1)] for dy in (-1, 0, 1)])
+        ref = np.array([[-1, -2, -1], [-2, 12, -2], [-1, -2, -1]]) / (16 * h * h)
+        assert np.allclose(block.real, ref, rtol=0, atol=1e-9 / h ** 2) and np.abs(block.imag).max() == 0
