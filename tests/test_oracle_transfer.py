@@ -219,3 +219,31 @@ def test_galerkin_values_are_tap_convolutions(rk, pk):
         block = np.array([[Al[row, (16 + dy) * nc + 16 + dx] for dx in (-1, 0, 1)] for dy in (-1, 0, 1)])
         ref = np.array([[-1, -2, -1], [-2, 12, -2], [-1, -2, -1]]) / (16 * h * h)
         assert np.allclose(block.real, ref, rtol=0, atol=1e-9 / h ** 2) and np.abs(block.imag).max() == 0
+
+
+@pytest.mark.parametrize("kind", ["linear", "cubic"])
+def test_galerkin_values_are_tap_convolutions_3d(kind):
+    """3D: interior rows of R A P for a constant complex 7-point stencil equal
+    c0 Gd x Gd x Gd + e (Gs x Gd x Gd + Gd x Gs x Gd + Gd x Gd x Gs)."""
+    n = 17
+    h = 1.0 / (n - 1)
+    st = operator.five_point_stencil(h, 300.0 * (1 - 0.05j), 3)
+    shape = (n, n, n)
+    A = operator.stencil_matrix(shape, st)
+    sc = transfer.coarse_shape(shape)
+    Ac = (transfer.restriction(sc, kind) @ A @ transfer.prolongation(sc, kind)).tocsr()
+    c0, e = st[(0, 0, 0)], st[(1, 0, 0)]
+    gd, md = _galerkin_1d(np.array([1.0]), kind, kind)
+    gs, ms = _galerkin_1d(np.array([1.0, 0.0, 1.0]), kind, kind)
+    r = max(md, ms)
+    gd, gs = np.pad(gd, (r - md, r - md)), np.pad(gs, (r - ms, r - ms))
+    o = lambda a, b, c: np.einsum("i,j,k->ijk", a, b, c)       # [dz, dy, dx]
+    expect = c0 * o(gd, gd, gd) + e * (o(gd, gd, gs) + o(gd, gs, gd) + o(gs, gd, gd))
+    nc = sc[0]
+    J = (4, 4, 4)
+    row = (J[2] * nc + J[1]) * nc + J[0]
+    for dz in range(-r, r + 1):
+        for dy in range(-r, r + 1):
+            for dx in range(-r, r + 1):
+                got = Ac[row, ((J[2] + dz) * nc + J[1] + dy) * nc + J[0] + dx]
+                assert abs(got - expect[dz + r, dy + r, dx + r]) <= 1e-12 * abs(c0), (dx, dy, dz, got)
