@@ -367,7 +367,9 @@ hz_status hz_setup_seconds(const hz_ctx* ctx, double* seconds);
  * formed at restarts) and the Arnoldi estimate.  A batched solve clears it.
  *   cap        capacity of the output arrays (host); entries beyond it are dropped
  *   iters, relres_true, relres_est   host arrays of cap values, each may be NULL
- *   n          out: entries recorded (may exceed cap) */
+ *   n          out: entries recorded (may exceed cap)
+ * Call it from the thread that drives the context, or when no solve is in
+ * flight on it (hz_solve_step appends to the history). */
 hz_status hz_solve_history(const hz_ctx* ctx, int cap, int* iters, double* relres_true, double* relres_est,
                            int* n);
 
