@@ -309,9 +309,26 @@ hz_status hz_kernel_launches(const hz_ctx* ctx, int64_t* count);
 hz_status hz_profile_select(hz_ctx* ctx, int kernel_class);
 hz_status hz_profile_read(const hz_ctx* ctx, double* total_ms, int64_t* launches, double* bytes, double* flops);
 
+/* Measured arithmetic peak of the current device, the denominator of the
+ * roofline fraction of the FP64 Krylov passes.  No counterpart in the paper:
+ * a measurement hook.  kind 0: FP64 fused multiply-add (DFMA); kind 1: FP32
+ * (FFMA).  Every thread of a whole number of waves (SMs x resident blocks of
+ * 256 threads) runs 8 independent multiply-add chains with no memory traffic;
+ * the best of five launches, timed with CUDA events after two warm-up
+ * launches, gives *tflops (2 flops per FMA) and *ms (that launch's time; may
+ * be NULL).  Allocates and frees a small device buffer on a private stream
+ * and synchronizes it.  HZ_ERR_INVALID_ARG for another kind or a NULL
+ * tflops; HZ_ERR_NO_DEVICE without a device. */
+hz_status hz_measure_peak(int kind, double* tflops, double* ms);
+
 /* ---- component entry points (one row of the method each) ---------------
  * Level fields are device arrays in the context's V-cycle precision (c128
  * for HZ_PREC_FP64, c64 for HZ_PREC_MIXED) of the level's node count. */
+
+/* The context's CUDA device ordinal, V-cycle precision (so the element type
+ * of level fields: c64 for HZ_PREC_MIXED, c128 for HZ_PREC_FP64) and the
+ * widest batch it was set up for; any output pointer may be NULL. */
+hz_status hz_context_info(const hz_ctx* ctx, int* device, int* precision, int* nrhs_max);
 
 hz_status hz_level_count(const hz_ctx* ctx, int* levels);
 hz_status hz_level_describe(const hz_ctx* ctx, int level, hz_level_desc* out);

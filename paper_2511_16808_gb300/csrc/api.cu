@@ -180,6 +180,25 @@ double default_damping(int dim, hz_patch p, int level) {
   return d3[col][r];
 }
 
+// Makes `dev` current for the life of a scope and restores the caller's
+// device on every exit path (exceptions included).
+struct DeviceGuard {
+  int prev = -1;
+  bool switched = false;
+  explicit DeviceGuard(int dev) {
+    HZ_CUDA(cudaGetDevice(&prev));
+    if (prev != dev) {
+      HZ_CUDA(cudaSetDevice(dev));
+      switched = true;
+    }
+  }
+  ~DeviceGuard() {
+    if (switched) cudaSetDevice(prev);
+  }
+  DeviceGuard(const DeviceGuard&) = delete;
+  DeviceGuard& operator=(const DeviceGuard&) = delete;
+};
+
 // Device address of g_noalloc_scratch on `dev`.  Host code only sees a
 // host-side stand-in under the array's name, so the address is looked up once
 // per device, with that device current, and cached.
@@ -189,12 +208,12 @@ void* noalloc_scratch(int dev) {
   require(dev >= 0 && dev < 256, "device ordinal out of range");
   std::lock_guard<std::mutex> lock(mu);
   if (!addr[dev]) {
-    int prev = -1;
-    HZ_CUDA(cudaGetDevice(&prev));
-    if (prev != dev) HZ_CUDA(cudaSetDevice(dev));
     void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (prev != dev) cudaSetDevice(prev);
+    cudaError_t e;
+    {
+      DeviceGuard dg(dev);
+      e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    }
     if (e != cudaSuccess || p == nullptr) {
       (void)cudaGetLastError();
       throw Error(HZ_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
@@ -454,6 +473,15 @@ hz_status hz_profile_read(const hz_ctx* ctx, double* total_ms, int64_t* launches
   });
 }
 
+hz_status hz_context_info(const hz_ctx* ctx, int* device, int* precision, int* nrhs_max) {
+  return guarded([&] {
+    require(ctx != nullptr, "null context");
+    if (device) *device = ctx->c.dev;
+    if (precision) *precision = ctx->c.mixed ? HZ_PREC_MIXED : HZ_PREC_FP64;
+    if (nrhs_max) *nrhs_max = ctx->c.opts.nrhs_max;
+  });
+}
+
 hz_status hz_level_count(const hz_ctx* ctx, int* levels) {
   return guarded([&] {
     require(ctx && levels, "null argument");
@@ -539,13 +567,10 @@ hz_status hz_level_smooth_noalloc(hz_ctx* ctx, int level, void* u, const void* f
     void* r = noalloc_scratch(c.dev);
     c.nrhs = 1;
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    int prev = -1;
-    HZ_CUDA(cudaGetDevice(&prev));
-    if (prev != c.dev) HZ_CUDA(cudaSetDevice(c.dev));
+    DeviceGuard dg(c.dev);
     // every scratch entry is written by the residual before it is read: no clearing needed
     level_residual(c, level, u, f, r, nullptr, s);
     level_vanka_apply(c, level, r, u, s);
-    if (prev != c.dev) HZ_CUDA(cudaSetDevice(prev));
   });
 }
 
@@ -589,6 +614,7 @@ hz_status hz_solve_history(const hz_ctx* ctx, int cap, int* iters, double* relre
                            int* n) {
   return guarded([&] {
     require(ctx && n && cap >= 0, "null argument or negative capacity");
+    std::lock_guard<std::mutex> lk(const_cast<hz_ctx*>(ctx)->c.history_mu);
     const auto& hst = ctx->c.history;
     *n = (int)hst.size();
     for (int i = 0; i < cap && i < (int)hst.size(); ++i) {

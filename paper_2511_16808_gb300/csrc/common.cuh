@@ -28,6 +28,7 @@
 #include <cstdio>
 #include <stdexcept>
 #include <string>
+#include <mutex>
 #include <vector>
 
 #include "hz.h"
@@ -399,6 +400,7 @@ struct Ctx {
   // per status read of the last single-RHS solve (start, then every restart
   // cycle): iterations so far, true relative residual, Arnoldi estimate
   std::vector<std::array<double, 3>> history;
+  std::mutex history_mu;        // hz_solve_history may read while a solve appends
   double omega = 0, alpha = 0, h = 0;
   int dev = 0;
   bool mixed = true;

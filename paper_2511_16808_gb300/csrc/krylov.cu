@@ -487,7 +487,10 @@ void solve_begin_t(Ctx& c, const double2* q, cudaStream_t user) {
   c.launches += 2;
   HZ_CUDA(cudaMemcpyAsync(hs, &st->st, sizeof(KrylovStatus), cudaMemcpyDeviceToHost, s));
   HZ_CUDA(cudaEventRecord(c.ev_status, s));
-  c.history.clear();
+  {
+    std::lock_guard<std::mutex> lk(c.history_mu);
+    c.history.clear();
+  }
   c.as_before = 0;
   c.as_replayed = false;
   c.as_state = 1;
@@ -506,7 +509,10 @@ int solve_step(Ctx& c, bool block) {
   }
   KrylovStatus* hs = (KrylovStatus*)c.ks_host;
   if (c.as_replayed && c.prof_class) prof_collect(c, hs->iters - c.as_before, nullptr, 1);
-  c.history.push_back({(double)hs->iters, hs->relres_true, hs->relres_est});
+  {
+    std::lock_guard<std::mutex> lk(c.history_mu);
+    c.history.push_back({(double)hs->iters, hs->relres_true, hs->relres_est});
+  }
   if (hs->done) {
     c.as_state = 2;
     return 1;

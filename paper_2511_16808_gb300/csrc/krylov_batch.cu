@@ -489,7 +489,10 @@ void solve_b(Ctx& c, const double2* q, double2* p, int R, hz_info* info, cudaStr
 
 void fgmres_solve_batch(Ctx& c, const double2* q, double2* p, int nrhs, hz_info* info, cudaStream_t s) {
   NvtxRange range("hz batched solve");
-  c.history.clear();
+  {
+    std::lock_guard<std::mutex> lk(c.history_mu);
+    c.history.clear();
+  }
   if (c.mixed) solve_b<float2>(c, q, p, nrhs, info, s);
   else solve_b<double2>(c, q, p, nrhs, info, s);
 }

@@ -1,0 +1,87 @@
+// Measured arithmetic peak of the current device: the denominator of the
+// roofline fraction reported for the FP64 Krylov passes (and, for reference,
+// the FP32 rate that the V-cycle arithmetic runs at).  A measurement hook;
+// the paper has no counterpart.
+//
+// Every thread runs CH independent multiply-add chains a = a*b + c for ITER
+// steps (no loads or stores in the loop), so the only limit is the issue rate
+// of the FMA pipe of that precision.  The grid is a whole number of waves:
+// blocks = SMs x the resident blocks per SM.  Timed with CUDA events on a
+// stream of its own, best of several launches.
+#include "common.cuh"
+
+namespace hz {
+namespace {
+
+constexpr int kCh = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_fma_chains(int iters, T b, T c, T* out) {
+  T a[kCh];
+#pragma unroll
+  for (int k = 0; k < kCh; ++k) a[k] = (T)(threadIdx.x + k) * (T)1e-3;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < kCh; ++k) a[k] = fma(a[k], b, c);
+  }
+  T s = 0;
+#pragma unroll
+  for (int k = 0; k < kCh; ++k) s += a[k];
+  // never true for the inputs used (|a| stays below 1e3); keeps the chains live
+  if (s == (T)-12345.0) out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+template <typename T>
+double measure(int iters, int repeats, double* best_ms) {
+  int dev = 0, sms = 0, per_sm = 0;
+  HZ_CUDA(cudaGetDevice(&dev));
+  HZ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  HZ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fma_chains<T>, 256, 0));
+  const int blocks = sms * std::max(per_sm, 1);
+  cudaStream_t s;
+  HZ_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  cudaEvent_t e0, e1;
+  HZ_CUDA(cudaEventCreate(&e0));
+  HZ_CUDA(cudaEventCreate(&e1));
+  T* out = nullptr;   // written only if the chains ever hit the sentinel
+  HZ_CUDA(cudaMallocAsync((void**)&out, sizeof(T) * blocks * 256, s));
+  const T b = (T)0.999999, c = (T)1e-4;      // a converges to c / (1 - b) = 100
+  float best = 1e30f;
+  for (int r = 0; r < repeats + 2; ++r) {     // the first two launches warm up
+    HZ_CUDA(cudaEventRecord(e0, s));
+    k_fma_chains<T><<<blocks, 256, 0, s>>>(iters, b, c, out);
+    HZ_CUDA(cudaGetLastError());
+    HZ_CUDA(cudaEventRecord(e1, s));
+    HZ_CUDA(cudaEventSynchronize(e1));
+    float ms = 0;
+    HZ_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (r >= 2) best = std::min(best, ms);
+  }
+  HZ_CUDA(cudaFreeAsync(out, s));
+  HZ_CUDA(cudaStreamSynchronize(s));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamDestroy(s);
+  *best_ms = best;
+  const double flops = 2.0 * kCh * (double)iters * blocks * 256.0;
+  return flops / (best / 1e3) / 1e12;
+}
+
+}  // namespace
+}  // namespace hz
+
+using namespace hz;
+
+extern "C" hz_status hz_measure_peak(int kind, double* tflops, double* ms) {
+  return guarded([&] {
+    require(tflops != nullptr, "null output");
+    require(kind == 0 || kind == 1, "kind must be 0 (FP64) or 1 (FP32)");
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) throw Error(HZ_ERR_NO_DEVICE, "no CUDA device");
+    double t = 0;
+    // about 10-20 ms per launch at the expected rates
+    const double r = kind == 0 ? measure<double>(1024, 5, &t) : measure<float>(32768, 5, &t);
+    *tflops = r;
+    if (ms) *ms = t;
+  });
+}

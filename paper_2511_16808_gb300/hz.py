@@ -111,6 +111,8 @@ _SIGS = {
     "hz_profile_select": ([_P, C.c_int], C.c_int),
     "hz_profile_read": ([_P, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_double),
                          C.POINTER(C.c_double)], C.c_int),
+    "hz_measure_peak": ([C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)], C.c_int),
+    "hz_context_info": ([_P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
     "hz_level_count": ([_P, C.POINTER(C.c_int)], C.c_int),
     "hz_level_describe": ([_P, C.c_int, C.POINTER(hz_level_desc)], C.c_int),
     "hz_level_export": ([_P, C.c_int, C.c_int, _P], C.c_int),
@@ -284,6 +286,14 @@ def hz_kernel_launches(ctx) -> int:
     return out.value
 
 
+def hz_measure_peak(kind: str = "fp64"):
+    """(TFLOP/s, ms of the best launch) of the device's FP64 (kind 'fp64') or
+    FP32 ('fp32') fused multiply-add pipe, measured by a chain kernel."""
+    t, ms = C.c_double(), C.c_double()
+    _check(lib.hz_measure_peak({"fp64": 0, "fp32": 1}.get(kind, kind), C.byref(t), C.byref(ms)), "hz_measure_peak")
+    return t.value, ms.value
+
+
 # 1: Gram-Schmidt update pass(es); 2: the pass with the FP64 operator and the
 # inner products; 3: the whole V-cycle
 PROFILE = {"none": 0, "gs_update": 1, "gs_apply": 2, "vcycle": 3}
@@ -327,29 +337,65 @@ def hz_level_export(ctx, level: int, what: int) -> np.ndarray:
     return out
 
 
+def hz_context_info(ctx) -> dict:
+    """{"device", "precision" ('mixed' | 'fp64'), "nrhs_max"} of a context."""
+    dev, prec, nr = C.c_int(), C.c_int(), C.c_int()
+    _check(lib.hz_context_info(ctx, C.byref(dev), C.byref(prec), C.byref(nr)), "hz_context_info")
+    return {"device": dev.value, "precision": {v: k for k, v in PRECISION.items()}[prec.value],
+            "nrhs_max": nr.value}
+
+
+def _level_fields(ctx, where, **fields):
+    """Reject level fields the library would read or write out of bounds: each
+    must be a contiguous CUDA tensor on the context's device, of the V-cycle
+    element type (complex64 mixed / complex128 fp64) and exactly the node count
+    of its level.  fields: name -> (tensor, level)."""
+    info = hz_context_info(ctx)
+    want = "torch.complex64" if info["precision"] == "mixed" else "torch.complex128"
+    for name, (t, lv) in fields.items():
+        if not (hasattr(t, "is_cuda") and t.is_cuda):
+            raise ValueError(f"{where}: {name} must be a CUDA tensor")
+        if t.device.index != info["device"]:
+            raise ValueError(f"{where}: {name} is on cuda:{t.device.index}, the context on cuda:{info['device']}")
+        if str(t.dtype) != want:
+            raise ValueError(f"{where}: {name} has dtype {t.dtype}, the context's V-cycle needs {want}")
+        nodes = hz_level_describe(ctx, lv)["nodes"]
+        if t.numel() != nodes:
+            raise ValueError(f"{where}: {name} has {t.numel()} values, level {lv} has {nodes} nodes")
+        if not t.is_contiguous():
+            raise ValueError(f"{where}: {name} must be contiguous")
+
+
 def hz_level_residual(ctx, level, u, f, r, stream=None):
+    _level_fields(ctx, "hz_level_residual", u=(u, level), f=(f, level), r=(r, level))
     _check(lib.hz_level_residual(ctx, level, _ptr(u), _ptr(f), _ptr(r), _stream(stream)), "hz_level_residual")
 
 
 def hz_level_smooth(ctx, level, u, f, stream=None):
+    _level_fields(ctx, "hz_level_smooth", u=(u, level), f=(f, level))
     _check(lib.hz_level_smooth(ctx, level, _ptr(u), _ptr(f), _stream(stream)), "hz_level_smooth")
 
 
 def hz_level_smooth_noalloc(ctx, level, u, f, stream=None):
     """hz_level_smooth without any device allocation (scratch in static device memory)."""
+    _level_fields(ctx, "hz_level_smooth_noalloc", u=(u, level), f=(f, level))
     _check(lib.hz_level_smooth_noalloc(ctx, level, _ptr(u), _ptr(f), _stream(stream)),
            "hz_level_smooth_noalloc")
 
 
 def hz_level_restrict(ctx, level, r, fc, stream=None):
+    _level_fields(ctx, "hz_level_restrict", r=(r, level), fc=(fc, level + 1))
     _check(lib.hz_level_restrict(ctx, level, _ptr(r), _ptr(fc), _stream(stream)), "hz_level_restrict")
 
 
 def hz_level_prolong_add(ctx, level, ec, u, stream=None):
+    _level_fields(ctx, "hz_level_prolong_add", ec=(ec, level + 1), u=(u, level))
     _check(lib.hz_level_prolong_add(ctx, level, _ptr(ec), _ptr(u), _stream(stream)), "hz_level_prolong_add")
 
 
 def hz_coarse_solve(ctx, f, u, stream=None):
+    last = hz_level_count(ctx) - 1
+    _level_fields(ctx, "hz_coarse_solve", f=(f, last), u=(u, last))
     _check(lib.hz_coarse_solve(ctx, _ptr(f), _ptr(u), _stream(stream)), "hz_coarse_solve")
 
 

@@ -75,3 +75,19 @@ def test_server_log():
         assert r["iters"] == d["iters"] and r["status"] == "HZ_OK"
         assert r["queue_s"] >= 0 and r["setup_s"] >= 0 and r["solve_s"] >= 0
         assert abs(r["queue_s"] + r["setup_s"] + r["solve_s"] - r["latency_s"]) < 1e-9
+
+
+def test_measured_arithmetic_peaks_are_plausible():
+    """The chain kernel's FP64 and FP32 rates: positive, FP64 at most the
+    nominal figure of 152 SMs x 2 DFMA lanes x 2 flops x 2.07 GHz (5% margin
+    for clock reporting), and FP32 far above FP64 on this part."""
+    from paper_2511_16808_gb300 import hz
+    t64, ms64 = hz.hz_measure_peak("fp64")
+    t32, ms32 = hz.hz_measure_peak("fp32")
+    assert ms64 > 0 and ms32 > 0
+    props = torch.cuda.get_device_properties(0)
+    nominal64 = props.multi_processor_count * 2 * 2 * 2.07e9 / 1e12
+    assert 0.2 * nominal64 < t64 < 1.05 * nominal64, (t64, nominal64)
+    assert t32 > 8 * t64, (t32, t64)
+    with pytest.raises(hz.HzError):
+        hz.hz_measure_peak(7)
