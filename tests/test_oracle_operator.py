@@ -134,3 +134,77 @@ def test_shift_sign_reading():
     _, bad = solver.Problem(alpha=-0.25, **kw).solve(q, tol=1e-7, max_iter=200)
     assert good.converged and good.iters < 80
     assert not bad.converged or bad.iters > 2 * good.iters
+
+
+# ---- compact 4th-order stencils (Eqs. disc4thCompact, disc4thCompact3D) ----
+# Both are "Mehrstellen" discretisations: applied to a smooth u they give
+#   (L - sigma M) u = (I + h^2/12 Lap_h)(-Lap u - sigma u) + O(h^4),
+# with Lap_h the textbook 5-/7-point Laplacian, i.e. M = I + h^2/12 Lap_h and
+# L u = -Lap u - (h^2/12) Lap^2 u + O(h^4).  The stencils are even, so the
+# O(h^4) remainder holds only 6th derivatives: on polynomials of degree <= 5
+# the identity is exact (up to rounding).  The right side is built from the
+# analytic Laplacian and the textbook 2nd-order stencil only, so a wrong
+# centre, face, edge or mass weight of the printed stencils fails it.
+
+def _rand_poly(dim, deg, rng):
+    """{exponent tuple: coefficient} of a random polynomial of total degree <= deg."""
+    import itertools
+    return {e: rng.standard_normal() for e in itertools.product(range(deg + 1), repeat=dim) if sum(e) <= deg}
+
+
+def _poly_eval(p, x):
+    return sum(c * np.prod([xi ** ei for xi, ei in zip(x, e)]) for e, c in p.items())
+
+
+def _poly_lap(p):
+    """Analytic Laplacian of the polynomial."""
+    out = {}
+    for e, c in p.items():
+        for a in range(len(e)):
+            if e[a] >= 2:
+                f = list(e)
+                f[a] -= 2
+                out[tuple(f)] = out.get(tuple(f), 0.0) + c * e[a] * (e[a] - 1)
+    return out
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_compact_stencils_fourth_order_identity(dim):
+    rng = np.random.default_rng(11 + dim)
+    for trial in range(4):
+        h = [0.1, 0.05, 0.2, 0.125][trial]
+        sigma = complex(rng.uniform(5, 50), rng.uniform(-1, 0))
+        st = operator.compact9_stencil(h, sigma) if dim == 2 else operator.compact19_stencil(h, sigma)
+        p = _rand_poly(dim, 5, rng)
+        x0 = rng.uniform(-1, 1, dim)
+        lhs = sum(v * _poly_eval(p, x0 + h * np.asarray(off, float)) for off, v in st.items())
+        lap = _poly_lap(p)
+        g = lambda x: -_poly_eval(lap, x) - sigma * _poly_eval(p, x)       # -Lap u - sigma u
+        lap_h = sum(g(x0 + h * np.eye(dim)[a] * s) for a in range(dim) for s in (-1, 1)) - 2 * dim * g(x0)
+        rhs = g(x0) + lap_h / 12.0                                            # h^2/12 Lap_h g, Lap_h = (...)/h^2
+        scale = max(abs(lhs), abs(g(x0)), 1.0)
+        assert abs(lhs - rhs) <= 1e-9 * scale * (1 + abs(sigma)), (dim, trial, lhs, rhs)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_compact_stencils_not_fourth_order_on_degree_six(dim):
+    """The same identity fails on x^6 (a 6th-derivative term remains), so the
+    test above is not vacuous."""
+    h, sigma = 0.1, 0.0
+    st = operator.compact9_stencil(h, sigma) if dim == 2 else operator.compact19_stencil(h, sigma)
+    p = {tuple([6] + [0] * (dim - 1)): 1.0}
+    x0 = np.zeros(dim)
+    lhs = sum(v * _poly_eval(p, x0 + h * np.asarray(off, float)) for off, v in st.items())
+    lap = _poly_lap(p)
+    g = lambda x: -_poly_eval(lap, x)
+    lap_h = sum(g(x0 + h * np.eye(dim)[a] * s) for a in range(dim) for s in (-1, 1)) - 2 * dim * g(x0)
+    assert abs(lhs - (g(x0) + lap_h / 12.0)) > 1e-3 * h ** 4
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_compact_stencils_row_sums(dim):
+    """L annihilates constants and M sums to one (the mass of a node)."""
+    st0 = operator.compact9_stencil(0.1, 0.0) if dim == 2 else operator.compact19_stencil(0.1, 0.0)
+    st1 = operator.compact9_stencil(0.1, 1.0) if dim == 2 else operator.compact19_stencil(0.1, 1.0)
+    assert abs(sum(st0.values())) < 1e-10
+    assert abs(sum(st0.values()) - sum(st1.values()) - 1.0) < 1e-12
