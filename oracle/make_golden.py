@@ -3,8 +3,10 @@
 Runs the FP64 oracle (and nothing else) on a workload from `workloads` and
 stores, in tests/golden/oracle_<name>.json: the FGMRES iteration count and
 true relative residual at the workload's tolerance, the oracle's seconds per
-iteration on this host, and the solution of a tighter solve (tol 1e-10) at
-seeded sampled nodes, so that the full-size CUDA result can be checked one
+iteration on this host, and at seeded sampled nodes both the solution at the
+workload's tolerance (the result a GPU solve of the same algorithm must
+reproduce) and the solution of a tighter solve (tol 1e-10, close to the exact
+discrete solution), so that the full-size CUDA result can be checked one
 sampled output at a time.  For the multi-source, multi-frequency workload
 (config4) the same is stored per frequency for the first BATCH_SOURCES
 sources.  Usage: python -m oracle.make_golden config2 config4
@@ -65,6 +67,7 @@ def run(name: str, out_dir: str = os.path.join(ROOT, "tests", "golden")) -> dict
         "err_at_tol": float(np.linalg.norm(p - p_ref) / np.linalg.norm(p_ref)),
         "sample_idx": idx.tolist(),
         "p_ref_re": p_ref[idx].real.tolist(), "p_ref_im": p_ref[idx].imag.tolist(),
+        "p_tol_re": p[idx].real.tolist(), "p_tol_im": p[idx].imag.tolist(),
     }
     path = os.path.join(out_dir, f"oracle_{name}.json")
     with open(path, "w") as f:
@@ -90,7 +93,8 @@ def run_batch(name: str, out_dir: str = os.path.join(ROOT, "tests", "golden")) -
                         "relres_true": info.relres_true, "iters_tight": info_ref.iters,
                         "s_per_iter": t_solve / max(info.iters, 1),
                         "err_at_tol": float(np.linalg.norm(p - p_ref) / np.linalg.norm(p_ref)),
-                        "p_ref_re": p_ref[idx].real.tolist(), "p_ref_im": p_ref[idx].imag.tolist()})
+                        "p_ref_re": p_ref[idx].real.tolist(), "p_ref_im": p_ref[idx].imag.tolist(),
+                        "p_tol_re": p[idx].real.tolist(), "p_tol_im": p[idx].imag.tolist()})
         freqs.append({"workload": w.name, "omega": w.omega, "ppw": w.meta["ppw"], "sources": per})
     rec = {"workload": name, "nodes": ws[0].nodes, "levels": ws[0].levels, "alpha": ws[0].alpha,
            "patch": ws[0].patch, "intergrid": ws[0].intergrid, "tol": ws[0].tol,

@@ -62,3 +62,26 @@ def rel_err(a, b):
     a = np.asarray(a)
     b = np.asarray(b)
     return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+# Solution agreement with the oracle (relative L2): the GPU solution must match
+# the oracle's solution of the same problem at the same tolerance within these
+# bounds; the error against an oracle solve to 1e-10 (about the exact discrete
+# solution) is reported beside it.
+AGREE = {"fp64": 1e-6, "mixed": 1e-5}
+
+
+def l2_rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def check_agreement(p, p_tol, p_ref, precision, label=""):
+    """Assert |p - p_tol| / |p_tol| <= AGREE[precision], p_tol the oracle's
+    solution at the same tolerance; returns (error vs p_tol, error vs p_ref).
+    The tight-solve error is a second, reported number: it may exceed the bound
+    by the oracle's own error at the tolerance."""
+    e_tol = l2_rel(p, p_tol)
+    e_ref = l2_rel(p, p_ref) if p_ref is not None else float("nan")
+    print(f"agreement {label} {precision}: vs oracle at tol {e_tol:.3e}, vs tight oracle {e_ref:.3e}")
+    assert e_tol <= AGREE[precision], (label, precision, e_tol, e_ref)
+    return e_tol, e_ref

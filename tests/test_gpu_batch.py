@@ -19,7 +19,7 @@ import pytest
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-from pairs import medium, rel_err  # noqa: E402
+from pairs import check_agreement, medium, rel_err  # noqa: E402
 
 CASES = [
     dict(dim=2, n=65, levels=3, patch="rb", scheme="leveldep", layer=8),
@@ -94,9 +94,9 @@ def test_batched_vcycle_mixed_matches_single(case):
     gpu.close()
 
 
-@pytest.mark.parametrize("precision,err_tol", [("fp64", 1e-6), ("mixed", 1e-5)])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("case", CASES[:3], ids=_ids(CASES[:3]))
-def test_batched_solve(case, precision, err_tol):
+def test_batched_solve(case, precision):
     R = 4
     orc, gpu = _pair(case, precision, R)
     Q = _sources(case, R, 3)
@@ -113,9 +113,7 @@ def test_batched_solve(case, precision, err_tol):
         assert abs(infos[r].iters - info_o.iters) <= 1, (r, infos[r].iters, info_o.iters)
         qh = orc.rhs(q)
         assert np.linalg.norm(qh - orc.A @ P[:, r]) / np.linalg.norm(qh) < tol
-        err = np.linalg.norm(P[:, r] - p_ref) / np.linalg.norm(p_ref)
-        err_o = np.linalg.norm(p_o - p_ref) / np.linalg.norm(p_ref)
-        assert err < max(err_tol, 2 * err_o), (r, err, err_o)
+        check_agreement(P[:, r], p_o, p_ref, precision, f"rhs {r}")
     gpu.close()
 
 
@@ -157,8 +155,9 @@ def test_batched_nrhs_rejected():
 @pytest.mark.parametrize("case,R", [(CASES[1], 64), (CASES[3], 16)], ids=["2d-n33-R64", "3d-n9-R16"])
 def test_batched_solve_wide(case, R):
     """The widest batches (RHS packs of 4 complex floats, tiled coarsest GEMM)
-    on small grids with ragged tiles: every column converges to the oracle's
-    tight solution and takes the single-RHS iteration count +-1."""
+    on small grids with ragged tiles: every sampled column agrees with the
+    oracle's solution at the same tolerance and takes the single-RHS iteration
+    count +-1."""
     orc, gpu = _pair(case, "mixed", R)
     n, dim = case["n"], case["dim"]
     import workloads
@@ -174,6 +173,7 @@ def test_batched_solve_wide(case, R):
         q = Q[:, r].copy()
         p1, info1 = gpu.solve(torch.tensor(q, device="cuda"))
         assert infos[r].converged == 1 and abs(infos[r].iters - info1.iters) <= 1
+        p_o, _ = orc.solve(q, tol=1e-7)
         p_ref, _ = orc.solve(q, tol=1e-10)
-        assert np.linalg.norm(P[:, r] - p_ref) / np.linalg.norm(p_ref) < 1e-5
+        check_agreement(P[:, r], p_o, p_ref, "mixed", f"rhs {r}")
     gpu.close()
