@@ -1,23 +1,11 @@
 // Precision dispatch of the V-cycle pieces (kernels in cycle_impl.cuh,
-// instantiated by cycle_f32.cu and cycle_f64.cu).
-#include "cycle_impl.cuh"
+// instantiated by cycle_f32*.cu and cycle_f64*.cu).
+#include "cycle_inst.cuh"
 
 namespace hz {
 namespace cyc {
-extern template void resid<float>(Ctx&, int, const void*, const void*, void*, const int*, cudaStream_t);
-extern template void sweep_out<float>(Ctx&, int, const void*, const void*, void*, const int*, cudaStream_t);
-extern template void sweep0<float>(Ctx&, int, const void*, void*, const int*, cudaStream_t);
-extern template void restrict_t<float>(Ctx&, int, const void*, void*, const int*, cudaStream_t);
-extern template void prolong_t<float>(Ctx&, int, const void*, const void*, void*, const int*, cudaStream_t);
-extern template void coarse_t<float>(Ctx&, const void*, void*, const int*, cudaStream_t);
-extern template void vcycle_t<float>(Ctx&, int, const void*, void*, const int*, cudaStream_t);
-extern template void resid<double>(Ctx&, int, const void*, const void*, void*, const int*, cudaStream_t);
-extern template void sweep_out<double>(Ctx&, int, const void*, const void*, void*, const int*, cudaStream_t);
-extern template void sweep0<double>(Ctx&, int, const void*, void*, const int*, cudaStream_t);
-extern template void restrict_t<double>(Ctx&, int, const void*, void*, const int*, cudaStream_t);
-extern template void prolong_t<double>(Ctx&, int, const void*, const void*, void*, const int*, cudaStream_t);
-extern template void coarse_t<double>(Ctx&, const void*, void*, const int*, cudaStream_t);
-extern template void vcycle_t<double>(Ctx&, int, const void*, void*, const int*, cudaStream_t);
+HZ_CYC_ALL(extern, float)
+HZ_CYC_ALL(extern, double)
 }  // namespace cyc
 using namespace cyc;
 

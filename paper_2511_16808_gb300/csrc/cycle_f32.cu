@@ -1,16 +1,14 @@
-// Working-precision instantiation (float) of the V-cycle kernels and drivers
-// defined in cycle_impl.cuh; compiled as its own translation unit so the
-// single- and double-precision kernels build in parallel.
-#include "cycle_impl.cuh"
+// Working-precision instantiation (float) of the V-cycle itself (Algorithm 1,
+// recursive) and of the coarsest solve; the operator, smoother and transfer
+// drivers it calls are instantiated by cycle_f32_ops.cu, cycle_f32_smooth.cu
+// and cycle_f32_xfer.cu.
+#include "cycle_inst.cuh"
 
 namespace hz {
 namespace cyc {
-template void resid<float>(Ctx&, int, const void*, const void*, void*, const int*, cudaStream_t);
-template void sweep_out<float>(Ctx&, int, const void*, const void*, void*, const int*, cudaStream_t);
-template void sweep0<float>(Ctx&, int, const void*, void*, const int*, cudaStream_t);
-template void restrict_t<float>(Ctx&, int, const void*, void*, const int*, cudaStream_t);
-template void prolong_t<float>(Ctx&, int, const void*, const void*, void*, const int*, cudaStream_t);
-template void coarse_t<float>(Ctx&, const void*, void*, const int*, cudaStream_t);
-template void vcycle_t<float>(Ctx&, int, const void*, void*, const int*, cudaStream_t);
+HZ_CYC_OPS(extern, float)
+HZ_CYC_SMOOTH(extern, float)
+HZ_CYC_XFER(extern, float)
+HZ_CYC_TOP(, float)
 }  // namespace cyc
 }  // namespace hz

@@ -1,16 +1,14 @@
-// Working-precision instantiation (double) of the V-cycle kernels and drivers
-// defined in cycle_impl.cuh; compiled as its own translation unit so the
-// single- and double-precision kernels build in parallel.
-#include "cycle_impl.cuh"
+// Working-precision instantiation (double) of the V-cycle itself (Algorithm 1,
+// recursive) and of the coarsest solve; the operator, smoother and transfer
+// drivers it calls are instantiated by cycle_f64_ops.cu, cycle_f64_smooth.cu
+// and cycle_f64_xfer.cu.
+#include "cycle_inst.cuh"
 
 namespace hz {
 namespace cyc {
-template void resid<double>(Ctx&, int, const void*, const void*, void*, const int*, cudaStream_t);
-template void sweep_out<double>(Ctx&, int, const void*, const void*, void*, const int*, cudaStream_t);
-template void sweep0<double>(Ctx&, int, const void*, void*, const int*, cudaStream_t);
-template void restrict_t<double>(Ctx&, int, const void*, void*, const int*, cudaStream_t);
-template void prolong_t<double>(Ctx&, int, const void*, const void*, void*, const int*, cudaStream_t);
-template void coarse_t<double>(Ctx&, const void*, void*, const int*, cudaStream_t);
-template void vcycle_t<double>(Ctx&, int, const void*, void*, const int*, cudaStream_t);
+HZ_CYC_OPS(extern, double)
+HZ_CYC_SMOOTH(extern, double)
+HZ_CYC_XFER(extern, double)
+HZ_CYC_TOP(, double)
 }  // namespace cyc
 }  // namespace hz

@@ -395,8 +395,8 @@ __device__ __forceinline__ auto sym_Au(const Geo& g, const LST& m, const c_t<T>*
 // ------------------------------------------------------------------ kernels
 
 // r = f - A u
-template <typename T, int DIM, int AK, int VR>
-__global__ void __launch_bounds__(BX* BY) k_resid(Geo g, T invh2, const c_t<T>* __restrict__ A,
+template <typename T, int DIM, int AK, int VR, int MB>
+__global__ void __launch_bounds__(BX* BY, MB) k_resid(Geo g, T invh2, const c_t<T>* __restrict__ A,
                                                   const c_t<T>* __restrict__ u, const c_t<T>* __restrict__ f,
                                                   c_t<T>* __restrict__ r, const int* active) {
   pdl_enter();
@@ -412,8 +412,8 @@ __global__ void __launch_bounds__(BX* BY) k_resid(Geo g, T invh2, const c_t<T>* 
 }
 
 // u = w M f  (first sweep from u = 0)
-template <typename T, int DIM, int VR>
-__global__ void __launch_bounds__(BX* BY) k_sweep0(Geo g, MList m, const c_t<T>* __restrict__ M, T w,
+template <typename T, int DIM, int VR, int MB>
+__global__ void __launch_bounds__(BX* BY, MB) k_sweep0(Geo g, MList m, const c_t<T>* __restrict__ M, T w,
                                                    const c_t<T>* __restrict__ f, c_t<T>* __restrict__ u,
                                                    const int* active) {
   pdl_enter();
@@ -428,8 +428,8 @@ __global__ void __launch_bounds__(BX* BY) k_sweep0(Geo g, MList m, const c_t<T>*
 }
 
 // symmetric half form: u = w D^{-1} M' f
-template <typename T, int DIM, int VR>
-__global__ void __launch_bounds__(BX* BY) k_sweep0_sym(Geo g, SList m, const c_t<T>* __restrict__ M,
+template <typename T, int DIM, int VR, int MB>
+__global__ void __launch_bounds__(BX* BY, MB) k_sweep0_sym(Geo g, SList m, const c_t<T>* __restrict__ M,
                                                    const T* __restrict__ wc, T w, const c_t<T>* __restrict__ f,
                                                    c_t<T>* __restrict__ u, const int* active) {
   pdl_enter();
@@ -444,8 +444,8 @@ __global__ void __launch_bounds__(BX* BY) k_sweep0_sym(Geo g, SList m, const c_t
 }
 
 // diagonal M: u = w m0 f and r = f - A u in one pass
-template <typename T, int DIM, int AK, int VR>
-__global__ void __launch_bounds__(BX* BY) k_sweep0_resid_diag(Geo g, T invh2, const c_t<T>* __restrict__ A,
+template <typename T, int DIM, int AK, int VR, int MB>
+__global__ void __launch_bounds__(BX* BY, MB) k_sweep0_resid_diag(Geo g, T invh2, const c_t<T>* __restrict__ A,
                                                               const c_t<T>* __restrict__ m0, T w,
                                                               const c_t<T>* __restrict__ f, c_t<T>* __restrict__ u,
                                                               c_t<T>* __restrict__ r, const int* active) {
@@ -465,8 +465,8 @@ __global__ void __launch_bounds__(BX* BY) k_sweep0_resid_diag(Geo g, T invh2, co
 }
 
 // out = in + w M r  (out may alias in)
-template <typename T, int DIM, int VR>
-__global__ void __launch_bounds__(BX* BY) k_sweep_out(Geo g, MList m, const c_t<T>* __restrict__ M, T w,
+template <typename T, int DIM, int VR, int MB>
+__global__ void __launch_bounds__(BX* BY, MB) k_sweep_out(Geo g, MList m, const c_t<T>* __restrict__ M, T w,
                                                       const c_t<T>* __restrict__ r, const c_t<T>* in, c_t<T>* out,
                                                       const int* active) {
   pdl_enter();
@@ -481,8 +481,8 @@ __global__ void __launch_bounds__(BX* BY) k_sweep_out(Geo g, MList m, const c_t<
 }
 
 // symmetric half form: out = in + w D^{-1} M' r
-template <typename T, int DIM, int VR>
-__global__ void __launch_bounds__(BX* BY) k_sweep_out_sym(Geo g, SList m, const c_t<T>* __restrict__ M,
+template <typename T, int DIM, int VR, int MB>
+__global__ void __launch_bounds__(BX* BY, MB) k_sweep_out_sym(Geo g, SList m, const c_t<T>* __restrict__ M,
                                                       const T* __restrict__ wc, T w, const c_t<T>* __restrict__ r,
                                                       const c_t<T>* in, c_t<T>* out, const int* active) {
   pdl_enter();
@@ -497,8 +497,8 @@ __global__ void __launch_bounds__(BX* BY) k_sweep_out_sym(Geo g, SList m, const 
 }
 
 // diagonal M: out = in + w m0 (f - A in)   (out != in)
-template <typename T, int DIM, int AK, int VR>
-__global__ void __launch_bounds__(BX* BY) k_resid_sweep_diag(Geo g, T invh2, const c_t<T>* __restrict__ A,
+template <typename T, int DIM, int AK, int VR, int MB>
+__global__ void __launch_bounds__(BX* BY, MB) k_resid_sweep_diag(Geo g, T invh2, const c_t<T>* __restrict__ A,
                                                              const c_t<T>* __restrict__ m0, T w,
                                                              const c_t<T>* __restrict__ f, const c_t<T>* __restrict__ in,
                                                              c_t<T>* __restrict__ out, const int* active) {
@@ -528,8 +528,8 @@ __device__ __forceinline__ float p1f(int kind, int nf, int nc, int j, int J) {
 }
 
 // f_c = R r, one thread per coarse node (and RHS pack)
-template <typename T, int DIM, int KIND, int VR>
-__global__ void __launch_bounds__(BX* BY) k_restrict(Geo gf, Geo gc, const c_t<T>* __restrict__ r,
+template <typename T, int DIM, int KIND, int VR, int MB>
+__global__ void __launch_bounds__(BX* BY, MB) k_restrict(Geo gf, Geo gc, const c_t<T>* __restrict__ r,
                                                      c_t<T>* __restrict__ fc, const int* active) {
   pdl_enter();
   if (active && !*active) return;
@@ -628,8 +628,8 @@ __device__ __forceinline__ pk_t<T, VR> prolong_at(const Geo& gf, const Geo& gc, 
 }
 
 // out = in + P e_c (pointwise; out may alias in)
-template <typename T, int DIM, int KIND, int VR>
-__global__ void __launch_bounds__(BX* BY) k_prolong(Geo gf, Geo gc, const c_t<T>* __restrict__ ec, const c_t<T>* in,
+template <typename T, int DIM, int KIND, int VR, int MB>
+__global__ void __launch_bounds__(BX* BY, MB) k_prolong(Geo gf, Geo gc, const c_t<T>* __restrict__ ec, const c_t<T>* in,
                                                     c_t<T>* out, const int* active) {
   pdl_enter();
   if (active && !*active) return;
@@ -641,8 +641,8 @@ __global__ void __launch_bounds__(BX* BY) k_prolong(Geo gf, Geo gc, const c_t<T>
 // 2D: u' = t + P e_c on a tile with halo RA in shared memory, then
 //   DIAG = false: out = u', r = f - A u'
 //   DIAG = true : out = u' + w m0 (f - A u')
-template <typename T, int AK, int KIND, bool DIAG>
-__global__ void __launch_bounds__(BX* BY) k_prolong_fused_2d(Geo gf, Geo gc, T invh2, const c_t<T>* __restrict__ A,
+template <typename T, int AK, int KIND, bool DIAG, int MB>
+__global__ void __launch_bounds__(BX* BY, MB) k_prolong_fused_2d(Geo gf, Geo gc, T invh2, const c_t<T>* __restrict__ A,
                                                              const c_t<T>* __restrict__ ec, const c_t<T>* __restrict__ t,
                                                              const c_t<T>* __restrict__ f, const c_t<T>* __restrict__ m0,
                                                              T w, c_t<T>* __restrict__ out, c_t<T>* __restrict__ r,
@@ -867,15 +867,37 @@ void with_vr(int nrhs, F&& f) {
   else f(std::integral_constant<int, 1>{});
 }
 
+// Register budget of a launch (the MB template argument: minimum resident
+// blocks per SM in the launch bounds).  MB = 0 leaves ptxas its default
+// target of full occupancy (32 registers a thread), which suits the
+// bandwidth-bound large levels: many warps hide the latency.  On a small level
+// (one right-hand side, at most kIlpNodes nodes: a few blocks per SM at most)
+// occupancy cannot hide it, and with 32 registers the stencil loads go out in
+// small dependent batches (measured on a 65^2 level: ~9 us per launch in L2
+// round trips); MB = 2 allows up to 128 registers, so every coefficient and
+// neighbour load of a node is issued before the first use.
+constexpr long long kIlpNodes = 20000;
+template <typename T, typename F>
+void with_vr_mb(int nrhs, long long nodes, F&& f) {
+  with_vr<T>(nrhs, [&](auto V) {
+    constexpr int VR = decltype(V)::value;
+    if constexpr (VR == 1) {
+      if (nrhs == 1 && nodes <= kIlpNodes) return f(V, std::integral_constant<int, 2>{});
+    }
+    f(V, std::integral_constant<int, 0>{});
+  });
+}
+
 template <typename T>
 void resid(Ctx& c, int l, const void* u, const void* f, void* r, const int* active, cudaStream_t s) {
   Level& L = c.L[l];
   const T invh2 = (T)(1.0 / (c.h * c.h));
-  with_vr<T>(c.nrhs, [&](auto V) {
+  with_vr_mb<T>(c.nrhs, L.g.N, [&](auto V, auto MBc) {
     constexpr int VR = decltype(V)::value;
+    constexpr int MB = decltype(MBc)::value;
     const Geo g = geo(L.g, c.nrhs, VR);
     with_dim_ak(L.g.dim, akind(L), [&](auto D, auto K) {
-      launch_pdl(k_resid<T, D, K, VR>, grid_of(g), dim3(BX, BY), s, g, invh2, (const c_t<T>*)L.Aw, (const c_t<T>*)u,
+      launch_pdl(k_resid<T, D, K, VR, MB>, grid_of(g), dim3(BX, BY), s, g, invh2, (const c_t<T>*)L.Aw, (const c_t<T>*)u,
                                                                (const c_t<T>*)f, (c_t<T>*)r, active);
     });
   });
@@ -885,17 +907,18 @@ void resid(Ctx& c, int l, const void* u, const void* f, void* r, const int* acti
 template <typename T>
 void sweep_out(Ctx& c, int l, const void* r, const void* in, void* out, const int* active, cudaStream_t s) {
   Level& L = c.L[l];
-  with_vr<T>(c.nrhs, [&](auto V) {
+  with_vr_mb<T>(c.nrhs, L.g.N, [&](auto V, auto MBc) {
     constexpr int VR = decltype(V)::value;
+    constexpr int MB = decltype(MBc)::value;
     const Geo g = geo(L.g, c.nrhs, VR);
     auto go = [&](auto D, auto S) {
       constexpr int DIM = decltype(D)::value;
       if constexpr (decltype(S)::value)
-        launch_pdl(k_sweep_out_sym<T, DIM, VR>, grid_of(g), dim3(BX, BY), s, g, slist(L, c.nrhs),
+        launch_pdl(k_sweep_out_sym<T, DIM, VR, MB>, grid_of(g), dim3(BX, BY), s, g, slist(L, c.nrhs),
                    (const c_t<T>*)L.Mhw, (const T*)L.wcw, (T)L.damping, (const c_t<T>*)r, (const c_t<T>*)in,
                    (c_t<T>*)out, active);
       else
-        launch_pdl(k_sweep_out<T, DIM, VR>, grid_of(g), dim3(BX, BY), s, g, mlist(L, c.nrhs),
+        launch_pdl(k_sweep_out<T, DIM, VR, MB>, grid_of(g), dim3(BX, BY), s, g, mlist(L, c.nrhs),
                    (const c_t<T>*)L.Mhw, (T)L.damping, (const c_t<T>*)r, (const c_t<T>*)in, (c_t<T>*)out, active);
     };
     dispatch_dim_sym(L, go);
@@ -906,16 +929,17 @@ void sweep_out(Ctx& c, int l, const void* r, const void* in, void* out, const in
 template <typename T>
 void sweep0(Ctx& c, int l, const void* f, void* u, const int* active, cudaStream_t s) {
   Level& L = c.L[l];
-  with_vr<T>(c.nrhs, [&](auto V) {
+  with_vr_mb<T>(c.nrhs, L.g.N, [&](auto V, auto MBc) {
     constexpr int VR = decltype(V)::value;
+    constexpr int MB = decltype(MBc)::value;
     const Geo g = geo(L.g, c.nrhs, VR);
     auto go = [&](auto D, auto S) {
       constexpr int DIM = decltype(D)::value;
       if constexpr (decltype(S)::value)
-        launch_pdl(k_sweep0_sym<T, DIM, VR>, grid_of(g), dim3(BX, BY), s, g, slist(L, c.nrhs),
+        launch_pdl(k_sweep0_sym<T, DIM, VR, MB>, grid_of(g), dim3(BX, BY), s, g, slist(L, c.nrhs),
                    (const c_t<T>*)L.Mhw, (const T*)L.wcw, (T)L.damping, (const c_t<T>*)f, (c_t<T>*)u, active);
       else
-        launch_pdl(k_sweep0<T, DIM, VR>, grid_of(g), dim3(BX, BY), s, g, mlist(L, c.nrhs), (const c_t<T>*)L.Mhw,
+        launch_pdl(k_sweep0<T, DIM, VR, MB>, grid_of(g), dim3(BX, BY), s, g, mlist(L, c.nrhs), (const c_t<T>*)L.Mhw,
                    (T)L.damping, (const c_t<T>*)f, (c_t<T>*)u, active);
     };
     dispatch_dim_sym(L, go);
@@ -927,11 +951,12 @@ template <typename T>
 void sweep0_resid_diag(Ctx& c, int l, const void* f, void* u, void* r, const int* active, cudaStream_t s) {
   Level& L = c.L[l];
   const T invh2 = (T)(1.0 / (c.h * c.h));
-  with_vr<T>(c.nrhs, [&](auto V) {
+  with_vr_mb<T>(c.nrhs, L.g.N, [&](auto V, auto MBc) {
     constexpr int VR = decltype(V)::value;
+    constexpr int MB = decltype(MBc)::value;
     const Geo g = geo(L.g, c.nrhs, VR);
     with_dim_ak(L.g.dim, akind(L), [&](auto D, auto K) {
-      launch_pdl(k_sweep0_resid_diag<T, D, K, VR>, grid_of(g), dim3(BX, BY), s, g, invh2, (const c_t<T>*)L.Aw, (const c_t<T>*)L.Mw, (T)L.damping, (const c_t<T>*)f, (c_t<T>*)u,
+      launch_pdl(k_sweep0_resid_diag<T, D, K, VR, MB>, grid_of(g), dim3(BX, BY), s, g, invh2, (const c_t<T>*)L.Aw, (const c_t<T>*)L.Mw, (T)L.damping, (const c_t<T>*)f, (c_t<T>*)u,
           (c_t<T>*)r, active);
     });
   });
@@ -942,11 +967,12 @@ template <typename T>
 void resid_sweep_diag(Ctx& c, int l, const void* f, const void* in, void* out, const int* active, cudaStream_t s) {
   Level& L = c.L[l];
   const T invh2 = (T)(1.0 / (c.h * c.h));
-  with_vr<T>(c.nrhs, [&](auto V) {
+  with_vr_mb<T>(c.nrhs, L.g.N, [&](auto V, auto MBc) {
     constexpr int VR = decltype(V)::value;
+    constexpr int MB = decltype(MBc)::value;
     const Geo g = geo(L.g, c.nrhs, VR);
     with_dim_ak(L.g.dim, akind(L), [&](auto D, auto K) {
-      launch_pdl(k_resid_sweep_diag<T, D, K, VR>, grid_of(g), dim3(BX, BY), s, g, invh2, (const c_t<T>*)L.Aw, (const c_t<T>*)L.Mw, (T)L.damping, (const c_t<T>*)f, (const c_t<T>*)in,
+      launch_pdl(k_resid_sweep_diag<T, D, K, VR, MB>, grid_of(g), dim3(BX, BY), s, g, invh2, (const c_t<T>*)L.Aw, (const c_t<T>*)L.Mw, (T)L.damping, (const c_t<T>*)f, (const c_t<T>*)in,
           (c_t<T>*)out, active);
     });
   });
@@ -957,11 +983,12 @@ template <typename T>
 void restrict_t(Ctx& c, int l, const void* r, void* fc, const int* active, cudaStream_t s) {
   Level& L = c.L[l];
   Level& C = c.L[l + 1];
-  with_vr<T>(c.nrhs, [&](auto V) {
+  with_vr_mb<T>(c.nrhs, C.g.N, [&](auto V, auto MBc) {
     constexpr int VR = decltype(V)::value;
+    constexpr int MB = decltype(MBc)::value;
     const Geo gf = geo(L.g, c.nrhs, VR), gc = geo(C.g, c.nrhs, VR);
     auto go = [&](auto D, auto KIND) {
-      launch_pdl(k_restrict<T, D, KIND, VR>, grid_of(gc), dim3(BX, BY), s, gf, gc, (const c_t<T>*)r, (c_t<T>*)fc,
+      launch_pdl(k_restrict<T, D, KIND, VR, MB>, grid_of(gc), dim3(BX, BY), s, gf, gc, (const c_t<T>*)r, (c_t<T>*)fc,
                                                                       active);
     };
     using I2 = std::integral_constant<int, 2>;
@@ -978,11 +1005,12 @@ template <typename T>
 void prolong_t(Ctx& c, int l, const void* ec, const void* in, void* out, const int* active, cudaStream_t s) {
   Level& L = c.L[l];
   Level& C = c.L[l + 1];
-  with_vr<T>(c.nrhs, [&](auto V) {
+  with_vr_mb<T>(c.nrhs, L.g.N, [&](auto V, auto MBc) {
     constexpr int VR = decltype(V)::value;
+    constexpr int MB = decltype(MBc)::value;
     const Geo gf = geo(L.g, c.nrhs, VR), gc = geo(C.g, c.nrhs, VR);
     auto go = [&](auto D, auto KIND) {
-      launch_pdl(k_prolong<T, D, KIND, VR>, grid_of(gf), dim3(BX, BY), s, gf, gc, (const c_t<T>*)ec, (const c_t<T>*)in,
+      launch_pdl(k_prolong<T, D, KIND, VR, MB>, grid_of(gf), dim3(BX, BY), s, gf, gc, (const c_t<T>*)ec, (const c_t<T>*)in,
                                                                      (c_t<T>*)out, active);
     };
     using I2 = std::integral_constant<int, 2>;
@@ -1005,8 +1033,13 @@ void prolong_fused_2d(Ctx& c, int l, const void* ec, const void* t, const void* 
   const Geo gf = geo(L.g), gc = geo(C.g);
   const T invh2 = (T)(1.0 / (c.h * c.h));
   auto go = [&](auto K, auto KIND) {
-    launch_pdl(k_prolong_fused_2d<T, K, KIND, DIAG>, grid_of(gf), dim3(BX, BY), s, gf, gc, invh2, (const c_t<T>*)L.Aw, (const c_t<T>*)ec, (const c_t<T>*)t, (const c_t<T>*)f,
-        (const c_t<T>*)L.Mw, (T)L.damping, (c_t<T>*)out, (c_t<T>*)r, active);
+    auto launch = [&](auto MBc) {
+      launch_pdl(k_prolong_fused_2d<T, K, KIND, DIAG, decltype(MBc)::value>, grid_of(gf), dim3(BX, BY), s, gf, gc,
+                 invh2, (const c_t<T>*)L.Aw, (const c_t<T>*)ec, (const c_t<T>*)t, (const c_t<T>*)f,
+                 (const c_t<T>*)L.Mw, (T)L.damping, (c_t<T>*)out, (c_t<T>*)r, active);
+    };
+    if (L.g.N <= kIlpNodes) launch(std::integral_constant<int, 2>{});
+    else launch(std::integral_constant<int, 0>{});
   };
   using K0 = std::integral_constant<int, 0>;
   using K1 = std::integral_constant<int, 1>;
