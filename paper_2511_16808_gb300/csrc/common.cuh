@@ -444,6 +444,26 @@ struct Ctx {
   long long launches = 0;       // kernels launched by hz_solve on this context
 };
 
+// Whether a cycle from zero at level l runs the fine level as two fused
+// passes (cycle_impl.cuh k_fine_down_diag_*, k_fine_up_diag_*): level 0 with
+// a diagonal smoother, one pre- and one post-sweep, one right-hand side.
+inline bool fine_two_pass(const Ctx& c, int l) {
+  const Level& L = c.L[l];
+  return l == 0 && L.fine && !L.coarsest && L.m_diag && c.opts.nu1 == 1 && c.opts.nu2 == 1 && c.nrhs == 1 &&
+         L.g.dim == 2;
+}
+
+// Whether a cycle from zero at coarse 2D level l runs as two fused tile
+// passes (cycle_impl.cuh k_level_down_2d, k_level_up_2d): a small level
+// (where launch and memory latency, not bandwidth, set the time), a stored operator
+// of radius <= 3, a non-diagonal smoother of reach <= 2, one pre- and one
+// post-sweep, one right-hand side.
+inline bool level_two_pass_2d(const Ctx& c, int l) {
+  const Level& L = c.L[l];
+  return L.g.N <= 70000 && !L.fine && !L.coarsest && !L.m_diag && L.g.dim == 2 && c.opts.nu1 == 1 && c.opts.nu2 == 1 &&
+         c.nrhs == 1 && L.A.off.rho <= (L.a_half ? 2 : 3) && L.Mh.off.rho <= 2;
+}
+
 // allocation helpers (all device memory of a context goes through these)
 void* ctx_alloc(Ctx& c, size_t bytes);          // stream-ordered, on c.alloc_stream
 void* ctx_alloc(Ctx& c, size_t bytes, cudaStream_t s);

@@ -712,6 +712,507 @@ __global__ void __launch_bounds__(BX* BY, MB) k_prolong_fused_2d(Geo gf, Geo gc,
   }
 }
 
+// ---- fine level with a diagonal smoother, one right-hand side --------------
+// With M diagonal (damped Jacobi, or RB patches on the 2d+1-point fine
+// stencil) and nu1 = nu2 = 1 the fine level of a V-cycle is two passes:
+//   down:  t = w m0 f,  r = f - A t,  f_c = R r      (t, r in shared memory only)
+//   up:    u' = w m0 f + P e_c,  out = u' + w m0 (f - A u')
+// t = w m0 f is recomputed by the upward pass from f and m0, which it reads
+// for the post-smoothing anyway, so neither t nor r ever goes to HBM: per
+// fine node the level moves f, m0, A twice and out once (plus the coarse
+// vectors), against the five separate reads/writes of t and r otherwise.
+// Out-of-grid tile entries are zero, so the neighbour sums are the in-grid
+// sums; the operator uses the half-cell boundary weights of the fine stencil.
+
+// fine 2D operator at tile position (ly, lx) of a tile holding u with zeros
+// outside the grid: A u = d u - (1/h^2)(wy (u_W + u_E) + wx (u_S + u_N))
+template <typename T, int W>
+__device__ __forceinline__ c_t<T> fine_tile_Au_2d(const c_t<T> (*su)[W], int ly, int lx, c_t<T> d, T invh2, int x,
+                                                  int y, const Geo& g) {
+  const T wx = (x == 0 || x == g.nx - 1) ? T(0.5) : T(1);
+  const T wy = (y == 0 || y == g.ny - 1) ? T(0.5) : T(1);
+  const c_t<T> up = su[ly][lx];
+  const c_t<T> sx = su[ly][lx - 1] + su[ly][lx + 1];
+  const c_t<T> sy = su[ly - 1][lx] + su[ly + 1][lx];
+  c_t<T> a = cmul(d, up);
+  a.x -= invh2 * (wy * sx.x + wx * sy.x);
+  a.y -= invh2 * (wy * sx.y + wx * sy.y);
+  return a;
+}
+
+// down pass, 2D: one block = CX x CY coarse nodes (32 x 8 threads).  The
+// restriction is applied separably: first along x for every fine row of the
+// residual region, then along y.
+template <typename T, int RK, int MB>
+__global__ void __launch_bounds__(BX* BY, MB ? MB : 4) k_fine_down_diag_2d(Geo gf, Geo gc, T invh2, const c_t<T>* __restrict__ A,
+                                                                  const c_t<T>* __restrict__ m0, T w,
+                                                                  const c_t<T>* __restrict__ f,
+                                                                  c_t<T>* __restrict__ fc, const int* active) {
+  constexpr int CX = 32, CY = sizeof(T) == 4 ? 8 : 4;
+  constexpr int RR = RK ? 2 : 1;                       // restriction reach in fine nodes
+  constexpr int RX = 2 * CX - 1 + 2 * RR, RY = 2 * CY - 1 + 2 * RR;   // residual region
+  constexpr int TX = RX + 2, TY = RY + 2;             // t region (residual region + operator halo)
+  constexpr int NTH = BX * BY;
+  __shared__ c_t<T> st[TY][TX];
+  __shared__ c_t<T> sr[RY][RX];
+  __shared__ c_t<T> sh[RY][CX];                       // residual rows restricted along x
+  pdl_enter();
+  if (active && !*active) return;
+  const int tid = threadIdx.y * BX + threadIdx.x;
+  const int X0 = blockIdx.x * CX, Y0 = blockIdx.y * CY;
+  const int rx0 = 2 * X0 - RR, ry0 = 2 * Y0 - RR;
+  // every entry's loads of a phase are issued before any is used (fixed,
+  // unrolled trip counts): one memory round trip per phase
+  constexpr int NT = (TX * TY + NTH - 1) / NTH, NR = (RX * RY + NTH - 1) / NTH;
+  {
+    c_t<T> mv[NT], fv[NT];
+#pragma unroll
+    for (int k = 0; k < NT; ++k) {
+      const int i = tid + k * NTH, ty = i / TX, tx = i - ty * TX;
+      const int gx = rx0 - 1 + tx, gy = ry0 - 1 + ty;
+      const bool in = i < TX * TY && gx >= 0 && gx < gf.nx && gy >= 0 && gy < gf.ny;
+      const int p = in ? gy * gf.nx + gx : 0;
+      mv[k] = in ? m0[p] : cmk<c_t<T>>(0, 0);
+      fv[k] = in ? f[p] : cmk<c_t<T>>(0, 0);
+    }
+#pragma unroll
+    for (int k = 0; k < NT; ++k) {
+      const int i = tid + k * NTH, ty = i / TX, tx = i - ty * TX;
+      if (i < TX * TY) st[ty][tx] = w * cmul(mv[k], fv[k]);
+    }
+  }
+  __syncthreads();
+  {
+    c_t<T> av[NR], fv[NR];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+      const int i = tid + k * NTH, ry = i / RX, rx = i - ry * RX;
+      const int gx = rx0 + rx, gy = ry0 + ry;
+      const bool in = i < RX * RY && gx >= 0 && gx < gf.nx && gy >= 0 && gy < gf.ny;
+      const int p = in ? gy * gf.nx + gx : 0;
+      av[k] = in ? A[p] : cmk<c_t<T>>(0, 0);
+      fv[k] = in ? f[p] : cmk<c_t<T>>(0, 0);
+    }
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+      const int i = tid + k * NTH, ry = i / RX, rx = i - ry * RX;
+      const int gx = rx0 + rx, gy = ry0 + ry;
+      if (i >= RX * RY) continue;
+      const bool in = gx >= 0 && gx < gf.nx && gy >= 0 && gy < gf.ny;
+      sr[ry][rx] = in ? fv[k] - fine_tile_Au_2d<T, TX>(st, ry + 1, rx + 1, av[k], invh2, gx, gy, gf)
+                      : cmk<c_t<T>>(0, 0);
+    }
+  }
+  __syncthreads();
+  // R r = Ry (Rx r): weights 0.5 * P(j, J) per axis, zero outside the fine grid
+  const int cx = threadIdx.x, X = X0 + cx;
+  {
+    T wx[2 * RR + 1];
+#pragma unroll
+    for (int k = 0; k <= 2 * RR; ++k) {
+      const int jx = 2 * X - RR + k;
+      wx[k] = (jx >= 0 && jx < gf.nx && X < gc.nx) ? (T)(0.5f * p1f(RK, gf.nx, gc.nx, jx, X)) : T(0);
+    }
+    for (int ry = threadIdx.y; ry < RY; ry += BY) {
+      c_t<T> acc = cmk<c_t<T>>(0, 0);
+#pragma unroll
+      for (int k = 0; k <= 2 * RR; ++k) acc = acc + wx[k] * sr[ry][2 * cx + k];
+      sh[ry][cx] = acc;
+    }
+  }
+  __syncthreads();
+  const int cy = threadIdx.y, Y = Y0 + cy;
+  if (cy >= CY || X >= gc.nx || Y >= gc.ny) return;
+  c_t<T> acc = cmk<c_t<T>>(0, 0);
+#pragma unroll
+  for (int k = 0; k <= 2 * RR; ++k) {
+    const int jy = 2 * Y - RR + k;
+    const T wy = (jy >= 0 && jy < gf.ny) ? (T)(0.5f * p1f(RK, gf.ny, gc.ny, jy, Y)) : T(0);
+    acc = acc + wy * sh[2 * cy + k][cx];
+  }
+  fc[Y * gc.nx + X] = acc;
+}
+
+// up pass, 2D: one block = 64 x FY fine nodes (2 x FY/8 per thread).  The
+// coarse correction's tile is staged in shared memory and prolongated
+// separably: along x for each coarse row the tile needs (weights and first
+// coarse index per fine column and row computed once per block), then along y.
+template <typename T, int PK, int MB>
+__global__ void __launch_bounds__(BX* BY, MB ? MB : 4) k_fine_up_diag_2d(Geo gf, Geo gc, T invh2, const c_t<T>* __restrict__ A,
+                                                                const c_t<T>* __restrict__ m0, T w,
+                                                                const c_t<T>* __restrict__ f,
+                                                                const c_t<T>* __restrict__ ec, c_t<T>* __restrict__ out,
+                                                                const int* active) {
+  constexpr int FX = 64, FY = sizeof(T) == 4 ? 16 : 8;
+  constexpr int UX = FX + 2, UY = FY + 2;            // u' tile with the operator halo
+  constexpr int EX = FX / 2 + 4, EY = FY / 2 + 4;    // coarse values the tile's prolongation reads
+  constexpr int NTH = BX * BY;
+  __shared__ c_t<T> su[UY][UX];
+  __shared__ c_t<T> sf[UY][UX];
+  __shared__ c_t<T> sm[UY][UX];
+  __shared__ c_t<T> se[EY][EX];
+  __shared__ c_t<T> sh[EY][UX];                      // coarse rows prolongated along x
+  __shared__ float wcx[UX][3], wcy[UY][3];
+  __shared__ int icx[UX], icy[UY];
+  pdl_enter();
+  if (active && !*active) return;
+  const int tid = threadIdx.y * BX + threadIdx.x;
+  const int x0 = blockIdx.x * FX, y0 = blockIdx.y * FY;
+  const int ex0 = ((x0 - 1) >> 1) - 1, ey0 = ((y0 - 1) >> 1) - 1;   // coarse origin (floor division)
+  constexpr int NE = (EX * EY + NTH - 1) / NTH, NU = (UX * UY + NTH - 1) / NTH;
+  c_t<T> fvs[NU], mvs[NU];
+  {
+    c_t<T> ev[NE];
+#pragma unroll
+    for (int k = 0; k < NE; ++k) {
+      const int i = tid + k * NTH, ey = i / EX, exx = i - ey * EX;
+      const int gx = ex0 + exx, gy = ey0 + ey;
+      const bool in = i < EX * EY && gx >= 0 && gx < gc.nx && gy >= 0 && gy < gc.ny;
+      ev[k] = in ? ec[gy * gc.nx + gx] : cmk<c_t<T>>(0, 0);
+    }
+#pragma unroll
+    for (int k = 0; k < NU; ++k) {
+      const int i = tid + k * NTH, uy = i / UX, ux = i - uy * UX;
+      const int gx = x0 - 1 + ux, gy = y0 - 1 + uy;
+      const bool in = i < UX * UY && gx >= 0 && gx < gf.nx && gy >= 0 && gy < gf.ny;
+      const int p = in ? gy * gf.nx + gx : 0;
+      fvs[k] = in ? f[p] : cmk<c_t<T>>(0, 0);
+      mvs[k] = in ? m0[p] : cmk<c_t<T>>(0, 0);
+    }
+#pragma unroll
+    for (int k = 0; k < NE; ++k) {
+      const int i = tid + k * NTH, ey = i / EX, exx = i - ey * EX;
+      if (i < EX * EY) se[ey][exx] = ev[k];
+    }
+  }
+  // per fine column / row of the tile: first coarse index (tile-local) and weights
+  if (tid < UX) {
+    const int gx = min(max(x0 - 1 + tid, 0), gf.nx - 1);
+    float wv[3];
+    icx[tid] = p1_stencil<PK>(gx, gf.nx, gc.nx, wv) - ex0;
+    wcx[tid][0] = wv[0];
+    wcx[tid][1] = wv[1];
+    wcx[tid][2] = wv[2];
+  } else if (tid >= 128 && tid < 128 + UY) {
+    const int t = tid - 128, gy = min(max(y0 - 1 + t, 0), gf.ny - 1);
+    float wv[3];
+    icy[t] = p1_stencil<PK>(gy, gf.ny, gc.ny, wv) - ey0;
+    wcy[t][0] = wv[0];
+    wcy[t][1] = wv[1];
+    wcy[t][2] = wv[2];
+  }
+  __syncthreads();
+  for (int i = tid; i < EY * UX; i += NTH) {
+    const int ey = i / UX, ux = i - ey * UX;
+    const int c0 = icx[ux];
+    sh[ey][ux] = (T)wcx[ux][0] * se[ey][c0] + (T)wcx[ux][1] * se[ey][c0 + 1] + (T)wcx[ux][2] * se[ey][c0 + 2];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NU; ++k) {
+    const int i = tid + k * NTH, uy = i / UX, ux = i - uy * UX;
+    if (i >= UX * UY) continue;
+    const int gx = x0 - 1 + ux, gy = y0 - 1 + uy;
+    c_t<T> v = cmk<c_t<T>>(0, 0);
+    if (gx >= 0 && gx < gf.nx && gy >= 0 && gy < gf.ny) {
+      const int r0 = icy[uy];
+      const c_t<T> pe = (T)wcy[uy][0] * sh[r0][ux] + (T)wcy[uy][1] * sh[r0 + 1][ux] + (T)wcy[uy][2] * sh[r0 + 2][ux];
+      v = w * cmul(mvs[k], fvs[k]) + pe;
+    }
+    su[uy][ux] = v;
+    sf[uy][ux] = fvs[k];
+    sm[uy][ux] = mvs[k];
+  }
+  __syncthreads();
+  constexpr int NO = (FY / BY) * (FX / BX);
+  c_t<T> dv[NO];
+#pragma unroll
+  for (int k = 0; k < NO; ++k) {
+    const int lx = threadIdx.x + (k % (FX / BX)) * BX, ly = threadIdx.y + (k / (FX / BX)) * BY;
+    const int x = x0 + lx, y = y0 + ly;
+    const bool in = x < gf.nx && y < gf.ny;
+    dv[k] = in ? A[y * gf.nx + x] : cmk<c_t<T>>(0, 0);
+  }
+#pragma unroll
+  for (int k = 0; k < NO; ++k) {
+    const int lx = threadIdx.x + (k % (FX / BX)) * BX, ly = threadIdx.y + (k / (FX / BX)) * BY;
+    const int x = x0 + lx, y = y0 + ly;
+    if (x >= gf.nx || y >= gf.ny) continue;
+    const c_t<T> a = fine_tile_Au_2d<T, UX>(su, ly + 1, lx + 1, dv[k], invh2, x, y, gf);
+    out[y * gf.nx + x] = su[ly + 1][lx + 1] + w * cmul(sm[ly + 1][lx + 1], sf[ly + 1][lx + 1] - a);
+  }
+}
+
+// ---- coarse levels in 2D, one right-hand side: two fused passes -----------
+// A coarse level of a V(1,1)-cycle from zero is, as separate launches,
+// sweep0 -> residual -> restriction down and prolongation + residual ->
+// sweep up: five dependent kernels, each paying launch and memory latency
+// (on the small levels that latency, not bandwidth, sets the time).  Here
+// each direction is one kernel over shared-memory tiles with the halos the
+// chained stencils need, recomputed by every block:
+//   down:  t = w M f  (tile + R reach + A reach),  r = f - A t  (tile + R reach),
+//          f_c = R r;  t is written for the block's own fine nodes
+//   up:    u' = t + P e_c  (tile + M reach + A reach),  r = f - A u'  (tile + M
+//          reach),  out = u' + w M r
+// The stencil coefficients are read from their planes in HBM / L2 as in the
+// separate kernels (same terms in the same order, so t and the residuals are
+// the separate kernels' values); only field values go through the tiles.
+// Tiles hold zeros outside the grid; an out-of-grid neighbour always has a
+// zero coefficient.  The smoother's stencil reach is at most 2 in 2D.
+
+constexpr int kTileRM = 2;
+// one block of 1024 threads per tile, so every phase has at most one tile
+// point per thread (a phase then waits for about one round of loads)
+constexpr int kTileThreads = 1024;
+
+// (M v) at node p from a tile of v (row pitch W; (lx, ly) = p's position):
+// the stored half of M' with mirrored entries read at the neighbour, then
+// the weight 1/count (SYM), or the planes of M itself
+template <typename T, bool SYM, typename LST>
+__device__ __forceinline__ c_t<T> tile_Mv(const Geo& g, const LST& m, const c_t<T>* __restrict__ P,
+                                          const T* __restrict__ wc, const c_t<T>* tile, int W, int lx, int ly, int p,
+                                          int x, int y) {
+  c_t<T> acc = cmk<c_t<T>>(0, 0);
+#pragma unroll 8
+  for (int s = 0; s < m.n; ++s) {
+    const int dx = m.d[s][0], dy = m.d[s][1];
+    acc = cfma(P[s * g.N + p], tile[(ly + dy) * W + lx + dx], acc);
+    if constexpr (SYM) {
+      if (m.mirror[s]) {
+        const bool okm = x - dx >= 0 && x - dx < g.nx && y - dy >= 0 && y - dy < g.ny;
+        const c_t<T> cm = okm ? P[s * g.N + p - m.nflat[s]] : cmk<c_t<T>>(0, 0);
+        acc = cfma(cm, tile[(ly - dy) * W + lx - dx], acc);
+      }
+    }
+  }
+  if constexpr (SYM) return wc[p] * acc;
+  else return acc;
+}
+
+// (A v) at node p for a stored box stencil (AK = rho) or its symmetric half
+// (AK = 10 + rho), from a tile of v
+template <typename T, int AK>
+__device__ __forceinline__ c_t<T> tile_Av(const Geo& g, const c_t<T>* __restrict__ A, const c_t<T>* tile, int W, int lx,
+                                          int ly, int p, int x, int y) {
+  constexpr int RHO = AK % 10, WB = 2 * RHO + 1, C = (WB * WB - 1) / 2;
+  c_t<T> acc = cmk<c_t<T>>(0, 0);
+#pragma unroll
+  for (int dy = -RHO; dy <= RHO; ++dy)
+#pragma unroll
+    for (int dx = -RHO; dx <= RHO; ++dx) {
+      const int s = (dy + RHO) * WB + (dx + RHO);
+      if constexpr (AK > 10) {
+        if (s < C) continue;
+        acc = cfma(A[(s - C) * g.N + p], tile[(ly + dy) * W + lx + dx], acc);
+        if (s == C) continue;
+        const bool ok = x - dx >= 0 && x - dx < g.nx && y - dy >= 0 && y - dy < g.ny;
+        const c_t<T> cm = ok ? A[(s - C) * g.N + p - dx - dy * g.nx] : cmk<c_t<T>>(0, 0);
+        acc = cfma(cm, tile[(ly - dy) * W + lx - dx], acc);
+      } else {
+        acc = cfma(A[s * g.N + p], tile[(ly + dy) * W + lx + dx], acc);
+      }
+    }
+  return acc;
+}
+
+template <typename T, int AK, bool SYM, int RK, int MB, typename LST>
+__global__ void __launch_bounds__(kTileThreads, 1) k_level_down_2d(Geo gf, Geo gc, const c_t<T>* __restrict__ A,
+                                                               LST m, const c_t<T>* __restrict__ M,
+                                                               const T* __restrict__ wc, T w,
+                                                               const c_t<T>* __restrict__ f, c_t<T>* __restrict__ t,
+                                                               c_t<T>* __restrict__ fc, const int* active) {
+  constexpr int CX = 16, CY = sizeof(T) == 4 ? 8 : 4;
+  constexpr int RR = RK ? 2 : 1, RA = AK % 10, RM = kTileRM;
+  constexpr int RX = 2 * CX - 1 + 2 * RR, RY = 2 * CY - 1 + 2 * RR;   // residual region
+  constexpr int TX = RX + 2 * RA, TY = RY + 2 * RA;                   // t region
+  constexpr int FX = TX + 2 * RM, FY = TY + 2 * RM;                   // f region
+  constexpr int NTH = kTileThreads;
+  __shared__ c_t<T> sf[FY * FX];
+  __shared__ c_t<T> st[TY * TX];
+  __shared__ c_t<T> sr[RY * RX];
+  __shared__ c_t<T> sh[RY * CX];
+  pdl_enter();
+  if (active && !*active) return;
+  const int tid = threadIdx.x;
+  const int X0 = blockIdx.x * CX, Y0 = blockIdx.y * CY;
+  const int rx0 = 2 * X0 - RR, ry0 = 2 * Y0 - RR;
+  const int tx0 = rx0 - RA, ty0 = ry0 - RA, fx0 = tx0 - RM, fy0 = ty0 - RM;
+  constexpr int NF = (FX * FY + NTH - 1) / NTH;
+  {
+    c_t<T> v[NF];
+#pragma unroll
+    for (int k = 0; k < NF; ++k) {
+      const int i = tid + k * NTH, ly = i / FX, lx = i - ly * FX;
+      const int gx = fx0 + lx, gy = fy0 + ly;
+      const bool in = i < FX * FY && gx >= 0 && gx < gf.nx && gy >= 0 && gy < gf.ny;
+      v[k] = in ? f[gy * gf.nx + gx] : cmk<c_t<T>>(0, 0);
+    }
+#pragma unroll
+    for (int k = 0; k < NF; ++k) {
+      const int i = tid + k * NTH;
+      if (i < FX * FY) sf[i] = v[k];
+    }
+  }
+  __syncthreads();
+  // t = w M f on the t region; written out for the block's own fine nodes
+  for (int i = tid; i < TX * TY; i += NTH) {
+    const int ly = i / TX, lx = i - ly * TX;
+    const int gx = tx0 + lx, gy = ty0 + ly;
+    c_t<T> v = cmk<c_t<T>>(0, 0);
+    if (gx >= 0 && gx < gf.nx && gy >= 0 && gy < gf.ny) {
+      const int p = gy * gf.nx + gx;
+      v = w * tile_Mv<T, SYM>(gf, m, M, wc, sf, FX, lx + RM, ly + RM, p, gx, gy);
+      if (gx >= 2 * X0 && gx < 2 * X0 + 2 * CX && gy >= 2 * Y0 && gy < 2 * Y0 + 2 * CY) t[p] = v;
+    }
+    st[i] = v;
+  }
+  __syncthreads();
+  for (int i = tid; i < RX * RY; i += NTH) {
+    const int ly = i / RX, lx = i - ly * RX;
+    const int gx = rx0 + lx, gy = ry0 + ly;
+    c_t<T> v = cmk<c_t<T>>(0, 0);
+    if (gx >= 0 && gx < gf.nx && gy >= 0 && gy < gf.ny) {
+      const int p = gy * gf.nx + gx;
+      v = sf[(ly + RA + RM) * FX + lx + RA + RM] - tile_Av<T, AK>(gf, A, st, TX, lx + RA, ly + RA, p, gx, gy);
+    }
+    sr[i] = v;
+  }
+  __syncthreads();
+  // f_c = Ry (Rx r)
+  for (int i = tid; i < RY * CX; i += NTH) {
+    const int ly = i / CX, cx = i - ly * CX, X = X0 + cx;
+    c_t<T> acc = cmk<c_t<T>>(0, 0);
+    if (X < gc.nx) {
+#pragma unroll
+      for (int k = 0; k <= 2 * RR; ++k) {
+        const int jx = 2 * X - RR + k;
+        const T wx = (jx >= 0 && jx < gf.nx) ? (T)(0.5f * p1f(RK, gf.nx, gc.nx, jx, X)) : T(0);
+        acc = acc + wx * sr[ly * RX + 2 * cx + k];
+      }
+    }
+    sh[i] = acc;
+  }
+  __syncthreads();
+  for (int i = tid; i < CX * CY; i += NTH) {
+    const int cy = i / CX, cx = i - cy * CX, X = X0 + cx, Y = Y0 + cy;
+    if (X >= gc.nx || Y >= gc.ny) continue;
+    c_t<T> acc = cmk<c_t<T>>(0, 0);
+#pragma unroll
+    for (int k = 0; k <= 2 * RR; ++k) {
+      const int jy = 2 * Y - RR + k;
+      const T wy = (jy >= 0 && jy < gf.ny) ? (T)(0.5f * p1f(RK, gf.ny, gc.ny, jy, Y)) : T(0);
+      acc = acc + wy * sh[(2 * cy + k) * CX + cx];
+    }
+    fc[Y * gc.nx + X] = acc;
+  }
+}
+
+template <typename T, int AK, bool SYM, int PK, int MB, typename LST>
+__global__ void __launch_bounds__(kTileThreads, 1) k_level_up_2d(Geo gf, Geo gc, const c_t<T>* __restrict__ A,
+                                                             LST m, const c_t<T>* __restrict__ M,
+                                                             const T* __restrict__ wc, T w,
+                                                             const c_t<T>* __restrict__ f, const c_t<T>* __restrict__ t,
+                                                             const c_t<T>* __restrict__ ec, c_t<T>* __restrict__ out,
+                                                             const int* active) {
+  constexpr int OX = 32, OY = sizeof(T) == 4 ? 16 : 8;                 // owned fine nodes
+  constexpr int RA = AK % 10, RM = kTileRM;
+  constexpr int RX = OX + 2 * RM, RY = OY + 2 * RM;                   // residual region
+  constexpr int UX = RX + 2 * RA, UY = RY + 2 * RA;                   // u' region
+  constexpr int EX = UX / 2 + 4, EY = UY / 2 + 4;                     // coarse values P reads
+  constexpr int NTH = kTileThreads;
+  __shared__ c_t<T> su[UY * UX];
+  __shared__ c_t<T> sr[RY * RX];
+  __shared__ c_t<T> se[EY * EX];
+  __shared__ c_t<T> sh[EY * UX];
+  __shared__ float wcx[UX][3], wcy[UY][3];
+  __shared__ int icx[UX], icy[UY];
+  pdl_enter();
+  if (active && !*active) return;
+  const int tid = threadIdx.x;
+  const int x0 = blockIdx.x * OX, y0 = blockIdx.y * OY;
+  const int ux0 = x0 - RM - RA, uy0 = y0 - RM - RA;
+  const int ex0 = (ux0 >> 1) - 1, ey0 = (uy0 >> 1) - 1;             // floor division
+  constexpr int NE = (EX * EY + NTH - 1) / NTH, NU = (UX * UY + NTH - 1) / NTH;
+  c_t<T> tv[NU];
+  {
+    c_t<T> ev[NE];
+#pragma unroll
+    for (int k = 0; k < NE; ++k) {
+      const int i = tid + k * NTH, ly = i / EX, lx = i - ly * EX;
+      const int gx = ex0 + lx, gy = ey0 + ly;
+      const bool in = i < EX * EY && gx >= 0 && gx < gc.nx && gy >= 0 && gy < gc.ny;
+      ev[k] = in ? ec[gy * gc.nx + gx] : cmk<c_t<T>>(0, 0);
+    }
+#pragma unroll
+    for (int k = 0; k < NU; ++k) {
+      const int i = tid + k * NTH, ly = i / UX, lx = i - ly * UX;
+      const int gx = ux0 + lx, gy = uy0 + ly;
+      const bool in = i < UX * UY && gx >= 0 && gx < gf.nx && gy >= 0 && gy < gf.ny;
+      tv[k] = in ? t[gy * gf.nx + gx] : cmk<c_t<T>>(0, 0);
+    }
+#pragma unroll
+    for (int k = 0; k < NE; ++k) {
+      const int i = tid + k * NTH;
+      if (i < EX * EY) se[i] = ev[k];
+    }
+  }
+  if (tid < UX) {
+    const int gx = min(max(ux0 + tid, 0), gf.nx - 1);
+    float wv[3];
+    icx[tid] = p1_stencil<PK>(gx, gf.nx, gc.nx, wv) - ex0;
+    wcx[tid][0] = wv[0];
+    wcx[tid][1] = wv[1];
+    wcx[tid][2] = wv[2];
+  } else if (tid >= 128 && tid < 128 + UY) {
+    const int k = tid - 128, gy = min(max(uy0 + k, 0), gf.ny - 1);
+    float wv[3];
+    icy[k] = p1_stencil<PK>(gy, gf.ny, gc.ny, wv) - ey0;
+    wcy[k][0] = wv[0];
+    wcy[k][1] = wv[1];
+    wcy[k][2] = wv[2];
+  }
+  __syncthreads();
+  for (int i = tid; i < EY * UX; i += NTH) {
+    const int ly = i / UX, lx = i - ly * UX;
+    const int c0 = icx[lx];
+    sh[i] = (T)wcx[lx][0] * se[ly * EX + c0] + (T)wcx[lx][1] * se[ly * EX + c0 + 1] +
+            (T)wcx[lx][2] * se[ly * EX + c0 + 2];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NU; ++k) {
+    const int i = tid + k * NTH, ly = i / UX, lx = i - ly * UX;
+    if (i >= UX * UY) continue;
+    const int gx = ux0 + lx, gy = uy0 + ly;
+    c_t<T> v = cmk<c_t<T>>(0, 0);
+    if (gx >= 0 && gx < gf.nx && gy >= 0 && gy < gf.ny) {
+      const int r0 = icy[ly];
+      v = tv[k] + ((T)wcy[ly][0] * sh[r0 * UX + lx] + (T)wcy[ly][1] * sh[(r0 + 1) * UX + lx] +
+                   (T)wcy[ly][2] * sh[(r0 + 2) * UX + lx]);
+    }
+    su[i] = v;
+  }
+  __syncthreads();
+  for (int i = tid; i < RX * RY; i += NTH) {
+    const int ly = i / RX, lx = i - ly * RX;
+    const int gx = x0 - RM + lx, gy = y0 - RM + ly;
+    c_t<T> v = cmk<c_t<T>>(0, 0);
+    if (gx >= 0 && gx < gf.nx && gy >= 0 && gy < gf.ny) {
+      const int p = gy * gf.nx + gx;
+      v = f[p] - tile_Av<T, AK>(gf, A, su, UX, lx + RA, ly + RA, p, gx, gy);
+    }
+    sr[i] = v;
+  }
+  __syncthreads();
+  for (int i = tid; i < OX * OY; i += NTH) {
+    const int ly = i / OX, lx = i - ly * OX;
+    const int gx = x0 + lx, gy = y0 + ly;
+    if (gx >= gf.nx || gy >= gf.ny) continue;
+    const int p = gy * gf.nx + gx;
+    out[p] = su[(ly + RM + RA) * UX + lx + RM + RA] + w * tile_Mv<T, SYM>(gf, m, M, wc, sr, RX, lx + RM, ly + RM, p, gx, gy);
+  }
+}
+
 // u = Ainv f: TPR threads per row (256 / TPR rows per block of 256), four
 // independent accumulators per thread so that several row loads are in flight
 // (the matrix is streamed once per cycle); warp shuffles, then the row's warps
@@ -1057,6 +1558,114 @@ void prolong_fused_2d(Ctx& c, int l, const void* ec, const void* t, const void* 
 }
 
 template <typename T>
+void fine_down_diag(Ctx& c, const void* f, void* fc, const int* active, cudaStream_t s) {
+  Level& L = c.L[0];
+  Level& C = c.L[1];
+  const Geo gf = geo(L.g), gc = geo(C.g);
+  const T invh2 = (T)(1.0 / (c.h * c.h));
+  constexpr int CY = sizeof(T) == 4 ? 8 : 4;
+  const dim3 grid(nblk(gc.nx, 32), nblk(gc.ny, CY));
+  auto go = [&](auto RK, auto MBc) {
+    launch_pdl(k_fine_down_diag_2d<T, decltype(RK)::value, decltype(MBc)::value>, grid, dim3(BX, BY), s, gf, gc,
+               invh2, (const c_t<T>*)L.Aw, (const c_t<T>*)L.Mw, (T)L.damping, (const c_t<T>*)f, (c_t<T>*)fc, active);
+  };
+  auto mb = [&](auto RK) {
+    if (L.g.N <= kIlpNodes) go(RK, std::integral_constant<int, 2>{});
+    else go(RK, std::integral_constant<int, 0>{});
+  };
+  if (L.rkind) mb(std::integral_constant<int, 1>{});
+  else mb(std::integral_constant<int, 0>{});
+  HZ_LAUNCHED();
+}
+
+template <typename T>
+void fine_up_diag(Ctx& c, const void* ec, const void* f, void* out, const int* active, cudaStream_t s) {
+  Level& L = c.L[0];
+  Level& C = c.L[1];
+  const Geo gf = geo(L.g), gc = geo(C.g);
+  const T invh2 = (T)(1.0 / (c.h * c.h));
+  constexpr int FY = sizeof(T) == 4 ? 16 : 8;
+  const dim3 grid(nblk(gf.nx, 64), nblk(gf.ny, FY));
+  auto go = [&](auto PK, auto MBc) {
+    launch_pdl(k_fine_up_diag_2d<T, decltype(PK)::value, decltype(MBc)::value>, grid, dim3(BX, BY), s, gf, gc, invh2,
+               (const c_t<T>*)L.Aw, (const c_t<T>*)L.Mw, (T)L.damping, (const c_t<T>*)f, (const c_t<T>*)ec,
+               (c_t<T>*)out, active);
+  };
+  auto mb = [&](auto PK) {
+    if (L.g.N <= kIlpNodes) go(PK, std::integral_constant<int, 2>{});
+    else go(PK, std::integral_constant<int, 0>{});
+  };
+  if (L.pkind) mb(std::integral_constant<int, 1>{});
+  else mb(std::integral_constant<int, 0>{});
+  HZ_LAUNCHED();
+}
+
+// operator kind of a coarse 2D level as a compile-time constant
+template <typename F>
+void with_ak_2d(int ak, F&& f) {
+  switch (ak) {
+    case 1: return f(std::integral_constant<int, 1>{});
+    case 2: return f(std::integral_constant<int, 2>{});
+    case 3: return f(std::integral_constant<int, 3>{});
+    case 11: return f(std::integral_constant<int, 11>{});
+    case 12: return f(std::integral_constant<int, 12>{});
+    default: throw Error(HZ_ERR_INVALID_ARG, "unsupported stencil radius");
+  }
+}
+
+template <typename T>
+void level_down_2d(Ctx& c, int l, const void* f, void* t, void* fc, const int* active, cudaStream_t s) {
+  Level& L = c.L[l];
+  Level& C = c.L[l + 1];
+  const Geo gf = geo(L.g), gc = geo(C.g);
+  constexpr int CY = sizeof(T) == 4 ? 8 : 4;
+  const dim3 grid(nblk(gc.nx, 16), nblk(gc.ny, CY));
+  with_ak_2d(akind(L), [&](auto K) {
+    auto go = [&](auto SYMc, auto RK, auto MBc, const auto& lst) {
+      launch_pdl(k_level_down_2d<T, decltype(K)::value, decltype(SYMc)::value, decltype(RK)::value,
+                                 decltype(MBc)::value, std::decay_t<decltype(lst)>>,
+                 grid, dim3(kTileThreads), s, gf, gc, (const c_t<T>*)L.Aw, lst, (const c_t<T>*)L.Mhw,
+                 (const T*)L.wcw, (T)L.damping, (const c_t<T>*)f, (c_t<T>*)t, (c_t<T>*)fc, active);
+    };
+    auto rk = [&](auto SYMc, auto MBc, const auto& lst) {
+      if (L.rkind) go(SYMc, std::integral_constant<int, 1>{}, MBc, lst);
+      else go(SYMc, std::integral_constant<int, 0>{}, MBc, lst);
+    };
+    auto mb = [&](auto SYMc, const auto& lst) { rk(SYMc, std::integral_constant<int, 0>{}, lst); };
+    if (L.wcw) mb(std::true_type{}, slist(L));
+    else mb(std::false_type{}, mlist(L));
+  });
+  HZ_LAUNCHED();
+}
+
+template <typename T>
+void level_up_2d(Ctx& c, int l, const void* ec, const void* t, const void* f, void* out, const int* active,
+                 cudaStream_t s) {
+  Level& L = c.L[l];
+  Level& C = c.L[l + 1];
+  const Geo gf = geo(L.g), gc = geo(C.g);
+  constexpr int OY = sizeof(T) == 4 ? 16 : 8;
+  const dim3 grid(nblk(gf.nx, 32), nblk(gf.ny, OY));
+  with_ak_2d(akind(L), [&](auto K) {
+    auto go = [&](auto SYMc, auto PK, auto MBc, const auto& lst) {
+      launch_pdl(k_level_up_2d<T, decltype(K)::value, decltype(SYMc)::value, decltype(PK)::value,
+                               decltype(MBc)::value, std::decay_t<decltype(lst)>>,
+                 grid, dim3(kTileThreads), s, gf, gc, (const c_t<T>*)L.Aw, lst, (const c_t<T>*)L.Mhw,
+                 (const T*)L.wcw, (T)L.damping, (const c_t<T>*)f, (const c_t<T>*)t, (const c_t<T>*)ec,
+                 (c_t<T>*)out, active);
+    };
+    auto pk = [&](auto SYMc, auto MBc, const auto& lst) {
+      if (L.pkind) go(SYMc, std::integral_constant<int, 1>{}, MBc, lst);
+      else go(SYMc, std::integral_constant<int, 0>{}, MBc, lst);
+    };
+    auto mb = [&](auto SYMc, const auto& lst) { pk(SYMc, std::integral_constant<int, 0>{}, lst); };
+    if (L.wcw) mb(std::true_type{}, slist(L));
+    else mb(std::false_type{}, mlist(L));
+  });
+  HZ_LAUNCHED();
+}
+
+template <typename T>
 void coarse_t(Ctx& c, const void* f, void* u, const int* active, cudaStream_t s) {
   Level& L = c.L.back();
   const int n = (int)L.g.N;
@@ -1085,6 +1694,22 @@ void cycle_rec(Ctx& c, int l, const void* f, const void* u0, void* out, const in
   Level& L = c.L[l];
   if (L.coarsest) {
     coarse_t<T>(c, f, out, active, s);
+    return;
+  }
+  if (u0 == nullptr && level_two_pass_2d(c, l)) {
+    Level& C = c.L[l + 1];
+    level_down_2d<T>(c, l, f, L.t, C.f, active, s);
+    cycle_rec<T>(c, l + 1, C.f, nullptr, C.u, active, s);
+    for (int v = 1; v < c.opts.cycle_visits && !C.coarsest; ++v) cycle_rec<T>(c, l + 1, C.f, C.u, C.u, active, s);
+    level_up_2d<T>(c, l, C.u, L.t, f, out, active, s);
+    return;
+  }
+  if (u0 == nullptr && fine_two_pass(c, l)) {
+    Level& C = c.L[l + 1];
+    fine_down_diag<T>(c, f, C.f, active, s);
+    cycle_rec<T>(c, l + 1, C.f, nullptr, C.u, active, s);
+    for (int v = 1; v < c.opts.cycle_visits && !C.coarsest; ++v) cycle_rec<T>(c, l + 1, C.f, C.u, C.u, active, s);
+    fine_up_diag<T>(c, C.u, f, out, active, s);
     return;
   }
   const int nu1 = c.opts.nu1, nu2 = c.opts.nu2;

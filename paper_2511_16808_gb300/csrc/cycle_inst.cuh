@@ -19,7 +19,12 @@
   EXT template void prolong_fused_2d<T, true>(Ctx&, int, const void*, const void*, const void*, void*, void*,     \
                                               const int*, cudaStream_t);                                          \
   EXT template void prolong_fused_2d<T, false>(Ctx&, int, const void*, const void*, const void*, void*, void*,    \
-                                               const int*, cudaStream_t);
+                                               const int*, cudaStream_t);                                         \
+  EXT template void fine_down_diag<T>(Ctx&, const void*, void*, const int*, cudaStream_t);                       \
+  EXT template void fine_up_diag<T>(Ctx&, const void*, const void*, void*, const int*, cudaStream_t);       \
+  EXT template void level_down_2d<T>(Ctx&, int, const void*, void*, void*, const int*, cudaStream_t);            \
+  EXT template void level_up_2d<T>(Ctx&, int, const void*, const void*, const void*, void*, const int*,         \
+                                   cudaStream_t);
 #define HZ_CYC_TOP(EXT, T)                                                                                        \
   EXT template void coarse_t<T>(Ctx&, const void*, void*, const int*, cudaStream_t);                             \
   EXT template void vcycle_t<T>(Ctx&, int, const void*, void*, const int*, cudaStream_t);

@@ -655,7 +655,9 @@ double vcycle_bytes(const Ctx& c) {
     } else {
       const double sA = L.fine ? 1.0 : (L.a_half ? (L.A.off.n + 1) / 2 : L.A.off.n), sM = sMst;
       const double rc = L.g.dim == 3 ? 0.125 : 0.25;
-      if (L.m_diag) tot += N * b * (5 + (1 + rc) + (5 + rc)) + (sA - 1) * 2 * N * b;   // sweep0+resid, restrict, prolong+sweep
+      if (fine_two_pass(c, (int)l)) tot += N * b * (7 + 2 * rc);   // f, m0, A twice, out; coarse
+      else if (L.m_diag) tot += N * b * (5 + (1 + rc) + (5 + rc)) + (sA - 1) * 2 * N * b;   // sweep0+resid, restrict, prolong+sweep
+      else if (level_two_pass_2d(c, (int)l)) tot += N * b * (5 + 2 * rc) + 2 * (sA + sM) * N * b;   // fused tiles
       else tot += N * b * (2 * sM + 2 * sA + 13 + 2 * rc);
     }
     tot = t0 + vis * (tot - t0);
