@@ -16,6 +16,15 @@ memory and the solution returned to host memory (copies inside the timed
 region).  The plain FP64 GPU path is timed beside it, and the FP64 CPU
 oracle on a bounded sample of the same solve (cpu_baseline).
 
+The default run also times config 3 (the 3D geophysical medium at 257^3,
+the largest single-GPU configuration) as extra keys: its mixed and plain
+FP64 solves/s, iterations and V-cycle HBM roofline.
+
+`--probe` runs short solves of a workload for profiler captures (no timing,
+no JSON line): the hierarchy is built, then a few FGMRES solves capped at a
+small iteration count, so a capture sees the solver's kernels with few
+launches before them.
+
 Multi-GPU: independent replicas (one solve stream per rank, no data-path
 collective); value = all ranks' solves / max-over-ranks time.
 `--impl reference` times the FP64 CPU oracle instead (rank 0 only).
@@ -358,6 +367,47 @@ def _with_overrides(w, args):
     return replace(w, **kw) if kw else w
 
 
+def extra_workload(name, args, stream):
+    """A second workload timed in the same run (the largest single-GPU
+    configuration beside the headline one): mixed solves/s over a few device-
+    timed solves, its iterations, the V-cycle's HBM roofline and the plain
+    FP64 path's solves/s.  Reported as extra keys, not as the line's value."""
+    import torch
+    from paper_2511_16808_gb300 import hz as _hz
+    w = getattr(__import__("workloads"), name)()
+    peak, src = _peaks()
+    solver = make_solver(w, "mixed", stream)
+    q = torch.tensor(w.rhs(0), device="cuda")
+    p = torch.empty_like(q)
+    solver.solve(q, p)
+    steps = max(1, min(args.steps, 3))
+    ms, infos = time_solves(torch, solver, q, p, steps, stream)
+    _hz.hz_profile_select(solver.ctx, "vcycle")
+    solver.solve(q, p)
+    _hz.hz_profile_select(solver.ctx, "vcycle")
+    solver.solve(q, p)
+    torch.cuda.synchronize()
+    vprof = _hz.hz_profile_read(solver.ctx)
+    _hz.hz_profile_select(solver.ctx, "none")
+    solver.close()
+    v_gbs = vprof["bytes"] / (vprof["ms"] / 1e3) / 1e9 if vprof["ms"] else None
+    out = {"workload": w.name, "nodes": w.nodes, "levels": w.levels, "patch": w.patch,
+           "patch_coarse": w.patch_coarse or w.patch, "intergrid": w.intergrid, "alpha": w.alpha,
+           "value": steps / (ms / 1e3), "unit": UNIT, "ms_per_solve": ms / steps, "steps": steps,
+           "iters": infos[-1].iters, "relres_true": infos[-1].relres_true,
+           "vcycle_roofline": {"bound": "hbm", "achieved": v_gbs, "peak": peak, "unit": "GB/s",
+                               "frac": v_gbs / peak if v_gbs else None, "peak_source": src,
+                               "avg_vcycle_us": vprof["ms"] * 1e3 / max(vprof["launches"], 1)}}
+    if not args.no_fp64:
+        s64 = make_solver(w, "fp64", stream)
+        s64.solve(q, p)
+        ms64, inf64 = time_solves(torch, s64, q, p, 1, stream)
+        s64.close()
+        out["plain_fp64"] = {"value": 1.0 / (ms64 / 1e3), "unit": UNIT, "iters": inf64[-1].iters,
+                             "relres_true": inf64[-1].relres_true, "ms_per_solve": ms64}
+    return out
+
+
 def run_ours(args):
     import torch
     import workloads
@@ -499,6 +549,8 @@ def run_ours(args):
             "vanka_dof_per_s": vdofs,
             "err_vs_oracle": agree,
         }
+        if args.config == "config2" and not args.no_extra:
+            out["config3"] = extra_workload("config3", args, stream)
     solver.close()
     if dist:
         dist.destroy_process_group()
@@ -833,14 +885,46 @@ def run_reference(args):
     s_per_iter = sum(times) / (len(times) * per_step)
     value = 1.0 / (s_per_iter * ref_iters)
     sample = (f"{w.name}: each step = {per_step} FGMRES iterations of the oracle solve "
-              f"(setup untimed), scaled by the {ref_iters:g} iterations of a full oracle solve")
+              f"(setup untimed); solves/s scaled by the {ref_iters:g} iterations of a full oracle solve")
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * s_per_iter * ref_iters,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * s_per_iter * per_step,
+            "step": f"{per_step} FGMRES iterations of the oracle's solve of the workload",
+            "extrapolated_from_iters": per_step * len(times),
+            "ms_per_solve_extrapolated": 1e3 * s_per_iter * ref_iters,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
             "data": "synthetic (seeded layered medium)",
             "config": {"workload": w.name, "nodes": w.nodes, "levels": w.levels},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def run_probe(args):
+    """Short solves of a workload for profiler captures (see the module
+    docstring); --side/--levels select the workload's generator at a smaller
+    grid."""
+    import torch
+    import workloads
+    torch.cuda.set_device(0)
+    if args.side:
+        w = workloads.small_variant(args.config, args.side, args.levels or 4)
+    else:
+        w = _with_overrides(getattr(workloads, args.config)(), args)
+    if isinstance(w, list):
+        w = w[len(w) // 2]
+    from dataclasses import replace
+    w = replace(w, max_iter=args.max_iter)
+    s = make_solver(w, args.precision, nrhs_max=args.nrhs)
+    if args.nrhs > 1:
+        q = torch.tensor(np.ascontiguousarray(w.rhs_block()[:, : args.nrhs]), device="cuda")
+        for _ in range(args.solves):
+            s.solve_batch(q)
+    else:
+        q = torch.tensor(w.rhs(0), device="cuda")
+        for _ in range(args.solves):
+            s.solve(q)
+    torch.cuda.synchronize()
+    s.close()
+    print("probe done", file=sys.stderr)
 
 
 def main():
@@ -852,6 +936,7 @@ def main():
     ap.add_argument("--config", default="config2")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the second (3D) workload of the default run")
     ap.add_argument("--cpu-iters", type=int, default=25)
     ap.add_argument("--ref-iters-per-step", type=int, default=5)
     ap.add_argument("--requests", type=int, default=100, help="config5: requests in the stream")
@@ -864,7 +949,16 @@ def main():
     ap.add_argument("--patch", default=None, help="override the fine-level Vanka patch")
     ap.add_argument("--patch-coarse", default=None, help="patch on the coarse levels (default: the fine one)")
     ap.add_argument("--intergrid", default=None, help="override the intergrid scheme")
+    ap.add_argument("--probe", action="store_true", help="short solves for profiler captures (no JSON line)")
+    ap.add_argument("--side", type=int, default=0, help="--probe: the workload's generator at this grid side")
+    ap.add_argument("--solves", type=int, default=2, help="--probe: solves to run")
+    ap.add_argument("--max-iter", type=int, default=10, help="--probe: FGMRES iterations per solve")
+    ap.add_argument("--precision", default="mixed", help="--probe: mixed or fp64")
+    ap.add_argument("--nrhs", type=int, default=1, help="--probe: right-hand sides per solve")
     args = ap.parse_args()
+    if args.probe:
+        run_probe(args)
+        return
     if args.impl == "reference":
         out = run_reference(args)
     elif args.config == "config4":

@@ -325,6 +325,14 @@ hz_status hz_measure_peak(int kind, double* tflops, double* ms);
  * Level fields are device arrays in the context's V-cycle precision (c128
  * for HZ_PREC_FP64, c64 for HZ_PREC_MIXED) of the level's node count. */
 
+/* Device memory in use, for tests and monitoring (no counterpart in the
+ * paper).  *pool_used_bytes: bytes currently in use in the default
+ * stream-ordered pool of `device` (every context allocates from it);
+ * *device_allocations: device allocations the library has made in this
+ * process so far, all devices.  Either output may be NULL.
+ * HZ_ERR_INVALID_ARG for a bad ordinal; HZ_ERR_NO_DEVICE without a device. */
+hz_status hz_memory_stats(int device, uint64_t* pool_used_bytes, uint64_t* device_allocations);
+
 /* The context's CUDA device ordinal, V-cycle precision (so the element type
  * of level fields: c64 for HZ_PREC_MIXED, c128 for HZ_PREC_FP64) and the
  * widest batch it was set up for; any output pointer may be NULL. */

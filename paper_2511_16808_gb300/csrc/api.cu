@@ -13,6 +13,11 @@ namespace hz {
 
 static thread_local std::string g_last_error;
 
+std::atomic<unsigned long long>& device_alloc_count() {
+  static std::atomic<unsigned long long> n{0};
+  return n;
+}
+
 void set_last_error(const char* msg) {
   if (msg) g_last_error = msg;
   else g_last_error.clear();
@@ -46,7 +51,7 @@ void* ctx_alloc(Ctx& c, size_t bytes, cudaStream_t s) {
   void* p = nullptr;
   if (bytes == 0) bytes = 16;
   keep_pool_memory(c.dev);
-  cudaError_t e = cudaMallocAsync(&p, bytes, s);
+  cudaError_t e = counted_malloc_async(&p, bytes, s);
   if (e != cudaSuccess) {
     (void)cudaGetLastError();
     throw Error(e == cudaErrorMemoryAllocation ? HZ_ERR_OOM : HZ_ERR_CUDA,
@@ -470,6 +475,25 @@ hz_status hz_profile_read(const hz_ctx* ctx, double* total_ms, int64_t* launches
     *launches = c.prof_launches;
     *bytes = c.prof_bytes;
     *flops = c.prof_flops;
+  });
+}
+
+hz_status hz_memory_stats(int device, uint64_t* pool_used_bytes, uint64_t* device_allocations) {
+  return guarded([&] {
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0) {
+      (void)cudaGetLastError();
+      throw Error(HZ_ERR_NO_DEVICE, "no CUDA device");
+    }
+    require(device >= 0 && device < n, "device ordinal out of range");
+    if (pool_used_bytes) {
+      cudaMemPool_t pool;
+      HZ_CUDA(cudaDeviceGetDefaultMemPool(&pool, device));
+      uint64_t used = 0;
+      HZ_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used));
+      *pool_used_bytes = used;
+    }
+    if (device_allocations) *device_allocations = device_alloc_count().load();
   });
 }
 

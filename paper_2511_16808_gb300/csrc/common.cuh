@@ -464,6 +464,18 @@ inline bool level_two_pass_2d(const Ctx& c, int l) {
          c.nrhs == 1 && L.A.off.rho <= (L.a_half ? 2 : 3) && L.Mh.off.rho <= 2;
 }
 
+// Every device allocation of the library goes through counted_malloc_async,
+// which counts them process-wide (hz_memory_stats reports the count).
+std::atomic<unsigned long long>& device_alloc_count();
+inline cudaError_t counted_malloc_async(void** p, size_t bytes, cudaStream_t s) {
+  device_alloc_count().fetch_add(1);
+  return cudaMallocAsync(p, bytes, s);
+}
+template <typename P>
+inline cudaError_t counted_malloc_async(P** p, size_t bytes, cudaStream_t s) {
+  return counted_malloc_async(reinterpret_cast<void**>(p), bytes, s);
+}
+
 // allocation helpers (all device memory of a context goes through these)
 void* ctx_alloc(Ctx& c, size_t bytes);          // stream-ordered, on c.alloc_stream
 void* ctx_alloc(Ctx& c, size_t bytes, cudaStream_t s);

@@ -44,7 +44,7 @@ double measure(int iters, int repeats, double* best_ms) {
   HZ_CUDA(cudaEventCreate(&e0));
   HZ_CUDA(cudaEventCreate(&e1));
   T* out = nullptr;   // written only if the chains ever hit the sentinel
-  HZ_CUDA(cudaMallocAsync((void**)&out, sizeof(T) * blocks * 256, s));
+  HZ_CUDA(counted_malloc_async(&out, sizeof(T) * blocks * 256, s));
   const T b = (T)0.999999, c = (T)1e-4;      // a converges to c / (1 - b) = 100
   float best = 1e30f;
   for (int r = 0; r < repeats + 2; ++r) {     // the first two launches warm up

@@ -506,10 +506,10 @@ static void invert_dense(Ctx& c, Level& L, cudaStream_t s) {
   HZ_LAUNCHED();
   double2* col = nullptr;
   int *piv = nullptr, *perm = nullptr, *sing = nullptr;
-  HZ_CUDA(cudaMallocAsync(&col, sizeof(double2) * n, s));
-  HZ_CUDA(cudaMallocAsync(&piv, sizeof(int) * n, s));
-  HZ_CUDA(cudaMallocAsync(&perm, sizeof(int) * n, s));
-  HZ_CUDA(cudaMallocAsync(&sing, sizeof(int), s));
+  HZ_CUDA(counted_malloc_async(&col, sizeof(double2) * n, s));
+  HZ_CUDA(counted_malloc_async(&piv, sizeof(int) * n, s));
+  HZ_CUDA(counted_malloc_async(&perm, sizeof(int) * n, s));
+  HZ_CUDA(counted_malloc_async(&sing, sizeof(int), s));
   HZ_CUDA(cudaMemsetAsync(sing, 0, sizeof(int), s));
   for (int k = 0; k < n; ++k) {
     k_gj_pivot<<<1, 1024, 0, s>>>(D, (int)n, k, piv, sing);
@@ -552,7 +552,7 @@ static void launch_vanka(Level& L, const PatchDesc& pd, const StencilLut& Mfull,
   const int chunk = (int)std::max<size_t>(1, kSlabBytes / per_plane);     // node planes per slab
   const int span = std::min(ns, chunk + dmax - dmin);
   double2* Hinv = nullptr;
-  HZ_CUDA(cudaMallocAsync(&Hinv, per_plane * span, s));
+  HZ_CUDA(counted_malloc_async(&Hinv, per_plane * span, s));
   for (int n0 = 0; n0 < ns; n0 += chunk) {
     const int n1 = std::min(ns, n0 + chunk);
     // anchors of the patches of nodes n0..n1-1: node - d
@@ -600,13 +600,13 @@ static void assemble_smoother(Ctx& c, Level& L, cudaStream_t s) {
   StencilLut Mfull = make_lut(moffs);
   const long long N = L.g.N;
   double2* Mp = nullptr;
-  HZ_CUDA(cudaMallocAsync(&Mp, sizeof(double2) * N * Mfull.off.n, s));
+  HZ_CUDA(counted_malloc_async(&Mp, sizeof(double2) * N * Mfull.off.n, s));
   HZ_CUDA(cudaMemsetAsync(Mp, 0, sizeof(double2) * N * Mfull.off.n, s));
   int* sing = nullptr;
   unsigned long long* amax = nullptr;
-  HZ_CUDA(cudaMallocAsync(&sing, sizeof(int), s));
+  HZ_CUDA(counted_malloc_async(&sing, sizeof(int), s));
   HZ_CUDA(cudaMemsetAsync(sing, 0, sizeof(int), s));
-  HZ_CUDA(cudaMallocAsync(&amax, sizeof(unsigned long long) * Mfull.off.n, s));
+  HZ_CUDA(counted_malloc_async(&amax, sizeof(unsigned long long) * Mfull.off.n, s));
   HZ_CUDA(cudaMemsetAsync(amax, 0, sizeof(unsigned long long) * Mfull.off.n, s));
   switch (pd.np) {
     case 1: launch_vanka<1>(L, pd, Mfull, Mp, sing, s); break;
@@ -670,7 +670,7 @@ static void assemble_smoother(Ctx& c, Level& L, cudaStream_t s) {
     L.Mh = make_lut(half);
     for (size_t k = 0; k < half.size(); ++k) L.mh_mirror[k] = mirror[k];
     short* dsrc = nullptr;
-    HZ_CUDA(cudaMallocAsync(&dsrc, sizeof(short) * hsrc.size(), s));
+    HZ_CUDA(counted_malloc_async(&dsrc, sizeof(short) * hsrc.size(), s));
     HZ_CUDA(cudaMemcpyAsync(dsrc, hsrc.data(), sizeof(short) * hsrc.size(), cudaMemcpyHostToDevice, s));
     double2* Mh64 = (double2*)ctx_alloc(c, sizeof(double2) * N * half.size());
     double* wc64 = (double*)ctx_alloc(c, sizeof(double) * N);

@@ -432,7 +432,7 @@ extern "C" hz_status hz_lfa_factors(int dim, const double* stencil, hz_patch pat
     } b{s};
     const size_t inv_b = sizeof(double2) * kMaxPatch * kMaxPatch;
     const size_t bytes = inv_b + sizeof(double) * nw + 2 * sizeof(unsigned long long) * nw + 16;
-    HZ_CUDA(cudaMallocAsync(&b.p, bytes, s));
+    HZ_CUDA(counted_malloc_async(&b.p, bytes, s));
     char* base = (char*)b.p;
     double2* inv = (double2*)base;
     double* wd = (double*)(base + inv_b);

@@ -112,6 +112,7 @@ _SIGS = {
     "hz_profile_read": ([_P, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_double),
                          C.POINTER(C.c_double)], C.c_int),
     "hz_measure_peak": ([C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)], C.c_int),
+    "hz_memory_stats": ([C.c_int, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)], C.c_int),
     "hz_context_info": ([_P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
     "hz_level_count": ([_P, C.POINTER(C.c_int)], C.c_int),
     "hz_level_describe": ([_P, C.c_int, C.POINTER(hz_level_desc)], C.c_int),
@@ -335,6 +336,14 @@ def hz_level_export(ctx, level: int, what: int) -> np.ndarray:
     out = np.zeros((n, d["nodes"]), dtype=np.complex128)
     _check(lib.hz_level_export(ctx, level, what, out.ctypes.data), "hz_level_export")
     return out
+
+
+def hz_memory_stats(device: int = 0) -> dict:
+    """{"pool_used_bytes", "device_allocations"}: bytes in use in the device's
+    default stream-ordered pool and the library's device allocations so far."""
+    used, n = C.c_uint64(), C.c_uint64()
+    _check(lib.hz_memory_stats(device, C.byref(used), C.byref(n)), "hz_memory_stats")
+    return {"pool_used_bytes": used.value, "device_allocations": n.value}
 
 
 def hz_context_info(ctx) -> dict:
