@@ -378,6 +378,16 @@ hz_status hz_level_restrict(hz_ctx* ctx, int level, const void* r, void* fc, voi
 hz_status hz_level_prolong_add(hz_ctx* ctx, int level, const void* ec, void* u, void* cuda_stream);
 /* u = (A_s^L)^{-1} f on the coarsest level L (dense inverse from setup). */
 hz_status hz_coarse_solve(hz_ctx* ctx, const void* f, void* u, void* cuda_stream);
+/* U = (A_s^L)^{-1} F for nrhs right-hand sides (a power of two <= nrhs_max;
+ * fields node-major, RHS innermost, in the V-cycle precision) with a chosen
+ * variant of the product (Algorithm 1 step 3 at a batch width):
+ *   variant 0   CUDA-core complex GEMM;
+ *   variant s   (1 <= s <= 8) tcgen05 tensor cores, tf32 with the 3xTF32 split
+ *               and FP32 accumulation, K split over s CTAs per row tile
+ *               (mixed precision and nrhs = 16, 32 or 64 only);
+ *   variant -1  the context's current choice (hz_autotune, else the default).
+ * HZ_ERR_INVALID_ARG for a variant the context cannot run. */
+hz_status hz_coarse_solve_batch(hz_ctx* ctx, const void* f, void* u, int nrhs, int variant, void* cuda_stream);
 
 /* ---- per-solve metrics -------------------------------------------------- */
 

@@ -627,6 +627,33 @@ hz_status hz_coarse_solve(hz_ctx* ctx, const void* f, void* u, void* cuda_stream
   });
 }
 
+hz_status hz_coarse_solve_batch(hz_ctx* ctx, const void* f, void* u, int nrhs, int variant, void* cuda_stream) {
+  return guarded([&] {
+    require(ctx && f && u, "null argument");
+    Ctx& c = ctx->c;
+    require(nrhs >= 1 && nrhs <= c.opts.nrhs_max && (nrhs & (nrhs - 1)) == 0,
+            "nrhs must be a power of two <= nrhs_max (and <= 64)");
+    require(variant >= -1 && variant <= kTcMaxSplit, "variant must be -1, 0 or a split of 1..8");
+    require(variant <= 0 || coarse_tc_supported(c, nrhs),
+            "tensor-core variant: mixed precision and 16, 32 or 64 right-hand sides");
+    BusyGuard bg(&c);
+    int lg = 0;
+    while ((1 << lg) < nrhs) ++lg;
+    const int keep = c.coarse_variant[lg];
+    if (variant >= 0) c.coarse_variant[lg] = variant;
+    c.nrhs = nrhs;
+    try {
+      coarse_solve(c, f, u, nullptr, (cudaStream_t)cuda_stream);
+    } catch (...) {
+      c.coarse_variant[lg] = keep;
+      c.nrhs = 1;
+      throw;
+    }
+    c.coarse_variant[lg] = keep;
+    c.nrhs = 1;
+  });
+}
+
 hz_status hz_setup_seconds(const hz_ctx* ctx, double* seconds) {
   return guarded([&] {
     require(ctx && seconds, "null argument");

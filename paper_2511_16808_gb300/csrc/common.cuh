@@ -442,6 +442,13 @@ struct Ctx {
   double prof_ms = 0, prof_bytes = 0, prof_flops = 0;
   long long prof_launches = 0;
   long long launches = 0;       // kernels launched by hz_solve on this context
+  // coarsest solve of a batched cycle on the tensor cores (tc_gemm.cu):
+  // FP32 partial sums of a split K [kTcMaxSplit][2 n][nrhs_max], a device
+  // error word (set if a bounded wait gave up), and the chosen variant per
+  // batch width: 0 CUDA-core GEMM, s >= 1 tensor cores with K split s ways
+  float* tc_partial = nullptr;
+  int* tc_err = nullptr;
+  int coarse_variant[7] = {-1, -1, -1, -1, -1, -1, -1};   // by log2(nrhs); -1: default rule
 };
 
 // Whether a cycle from zero at level l runs the fine level as two fused
@@ -482,6 +489,21 @@ void* ctx_alloc(Ctx& c, size_t bytes, cudaStream_t s);
 void* pinned_small_alloc(size_t bytes);         // <= 4 KB pinned host block (shared arena)
 void pinned_small_free(void* p);
 void ctx_free_all(Ctx& c);
+
+// tc_gemm.cu: coarsest multi-RHS solve on the tensor cores
+constexpr int kTcMaxSplit = 8;
+bool coarse_tc_supported(const Ctx& c, int nrhs);
+void coarse_gemm_tc(Ctx& c, const void* f, void* u, const int* active, cudaStream_t s, int split);
+size_t smem_max_tc();
+// variant of the coarsest solve for the context's current batch width
+// (0: CUDA-core GEMM; s >= 1: tensor cores, K split s ways)
+inline int coarse_variant_for(const Ctx& c, int nrhs) {
+  int lg = 0;
+  while ((1 << lg) < nrhs) ++lg;
+  const int v = lg < 7 ? c.coarse_variant[lg] : -1;
+  if (v >= 0) return v;
+  return coarse_tc_supported(c, nrhs) ? 4 : 0;
+}
 
 // setup.cu
 void build_hierarchy(Ctx& c, const double* kappa_dev, const double* gamma_dev, double gamma0,

@@ -1677,6 +1677,8 @@ void coarse_t(Ctx& c, const void* f, void* u, const int* active, cudaStream_t s)
       launch_pdl(k_dense_gemv<T, 128>, nblk(n, 2), 256, s, n, (const c_t<T>*)L.Ainvw, (const c_t<T>*)f, (c_t<T>*)u,
                  active);
   }
+  else if (c.nrhs >= 16 && std::is_same<T, float>::value && coarse_variant_for(c, c.nrhs) > 0)
+    coarse_gemm_tc(c, f, u, active, s, coarse_variant_for(c, c.nrhs));
   else if (c.nrhs >= 8)
     launch_pdl(k_dense_gemm_rhs<T>, nblk(n, 512 / c.nrhs), 256, s, n, c.nrhs, (const c_t<T>*)L.Ainvw, (const c_t<T>*)f,
                                                                (c_t<T>*)u, active);

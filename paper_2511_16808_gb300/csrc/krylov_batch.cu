@@ -495,6 +495,16 @@ void fgmres_solve_batch(Ctx& c, const double2* q, double2* p, int nrhs, hz_info*
   }
   if (c.mixed) solve_b<float2>(c, q, p, nrhs, info, s);
   else solve_b<double2>(c, q, p, nrhs, info, s);
+  if (c.tc_err) {
+    // a bounded wait of the tensor-core coarsest solve that gave up leaves its
+    // output untouched: report it instead of a result built on it
+    int e = 0;
+    HZ_CUDA(cudaMemcpy(&e, c.tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e) {
+      HZ_CUDA(cudaMemset(c.tc_err, 0, sizeof(int)));
+      throw Error(HZ_ERR_TIMEOUT, "tensor-core coarsest solve: a bounded wait for the MMAs gave up");
+    }
+  }
 }
 
 }  // namespace hz

@@ -123,6 +123,7 @@ _SIGS = {
     "hz_level_restrict": ([_P, C.c_int, _P, _P, _P], C.c_int),
     "hz_level_prolong_add": ([_P, C.c_int, _P, _P, _P], C.c_int),
     "hz_coarse_solve": ([_P, _P, _P, _P], C.c_int),
+    "hz_coarse_solve_batch": ([_P, _P, _P, C.c_int, C.c_int, _P], C.c_int),
     "hz_setup_seconds": ([_P, C.POINTER(C.c_double)], C.c_int),
     "hz_solve_history": ([_P, C.c_int, _P, _P, _P, C.POINTER(C.c_int)], C.c_int),
     "hz_cycle_factor": ([_P, _P, _P, C.c_int, C.c_double, C.c_int, C.POINTER(C.c_double),
@@ -406,6 +407,22 @@ def hz_coarse_solve(ctx, f, u, stream=None):
     last = hz_level_count(ctx) - 1
     _level_fields(ctx, "hz_coarse_solve", f=(f, last), u=(u, last))
     _check(lib.hz_coarse_solve(ctx, _ptr(f), _ptr(u), _stream(stream)), "hz_coarse_solve")
+
+
+def hz_coarse_solve_batch(ctx, f, u, nrhs, variant=-1, stream=None):
+    """U = Ainv F on the coarsest level for nrhs right-hand sides (RHS
+    innermost) with variant 0 (CUDA cores), s in 1..8 (tensor cores, K split s
+    ways) or -1 (the context's choice)."""
+    last = hz_level_count(ctx) - 1
+    info = hz_context_info(ctx)
+    want = "torch.complex64" if info["precision"] == "mixed" else "torch.complex128"
+    nodes = hz_level_describe(ctx, last)["nodes"]
+    for name, t in (("f", f), ("u", u)):
+        if not (hasattr(t, "is_cuda") and t.is_cuda) or str(t.dtype) != want or t.numel() != nodes * nrhs:
+            raise ValueError(f"hz_coarse_solve_batch: {name} must be a CUDA {want} tensor of {nodes * nrhs} values")
+        if not t.is_contiguous():
+            raise ValueError(f"hz_coarse_solve_batch: {name} must be contiguous")
+    _check(lib.hz_coarse_solve_batch(ctx, _ptr(f), _ptr(u), nrhs, variant, _stream(stream)), "hz_coarse_solve_batch")
 
 
 def hz_setup_seconds(ctx) -> float:
