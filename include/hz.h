@@ -389,6 +389,40 @@ hz_status hz_coarse_solve(hz_ctx* ctx, const void* f, void* u, void* cuda_stream
  * HZ_ERR_INVALID_ARG for a variant the context cannot run. */
 hz_status hz_coarse_solve_batch(hz_ctx* ctx, const void* f, void* u, int nrhs, int variant, void* cuda_stream);
 
+/* ---- autotuning of kernel choices --------------------------------------
+ * No counterpart in the paper: these choose how V-cycle steps run on this
+ * GPU, never what they compute.  hz_autotune times every candidate of every
+ * knob of the context for batch width nrhs (a few repetitions between CUDA
+ * events on the context's own level vectors, which it overwrites: call it
+ * between solves), keeps the fastest on the context and reports them all.
+ * Knobs (kind, candidate values = what hz_tune_set takes):
+ *   0  coarsest product (level = coarsest): 0 CUDA-core GEMM, or the tcgen05
+ *      tensor-core GEMM with K split 1, 2, 4 or 8 ways (mixed, nrhs 16..64)
+ *   1  RHS pack of a level's kernels (nrhs >= 4): 1 one value per thread,
+ *      2 packs of 32 bytes per thread
+ *   2  register budget of a level's one-RHS kernels: 0 full occupancy,
+ *      2 two blocks per SM (all of a node's stencil loads in flight)
+ *   3  a small coarse 2D level as two fused tile passes (1) or as five
+ *      separate kernels (0)
+ * Without tuning, fixed rules decide (batch width, level size).  Captured
+ * restart-cycle graphs are dropped so the next solve uses the choices.
+ *   reps      repetitions per candidate (1..1000)
+ *   entries   host array of cap entries (may be NULL when cap = 0)
+ *   n         out: entries produced (may exceed cap) */
+typedef struct {
+  int kind;       /* 0..3 as above */
+  int level;      /* level the knob belongs to */
+  int nrhs;       /* batch width it was timed at */
+  int candidate;  /* candidate value */
+  double us;      /* device time per repetition, microseconds */
+  int chosen;     /* 1 for the candidate kept */
+} hz_tune_entry;
+hz_status hz_autotune(hz_ctx* ctx, int nrhs, int reps, hz_tune_entry* entries, int cap, int* n);
+/* Applies one stored choice (e.g. from a cache of an earlier hz_autotune of
+ * the same level shapes); HZ_ERR_INVALID_ARG for a knob or value that does not
+ * apply to the level. */
+hz_status hz_tune_set(hz_ctx* ctx, int kind, int level, int nrhs, int candidate);
+
 /* ---- per-solve metrics -------------------------------------------------- */
 
 /* Wall time of hz_setup for this context, seconds (host clock around the whole

@@ -116,14 +116,6 @@ void ctx_free_all(Ctx& c) {
 
 namespace {
 
-struct BusyGuard {
-  Ctx* c;
-  explicit BusyGuard(Ctx* ctx) : c(ctx) {
-    int expected = 0;
-    if (!c->busy.compare_exchange_strong(expected, 1)) throw Error(HZ_ERR_BUSY, "context in use");
-  }
-  ~BusyGuard() { c->busy.store(0); }
-};
 
 bool is_device_ptr(const void* p) {
   cudaPointerAttributes a;

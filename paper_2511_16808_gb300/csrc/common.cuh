@@ -377,6 +377,11 @@ struct Level {
   void* r = nullptr;             // residual
   void* t = nullptr;             // pre-smoothed iterate (the post-smoothing writes the output)
   bool m_diag = false;           // assembled Vanka sum is diagonal (Jacobi / RB on 2d+1 points)
+  // kernel choices set by the autotuner (hz_autotune / hz_tune_set); the
+  // defaults follow fixed rules (batch width, level size)
+  int tune_vr = 0;               // RHS pack: 0 rule, 1 one value per thread, 2 packs of 32 bytes
+  int tune_mb = -1;              // one-RHS register budget: -1 rule, 0 occupancy, 2 two blocks per SM
+  int tune_fuse = -1;            // fused tile passes of a small 2D level: -1 rule, 0 off, 1 on
   // coarsest level: dense inverse [N][N] row-major
   double2* Ainv64 = nullptr;
   void* Ainvw = nullptr;
@@ -467,7 +472,7 @@ inline bool fine_two_pass(const Ctx& c, int l) {
 // post-sweep, one right-hand side.
 inline bool level_two_pass_2d(const Ctx& c, int l) {
   const Level& L = c.L[l];
-  return L.g.N <= 70000 && !L.fine && !L.coarsest && !L.m_diag && L.g.dim == 2 && c.opts.nu1 == 1 && c.opts.nu2 == 1 &&
+  return (L.tune_fuse >= 0 ? L.tune_fuse == 1 : L.g.N <= 70000) && !L.fine && !L.coarsest && !L.m_diag && L.g.dim == 2 && c.opts.nu1 == 1 && c.opts.nu2 == 1 &&
          c.nrhs == 1 && L.A.off.rho <= (L.a_half ? 2 : 3) && L.Mh.off.rho <= 2;
 }
 
@@ -482,6 +487,18 @@ template <typename P>
 inline cudaError_t counted_malloc_async(P** p, size_t bytes, cudaStream_t s) {
   return counted_malloc_async(reinterpret_cast<void**>(p), bytes, s);
 }
+
+// One host thread at a time per context: a second concurrent call gets HZ_ERR_BUSY.
+struct BusyGuard {
+  Ctx* c;
+  explicit BusyGuard(Ctx* ctx) : c(ctx) {
+    int expected = 0;
+    if (!c->busy.compare_exchange_strong(expected, 1)) throw Error(HZ_ERR_BUSY, "context in use");
+  }
+  ~BusyGuard() { c->busy.store(0); }
+  BusyGuard(const BusyGuard&) = delete;
+  BusyGuard& operator=(const BusyGuard&) = delete;
+};
 
 // allocation helpers (all device memory of a context goes through these)
 void* ctx_alloc(Ctx& c, size_t bytes);          // stream-ordered, on c.alloc_stream

@@ -1378,22 +1378,27 @@ void with_vr(int nrhs, F&& f) {
 // round trips); MB = 2 allows up to 128 registers, so every coefficient and
 // neighbour load of a node is issued before the first use.
 constexpr long long kIlpNodes = 20000;
+// the two-blocks-per-SM register budget for a one-RHS kernel of level L
+inline bool ilp_level(const Level& L) { return L.tune_mb >= 0 ? L.tune_mb == 2 : L.g.N <= kIlpNodes; }
+
 template <typename T, typename F>
-void with_vr_mb(int nrhs, long long nodes, F&& f) {
-  with_vr<T>(nrhs, [&](auto V) {
-    constexpr int VR = decltype(V)::value;
-    if constexpr (VR == 1) {
-      if (nrhs == 1 && nodes <= kIlpNodes) return f(V, std::integral_constant<int, 2>{});
-    }
-    f(V, std::integral_constant<int, 0>{});
-  });
+void with_vr_mb(const Level& L, int nrhs, long long nodes, F&& f) {
+  // RHS pack: the level's autotuned choice (hz_autotune), else packs of 32
+  // bytes per thread once there are enough right-hand sides
+  const bool pack = L.tune_vr > 0 ? (L.tune_vr == 2 && vr_for(nrhs, kVRMax<T>) == kVRMax<T>)
+                                  : vr_for(nrhs, kVRMax<T>) == kVRMax<T>;
+  // register budget (one right-hand side): the autotuned choice, else by size
+  const bool ilp = nrhs == 1 && (L.tune_mb >= 0 ? L.tune_mb == 2 : nodes <= kIlpNodes);
+  if (pack) f(std::integral_constant<int, kVRMax<T>>{}, std::integral_constant<int, 0>{});
+  else if (ilp) f(std::integral_constant<int, 1>{}, std::integral_constant<int, 2>{});
+  else f(std::integral_constant<int, 1>{}, std::integral_constant<int, 0>{});
 }
 
 template <typename T>
 void resid(Ctx& c, int l, const void* u, const void* f, void* r, const int* active, cudaStream_t s) {
   Level& L = c.L[l];
   const T invh2 = (T)(1.0 / (c.h * c.h));
-  with_vr_mb<T>(c.nrhs, L.g.N, [&](auto V, auto MBc) {
+  with_vr_mb<T>(L, c.nrhs, L.g.N, [&](auto V, auto MBc) {
     constexpr int VR = decltype(V)::value;
     constexpr int MB = decltype(MBc)::value;
     const Geo g = geo(L.g, c.nrhs, VR);
@@ -1408,7 +1413,7 @@ void resid(Ctx& c, int l, const void* u, const void* f, void* r, const int* acti
 template <typename T>
 void sweep_out(Ctx& c, int l, const void* r, const void* in, void* out, const int* active, cudaStream_t s) {
   Level& L = c.L[l];
-  with_vr_mb<T>(c.nrhs, L.g.N, [&](auto V, auto MBc) {
+  with_vr_mb<T>(L, c.nrhs, L.g.N, [&](auto V, auto MBc) {
     constexpr int VR = decltype(V)::value;
     constexpr int MB = decltype(MBc)::value;
     const Geo g = geo(L.g, c.nrhs, VR);
@@ -1430,7 +1435,7 @@ void sweep_out(Ctx& c, int l, const void* r, const void* in, void* out, const in
 template <typename T>
 void sweep0(Ctx& c, int l, const void* f, void* u, const int* active, cudaStream_t s) {
   Level& L = c.L[l];
-  with_vr_mb<T>(c.nrhs, L.g.N, [&](auto V, auto MBc) {
+  with_vr_mb<T>(L, c.nrhs, L.g.N, [&](auto V, auto MBc) {
     constexpr int VR = decltype(V)::value;
     constexpr int MB = decltype(MBc)::value;
     const Geo g = geo(L.g, c.nrhs, VR);
@@ -1452,7 +1457,7 @@ template <typename T>
 void sweep0_resid_diag(Ctx& c, int l, const void* f, void* u, void* r, const int* active, cudaStream_t s) {
   Level& L = c.L[l];
   const T invh2 = (T)(1.0 / (c.h * c.h));
-  with_vr_mb<T>(c.nrhs, L.g.N, [&](auto V, auto MBc) {
+  with_vr_mb<T>(L, c.nrhs, L.g.N, [&](auto V, auto MBc) {
     constexpr int VR = decltype(V)::value;
     constexpr int MB = decltype(MBc)::value;
     const Geo g = geo(L.g, c.nrhs, VR);
@@ -1468,7 +1473,7 @@ template <typename T>
 void resid_sweep_diag(Ctx& c, int l, const void* f, const void* in, void* out, const int* active, cudaStream_t s) {
   Level& L = c.L[l];
   const T invh2 = (T)(1.0 / (c.h * c.h));
-  with_vr_mb<T>(c.nrhs, L.g.N, [&](auto V, auto MBc) {
+  with_vr_mb<T>(L, c.nrhs, L.g.N, [&](auto V, auto MBc) {
     constexpr int VR = decltype(V)::value;
     constexpr int MB = decltype(MBc)::value;
     const Geo g = geo(L.g, c.nrhs, VR);
@@ -1484,7 +1489,7 @@ template <typename T>
 void restrict_t(Ctx& c, int l, const void* r, void* fc, const int* active, cudaStream_t s) {
   Level& L = c.L[l];
   Level& C = c.L[l + 1];
-  with_vr_mb<T>(c.nrhs, C.g.N, [&](auto V, auto MBc) {
+  with_vr_mb<T>(L, c.nrhs, C.g.N, [&](auto V, auto MBc) {
     constexpr int VR = decltype(V)::value;
     constexpr int MB = decltype(MBc)::value;
     const Geo gf = geo(L.g, c.nrhs, VR), gc = geo(C.g, c.nrhs, VR);
@@ -1506,7 +1511,7 @@ template <typename T>
 void prolong_t(Ctx& c, int l, const void* ec, const void* in, void* out, const int* active, cudaStream_t s) {
   Level& L = c.L[l];
   Level& C = c.L[l + 1];
-  with_vr_mb<T>(c.nrhs, L.g.N, [&](auto V, auto MBc) {
+  with_vr_mb<T>(L, c.nrhs, L.g.N, [&](auto V, auto MBc) {
     constexpr int VR = decltype(V)::value;
     constexpr int MB = decltype(MBc)::value;
     const Geo gf = geo(L.g, c.nrhs, VR), gc = geo(C.g, c.nrhs, VR);
@@ -1539,7 +1544,7 @@ void prolong_fused_2d(Ctx& c, int l, const void* ec, const void* t, const void* 
                  invh2, (const c_t<T>*)L.Aw, (const c_t<T>*)ec, (const c_t<T>*)t, (const c_t<T>*)f,
                  (const c_t<T>*)L.Mw, (T)L.damping, (c_t<T>*)out, (c_t<T>*)r, active);
     };
-    if (L.g.N <= kIlpNodes) launch(std::integral_constant<int, 2>{});
+    if (ilp_level(L)) launch(std::integral_constant<int, 2>{});
     else launch(std::integral_constant<int, 0>{});
   };
   using K0 = std::integral_constant<int, 0>;
@@ -1570,7 +1575,7 @@ void fine_down_diag(Ctx& c, const void* f, void* fc, const int* active, cudaStre
                invh2, (const c_t<T>*)L.Aw, (const c_t<T>*)L.Mw, (T)L.damping, (const c_t<T>*)f, (c_t<T>*)fc, active);
   };
   auto mb = [&](auto RK) {
-    if (L.g.N <= kIlpNodes) go(RK, std::integral_constant<int, 2>{});
+    if (ilp_level(L)) go(RK, std::integral_constant<int, 2>{});
     else go(RK, std::integral_constant<int, 0>{});
   };
   if (L.rkind) mb(std::integral_constant<int, 1>{});
@@ -1592,7 +1597,7 @@ void fine_up_diag(Ctx& c, const void* ec, const void* f, void* out, const int* a
                (c_t<T>*)out, active);
   };
   auto mb = [&](auto PK) {
-    if (L.g.N <= kIlpNodes) go(PK, std::integral_constant<int, 2>{});
+    if (ilp_level(L)) go(PK, std::integral_constant<int, 2>{});
     else go(PK, std::integral_constant<int, 0>{});
   };
   if (L.pkind) mb(std::integral_constant<int, 1>{});

@@ -86,6 +86,11 @@ class hz_server_counters(C.Structure):
                 ("kernel_launches", C.c_int64)]
 
 
+class hz_tune_entry(C.Structure):
+    _fields_ = [("kind", C.c_int), ("level", C.c_int), ("nrhs", C.c_int), ("candidate", C.c_int),
+                ("us", C.c_double), ("chosen", C.c_int)]
+
+
 class HzError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
@@ -123,6 +128,8 @@ _SIGS = {
     "hz_level_restrict": ([_P, C.c_int, _P, _P, _P], C.c_int),
     "hz_level_prolong_add": ([_P, C.c_int, _P, _P, _P], C.c_int),
     "hz_coarse_solve": ([_P, _P, _P, _P], C.c_int),
+    "hz_autotune": ([_P, C.c_int, C.c_int, C.POINTER(hz_tune_entry), C.c_int, C.POINTER(C.c_int)], C.c_int),
+    "hz_tune_set": ([_P, C.c_int, C.c_int, C.c_int, C.c_int], C.c_int),
     "hz_coarse_solve_batch": ([_P, _P, _P, C.c_int, C.c_int, _P], C.c_int),
     "hz_setup_seconds": ([_P, C.POINTER(C.c_double)], C.c_int),
     "hz_solve_history": ([_P, C.c_int, _P, _P, _P, C.POINTER(C.c_int)], C.c_int),
@@ -423,6 +430,24 @@ def hz_coarse_solve_batch(ctx, f, u, nrhs, variant=-1, stream=None):
         if not t.is_contiguous():
             raise ValueError(f"hz_coarse_solve_batch: {name} must be contiguous")
     _check(lib.hz_coarse_solve_batch(ctx, _ptr(f), _ptr(u), nrhs, variant, _stream(stream)), "hz_coarse_solve_batch")
+
+
+TUNE_KINDS = {0: "coarsest product", 1: "RHS pack", 2: "register budget", 3: "fused tile passes"}
+
+
+def hz_autotune(ctx, nrhs: int = 1, reps: int = 10) -> list:
+    """Times every candidate kernel choice for batch width nrhs and keeps the
+    fastest on the context; returns one dict per candidate."""
+    n = C.c_int()
+    cap = 4 * MAX_LEVELS + 8                 # at most 3 knobs per level plus the coarsest's 5 candidates
+    buf = (hz_tune_entry * (2 * cap))()
+    _check(lib.hz_autotune(ctx, nrhs, reps, buf, 2 * cap, C.byref(n)), "hz_autotune")
+    return [{"kind": e.kind, "knob": TUNE_KINDS.get(e.kind, e.kind), "level": e.level, "nrhs": e.nrhs,
+             "candidate": e.candidate, "us": e.us, "chosen": bool(e.chosen)} for e in buf[: n.value]]
+
+
+def hz_tune_set(ctx, kind: int, level: int, nrhs: int, candidate: int) -> None:
+    _check(lib.hz_tune_set(ctx, kind, level, nrhs, candidate), "hz_tune_set")
 
 
 def hz_setup_seconds(ctx) -> float:

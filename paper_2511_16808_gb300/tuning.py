@@ -83,3 +83,52 @@ def damping_search(dim, n, kappa, omega, gamma, alpha, levels, level, candidates
         table.append((float(w), cf))
     best = min(table, key=lambda t: t[1])
     return best[0], table
+
+
+# ---- kernel-choice autotuning (no counterpart in the paper) ----------------
+
+def tune_key(solver: HelmholtzSolver, nrhs: int) -> str:
+    """Cache key of a context's tunable shape: device name, V-cycle precision,
+    batch width, and per level the grid, operator and smoother stencil sizes
+    and patch (what the kernel choices depend on; not the medium)."""
+    import json
+    import torch
+    info = hz.hz_context_info(solver.ctx)
+    levels = []
+    for l in range(hz.hz_level_count(solver.ctx)):
+        d = hz.hz_level_describe(solver.ctx, l)
+        levels.append([list(d["n"]), len(d["stencil"]), len(d["smoother"]), d["patch"], d["is_coarsest"]])
+    return json.dumps({"device": torch.cuda.get_device_name(info["device"]), "precision": info["precision"],
+                       "nrhs": nrhs, "levels": levels}, sort_keys=True)
+
+
+def autotune(solver: HelmholtzSolver, nrhs: int = 1, reps: int = 10, cache: str | None = None, log=print):
+    """Kernel choices for `solver` at batch width nrhs: taken from the JSON
+    cache file when it holds this shape (applied with hz_tune_set), else timed
+    by hz_autotune, logged candidate by candidate and stored in the cache.
+    Returns (entries, from_cache)."""
+    import json
+    import os
+    key = tune_key(solver, nrhs)
+    table = {}
+    if cache and os.path.exists(cache):
+        with open(cache) as f:
+            table = json.load(f)
+    if key in table:
+        entries = table[key]
+        for e in entries:
+            if e["chosen"]:
+                hz.hz_tune_set(solver.ctx, e["kind"], e["level"], e["nrhs"], e["candidate"])
+        return entries, True
+    entries = hz.hz_autotune(solver.ctx, nrhs, reps)
+    if log:
+        for e in entries:
+            log(f"autotune level {e['level']} {e['knob']:>17} candidate {e['candidate']}: "
+                f"{e['us']:9.2f} us{'  <- chosen' if e['chosen'] else ''}")
+    if cache:
+        table[key] = entries
+        tmp = cache + ".tmp"
+        with open(tmp, "w") as f:
+            json.dump(table, f, indent=1)
+        os.replace(tmp, cache)
+    return entries, False
