@@ -215,6 +215,19 @@ def oracle_agreement(name, p):
             "oracle_iters": g["iters"], "samples": int(len(idx))}
 
 
+def tune(solver, nrhs, args):
+    """Autotune the solver's kernel choices before anything is timed (part of
+    set-up, like building the hierarchy); returns the chosen candidates."""
+    if args.no_autotune:
+        return None
+    from paper_2511_16808_gb300 import tuning
+    entries, _ = tuning.autotune(solver, nrhs, reps=5, cache=None, log=None)
+    return [{"level": e["level"], "knob": e["knob"], "candidate": e["candidate"], "us": round(e["us"], 2),
+             "others_us": [round(o["us"], 2) for o in entries
+                           if (o["kind"], o["level"]) == (e["kind"], e["level"]) and not o["chosen"]]}
+            for e in entries if e["chosen"]]
+
+
 def time_solves(torch, solver, q, p, steps, stream):
     """Device time (ms) of `steps` consecutive solves with CUDA events on the launching stream."""
     from paper_2511_16808_gb300 import hz
@@ -377,6 +390,7 @@ def extra_workload(name, args, stream):
     w = getattr(__import__("workloads"), name)()
     peak, src = _peaks()
     solver = make_solver(w, "mixed", stream)
+    tuned = tune(solver, 1, args)
     q = torch.tensor(w.rhs(0), device="cuda")
     p = torch.empty_like(q)
     solver.solve(q, p)
@@ -394,7 +408,7 @@ def extra_workload(name, args, stream):
     out = {"workload": w.name, "nodes": w.nodes, "levels": w.levels, "patch": w.patch,
            "patch_coarse": w.patch_coarse or w.patch, "intergrid": w.intergrid, "alpha": w.alpha,
            "value": steps / (ms / 1e3), "unit": UNIT, "ms_per_solve": ms / steps, "steps": steps,
-           "iters": infos[-1].iters, "relres_true": infos[-1].relres_true,
+           "iters": infos[-1].iters, "relres_true": infos[-1].relres_true, "autotune": tuned,
            "vcycle_roofline": {"bound": "hbm", "achieved": v_gbs, "peak": peak, "unit": "GB/s",
                                "frac": v_gbs / peak if v_gbs else None, "peak_source": src,
                                "avg_vcycle_us": vprof["ms"] * 1e3 / max(vprof["launches"], 1)}}
@@ -424,6 +438,7 @@ def run_ours(args):
     if rank == 0:
         fp64_peak()                  # measured before the timed regions
     solver = make_solver(w, "mixed", stream)
+    tuned = tune(solver, 1, args)
     q = torch.tensor(w.rhs(0), device="cuda")
     p = torch.empty_like(q)
     for _ in range(args.warmup):
@@ -547,6 +562,7 @@ def run_ours(args):
             "gpu_launches": launches,
             "peak_source": src,
             "vanka_dof_per_s": vdofs,
+            "autotune": tuned,
             "err_vs_oracle": agree,
         }
         if args.config == "config2" and not args.no_extra:
@@ -597,6 +613,7 @@ def run_batched(args):
     if rank == 0:
         fp64_peak()                  # measured before the timed regions
     solvers = [make_solver(w, "mixed", stream, nrhs_max=R) for w in ws]
+    tuned = [tune(sv, R, args) for sv in solvers]
     Qs = [torch.tensor(w.rhs_block(), device="cuda") for w in ws]
     Ps = [torch.empty_like(Q) for Q in Qs]
 
@@ -727,6 +744,7 @@ def run_batched(args):
             "gpu_launches": launches,
             "peak_source": src,
             "vanka_dof_per_s": vdofs,
+            "autotune": tuned[0],
         }
     for sv in solvers:
         sv.close()
@@ -936,6 +954,7 @@ def main():
     ap.add_argument("--config", default="config2")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the fixed kernel-choice rules")
     ap.add_argument("--no-extra", action="store_true", help="skip the second (3D) workload of the default run")
     ap.add_argument("--cpu-iters", type=int, default=25)
     ap.add_argument("--ref-iters-per-step", type=int, default=5)

@@ -397,7 +397,7 @@ hz_status hz_coarse_solve_batch(hz_ctx* ctx, const void* f, void* u, int nrhs, i
  * between solves), keeps the fastest on the context and reports them all.
  * Knobs (kind, candidate values = what hz_tune_set takes):
  *   0  coarsest product (level = coarsest): 0 CUDA-core GEMM, or the tcgen05
- *      tensor-core GEMM with K split 1, 2, 4 or 8 ways (mixed, nrhs 16..64)
+ *      tensor-core GEMM with K split 1, 2, 4, 8 or 16 ways (mixed, nrhs 16..64)
  *   1  RHS pack of a level's kernels (nrhs >= 4): 1 one value per thread,
  *      2 packs of 32 bytes per thread
  *   2  register budget of a level's one-RHS kernels: 0 full occupancy,

@@ -625,7 +625,7 @@ hz_status hz_coarse_solve_batch(hz_ctx* ctx, const void* f, void* u, int nrhs, i
     Ctx& c = ctx->c;
     require(nrhs >= 1 && nrhs <= c.opts.nrhs_max && (nrhs & (nrhs - 1)) == 0,
             "nrhs must be a power of two <= nrhs_max (and <= 64)");
-    require(variant >= -1 && variant <= kTcMaxSplit, "variant must be -1, 0 or a split of 1..8");
+    require(variant >= -1 && variant <= kTcMaxSplit, "variant must be -1, 0 or a split of 1..16");
     require(variant <= 0 || coarse_tc_supported(c, nrhs),
             "tensor-core variant: mixed precision and 16, 32 or 64 right-hand sides");
     BusyGuard bg(&c);

@@ -448,10 +448,13 @@ struct Ctx {
   long long prof_launches = 0;
   long long launches = 0;       // kernels launched by hz_solve on this context
   // coarsest solve of a batched cycle on the tensor cores (tc_gemm.cu):
-  // FP32 partial sums of a split K [kTcMaxSplit][2 n][nrhs_max], a device
-  // error word (set if a bounded wait gave up), and the chosen variant per
-  // batch width: 0 CUDA-core GEMM, s >= 1 tensor cores with K split s ways
+  // FP32 partial sums of a split K [kTcMaxSplit][n][2 nrhs_max], operand
+  // images, a device error word (set if a bounded wait gave up), and the
+  // chosen variant per batch width: 0 CUDA-core GEMM, s >= 1 tensor cores
+  // with K split s ways
   float* tc_partial = nullptr;
+  float* tc_image = nullptr;    // split tf32 image of the real form of the coarsest inverse
+  float* tc_fimg = nullptr;     // split image of the right-hand sides of one product
   int* tc_err = nullptr;
   int coarse_variant[7] = {-1, -1, -1, -1, -1, -1, -1};   // by log2(nrhs); -1: default rule
 };
@@ -508,10 +511,11 @@ void pinned_small_free(void* p);
 void ctx_free_all(Ctx& c);
 
 // tc_gemm.cu: coarsest multi-RHS solve on the tensor cores
-constexpr int kTcMaxSplit = 8;
+constexpr int kTcMaxSplit = 16;
 bool coarse_tc_supported(const Ctx& c, int nrhs);
 void coarse_gemm_tc(Ctx& c, const void* f, void* u, const int* active, cudaStream_t s, int split);
-size_t smem_max_tc();
+void coarse_tc_alloc(Ctx& c);                       // buffers and the inverse's image (mixed, nrhs_max >= 16)
+size_t coarse_tc_bytes(long long n, int nrhs_max);  // their size, for admission
 // variant of the coarsest solve for the context's current batch width
 // (0: CUDA-core GEMM; s >= 1: tensor cores, K split s ways)
 inline int coarse_variant_for(const Ctx& c, int nrhs) {

@@ -676,7 +676,7 @@ size_t krylov_bytes(const hz_grid& g, const hz_opts& o) {
   if (o.precision == HZ_PREC_MIXED && R >= 16) {
     long long nc = 1;
     for (int a = 0; a < g.dim; ++a) nc *= (g.n[a] - 1) / (1 << (o.levels - 1)) + 1;
-    tc = sizeof(float) * (size_t)kTcMaxSplit * 2 * nc * R + 16;
+    tc = coarse_tc_bytes(nc, (int)R);
   }
   return (16ull * N * (m + 1) + vb * N * m + 16ull * N * 4) * R + 16ull * nb + sizeof(KrylovState) * R + tc;
 }
@@ -703,12 +703,7 @@ void krylov_alloc(Ctx& c) {
   c.ks = (KrylovState*)ctx_alloc(c, sizeof(KrylovState) * R);
   HZ_CUDA(cudaMemsetAsync(c.ks, 0, sizeof(KrylovState) * R, c.alloc_stream));
   c.n_active = (int*)ctx_alloc(c, sizeof(int));
-  if (c.mixed && R >= 16) {
-    const long long nc = c.L.back().g.N;
-    c.tc_partial = (float*)ctx_alloc(c, sizeof(float) * kTcMaxSplit * 2 * nc * R);
-    c.tc_err = (int*)ctx_alloc(c, sizeof(int));
-    HZ_CUDA(cudaMemsetAsync(c.tc_err, 0, sizeof(int), c.alloc_stream));
-  }
+  coarse_tc_alloc(c);
   c.ks_host = pinned_small_alloc(sizeof(KrylovStatus) * R);
   HZ_CUDA(cudaStreamCreateWithFlags(&c.graph_stream, cudaStreamNonBlocking));
   HZ_CUDA(cudaEventCreateWithFlags(&c.ev_in, cudaEventDisableTiming));

@@ -1,170 +1,209 @@
 // Coarsest-level solve of a multi-RHS V-cycle on the tensor cores (Algorithm
 // 1 step 3, exact solve by the dense inverse from setup): U = Ainv F with R
 // right-hand sides (R = 16, 32 or 64), complex FP32 data, as one real GEMM
+// with the complex structure on the small operand:
 //
-//   C' (2n x R) = A' (2n x 2n) F' (2n x R),   A'[2i+a][2j+b] = [[Ar, -Ai], [Ai, Ar]]_ab,
-//                                             F'[2j+b][r] = (Fr, Fi)_b,  C'[2i+a][r] = (Ur, Ui)_a
+//   [Ur | Ui] (n x 2R) = [Ar Ai interleaved] (n x 2n) B (2n x 2R),
+//   B[2j][r] = Fr, B[2j][R+r] = Fi, B[2j+1][r] = -Fi, B[2j+1][R+r] = Fr   (F = F[j][r])
 //
-// on tcgen05 (kind::tf32, FP32 accumulation in tensor memory) with the
-// 3xTF32 split: x = x_hi + x_lo with both parts tf32, x y ~ x_hi y_hi +
-// x_hi y_lo + x_lo y_hi (relative error about 2^-22, at the level of the
-// FP32 CUDA-core product it replaces).  A CTA of 128 threads owns 128 rows of
-// C' (64 complex rows) and all R columns; K is walked in chunks of 32 (16
-// complex columns) staged by all threads in shared memory (double buffered:
-// the next chunk is loaded while the tensor core works on the current one);
-// one thread issues the 12 MMAs of a chunk and commits them to the buffer's
-// mbarrier.  With a split of K over S CTAs per row tile, each writes FP32
-// partial sums and a second kernel adds them in split order (deterministic).
+// so the inverse enters as it is stored (each complex entry two reals, no
+// duplication), on tcgen05 (kind::tf32, FP32 accumulation in tensor memory)
+// with the 3xTF32 split: x = x_hi + x_lo with both parts tf32, x y ~ x_hi y_hi
+// + x_hi y_lo + x_lo y_hi (relative error about 2^-22, at the level of the
+// FP32 CUDA-core product it replaces).
+//
+// Operand images.  The inverse never changes after setup, so its split halves
+// are written once, tile by tile, in the exact shared-memory layout the MMA
+// reads (K-major, no swizzle; tc_ops.cuh): block (row tile t, K chunk c) =
+// 128 rows x 32 real columns of hi, then of lo, 32 KB contiguous.  B is
+// written the same way by a small kernel before each product (2R rows x 32
+// columns per chunk).  The product kernel moves whole blocks with bulk
+// copies (the TMA's non-tensor form) into a ring of shared-memory stages,
+// counted on one mbarrier per stage; one thread drives the ring and issues the
+// 12 MMAs of a chunk (4 K-steps x 3 split products), whose commit frees the
+// stage.  A CTA owns one tile of 128 complex rows and all 2R columns; with K
+// split s ways the CTAs of a tile write FP32 partial sums that a second kernel
+// adds in split order (deterministic).
 #include "common.cuh"
 #include "tc_ops.cuh"
 
 namespace hz {
 namespace {
 
-constexpr int kTcThreads = 128, kTcM = 128, kTcK = 32;
-constexpr long long kTcWaitPolls = 20000000LL;    // ~a second or more of polling: far beyond any MMA
+constexpr int kTcThreads = 128, kTcM = 128, kTcK = 32, kStages = 3;
+constexpr int kTileFloats = kTcM * kTcK;                       // one 16 KB operand tile of the inverse
+constexpr long long kTcWaitPolls = 20000000LL;                 // seconds of polling: far beyond any copy or MMA
+constexpr int kTcMaxN = 4096;                                  // coarsest sizes given an image (<= 134 MB)
 
-__host__ __device__ inline size_t tc_buffer_bytes(int R) { return 2 * (size_t)kTcM * kTcK * 4 + 2 * (size_t)R * kTcK * 4; }
+__host__ __device__ inline int tc_chunks(int n) { return (n + 15) / 16; }      // 32 real columns = 16 complex
+__host__ __device__ inline int tc_tiles(int n) { return (n + kTcM - 1) / kTcM; }
+__host__ __device__ inline uint32_t tc_fblock_bytes(int R) { return 2u * (uint32_t)(2 * R) * kTcK * 4u; }
+__host__ __device__ inline uint32_t tc_stage_bytes(int R) { return 2u * kTileFloats * 4u + tc_fblock_bytes(R); }
 
-__global__ void __launch_bounds__(kTcThreads) k_coarse_gemm_tc(int n, int R, int split, const float2* __restrict__ A,
-                                                               const float2* __restrict__ F, float* __restrict__ part,
-                                                               float2* __restrict__ U, int* err, const int* active) {
+// the split image of the inverse viewed as n x 2n reals: one thread per
+// (tile, chunk, row, column)
+__global__ void k_build_a_image(int n, const float2* __restrict__ A, float* __restrict__ img) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long per = (long long)kTcM * kTcK;
+  const long long total = (long long)tc_tiles(n) * tc_chunks(n) * per;
+  if (e >= total) return;
+  const long long blk = e / per;
+  const int w = (int)(e - blk * per), m = w / kTcK, k = w - m * kTcK;
+  const int t = (int)(blk / tc_chunks(n)), c = (int)(blk - (long long)t * tc_chunks(n));
+  const int i = t * kTcM + m, gk = c * kTcK + k, j = gk >> 1;
+  float x = 0.f;
+  if (i < n && j < n) {
+    const float2 v = A[(long long)i * n + j];
+    x = (gk & 1) ? v.y : v.x;
+  }
+  const float hi = tc::tf32_rna(x), lo = tc::tf32_rna(x - hi);
+  float* base = img + blk * 2 * per;
+  const int off = tc::kmajor_offset<kTcK>(m, k) / 4;
+  base[off] = hi;
+  base[per + off] = lo;
+}
+
+// the split image of B for R right-hand sides: one thread per (chunk, output
+// column nn < 2R, K column k); row k = 2 lj + b of chunk c multiplies the
+// real (b = 0) or imaginary (b = 1) part of the inverse's column j = 16 c + lj
+__global__ void k_build_f_image(int n, int R, const float2* __restrict__ F, float* __restrict__ img,
+                                const int* active) {
+  pdl_enter();
+  if (active && !*active) return;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long per = (long long)2 * R * kTcK;
+  if (e >= (long long)tc_chunks(n) * per) return;
+  const int c = (int)(e / per), w = (int)(e - (long long)c * per), nn = w / kTcK, k = w - nn * kTcK;
+  const int j = c * 16 + (k >> 1), b = k & 1, r = nn < R ? nn : nn - R;
+  const float2 v = j < n ? F[(long long)j * R + r] : make_float2(0.f, 0.f);
+  // b = 0: (Fr | Fi); b = 1: (-Fi | Fr)
+  const float x = nn < R ? (b ? -v.y : v.x) : (b ? v.x : v.y);
+  const float hi = tc::tf32_rna(x), lo = tc::tf32_rna(x - hi);
+  float* base = img + (long long)c * 2 * per;
+  const int off = tc::kmajor_offset<kTcK>(nn, k) / 4;
+  base[off] = hi;
+  base[per + off] = lo;
+}
+
+__global__ void __launch_bounds__(kTcThreads) k_coarse_gemm_tc(int n, int R, int split, const float* __restrict__ aimg,
+                                                               const float* __restrict__ fimg,
+                                                               float* __restrict__ part, float2* __restrict__ U,
+                                                               int* err, const int* active) {
   extern __shared__ unsigned char smraw[];
-  __shared__ uint64_t mbar[2];
+  __shared__ uint64_t full[kStages], empty[kStages];
   __shared__ uint32_t taddr_s;
+  __shared__ int ok_s;
   pdl_enter();
   if (active && !*active) return;
   unsigned char* sm = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const size_t BUF = tc_buffer_bytes(R);
-  const uint32_t cols = R < 32 ? 32u : (uint32_t)R;
+  const uint32_t SB = tc_stage_bytes(R), FB = tc_fblock_bytes(R);
+  const uint32_t cols = (uint32_t)(2 * R);                // 32, 64 or 128 accumulator columns
   const int tile = blockIdx.x, sidx = blockIdx.y;
-  const int nch = (n + 15) / 16;                       // chunks of 16 complex columns
+  const int nch = tc_chunks(n);
   const int per = (nch + split - 1) / split;
-  const int c0 = min(sidx * per, nch), c1 = min(c0 + per, nch);
+  const int c0 = min(sidx * per, nch), c1 = min(c0 + per, nch), nl = c1 - c0;
   if (warp == 0) tc::tmem_alloc(&taddr_s, cols);
   if (tid == 0) {
-    tc::mbar_init(&mbar[0], 1);
-    tc::mbar_init(&mbar[1], 1);
+    for (int s = 0; s < kStages; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], 1);
+    }
+    ok_s = 1;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t taddr = taddr_s;
-  const uint32_t idesc = tc::idesc_tf32(kTcM, R < 16 ? 16 : R);
-  const int i0 = tile * (kTcM / 2);                     // first complex row of the tile
-  bool ok = true;
-  int issued = 0;                                        // chunks whose MMAs were committed
-  for (int c = c0; c < c1; ++c) {
-    const int L = c - c0, b = L & 1;
-    unsigned char* buf = sm + b * BUF;
-    float* a_hi = (float*)buf;
-    float* a_lo = (float*)(buf + kTcM * kTcK * 4);
-    float* b_hi = (float*)(buf + 2 * kTcM * kTcK * 4);
-    float* b_lo = (float*)(buf + 2 * kTcM * kTcK * 4 + R * kTcK * 4);
-    const int j0 = c * 16;
-    // this chunk's A (64 x 16 complex) and F (16 x R complex) values
-    float2 av[8], fv[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int e = tid + q * kTcThreads, li = e >> 4, lj = e & 15;
-      const int i = i0 + li, j = j0 + lj;
-      av[q] = (i < n && j < n) ? A[(long long)i * n + j] : make_float2(0.f, 0.f);
-    }
-    const int nf = 16 * R / kTcThreads;                 // 2, 4 or 8
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      if (q < nf) {
-        const int e = tid + q * kTcThreads, lj = e / R, r = e - lj * R, j = j0 + lj;
-        fv[q] = j < n ? F[(long long)j * R + r] : make_float2(0.f, 0.f);
+  if (tid == 0 && nl > 0) {
+    const uint32_t idesc = tc::idesc_tf32(kTcM, 2 * R);
+    const uint32_t sbo_a = 128 * kTcK / 4, sbo_b = 128 * kTcK / 4;
+    auto load = [&](int L) {                          // chunk c0 + L into stage L % kStages
+      const int st = L % kStages, c = c0 + L;
+      unsigned char* dst = sm + st * SB;
+      tc::mbar_expect_tx(&full[st], SB);
+      tc::bulk_g2s(dst, aimg + ((long long)tile * nch + c) * 2 * kTileFloats, 2 * kTileFloats * 4, &full[st]);
+      tc::bulk_g2s(dst + 2 * kTileFloats * 4, fimg + (long long)c * (FB / 4), FB, &full[st]);
+    };
+    int loaded = 0;                                   // chunks whose copies were issued
+    for (; loaded < kStages && loaded < nl; ++loaded) load(loaded);
+    bool ok = true;
+    int issued = 0;                                   // chunks whose MMAs were committed
+    for (int L = 0; L < nl && ok; ++L) {
+      const int st = L % kStages;
+      const uint32_t ph = (uint32_t)(L / kStages) & 1;
+      if (!tc::mbar_wait(&full[st], ph, kTcWaitPolls)) {
+        ok = false;
+        break;
       }
-    }
-    // the buffer is free once the MMAs of chunk c - 2 completed (the
-    // decision is made by all threads together, so they leave the loop alike)
-    if (L >= 2 && !__syncthreads_and(tc::mbar_wait(&mbar[b], ((L - 2) >> 1) & 1, kTcWaitPolls))) {
-      ok = false;
-      break;
-    }
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int e = tid + q * kTcThreads, li = e >> 4, lj = e & 15;
-      const float ar = av[q].x, ai = av[q].y;
-      const float rh = tc::tf32_rna(ar), rl = tc::tf32_rna(ar - rh);
-      const float ih = tc::tf32_rna(ai), il = tc::tf32_rna(ai - ih);
-      const int m0 = 2 * li, k0 = 2 * lj;
-      *(float*)((unsigned char*)a_hi + tc::kmajor_offset<kTcK>(m0, k0)) = rh;
-      *(float*)((unsigned char*)a_hi + tc::kmajor_offset<kTcK>(m0, k0 + 1)) = -ih;
-      *(float*)((unsigned char*)a_hi + tc::kmajor_offset<kTcK>(m0 + 1, k0)) = ih;
-      *(float*)((unsigned char*)a_hi + tc::kmajor_offset<kTcK>(m0 + 1, k0 + 1)) = rh;
-      *(float*)((unsigned char*)a_lo + tc::kmajor_offset<kTcK>(m0, k0)) = rl;
-      *(float*)((unsigned char*)a_lo + tc::kmajor_offset<kTcK>(m0, k0 + 1)) = -il;
-      *(float*)((unsigned char*)a_lo + tc::kmajor_offset<kTcK>(m0 + 1, k0)) = il;
-      *(float*)((unsigned char*)a_lo + tc::kmajor_offset<kTcK>(m0 + 1, k0 + 1)) = rl;
-    }
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      if (q < nf) {
-        const int e = tid + q * kTcThreads, lj = e / R, r = e - lj * R;
-        const float fr = fv[q].x, fi = fv[q].y;
-        const float rh = tc::tf32_rna(fr), ih = tc::tf32_rna(fi);
-        *(float*)((unsigned char*)b_hi + tc::kmajor_offset<kTcK>(r, 2 * lj)) = rh;
-        *(float*)((unsigned char*)b_hi + tc::kmajor_offset<kTcK>(r, 2 * lj + 1)) = ih;
-        *(float*)((unsigned char*)b_lo + tc::kmajor_offset<kTcK>(r, 2 * lj)) = tc::tf32_rna(fr - rh);
-        *(float*)((unsigned char*)b_lo + tc::kmajor_offset<kTcK>(r, 2 * lj + 1)) = tc::tf32_rna(fi - ih);
-      }
-    }
-    tc::fence_async_smem();
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-    if (tid == 0) {
-      const uint32_t sbo_a = 128 * kTcK / 4, sbo_b = 128 * kTcK / 4;
+      tc::fence_after_sync();
+      const uint32_t a_hi = tc::smem_u32(sm + st * SB), a_lo = a_hi + kTileFloats * 4;
+      const uint32_t b_hi = a_hi + 2 * kTileFloats * 4, b_lo = b_hi + FB / 2;
 #pragma unroll
       for (int k = 0; k < kTcK / 8; ++k) {
-        const uint64_t ah = tc::smem_desc(tc::smem_u32(a_hi) + 256 * k, 128, sbo_a);
-        const uint64_t al = tc::smem_desc(tc::smem_u32(a_lo) + 256 * k, 128, sbo_a);
-        const uint64_t bh = tc::smem_desc(tc::smem_u32(b_hi) + 256 * k, 128, sbo_b);
-        const uint64_t bl = tc::smem_desc(tc::smem_u32(b_lo) + 256 * k, 128, sbo_b);
+        const uint64_t ah = tc::smem_desc(a_hi + 256 * k, 128, sbo_a);
+        const uint64_t al = tc::smem_desc(a_lo + 256 * k, 128, sbo_a);
+        const uint64_t bh = tc::smem_desc(b_hi + 256 * k, 128, sbo_b);
+        const uint64_t bl = tc::smem_desc(b_lo + 256 * k, 128, sbo_b);
         tc::mma_tf32(taddr, ah, bh, idesc, L > 0 || k > 0);
         tc::mma_tf32(taddr, ah, bl, idesc, true);
         tc::mma_tf32(taddr, al, bh, idesc, true);
       }
-      tc::mma_commit(&mbar[b]);
+      tc::mma_commit(&empty[st]);
+      issued = L + 1;
+      if (L + kStages < nl) {
+        // the stage is refilled once its MMAs have read it
+        if (!tc::mbar_wait(&empty[st], ph, kTcWaitPolls)) {
+          ok = false;
+          break;
+        }
+        load(L + kStages);
+        ++loaded;
+      }
     }
-    ++issued;
+    // every MMA done: the last commit completes after all earlier ones; a
+    // wait that gave up is recorded (after one more bounded wait for the
+    // MMAs in flight) and the result is left alone
+    if (ok && !tc::mbar_wait(&empty[(issued - 1) % kStages], (uint32_t)((issued - 1) / kStages) & 1, kTcWaitPolls))
+      ok = false;
+    if (!ok) {
+      atomicExch(err, 1);
+      if (issued > 0)
+        tc::mbar_wait(&empty[(issued - 1) % kStages], (uint32_t)((issued - 1) / kStages) & 1, kTcWaitPolls);
+      // copies issued but not yet consumed must land before the CTA leaves
+      for (int L = issued; L < loaded; ++L)
+        tc::mbar_wait(&full[L % kStages], (uint32_t)(L / kStages) & 1, kTcWaitPolls);
+      ok_s = 0;
+    }
   }
-  // the last commit completes after every earlier MMA of the CTA
-  const int nl = c1 - c0;
-  if (ok && issued > 0)
-    ok = __syncthreads_and(tc::mbar_wait(&mbar[(issued - 1) & 1], ((issued - 1) >> 1) & 1, kTcWaitPolls));
-  // a wait that gave up: record it, wait once more (bounded) for the MMAs in
-  // flight before the tensor memory is released, and leave the result alone
-  if (!ok) {
-    if (lane == 0) atomicExch(err, 1);
-    if (issued > 0) tc::mbar_wait(&mbar[(issued - 1) & 1], ((issued - 1) >> 1) & 1, kTcWaitPolls);
-  }
-  const int mrow = tile * kTcM + 32 * warp + lane;     // row of C' held by this thread
-  const bool rowok = mrow < 2 * n;
+  tc::fence_before_sync();
+  __syncthreads();
   tc::fence_after_sync();
-  if (ok) {
+  if (ok_s) {
+    const int i = tile * kTcM + 32 * warp + lane;     // complex row held by this thread
+    const bool rowok = i < n;
+    // columns c < R are Re U[i][c], columns R + c are Im U[i][c]
     for (int c = 0; c < R; c += 16) {
-      float v[16];
-      if (nl > 0) tc::tmem_ld16(taddr + ((uint32_t)(32 * warp) << 16) + (uint32_t)c, v);
-      else {
+      float re[16], im[16];
+      if (nl > 0) {
+        tc::tmem_ld16(taddr + ((uint32_t)(32 * warp) << 16) + (uint32_t)c, re);
+        tc::tmem_ld16(taddr + ((uint32_t)(32 * warp) << 16) + (uint32_t)(R + c), im);
+      } else {
 #pragma unroll
-        for (int q = 0; q < 16; ++q) v[q] = 0.f;
+        for (int q = 0; q < 16; ++q) re[q] = im[q] = 0.f;
       }
       if (!rowok) continue;
       if (split == 1) {
-        float* u = (float*)U;
-        const int i = mrow >> 1, a = mrow & 1;
 #pragma unroll
-        for (int q = 0; q < 16; ++q) u[((long long)i * R + c + q) * 2 + a] = v[q];
+        for (int q = 0; q < 16; ++q) U[(long long)i * R + c + q] = make_float2(re[q], im[q]);
       } else {
-        float* pp = part + ((long long)sidx * 2 * n + mrow) * R + c;
+        float* pp = part + ((long long)sidx * n + i) * 2 * R;
 #pragma unroll
-        for (int q = 0; q < 16; ++q) pp[q] = v[q];
+        for (int q = 0; q < 16; ++q) {
+          pp[c + q] = re[q];
+          pp[R + c + q] = im[q];
+        }
       }
     }
   }
@@ -183,8 +222,9 @@ __global__ void k_coarse_gemm_reduce(int n, int R, int split, const float* __res
   const long long i = e / R, r = e - i * R;
   float re = 0.f, im = 0.f;
   for (int s = 0; s < split; ++s) {
-    re += part[((long long)s * 2 * n + 2 * i) * R + r];
-    im += part[((long long)s * 2 * n + 2 * i + 1) * R + r];
+    const float* pp = part + ((long long)s * n + i) * 2 * R;
+    re += pp[r];
+    im += pp[R + r];
   }
   U[e] = make_float2(re, im);
 }
@@ -204,12 +244,36 @@ void launch_smem(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cud
   HZ_CUDA(cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...));
 }
 
+size_t tc_smem(int R) { return 1024 + (size_t)kStages * tc_stage_bytes(R); }
+
 }  // namespace
 
-size_t smem_max_tc() { return 1024 + 2 * tc_buffer_bytes(64); }
-
 bool coarse_tc_supported(const Ctx& c, int nrhs) {
-  return c.mixed && (nrhs == 16 || nrhs == 32 || nrhs == 64) && c.tc_err != nullptr;
+  return c.mixed && (nrhs == 16 || nrhs == 32 || nrhs == 64) && c.tc_err != nullptr && c.tc_image != nullptr &&
+         nrhs <= c.opts.nrhs_max;
+}
+
+size_t coarse_tc_bytes(long long n, int nrhs_max) {
+  if (n > kTcMaxN || nrhs_max < 16) return 0;
+  const size_t img = sizeof(float) * 2 * (size_t)kTileFloats * tc_tiles((int)n) * tc_chunks((int)n);
+  const size_t fimg = (size_t)tc_chunks((int)n) * tc_fblock_bytes(nrhs_max);
+  const size_t part = sizeof(float) * kTcMaxSplit * (size_t)n * 2 * nrhs_max;
+  return img + fimg + part + 256;
+}
+
+void coarse_tc_alloc(Ctx& c) {
+  const Level& L = c.L.back();
+  const int R = c.opts.nrhs_max;
+  if (!c.mixed || R < 16 || L.g.N > kTcMaxN) return;
+  const int n = (int)L.g.N;
+  const long long elems = (long long)tc_tiles(n) * tc_chunks(n) * kTileFloats;
+  c.tc_image = (float*)ctx_alloc(c, sizeof(float) * 2 * elems);
+  c.tc_fimg = (float*)ctx_alloc(c, (size_t)tc_chunks(n) * tc_fblock_bytes(R));
+  c.tc_partial = (float*)ctx_alloc(c, sizeof(float) * kTcMaxSplit * 2 * (size_t)n * R);
+  c.tc_err = (int*)ctx_alloc(c, sizeof(int));
+  HZ_CUDA(cudaMemsetAsync(c.tc_err, 0, sizeof(int), c.alloc_stream));
+  k_build_a_image<<<(unsigned)((elems + 255) / 256), 256, 0, c.alloc_stream>>>(n, (const float2*)L.Ainvw, c.tc_image);
+  HZ_CUDA(cudaGetLastError());
 }
 
 void coarse_gemm_tc(Ctx& c, const void* f, void* u, const int* active, cudaStream_t s, int split) {
@@ -217,16 +281,17 @@ void coarse_gemm_tc(Ctx& c, const void* f, void* u, const int* active, cudaStrea
   const int n = (int)L.g.N, R = c.nrhs;
   require(coarse_tc_supported(c, R), "tensor-core coarsest solve: mixed precision, 16/32/64 right-hand sides");
   require(split >= 1 && split <= kTcMaxSplit, "tensor-core split out of range");
-  require(split == 1 || c.tc_partial != nullptr, "tensor-core split needs the partial-sum buffer");
-  const size_t smem = 1024 + 2 * tc_buffer_bytes(R);
   static bool attr_set[256] = {};
   if (!attr_set[c.dev & 255]) {
-    HZ_CUDA(cudaFuncSetAttribute(k_coarse_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max_tc()));
+    HZ_CUDA(cudaFuncSetAttribute(k_coarse_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem(64)));
     attr_set[c.dev & 255] = true;
   }
-  const dim3 grid((unsigned)((2 * n + kTcM - 1) / kTcM), (unsigned)split);
-  launch_smem(k_coarse_gemm_tc, grid, dim3(kTcThreads), smem, s, n, R, split, (const float2*)L.Ainvw,
-              (const float2*)f, c.tc_partial, (float2*)u, c.tc_err, active);
+  const long long fe = (long long)tc_chunks(n) * 2 * R * kTcK;
+  launch_smem(k_build_f_image, dim3((unsigned)((fe + 255) / 256)), dim3(256), 0, s, n, R, (const float2*)f, c.tc_fimg,
+              active);
+  const dim3 grid((unsigned)tc_tiles(n), (unsigned)split);
+  launch_smem(k_coarse_gemm_tc, grid, dim3(kTcThreads), tc_smem(R), s, n, R, split, (const float*)c.tc_image,
+              (const float*)c.tc_fimg, c.tc_partial, (float2*)u, c.tc_err, active);
   if (split > 1)
     launch_smem(k_coarse_gemm_reduce, dim3((unsigned)(((long long)n * R + 255) / 256)), dim3(256), 0, s, n, R, split,
                 (const float*)c.tc_partial, (float2*)u, active);

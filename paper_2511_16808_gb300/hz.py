@@ -418,7 +418,7 @@ def hz_coarse_solve(ctx, f, u, stream=None):
 
 def hz_coarse_solve_batch(ctx, f, u, nrhs, variant=-1, stream=None):
     """U = Ainv F on the coarsest level for nrhs right-hand sides (RHS
-    innermost) with variant 0 (CUDA cores), s in 1..8 (tensor cores, K split s
+    innermost) with variant 0 (CUDA cores), s in 1..16 (tensor cores, K split s
     ways) or -1 (the context's choice)."""
     last = hz_level_count(ctx) - 1
     info = hz_context_info(ctx)

@@ -80,7 +80,7 @@ def test_autotune_batched_includes_tensor_core_product():
     kinds = {e["kind"] for e in entries}
     assert 0 in kinds and 1 in kinds
     coarse = [e for e in entries if e["kind"] == 0]
-    assert sorted(e["candidate"] for e in coarse) == [0, 1, 2, 4, 8]
+    assert sorted(e["candidate"] for e in coarse) == [0, 1, 2, 4, 8, 16]
     rng = np.random.default_rng(4)
     nodes = [tuple(int(v) for v in rng.integers(2, n - 2, size=2)) for _ in range(R)]
     Q = np.stack([workloads.point_source((n, n), nd, h).ravel() for nd in nodes], axis=1)

@@ -2,7 +2,7 @@
 
 hz_coarse_solve_batch runs U = A_L^{-1} F (Algorithm 1 step 3) for R
 right-hand sides with a chosen variant: 0 is the CUDA-core complex GEMM, s in
-1..8 the tensor-core kernel (tf32 with the 3xTF32 split, FP32 accumulation in
+1..16 the tensor-core kernel (tf32 with the 3xTF32 split, FP32 accumulation in
 tensor memory) with K split over s CTAs per row tile.  Checked here:
 - every tensor-core variant against the oracle's coarsest LU solve in FP64
   (the mixed path's 1e-4 of the largest entry, as for the CUDA-core GEMM), and
@@ -50,7 +50,7 @@ def test_tensor_core_coarsest_solve(case, R):
     ref = Lc.lu.solve(F.astype(np.complex128))
     scale = np.max(np.abs(ref))
     outs = {}
-    for v in (0, 1, 2, 4, 8):
+    for v in (0, 1, 2, 4, 8, 16):
         U = torch.empty_like(Fd)
         hz.hz_coarse_solve_batch(gpu.ctx, Fd, U, R, v)
         torch.cuda.synchronize()
@@ -62,7 +62,7 @@ def test_tensor_core_coarsest_solve(case, R):
     # bounds, 2 * (2 nc) 2^-22 (|Ainv| |F|) elementwise (worst case)
     Ainv = np.linalg.inv(Lc.A.toarray())
     bound = 4 * nc * 2.0 ** -22 * (np.abs(Ainv) @ np.abs(F.astype(np.complex128)))
-    for v in (1, 2, 4, 8):
+    for v in (1, 2, 4, 8, 16):
         assert np.all(np.abs(outs[v] - outs[0]) <= bound), v
     U2 = torch.empty_like(Fd)
     hz.hz_coarse_solve_batch(gpu.ctx, Fd, U2, R, 4)
