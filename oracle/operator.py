@@ -192,3 +192,54 @@ def compact19_stencil(h: float, sigma: complex) -> dict:
             off[a] = s
             st[tuple(off)] -= sigma * 1.0 / 12.0
     return st
+
+
+# --------------------------------------------------------------------------
+# Compact fourth-order operator (Eqs. disc4thCompact, disc4thCompact3D)
+# --------------------------------------------------------------------------
+# The printed stencils are H = L - sigma M for a constant sigma =
+# kappa^2 omega^2 (1 - i gamma/omega) (Eq. 1's coefficient; Section 2.1).
+# Readings for a variable medium and the boundary (the paper is silent):
+#   - sigma varies per node: H = L - (Sigma M + M Sigma)/2, Sigma = diag(sigma):
+#     complex symmetric, the printed stencil wherever sigma is constant, fourth
+#     order there and second order where sigma varies;
+#   - boundary: the stencils are applied at every node with the neighbours
+#     outside the grid dropped (homogeneous Dirichlet truncation); absorption
+#     comes from the attenuation layer of the medium (gamma), not from a
+#     boundary condition;
+#   - right-hand side q_hat = M q (the mass stencil applied to the source, as
+#     the fourth-order compact scheme requires);
+#   - shift (Eq. shift with M the compact mass stencil): A_s = A + i alpha omega^2 M.
+
+def compact_parts(shape_xyz, h: float, periodic: bool = False):
+    """(L, M): the matrices of the compact Laplacian stencil (divided by h^2)
+    and of the compact mass stencil, truncated at the boundary."""
+    d = len(shape_xyz)
+    st0 = compact9_stencil(h, 0.0) if d == 2 else compact19_stencil(h, 0.0)
+    st1 = compact9_stencil(h, 1.0) if d == 2 else compact19_stencil(h, 1.0)
+    mass = {k: st0[k] - st1.get(k, 0.0) for k in st0 if abs(st0[k] - st1.get(k, 0.0)) > 0}
+    return (stencil_matrix(shape_xyz, st0, periodic).real.astype(np.float64),
+            stencil_matrix(shape_xyz, mass, periodic).real.astype(np.float64))
+
+
+def helmholtz_compact(shape_xyz, h: float, kappa: np.ndarray, omega: float, gamma: np.ndarray,
+                      periodic: bool = False) -> sp.csr_matrix:
+    """H = L - (Sigma M + M Sigma)/2 (readings above)."""
+    L, M = compact_parts(shape_xyz, h, periodic)
+    kap = np.asarray(kappa, dtype=np.float64).ravel()
+    gam = np.asarray(gamma, dtype=np.float64).ravel()
+    S = sp.diags(omega ** 2 * kap ** 2 * (1.0 - 1j * gam / omega))
+    return sp.csr_matrix(L.astype(np.complex128) - 0.5 * (S @ M + M @ S))
+
+
+def shifted_compact(A: sp.csr_matrix, shape_xyz, h: float, omega: float, alpha: float,
+                    periodic: bool = False) -> sp.csr_matrix:
+    """A_s = A + i alpha omega^2 M with the compact mass stencil M."""
+    _, M = compact_parts(shape_xyz, h, periodic)
+    return sp.csr_matrix(A + 1j * alpha * omega ** 2 * M)
+
+
+def scaled_rhs_compact(q: np.ndarray, shape_xyz, h: float, periodic: bool = False) -> np.ndarray:
+    """q_hat = M q."""
+    _, M = compact_parts(shape_xyz, h, periodic)
+    return M @ np.asarray(q, dtype=np.complex128).ravel()
