@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define HZ_ABI_VERSION 2
+#define HZ_ABI_VERSION 3
 #define HZ_MAX_LEVELS 10
 #define HZ_MAX_STENCIL 343   /* 7^3: cubic Galerkin stencils in 3D */
 
@@ -109,6 +109,17 @@ typedef struct {
                                         level, Section 2.2: 1 = V-cycle,
                                         2 = W-cycle (the coarsest level, solved
                                         exactly, is solved once); 0 means 1  */
+  int stencil;                       /* fine-level discretisation, Section 2.1:
+                                        0 = second-order 5-point (2D) / 7-point
+                                        (3D) with the first-order absorbing
+                                        boundary (default);
+                                        1 = compact fourth-order 9-point /
+                                        19-point stencils (Eqs. disc4thCompact,
+                                        disc4thCompact3D) with a variable medium
+                                        as L - (Sigma M + M Sigma)/2, neighbours
+                                        outside the grid dropped, right-hand side
+                                        M q, shift i alpha omega^2 M; one
+                                        right-hand side per solve (nrhs_max 1) */
 } hz_opts;
 
 typedef struct hz_ctx hz_ctx;        /* opaque, owned by the library */

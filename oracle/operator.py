@@ -216,8 +216,14 @@ def compact_parts(shape_xyz, h: float, periodic: bool = False):
     and of the compact mass stencil, truncated at the boundary."""
     d = len(shape_xyz)
     st0 = compact9_stencil(h, 0.0) if d == 2 else compact19_stencil(h, 0.0)
-    st1 = compact9_stencil(h, 1.0) if d == 2 else compact19_stencil(h, 1.0)
-    mass = {k: st0[k] - st1.get(k, 0.0) for k in st0 if abs(st0[k] - st1.get(k, 0.0)) > 0}
+    # the printed mass stencils, written out (not recovered as a difference of
+    # two stencils, which would lose digits against the 1/h^2 entries)
+    mass = {tuple([0] * d): 2.0 / 3.0 if d == 2 else 6.0 / 12.0}
+    for a in range(d):
+        for sgn in (-1, 1):
+            off = [0] * d
+            off[a] = sgn
+            mass[tuple(off)] = 1.0 / 12.0
     return (stencil_matrix(shape_xyz, st0, periodic).real.astype(np.float64),
             stencil_matrix(shape_xyz, mass, periodic).real.astype(np.float64))
 

@@ -147,6 +147,8 @@ void validate(const hz_grid* g, const hz_opts* o) {
   require(o->tol > 0 && o->max_iter >= 1, "tol/max_iter out of range");
   require(o->nrhs_max >= 1 && o->nrhs_max <= 64, "nrhs_max must be in 1..64");
   require(o->cycle_visits >= 0 && o->cycle_visits <= 2, "cycle_visits must be 0, 1 (V) or 2 (W)");
+  require(o->stencil == 0 || o->stencil == 1, "stencil must be 0 (5/7-point) or 1 (compact)");
+  require(o->stencil == 0 || o->nrhs_max == 1, "the compact stencil takes one right-hand side (nrhs_max 1)");
   require(o->precision == HZ_PREC_FP64 || o->precision == HZ_PREC_MIXED, "bad precision");
   require(o->intergrid >= HZ_IG_LINEAR && o->intergrid <= HZ_IG_LEVELDEP, "bad intergrid");
   require(!(g->dim == 3 && o->intergrid == HZ_IG_CUBIC && o->levels >= 3),
@@ -270,6 +272,7 @@ hz_status hz_opts_default(int dim, hz_opts* out) {
     out->max_iter = 2000;
     out->nrhs_max = 1;
     out->cycle_visits = 1;
+    out->stencil = 0;
   });
 }
 
@@ -312,6 +315,7 @@ hz_status hz_setup(const hz_grid* g, const double* kappa, double omega, const do
     c.alpha = shift_alpha;
     c.h = g->h;
     c.mixed = opts->precision == HZ_PREC_MIXED;
+    c.compact = opts->stencil == 1;
     c.alloc_stream = s;
     HZ_CUDA(cudaGetDevice(&c.dev));
     const long long N = grid_nodes(c.grid);

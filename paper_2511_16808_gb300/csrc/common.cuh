@@ -342,10 +342,61 @@ hz_status guarded(F&& f) {
   }
 }
 
+// ---------------------------------------------------------------- compact stencil
+// Coefficients of the compact fourth-order stencils (Section 2.1) by the
+// number m of nonzero offset components: L (times 1/h^2) and the mass M.
+//   2D (Eq. disc4thCompact):   L = 10/3, -2/3, -1/6;      M = 2/3, 1/12, 0
+//   3D (Eq. disc4thCompact3D): L = 4, -1/3, -1/6, 0;      M = 1/2, 1/12, 0, 0
+__host__ __device__ __forceinline__ double compact_L(int dim, int m) {
+  if (dim == 2) return m == 0 ? 10.0 / 3.0 : (m == 1 ? -2.0 / 3.0 : -1.0 / 6.0);
+  return m == 0 ? 4.0 : (m == 1 ? -1.0 / 3.0 : (m == 2 ? -1.0 / 6.0 : 0.0));
+}
+__host__ __device__ __forceinline__ double compact_M(int dim, int m) {
+  if (m == 0) return dim == 2 ? 2.0 / 3.0 : 0.5;
+  return m == 1 ? 1.0 / 12.0 : 0.0;
+}
+
+// The compact operator at node p = (x, y, z) in FP64 with a variable medium
+// (reading: L - (Sigma M + M Sigma)/2, neighbours outside the grid dropped):
+//   (A v)_p = (1/h^2) (L v)_p - (s_p (M v)_p + (M (s v))_p) / 2,  s = sig + dsig
+// (dsig = -i alpha omega^2 gives the shifted operator).  ld(q) returns v at node q.
+template <typename LD>
+__device__ __forceinline__ double2 compact_Av(int nx, int ny, int nz, int dim, double invh2,
+                                              const double2* __restrict__ sig, double2 dsig, const LD& ld,
+                                              long long p, int x, int y, int z) {
+  double2 Lv = make_double2(0, 0), Mv = make_double2(0, 0), Msv = make_double2(0, 0);
+  const int zr = dim == 3 ? 1 : 0;
+  for (int dz = -zr; dz <= zr; ++dz)
+    for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int m = (dx != 0) + (dy != 0) + (dz != 0);
+        const double cl = compact_L(dim, m), cm = compact_M(dim, m);
+        if (cl == 0.0 && cm == 0.0) continue;
+        const int xx = x + dx, yy = y + dy, zz = z + dz;
+        if (xx < 0 || xx >= nx || yy < 0 || yy >= ny || zz < 0 || zz >= nz) continue;
+        const long long q = p + dx + (long long)dy * nx + (long long)dz * nx * ny;
+        const double2 v = ld(q);
+        Lv.x = fma(cl, v.x, Lv.x);
+        Lv.y = fma(cl, v.y, Lv.y);
+        if (cm != 0.0) {
+          const double2 sq = make_double2(sig[q].x + dsig.x, sig[q].y + dsig.y);
+          Mv.x = fma(cm, v.x, Mv.x);
+          Mv.y = fma(cm, v.y, Mv.y);
+          const double2 sv = make_double2(sq.x * v.x - sq.y * v.y, sq.x * v.y + sq.y * v.x);
+          Msv.x = fma(cm, sv.x, Msv.x);
+          Msv.y = fma(cm, sv.y, Msv.y);
+        }
+      }
+  const double2 sp = make_double2(sig[p].x + dsig.x, sig[p].y + dsig.y);
+  const double2 sMv = make_double2(sp.x * Mv.x - sp.y * Mv.y, sp.x * Mv.y + sp.y * Mv.x);
+  return make_double2(invh2 * Lv.x - 0.5 * (sMv.x + Msv.x), invh2 * Lv.y - 0.5 * (sMv.y + Msv.y));
+}
+
 // ---------------------------------------------------------------- context
 struct Level {
   GridDev g;
-  bool fine = false;
+  bool fine = false;            // the analytic 5-/7-point fine operator (level 0 without the compact stencil)
   bool coarsest = false;
   bool a_sym = false;           // A_s of this level is complex symmetric
   bool a_half = false;          // working copy Aw holds the planes s >= 0 only (symmetric box)
@@ -409,9 +460,11 @@ struct Ctx {
   double omega = 0, alpha = 0, h = 0;
   int dev = 0;
   bool mixed = true;
+  bool compact = false;         // compact fourth-order fine stencil (hz_opts.stencil = 1)
   int nrhs = 1;                 // right-hand sides of the current call (V-cycle batch width)
   std::vector<Level> L;
-  double2* diagA64 = nullptr;   // fine, unshifted A diagonal (FGMRES matvec), c128 [N]
+  double2* diagA64 = nullptr;   // fine, unshifted A diagonal (FGMRES matvec), c128 [N];
+                                // with the compact stencil: sigma = kappa^2 omega^2 (1 - i gamma/omega) per node
   double* wmass = nullptr;      // fine prod_a w_a per node (q_hat = wmass * q) [N]
   // Krylov workspace (c128 unless noted), nrhs_max wide
   double2* V = nullptr;         // (m+1) vectors

@@ -56,10 +56,36 @@ __global__ void k_fine_apply64(Geo gg, int dim, double invh2, const double2* __r
   w[q] = dim == 3 ? fine_Au<double, 3, true>(gg, invh2, diag[p], ld, q, x, y, z)
                   : fine_Au<double, 2, true>(gg, invh2, diag[p], ld, q, x, y, z);
 }
+// the compact fine operator in FP64 (sig = sigma per node, dsig the shift)
+template <typename U>
+__global__ void k_compact_apply64(GridDev gd, double invh2, const double2* __restrict__ sig, double2 dsig,
+                                  const U* __restrict__ v, double2* __restrict__ w) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= gd.N) return;
+  const int x = (int)(p % gd.nx);
+  const long long t = p / gd.nx;
+  const int y = (int)(t % gd.ny), z = (int)(t / gd.ny);
+  auto ld = [v](long long q) {
+    const U a = v[q];
+    return make_double2((double)a.x, (double)a.y);
+  };
+  w[p] = compact_Av(gd.nx, gd.ny, gd.nz, gd.dim, invh2, sig, dsig, ld, p, x, y, z);
+}
 }  // namespace
 
 void fine_apply_f64(Ctx& c, const void* v, bool v_single, double2* w, bool shifted, cudaStream_t s) {
   Level& L = c.L[0];
+  if (c.compact) {
+    require(c.nrhs == 1, "the compact stencil takes one right-hand side");
+    const double2 dsig = make_double2(0.0, shifted ? -c.alpha * c.omega * c.omega : 0.0);
+    const double invh2 = 1.0 / (c.h * c.h);
+    if (v_single)
+      k_compact_apply64<float2><<<nblk(L.g.N, 256), 256, 0, s>>>(L.g, invh2, c.diagA64, dsig, (const float2*)v, w);
+    else
+      k_compact_apply64<double2><<<nblk(L.g.N, 256), 256, 0, s>>>(L.g, invh2, c.diagA64, dsig, (const double2*)v, w);
+    HZ_LAUNCHED();
+    return;
+  }
   const double2* diag = shifted ? L.A64 : c.diagA64;    // plane 0 of the FP64 fine planes is diag(A_s)
   const double invh2 = 1.0 / (c.h * c.h);
   const Geo g = geo(L.g, c.nrhs);

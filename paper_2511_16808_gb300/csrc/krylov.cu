@@ -312,15 +312,37 @@ __global__ void __launch_bounds__(kRedBlock) k_true_residual(Geo g, double invh2
 }
 
 // q_hat = wmass * q; ||q_hat||^2, then (last block) the solver state
-__global__ void __launch_bounds__(kRedBlock) k_scale_rhs(int N, const double* __restrict__ wmass,
+// (compact stencil: q_hat = M q with the compact mass stencil, neighbours
+// outside the grid dropped)
+__global__ void __launch_bounds__(kRedBlock) k_scale_rhs(Geo g, const double* __restrict__ wmass,
                                                          const double2* __restrict__ q, double2* __restrict__ qhat,
                                                          double2* __restrict__ partials, KrylovState* st, double tol,
                                                          int max_iter, int m) {
   pdl_enter();
   double2 acc = make_double2(0, 0);
+  const int N = g.N;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p < N) {
-    const double2 v = wmass[p] * q[p];
+    double2 v;
+    if (g.compact) {
+      const int x = p % g.nx, t = p / g.nx, y = t % g.ny, z = t / g.ny;
+      v = make_double2(0, 0);
+      const int zr = g.dim == 3 ? 1 : 0;
+      for (int dz = -zr; dz <= zr; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+          for (int dx = -1; dx <= 1; ++dx) {
+            const int mm = (dx != 0) + (dy != 0) + (dz != 0);
+            const double cm = compact_M(g.dim, mm);
+            if (cm == 0.0) continue;
+            const int xx = x + dx, yy = y + dy, zz = z + dz;
+            if (xx < 0 || xx >= g.nx || yy < 0 || yy >= g.ny || zz < 0 || zz >= g.nz) continue;
+            const double2 qq = q[p + dx + dy * g.nx + dz * g.sxy];
+            v.x = fma(cm, qq.x, v.x);
+            v.y = fma(cm, qq.y, v.y);
+          }
+    } else {
+      v = wmass[p] * q[p];
+    }
     qhat[p] = v;
     acc.x = cabs2(v);
   }
@@ -360,7 +382,7 @@ __global__ void k_widen_vec(int N, const V* __restrict__ in, double2* __restrict
 template <typename TZ>
 void run_cycle(Ctx& c, cudaStream_t s) {
   Level& L0 = c.L[0];
-  const Geo g = geo(L0.g);
+  const Geo g = geo(L0.g, c.compact);
   const int N = g.N;
   const int m = c.opts.restart_m;
   const double invh2 = 1.0 / (c.h * c.h);
@@ -463,7 +485,7 @@ void ensure_graph(Ctx& c) {
 template <typename TZ>
 void solve_begin_t(Ctx& c, const double2* q, cudaStream_t user) {
   Level& L0 = c.L[0];
-  const Geo g = geo(L0.g);
+  const Geo g = geo(L0.g, c.compact);
   const int N = g.N;
   const double invh2 = 1.0 / (c.h * c.h);
   KrylovState* st = c.ks;
@@ -475,7 +497,7 @@ void solve_begin_t(Ctx& c, const double2* q, cudaStream_t user) {
   HZ_CUDA(cudaEventRecord(c.ev_in, user));
   HZ_CUDA(cudaStreamWaitEvent(s, c.ev_in, 0));
   HZ_CUDA(cudaMemsetAsync(&st->counter, 0, sizeof(unsigned), s));
-  launch_pdl(k_scale_rhs, nblk(N, kRedBlock), kRedBlock, s, N, c.wmass, q, c.qhat, c.partials, st, c.opts.tol,
+  launch_pdl(k_scale_rhs, nblk(N, kRedBlock), kRedBlock, s, g, c.wmass, q, c.qhat, c.partials, st, c.opts.tol,
                                                        c.opts.max_iter, c.opts.restart_m);
   HZ_CUDA(cudaMemsetAsync(c.p, 0, sizeof(double2) * N, s));
   {

@@ -47,8 +47,11 @@ inline unsigned nblk(long long n, int b) { return (unsigned)((n + b - 1) / b); }
 
 struct Geo {
   int nx, ny, nz, sxy, N, dim;
+  int compact;              // the fine operator is the compact fourth-order stencil (diag = sigma)
 };
-inline Geo geo(const GridDev& g) { return Geo{g.nx, g.ny, g.nz, g.nx * g.ny, (int)g.N, g.dim}; }
+inline Geo geo(const GridDev& g, bool compact = false) {
+  return Geo{g.nx, g.ny, g.nz, g.nx * g.ny, (int)g.N, g.dim, compact ? 1 : 0};
+}
 // 2D grid of 32 x 8 blocks over (x, y), kRows rows per thread; blockIdx.z strides over z
 inline dim3 grid_xy(const Geo& g) {
   return dim3((g.nx + BX - 1) / BX, (g.ny + BY * kRows - 1) / (BY * kRows), g.nz < 8 ? g.nz : 8);
@@ -136,6 +139,11 @@ __device__ __forceinline__ double2 nbr_sum(const float2 (&n)[NN]) {
 template <typename U>
 __device__ __forceinline__ double2 apply_A(const Geo& g, double invh2, const double2* __restrict__ diag,
                                            const U* __restrict__ v, int p, int x, int y, int z) {
+  if (g.compact) {
+    // the compact stencil (diag holds sigma): FP64 throughout
+    auto ld = [v](long long q) { return ld64(v, (int)q); };
+    return compact_Av(g.nx, g.ny, g.nz, g.dim, invh2, diag, make_double2(0, 0), ld, p, x, y, z);
+  }
   const double2 d = diag[p], vp = ld64(v, p);
   const bool inx = x > 0 && x < g.nx - 1, iny = y > 0 && y < g.ny - 1;
   const bool inz = g.dim == 2 || (z > 0 && z < g.nz - 1);

@@ -152,6 +152,41 @@ __global__ void k_fine_coeffs(GridDev g, double h, double omega, double alpha,
   }
 }
 
+// compact fine operator (Eqs. disc4thCompact, disc4thCompact3D): sigma per
+// node (the FGMRES operator's coefficient) and the planes of the shifted
+// operator over the radius-1 box, A_s(p, q) = L(q-p)/h^2 - M(q-p) (s_p + s_q)/2
+// with s = sigma - i alpha omega^2, zero where q leaves the grid
+__global__ void k_fine_coeffs_compact(GridDev g, double h, double omega, double alpha,
+                                      const double* __restrict__ kappa, const double* __restrict__ gamma,
+                                      double gamma0, double2* __restrict__ sig, double* __restrict__ wmass,
+                                      StencilOff off, double2* __restrict__ planes) {
+  long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= g.N) return;
+  int x, y, z;
+  node_coords(g, p, x, y, z);
+  auto sigma_at = [&](long long q) {
+    const double kap = kappa[q], gam = gamma ? gamma[q] : gamma0;
+    return make_double2(omega * omega * kap * kap, -omega * kap * kap * gam);
+  };
+  const double2 sp = sigma_at(p);
+  sig[p] = sp;
+  wmass[p] = 1.0;
+  const double invh2 = 1.0 / (h * h), shift = alpha * omega * omega;
+  for (int s = 0; s < off.n; ++s) {
+    const int dx = off.d[s][0], dy = off.d[s][1], dz = off.d[s][2];
+    double2 v = make_double2(0.0, 0.0);
+    if (in_grid(g, x + dx, y + dy, z + dz)) {
+      const int m = (dx != 0) + (dy != 0) + (dz != 0);
+      const double2 sq = sigma_at(flat(g, x + dx, y + dy, z + dz));
+      const double cm = compact_M(g.dim, m);
+      // (s_p + s_q)/2 with s = sigma - i alpha omega^2
+      const double2 savg = make_double2(0.5 * (sp.x + sq.x), 0.5 * (sp.y + sq.y) - shift);
+      v = make_double2(compact_L(g.dim, m) * invh2 - cm * savg.x, -cm * savg.y);
+    }
+    planes[(long long)s * g.N + p] = v;
+  }
+}
+
 // ------------------------------------------------------------------ a3
 // Ac(I, I+D) = sum_i R(I,i) sum_s Af(i, off_s) P(i + off_s, I + D)
 __global__ void k_galerkin(GridDev gf, StencilOff sf, const double2* __restrict__ Af, GridDev gc,
@@ -711,7 +746,7 @@ void build_hierarchy(Ctx& c, const double* kappa, const double* gamma, double ga
   for (int l = 0; l < levels; ++l) {
     Level& L = c.L[l];
     L.g = make_grid(dim, n);
-    L.fine = l == 0;
+    L.fine = l == 0 && !c.compact;       // the compact fine level is a stored-stencil level
     L.coarsest = l == levels - 1;
     L.patch = c.opts.patch[l];
     L.damping = c.opts.damping[l];
@@ -726,12 +761,16 @@ void build_hierarchy(Ctx& c, const double* kappa, const double* gamma, double ga
   {
     Level& L = c.L[0];
     const long long N = L.g.N;
-    L.A = make_lut(fine_offsets(dim));
+    L.A = make_lut(c.compact ? box_offsets(dim, 1) : fine_offsets(dim));
     L.A64 = (double2*)ctx_alloc(c, sizeof(double2) * N * L.A.off.n);
     c.diagA64 = (double2*)ctx_alloc(c, sizeof(double2) * N);
     c.wmass = (double*)ctx_alloc(c, sizeof(double) * N);
-    k_fine_coeffs<<<nblk(N, 256), 256, 0, s>>>(L.g, c.h, c.omega, c.alpha, kappa, gamma, gamma0,
-                                                c.diagA64, c.wmass, L.A.off, L.A64);
+    if (c.compact)
+      k_fine_coeffs_compact<<<nblk(N, 256), 256, 0, s>>>(L.g, c.h, c.omega, c.alpha, kappa, gamma, gamma0,
+                                                          c.diagA64, c.wmass, L.A.off, L.A64);
+    else
+      k_fine_coeffs<<<nblk(N, 256), 256, 0, s>>>(L.g, c.h, c.omega, c.alpha, kappa, gamma, gamma0,
+                                                  c.diagA64, c.wmass, L.A.off, L.A64);
     HZ_LAUNCHED();
   }
   static const char* kLevelRange[] = {"hz setup level 0", "hz setup level 1", "hz setup level 2",
@@ -790,9 +829,9 @@ size_t hierarchy_bytes(const hz_grid& g, const hz_opts& o) {
   int rho = 1;
   for (int l = 0; l < o.levels; ++l) {
     const long long N = n[0] * n[1] * n[2];
-    const int sA = l == 0 ? 2 * dim + 1 : (int)std::pow(2 * rho + 1, dim);
+    const int sA = l == 0 ? (o.stencil == 1 ? (int)std::pow(3, dim) : 2 * dim + 1) : (int)std::pow(2 * rho + 1, dim);
     total += 16ull * N * sA;                                   // FP64 operator planes
-    if (l == 0) total += 16ull * N + 8ull * N + vb * N;         // diag A, wmass, working diag
+    if (l == 0) total += 16ull * N + 8ull * N + vb * N * (o.stencil == 1 ? sA : 1);   // diag A / sigma, wmass, working operator
     else if (vb == 8) total += 8ull * N * sA;
     if (l == o.levels - 1) {
       total += 16ull * N * N * 2 + (vb == 8 ? 8ull * N * N : 0);   // dense work + inverse

@@ -44,7 +44,7 @@ class hz_opts(C.Structure):
                 ("damping", C.c_double * MAX_LEVELS), ("nu1", C.c_int), ("nu2", C.c_int),
                 ("intergrid", C.c_int), ("precision", C.c_int), ("restart_m", C.c_int),
                 ("tol", C.c_double), ("max_iter", C.c_int), ("nrhs_max", C.c_int),
-                ("cycle_visits", C.c_int)]
+                ("cycle_visits", C.c_int), ("stencil", C.c_int)]
 
 
 class hz_info(C.Structure):

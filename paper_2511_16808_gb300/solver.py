@@ -51,12 +51,14 @@ class HelmholtzSolver:
     flattened x-fastest.  patch: fine-level patch; patch_coarse: patch on the
     coarser levels (default: the same).  damping: per-level list, default the
     paper's table for each level's patch.  cycle: "V" or "W" (two cycles on
-    the next level per visit, Section 2.2).  log: a path or text file that
+    the next level per visit, Section 2.2).  stencil: "second" (5-/7-point)
+    or "compact" (the fourth-order stencils of Section 2.1).  log: a path or text file that
     receives one JSON line per solve (solve_record)."""
 
     def __init__(self, dim, n, kappa, omega, gamma, alpha, levels, patch="rb", intergrid="leveldep",
                  precision="mixed", tol=1e-6, restart=5, nu1=1, nu2=1, max_iter=2000,
-                 patch_coarse=None, damping=None, nrhs_max=1, stream=None, cycle="V", log=None):
+                 patch_coarse=None, damping=None, nrhs_max=1, stream=None, cycle="V", log=None,
+                 stencil="second"):
         n = list(n) if hasattr(n, "__len__") else [n] * dim
         self.dim = dim
         self.n = n + [1] * (3 - len(n))
@@ -65,7 +67,7 @@ class HelmholtzSolver:
         self.grid = hz.make_grid(dim, n, self.h)
         o = make_opts(dim, levels, patch=patch, intergrid=intergrid, precision=precision, tol=tol,
                       restart=restart, nu1=nu1, nu2=nu2, max_iter=max_iter, patch_coarse=patch_coarse,
-                      damping=damping, nrhs_max=nrhs_max, cycle=cycle)
+                      damping=damping, nrhs_max=nrhs_max, cycle=cycle, stencil=stencil)
         self.opts = o
         self.mixed = precision == "mixed"
         self.stream = stream
@@ -75,7 +77,8 @@ class HelmholtzSolver:
         self.log = JsonLines(log) if log is not None else None
         self._desc = {"dim": dim, "n": n[:dim], "levels": levels, "patch": patch,
                       "patch_coarse": patch_coarse or patch, "intergrid": intergrid, "precision": precision,
-                      "tol": tol, "restart": restart, "cycle": cycle, "alpha": alpha, "omega": omega}
+                      "tol": tol, "restart": restart, "cycle": cycle, "alpha": alpha, "omega": omega,
+                      "stencil": stencil}
 
     def _log(self, kind, infos, t0, single):
         if self.log is None:
@@ -143,7 +146,8 @@ class HelmholtzSolver:
 
 
 def make_opts(dim, levels, patch="rb", intergrid="leveldep", precision="mixed", tol=1e-6, restart=5, nu1=1,
-              nu2=1, max_iter=2000, patch_coarse=None, damping=None, nrhs_max=1, cycle="V") -> hz.hz_opts:
+              nu2=1, max_iter=2000, patch_coarse=None, damping=None, nrhs_max=1, cycle="V",
+              stencil="second") -> hz.hz_opts:
     """hz_opts from solver settings; damping defaults to the paper's table per
     level and patch."""
     o = hz.hz_opts_default(dim)
@@ -161,6 +165,7 @@ def make_opts(dim, levels, patch="rb", intergrid="leveldep", precision="mixed", 
     o.max_iter = max_iter
     o.nrhs_max = nrhs_max
     o.cycle_visits = {"V": 1, "W": 2}[cycle]
+    o.stencil = {"second": 0, "compact": 1}[stencil]
     return o
 
 

@@ -25,15 +25,15 @@ def medium(dim, n, seed=0, layer=0, ppw=10.0, kind="layered"):
 
 
 def make_pair(dim, n, levels, patch, scheme, precision="fp64", alpha=0.25, seed=0, layer=0,
-              kind="layered", patch_coarse=None, tol=1e-7, ppw=10.0, cycle="V"):
+              kind="layered", patch_coarse=None, tol=1e-7, ppw=10.0, cycle="V", stencil="second"):
     from paper_2511_16808_gb300.solver import HelmholtzSolver
     h, omega, kappa, gamma = medium(dim, n, seed, layer, ppw, kind)
     shape = (n,) * dim
     orc = osolver.Problem(shape, h, kappa, omega, gamma, alpha, levels, patch, scheme,
-                          patch_coarse=patch_coarse, cycle=cycle)
+                          patch_coarse=patch_coarse, cycle=cycle, stencil=stencil)
     gpu = HelmholtzSolver(dim, [n] * dim, kappa, omega, gamma, alpha, levels, patch=patch,
                           intergrid=scheme, precision=precision, tol=tol, patch_coarse=patch_coarse,
-                          cycle=cycle)
+                          cycle=cycle, stencil=stencil)
     return orc, gpu
 
 

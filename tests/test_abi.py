@@ -18,7 +18,7 @@ def test_exports_every_declared_symbol():
 
 
 def test_abi_version_and_status_strings():
-    assert hz.hz_abi_version() == 2
+    assert hz.hz_abi_version() == 3
     for code in hz.STATUS:
         assert hz.hz_status_string(code)
 
@@ -42,7 +42,7 @@ def test_oracle_damping_matches_printed_table():
 
 def test_opts_default_and_setup_bytes():
     o = hz.hz_opts_default(2)
-    assert o.levels == 4 and o.restart_m == 5 and o.nu1 == 1 and o.nu2 == 1 and o.cycle_visits == 1
+    assert o.levels == 4 and o.restart_m == 5 and o.nu1 == 1 and o.nu2 == 1 and o.cycle_visits == 1 and o.stencil == 0
     g = hz.make_grid(2, [129, 129], 1 / 128)
     b = hz.hz_setup_bytes(g, o)
     assert 129 * 129 * 16 * 6 < b < 1 << 31

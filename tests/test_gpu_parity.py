@@ -1,5 +1,6 @@
 """CUDA path vs the FP64 oracle, element by element, one test per row of the
-hot path, through the C ABI.
+hot path, through the C ABI, for the 5-/7-point operator and for the compact
+fourth-order stencils (hz_opts.stencil = 1).
 
 Tolerances: the FP64 path runs the same arithmetic in a different order, so
 relative differences are rounding-level (<= 1e-11 relative to the largest
@@ -36,12 +37,20 @@ CASES_3D = [
     dict(dim=3, n=17, levels=3, patch="jacobi", scheme="linear", layer=3, patch_coarse="element"),
     dict(dim=3, n=17, levels=4, patch="jacobi", scheme="linear", layer=3),
 ]
-ALL = CASES_2D + CASES_3D
+# the compact fourth-order stencils of Section 2.1 as the solved operator
+CASES_COMPACT = [
+    dict(dim=2, n=65, levels=3, patch="rb", scheme="leveldep", layer=8, stencil="compact"),
+    dict(dim=2, n=33, levels=3, patch="element", scheme="cubic", stencil="compact"),
+    dict(dim=2, n=129, levels=4, patch="plus", scheme="leveldep", kind="homogeneous", stencil="compact"),
+    dict(dim=3, n=17, levels=3, patch="element", scheme="linear", layer=3, stencil="compact"),
+]
+ALL = CASES_2D + CASES_3D + CASES_COMPACT
 
 
 def _ids(cases):
     return [f"{c['dim']}d-n{c['n']}-L{c['levels']}-{c['patch']}"
-            + (f"+{c['patch_coarse']}" if c.get("patch_coarse") else "") + f"-{c['scheme']}" for c in cases]
+            + (f"+{c['patch_coarse']}" if c.get("patch_coarse") else "") + f"-{c['scheme']}"
+            + ("-compact" if c.get("stencil") == "compact" else "") for c in cases]
 
 
 def case_id(c):
@@ -67,7 +76,13 @@ def test_operator_apply(case):
     v, vn = _rand(N, 1)
     for shifted, A in ((0, orc.A), (1, orc.A_s)):
         w = gpu.apply(v, shifted=bool(shifted)).cpu().numpy()
-        assert rel_err(w, A @ vn) < 1e-13
+        if case.get("stencil") == "compact":
+            # up to 27 terms of size |A_pq v_q| summed in another order: FP64
+            # rounding bound 32 u (|A| |v|) elementwise
+            bound = 32 * 2.0 ** -53 * (abs(A) @ np.abs(vn))
+            assert np.all(np.abs(w - A @ vn) <= bound)
+        else:
+            assert rel_err(w, A @ vn) < 1e-13
     gpu.close()
 
 
