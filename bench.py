@@ -774,10 +774,14 @@ def run_serving(args):
     if rank != 0:
         return None
     reqs = workloads.config5(n_requests=args.requests, rate=args.rate)
-    # media are inputs: generate them before timing, in worker processes
-    # started with spawn before this process touches the GPU
-    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
-        probs = pool.map(_serve_problem, reqs, chunksize=1)
+    # media are inputs: the first `pregenerate` are made before timing, the
+    # rest while the stream runs, `lookahead` requests ahead of the arrivals
+    # (the whole stream's media would not fit host memory: a 2049^2 request
+    # carries 134 MB, a 193^3 one 230 MB).  Worker processes are started with
+    # spawn before this process touches the GPU.
+    pool = mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1))
+    n_pre = min(len(reqs), max(args.pregenerate, 1))
+    probs = pool.map(_serve_problem, reqs[:n_pre], chunksize=1)
     import numpy as np
     import torch
     from paper_2511_16808_gb300 import hz
@@ -798,17 +802,40 @@ def run_serving(args):
         for t in [submit(srv, pr) for pr in small]:
             srv.wait(t)
     torch.cuda.synchronize()
+    pending = {}                                   # request index -> media being generated
+    nxt = n_pre
+
+    def refill(upto):
+        nonlocal nxt
+        while nxt < len(reqs) and nxt < upto:
+            pending[nxt] = pool.apply_async(_serve_problem, (reqs[nxt],))
+            nxt += 1
+
+    refill(n_pre + args.lookahead)
+    stats_media = {"n": 0, "bytes": 0}
+    lag = []                                       # submit time - scheduled arrival
     with ClockSampler(local) as clk, Server(max_active=args.max_active, setup_threads=args.setup_threads) as srv:
         t0 = time.perf_counter()
         tickets = []
-        for rq, pr in zip(reqs, probs):
+        for i, rq in enumerate(reqs):
+            if i < n_pre:
+                pr = probs[i]
+            else:
+                pr = pending.pop(i).get()
+                refill(i + 1 + args.lookahead)
             dt = rq.arrival_s - (time.perf_counter() - t0)
             if dt > 0:
                 time.sleep(dt)
             tickets.append(submit(srv, pr))
+            lag.append(time.perf_counter() - t0 - rq.arrival_s)
+            stats_media["n"] += 1
+            stats_media["bytes"] += pr["kappa"].nbytes + pr["gamma"].nbytes + pr["q"].nbytes
         res = [srv.wait(t) for t in tickets]
         wall = time.perf_counter() - t0
         st = srv.stats()
+    pool.close()
+    pool.join()
+    lag = np.array(lag)
     infos = [d for _, d in res]
     ok = [d for d in infos if d["state"] == "done" and d["status"] == "HZ_OK"]
     lat = np.array([d["t_done"] - d["t_submit"] for d in ok])
@@ -833,7 +860,8 @@ def run_serving(args):
         return {"value": k / (time.perf_counter() - t), "unit": UNIT, "requests": k,
                 "iters_mean": float(np.mean(its))}
     k = min(args.one_at_a_time, len(probs))
-    seq_mixed = one_at_a_time("mixed", len(probs))          # the whole stream, one request at a time
+    k_mixed = min(args.one_at_a_time_mixed, len(probs))
+    seq_mixed = one_at_a_time("mixed", k_mixed)             # the stream's first requests, one at a time
     seq_fp64 = one_at_a_time("fp64", k)
     served_k = len([d for d in infos[:k] if d["state"] == "done"]) / max(
         1e-9, max(d["t_done"] for d in infos[:k]) - min(d["t_submit"] for d in infos[:k]))
@@ -841,8 +869,10 @@ def run_serving(args):
     for rq in reqs:
         key = f"{rq.dim}d-{rq.n}"
         mix[key] = mix.get(key, 0) + 1
-    h2d = sum(pr["kappa"].nbytes + pr["gamma"].nbytes + pr["q"].nbytes for pr in probs)
-    d2h = sum(pr["q"].nbytes for pr in probs)
+    # every request's kappa, gamma (FP64) and source (c128) go up, its solution (c128) comes back
+    nodes = sum(rq.n ** rq.dim for rq in reqs)
+    h2d = nodes * (8 + 8 + 16)
+    d2h = nodes * 16
     pct = lambda a, q: float(np.percentile(a, q)) if len(a) else None  # noqa: E731
     return {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": len(small),
@@ -863,9 +893,16 @@ def run_serving(args):
         "setup_s": {"p50": pct(setup, 50), "p99": pct(setup, 99)},
         "solve_s": {"p50": pct(solve, 50), "p99": pct(solve, 99)},
         "offered_span_s": reqs[-1].arrival_s, "wall_s": wall,
+        "media": {"pregenerated": n_pre, "streamed": len(reqs) - n_pre, "lookahead": args.lookahead,
+                  "host_bytes_submitted": stats_media["bytes"],
+                  "submit_lag_s": {"p50": pct(lag, 50), "p99": pct(lag, 99), "max": float(lag.max())},
+                  "note": "submit lag = submit time - scheduled Poisson arrival (media generation "
+                          "running behind the arrivals shows here; latency counts from submit)"},
         "peak_hbm_bytes": st["peak_bytes"],
         "one_at_a_time_mixed": seq_mixed, "plain_fp64": seq_fp64,
         "served_vs_one_at_a_time": value / seq_mixed["value"],
+        "one_at_a_time_note": "setup + solve per request, sequential, on the stream's first requests "
+                              "(mixed: --one-at-a-time-mixed, plain FP64: --one-at-a-time)",
         "served_first_k": {"value": served_k, "unit": UNIT, "requests": k,
                            "note": "first k requests of the stream, served (arrival to completion)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -958,12 +995,16 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the second (3D) workload of the default run")
     ap.add_argument("--cpu-iters", type=int, default=25)
     ap.add_argument("--ref-iters-per-step", type=int, default=5)
-    ap.add_argument("--requests", type=int, default=100, help="config5: requests in the stream")
+    ap.add_argument("--requests", type=int, default=2000, help="config5: requests in the stream")
     ap.add_argument("--rate", type=float, default=40.0, help="config5: Poisson arrival rate per second")
     ap.add_argument("--max-active", type=int, default=32, help="config5: requests admitted at once")
     ap.add_argument("--one-at-a-time", type=int, default=24,
                     help="config5: requests timed one at a time on the plain FP64 path")
     ap.add_argument("--setup-threads", type=int, default=2, help="config5: hierarchies built concurrently")
+    ap.add_argument("--pregenerate", type=int, default=200, help="config5: media generated before timing")
+    ap.add_argument("--lookahead", type=int, default=48, help="config5: media generated ahead of the arrivals")
+    ap.add_argument("--one-at-a-time-mixed", type=int, default=200,
+                    help="config5: requests re-run one at a time (mixed) for the comparison")
     ap.add_argument("--levels", type=int, default=None, help="override the workload's cycle depth")
     ap.add_argument("--patch", default=None, help="override the fine-level Vanka patch")
     ap.add_argument("--patch-coarse", default=None, help="patch on the coarse levels (default: the fine one)")

@@ -123,7 +123,6 @@ __device__ __forceinline__ bool reduce_last_multi(const double2 (&acc)[NV], doub
   constexpr int CH = NV < 4 ? NV : 4;            // vectors per shared-memory round
   __shared__ double2 sm[CH][kRedBlock];
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-  const int lane = tid & 31, wid = tid >> 5;
 #pragma unroll
   for (int i0 = 0; i0 < NV; i0 += CH) {
     double2 v[CH];
@@ -144,17 +143,40 @@ __device__ __forceinline__ bool reduce_last_multi(const double2 (&acc)[NV], doub
   __syncthreads();
   if (!is_last) return false;
   __threadfence();
-  for (int i = wid; i < NV; i += kRedBlock / 32) {
-    const double2* pi = partials + (long long)i * nb;
-    double2 t = make_double2(0, 0);
-    for (int b = lane; b < nb; b += 32) t = t + __ldcg(pi + b);
-    for (int o = 16; o > 0; o >>= 1) {
-      t.x += __shfl_xor_sync(0xffffffffu, t.x, o);
-      t.y += __shfl_xor_sync(0xffffffffu, t.y, o);
+  // thread t sums partials t, t + kRedBlock, ... of each vector (four blocks'
+  // loads issued before their adds, which keep the index order), then the
+  // block sums the threads' values in a fixed tree: deterministic
+#pragma unroll
+  for (int i0 = 0; i0 < NV; i0 += CH) {
+    double2 v[CH];
+#pragma unroll
+    for (int c = 0; c < CH; ++c) v[c] = make_double2(0, 0);
+    int b = tid;
+    for (; b + 3 * kRedBlock < nb; b += 4 * kRedBlock) {
+      double2 q[CH][4];
+#pragma unroll
+      for (int c = 0; c < CH; ++c)
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          q[c][u] = i0 + c < NV ? __ldcg(partials + (long long)(i0 + c) * nb + b + u * kRedBlock) : make_double2(0, 0);
+#pragma unroll
+      for (int c = 0; c < CH; ++c)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[c] = v[c] + q[c][u];
     }
-    if (lane == 0) out[i] = t;
+    for (; b < nb; b += kRedBlock) {
+#pragma unroll
+      for (int c = 0; c < CH; ++c)
+        if (i0 + c < NV) v[c] = v[c] + __ldcg(partials + (long long)(i0 + c) * nb + b);
+    }
+    block_sums<CH, true>(v, sm, tid);
+    if (tid == 0) {
+#pragma unroll
+      for (int c = 0; c < CH; ++c)
+        if (i0 + c < NV) out[i0 + c] = v[c];
+    }
+    __syncthreads();                               // sm is restaged by the next round
   }
-  __syncthreads();
   if (tid == 0) *counter = 0u;
   return true;
 }
@@ -382,7 +404,7 @@ __global__ void k_widen_vec(int N, const V* __restrict__ in, double2* __restrict
 template <typename TZ>
 void run_cycle(Ctx& c, cudaStream_t s) {
   Level& L0 = c.L[0];
-  const Geo g = geo(L0.g, c.compact);
+  const Geo g = geo(L0.g, c.compact, 1.0 / (c.h * c.h));
   const int N = g.N;
   const int m = c.opts.restart_m;
   const double invh2 = 1.0 / (c.h * c.h);
@@ -485,7 +507,7 @@ void ensure_graph(Ctx& c) {
 template <typename TZ>
 void solve_begin_t(Ctx& c, const double2* q, cudaStream_t user) {
   Level& L0 = c.L[0];
-  const Geo g = geo(L0.g, c.compact);
+  const Geo g = geo(L0.g, c.compact, 1.0 / (c.h * c.h));
   const int N = g.N;
   const double invh2 = 1.0 / (c.h * c.h);
   KrylovState* st = c.ks;

@@ -29,11 +29,13 @@ constexpr int kPerB = 8;           // values per thread in the 1D passes
 struct GeoB {
   int nx, ny, nz, N, dim;
   int R, lr, nxR, sxyR, NR;
+  int p2;                  // 1/h^2 == 2^p2, else -1 (see pow2_exponent)
 };
-GeoB geob(const GridDev& g, int R) {
+GeoB geob(const GridDev& g, int R, double invh2) {
   int lr = 0;
   while ((1 << lr) < R) ++lr;
-  return GeoB{g.nx, g.ny, g.nz, (int)g.N, g.dim, R, lr, g.nx * R, g.nx * g.ny * R, (int)g.N * R};
+  return GeoB{g.nx, g.ny, g.nz, (int)g.N, g.dim, R, lr, g.nx * R, g.nx * g.ny * R, (int)g.N * R,
+              pow2_exponent(invh2)};
 }
 unsigned grid1(const GeoB& g) { return nblk(g.NR, kB * kPerB); }
 
@@ -49,9 +51,11 @@ __device__ __forceinline__ double2 apply_A_b(const GeoB& g, double invh2, const 
     if constexpr (std::is_same<U, float2>::value) {
       if (g.dim == 3) {
         const float2 n[6] = {v[q - g.R], v[q + g.R], v[q - g.nxR], v[q + g.nxR], v[q - g.sxyR], v[q + g.sxyR]};
+        if (g.p2 >= 0) return diag_minus(d, vp, nbr_sum_pow2<6>(n, g.p2));
         s = nbr_sum<6>(n);
       } else {
         const float2 n[4] = {v[q - g.R], v[q + g.R], v[q - g.nxR], v[q + g.nxR]};
+        if (g.p2 >= 0) return diag_minus(d, vp, nbr_sum_pow2<4>(n, g.p2));
         s = nbr_sum<4>(n);
       }
     } else {
@@ -428,7 +432,7 @@ void ensure_graph_b(Ctx& c, const GeoB& g) {
 
 template <typename TZ>
 void solve_b(Ctx& c, const double2* q, double2* p, int R, hz_info* info, cudaStream_t user) {
-  const GeoB g = geob(c.L[0].g, R);
+  const GeoB g = geob(c.L[0].g, R, 1.0 / (c.h * c.h));
   c.nrhs = R;
   ensure_graph_b<TZ>(c, g);
   cudaStream_t s = c.graph_stream;

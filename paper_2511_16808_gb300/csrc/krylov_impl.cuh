@@ -1,6 +1,7 @@
 // FGMRES state and device helpers shared by the single- and multi-RHS drivers
 // (krylov.cu, krylov_batch.cu).
 #pragma once
+#include <cmath>
 #include <cstddef>
 #include <type_traits>
 
@@ -45,12 +46,26 @@ struct KrylovState {
 
 inline unsigned nblk(long long n, int b) { return (unsigned)((n + b - 1) / b); }
 
+// k with v == 2^k exactly and 0 <= k <= 120, else -1.  When 1/h^2 is such a
+// power of two the FP32 neighbour sums of the operator take the factor in
+// their exact widening (an add to the exponent field), which leaves the
+// interior rows' two FP64 multiplies out with bit-identical results: scaling
+// by 2^k commutes with every rounding on the way (no FP64 overflow or
+// underflow is reachable from FP32 inputs and k <= 120).
+inline int pow2_exponent(double v) {
+  int e = 0;
+  const double m = std::frexp(v, &e);
+  return (m == 0.5 && e - 1 >= 0 && e - 1 <= 120) ? e - 1 : -1;
+}
+
 struct Geo {
   int nx, ny, nz, sxy, N, dim;
   int compact;              // the fine operator is the compact fourth-order stencil (diag = sigma)
+  int p2;                   // 1/h^2 == 2^p2 (second-order stencil only), else -1
 };
-inline Geo geo(const GridDev& g, bool compact = false) {
-  return Geo{g.nx, g.ny, g.nz, g.nx * g.ny, (int)g.N, g.dim, compact ? 1 : 0};
+inline Geo geo(const GridDev& g, bool compact = false, double invh2 = 0.0) {
+  return Geo{g.nx, g.ny, g.nz, g.nx * g.ny, (int)g.N, g.dim, compact ? 1 : 0,
+             (!compact && invh2 > 0.0) ? pow2_exponent(invh2) : -1};
 }
 // 2D grid of 32 x 8 blocks over (x, y), kRows rows per thread; blockIdx.z strides over z
 inline dim3 grid_xy(const Geo& g) {
@@ -134,6 +149,41 @@ __device__ __forceinline__ double2 nbr_sum(const float2 (&n)[NN]) {
   }
   return make_double2(fsum_wide<NN>(xs), fsum_wide<NN>(ys));
 }
+// exact widening of f * 2^k (0 <= k <= 120): zero, infinities and NaN pass
+// unchanged, every other value moves up k binades
+__host__ __device__ __forceinline__ double f2d_exact_pow2(float f, int k) {
+  unsigned hi, lo;
+  d_hilo(f2d_exact(f), hi, lo);
+  const unsigned E = (hi >> 20) & 0x7ffu;
+  if (E != 0u && E != 0x7ffu) hi += (unsigned)k << 20;
+  return hilo_d(hi, lo);
+}
+// fsum_wide times 2^k, exactly (the scaling commutes with the final FP64 add)
+template <int NN>
+__host__ __device__ __forceinline__ double fsum_wide_pow2(const float (&v)[NN], int k) {
+  float s = v[0], e = 0.0f;
+#pragma unroll
+  for (int i = 1; i < NN; ++i) {
+    float t;
+    two_sum(s, v[i], s, t);
+    e = fadd_rn(e, t);
+  }
+  return f2d_exact_pow2(s, k) + f2d_exact_pow2(e, k);
+}
+template <int NN>
+__device__ __forceinline__ double2 nbr_sum_pow2(const float2 (&n)[NN], int k) {
+  float xs[NN], ys[NN];
+#pragma unroll
+  for (int i = 0; i < NN; ++i) {
+    xs[i] = n[i].x;
+    ys[i] = n[i].y;
+  }
+  return make_double2(fsum_wide_pow2<NN>(xs, k), fsum_wide_pow2<NN>(ys, k));
+}
+// d v - s for a neighbour sum s already scaled by 1/h^2
+__device__ __forceinline__ double2 diag_minus(double2 d, double2 vp, double2 s) {
+  return make_double2(fma(d.x, vp.x, fma(-d.y, vp.y, -s.x)), fma(d.x, vp.y, fma(d.y, vp.x, -s.y)));
+}
 
 // FP64 fine-level (A v)_p, 5-/7-point with half-cell weights
 template <typename U>
@@ -152,9 +202,11 @@ __device__ __forceinline__ double2 apply_A(const Geo& g, double invh2, const dou
     if constexpr (std::is_same<U, float2>::value) {
       if (g.dim == 3) {
         const float2 n[6] = {v[p - 1], v[p + 1], v[p - g.nx], v[p + g.nx], v[p - g.sxy], v[p + g.sxy]};
+        if (g.p2 >= 0) return diag_minus(d, vp, nbr_sum_pow2<6>(n, g.p2));
         s = nbr_sum<6>(n);
       } else {
         const float2 n[4] = {v[p - 1], v[p + 1], v[p - g.nx], v[p + g.nx]};
+        if (g.p2 >= 0) return diag_minus(d, vp, nbr_sum_pow2<4>(n, g.p2));
         s = nbr_sum<4>(n);
       }
     } else {

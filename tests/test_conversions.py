@@ -126,3 +126,41 @@ def test_neighbour_sums_within_bound(conv_bin, tmp_path):
         partial = np.max(np.abs(np.cumsum(vals, axis=1)), axis=1)
         bound = (n - 1) ** 2 * 2.0 ** -48 * partial
         assert np.all(np.abs(r[:, k] - exact) <= bound), np.max(np.abs(r[:, k] - exact) / np.maximum(bound, 1e-300))
+
+
+@pytest.mark.parametrize("k", [0, 14, 20, 120])
+def test_power_of_two_widening_is_exact(conv_bin, tmp_path, k):
+    """f2d_exact_pow2(f, k) is the exact f * 2^k (the operator's 1/h^2 = 2^k
+    folded into the widening), for every class of float input."""
+    f = _float_patterns()
+    inp = os.path.join(str(tmp_path), "f.bin")
+    out = os.path.join(str(tmp_path), "w.bin")
+    f.tofile(inp)
+    subprocess.run([conv_bin, "--pow2", str(k), inp, out], check=True)
+    w = np.fromfile(out, dtype=np.float64)
+    with np.errstate(invalid="ignore"):
+        ref = np.ldexp(f.astype(np.float64), k)
+    nan = np.isnan(ref)
+    assert np.array_equal(w[~nan].view(np.uint64), ref[~nan].view(np.uint64))
+    assert np.all(np.isnan(w[nan]))
+
+
+@pytest.mark.parametrize("k", [10, 20])
+def test_power_of_two_neighbour_sums_match_scaled(conv_bin, tmp_path, k):
+    """fsum_wide_pow2(v, k) == 2^k fsum_wide(v) bit for bit: the operator's
+    interior rows give the same FP64 result with and without the folding."""
+    rng = np.random.default_rng(11)
+    m = 20000
+    g = rng.standard_normal((m, 6)) * 10.0 ** rng.integers(-30, 30, size=(m, 6))
+    g[: m // 4, 1] = -g[: m // 4, 0] * (1 + 1e-7 * rng.standard_normal(m // 4))
+    f = g.astype(np.float32)
+    f[m // 2: m // 2 + 100] = np.float32(1e-44)                   # float subnormals
+    inp = os.path.join(str(tmp_path), "s.bin")
+    a = os.path.join(str(tmp_path), "a.bin")
+    b = os.path.join(str(tmp_path), "b.bin")
+    f.tofile(inp)
+    subprocess.run([conv_bin, "--sum", inp, a], check=True)
+    subprocess.run([conv_bin, "--sum-pow2", str(k), inp, b], check=True)
+    plain = np.fromfile(a, dtype=np.float64)
+    folded = np.fromfile(b, dtype=np.float64)
+    assert np.array_equal(folded.view(np.uint64), np.ldexp(plain, k).view(np.uint64))
