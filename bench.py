@@ -612,16 +612,45 @@ def run_batched(args):
     stream = torch.cuda.current_stream()
     if rank == 0:
         fp64_peak()                  # measured before the timed regions
-    solvers = [make_solver(w, "mixed", stream, nrhs_max=R) for w in ws]
+    # --streams 1: the frequencies one after another on one stream; else each
+    # frequency's batched solve on its own stream, driven by its own host
+    # thread, so the three independent solves overlap on the device
+    conc = args.streams > 1
+    streams = [torch.cuda.Stream() for _ in ws] if conc else [stream] * len(ws)
+    solvers = [make_solver(w, "mixed", st, nrhs_max=R) for w, st in zip(ws, streams)]
     tuned = [tune(sv, R, args) for sv in solvers]
     Qs = [torch.tensor(w.rhs_block(), device="cuda") for w in ws]
     Ps = [torch.empty_like(Q) for Q in Qs]
+    torch.cuda.synchronize()
 
-    def step():
-        out = []
-        for sv, Q, P in zip(solvers, Qs, Ps):
-            ok, inf = hz.hz_solve(sv.ctx, Q, P, R, stream)
-            out.append(inf)
+    def step(Qsrc=None, Pdst=None):
+        """One batched solve per frequency (sources Qsrc[k], solutions Pdst[k];
+        device tensors by default, pinned host tensors for the e2e leg)."""
+        Qsrc = Qs if Qsrc is None else Qsrc
+        Pdst = Ps if Pdst is None else Pdst
+        if not conc:
+            out = []
+            for sv, Q, P in zip(solvers, Qsrc, Pdst):
+                ok, inf = hz.hz_solve(sv.ctx, Q, P, R, stream)
+                out.append(inf)
+            return out
+        import threading
+        mark = torch.cuda.Event()
+        mark.record(stream)
+        out = [None] * len(ws)
+
+        def one(k):
+            streams[k].wait_event(mark)
+            out[k] = hz.hz_solve(solvers[k].ctx, Qsrc[k], Pdst[k], R, streams[k])[1]
+        th = [threading.Thread(target=one, args=(k,)) for k in range(len(ws))]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        for st in streams:
+            stream.wait_stream(st)
+        if any(o is None for o in out):
+            raise RuntimeError("a concurrent batched solve failed")
         return out
 
     for _ in range(args.warmup):
@@ -655,8 +684,7 @@ def run_batched(args):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for sv, Q, P in zip(solvers, Qh, Ph):
-        hz.hz_solve(sv.ctx, Q, P, R, stream)
+    step(Qh, Ph)
     e1.record(stream)
     e1.synchronize()
     e2e_ms = e0.elapsed_time(e1)
@@ -725,6 +753,7 @@ def run_batched(args):
                        "patch": ws[0].patch, "intergrid": ws[0].intergrid, "alpha": ws[0].alpha,
                        "tol": ws[0].tol, "restart": ws[0].restart,
                        "l2": "working set per batched solve > 129 MB L2 (no flush)",
+                       "frequency_streams": args.streams if conc else 1,
                        "parallelism": f"replicas x{world}"},
             "solves_per_step": nsolve, "converged": conv, "relres_true_max": relres,
             "iters": {f"ppw{w.meta['ppw']:g}": {"min": min(it), "max": max(it), "mean": sum(it) / len(it)}
@@ -773,13 +802,13 @@ def run_serving(args):
     rank, world, local = _env_rank()
     if rank != 0:
         return None
-    reqs = workloads.config5(n_requests=args.requests, rate=args.rate)
+    reqs = workloads.config5(n_requests=args.requests, rate=args.rate, problems=args.problems)
     # media are inputs: the first `pregenerate` are made before timing, the
     # rest while the stream runs, `lookahead` requests ahead of the arrivals
     # (the whole stream's media would not fit host memory: a 2049^2 request
     # carries 134 MB, a 193^3 one 230 MB).  Worker processes are started with
     # spawn before this process touches the GPU.
-    pool = mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1))
+    pool = mp.get_context("spawn").Pool(max(1, min(args.media_workers, os.cpu_count() or 1)))
     n_pre = min(len(reqs), max(args.pregenerate, 1))
     probs = pool.map(_serve_problem, reqs[:n_pre], chunksize=1)
     import numpy as np
@@ -814,7 +843,8 @@ def run_serving(args):
     refill(n_pre + args.lookahead)
     stats_media = {"n": 0, "bytes": 0}
     lag = []                                       # submit time - scheduled arrival
-    with ClockSampler(local) as clk, Server(max_active=args.max_active, setup_threads=args.setup_threads) as srv:
+    with ClockSampler(local) as clk, Server(max_active=args.max_active, setup_threads=args.setup_threads,
+                                            group_max=args.group_max) as srv:
         t0 = time.perf_counter()
         tickets = []
         for i, rq in enumerate(reqs):
@@ -881,10 +911,14 @@ def run_serving(args):
         "config": {"workload": f"serving stream: {len(reqs)} requests, Poisson {args.rate:g}/s, "
                                "2D sides 257-2049 / 3D sides 65-193, 8-12 points per wavelength",
                    "requests": len(reqs), "rate_per_s": args.rate, "mix": mix, "max_active": st["max_active"],
+                   "setup_threads": args.setup_threads, "media_workers": args.media_workers,
+                   "problems": args.problems or "one per request", "group_max": args.group_max,
                    "hbm_budget_bytes": st["budget"], "tol": 1e-6,
                    "l2": "each request's working set > 129 MB L2 except the smallest; no flush",
                    "parallelism": "1 GPU, requests overlapped on streams"},
         "served": len(ok), "failed": st["failed"],
+        "groups": {"solves": st["groups"], "requests": st["grouped"],
+                   "note": "multi-RHS solves that served several requests of one problem together"},
         "not_ok": [{"rid": rq.rid, "dim": rq.dim, "n": rq.n, "medium": rq.generator, "ppw": round(rq.ppw, 2),
                     "status": d["status"], "iters": d["iters"], "relres_true": d["relres_true"]}
                    for rq, d in zip(reqs, infos) if not (d["state"] == "done" and d["status"] == "HZ_OK")],
@@ -995,6 +1029,8 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the second (3D) workload of the default run")
     ap.add_argument("--cpu-iters", type=int, default=25)
     ap.add_argument("--ref-iters-per-step", type=int, default=5)
+    ap.add_argument("--streams", type=int, default=3,
+                    help="config4: 1 = frequencies one after another; else one stream and host thread each")
     ap.add_argument("--requests", type=int, default=2000, help="config5: requests in the stream")
     ap.add_argument("--rate", type=float, default=40.0, help="config5: Poisson arrival rate per second")
     ap.add_argument("--max-active", type=int, default=32, help="config5: requests admitted at once")
@@ -1003,6 +1039,11 @@ def main():
     ap.add_argument("--setup-threads", type=int, default=2, help="config5: hierarchies built concurrently")
     ap.add_argument("--pregenerate", type=int, default=200, help="config5: media generated before timing")
     ap.add_argument("--lookahead", type=int, default=48, help="config5: media generated ahead of the arrivals")
+    ap.add_argument("--media-workers", type=int, default=16, help="config5: processes generating media")
+    ap.add_argument("--problems", type=int, default=0,
+                    help="config5: requests drawn from this many problems (sources differ); 0 = one per request")
+    ap.add_argument("--group-max", type=int, default=8,
+                    help="config5: queued requests of one problem solved together, at most (0 = alone)")
     ap.add_argument("--one-at-a-time-mixed", type=int, default=200,
                     help="config5: requests re-run one at a time (mixed) for the comparison")
     ap.add_argument("--levels", type=int, default=None, help="override the workload's cycle depth")

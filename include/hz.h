@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define HZ_ABI_VERSION 3
+#define HZ_ABI_VERSION 4
 #define HZ_MAX_LEVELS 10
 #define HZ_MAX_STENCIL 343   /* 7^3: cubic Galerkin stencils in 3D */
 
@@ -223,7 +223,22 @@ hz_status hz_solve_end(hz_ctx* ctx, void* p, hz_info* info, void* cuda_stream);
  * frees the hierarchy, which admits the next request.  Requests are
  * independent: one that fails records its status and releases its slot.
  * Results do not depend on what else runs: each request's kernels and
- * reductions are the ones hz_solve runs, in the same order. */
+ * reductions are the ones hz_solve runs, in the same order.
+ *
+ * Grouping (group_max >= 2): requests of the same problem (the same grid,
+ * medium, frequency, shift and solver options; only the source differs)
+ * that wait in the queue together are solved together: when the first of
+ * them is admitted, the later ones (in arrival order, up to group_max, and
+ * only as many as the budget allows) join it, share its hierarchy and run
+ * as the right-hand sides of one multi-RHS solve (hz_solve with nrhs = the
+ * group's size rounded up to a power of two, the extra right-hand sides
+ * zero), so every V-cycle of the group is one batched V-cycle over the same
+ * levels.  A grouped request's solution is that of the batched solve: its
+ * iteration count and its solution agree with its solve alone within the
+ * solver's tolerance, not bit for bit (the batched kernels sum in another
+ * order).  The group's solve runs in a setup thread, which it holds until the
+ * group finishes.  Requests with the compact stencil or with restarts longer
+ * than 16 are never grouped (the batched solve does not take them). */
 typedef struct hz_server hz_server;
 
 typedef struct {
@@ -231,6 +246,8 @@ typedef struct {
   int max_active;      /* requests admitted at once (set up or solving); 0 = 32 */
   int device;          /* CUDA device ordinal; -1 = the calling thread's current device */
   int setup_threads;   /* host threads building hierarchies concurrently (1..8); 0 = 2 */
+  int group_max;       /* requests of the same problem solved together, at most
+                          (a power of two 2..64); 0 or 1 = every request alone */
 } hz_server_opts;
 
 typedef struct {
@@ -255,6 +272,8 @@ typedef struct {
   double t_submit, t_admit, t_start, t_done;   /* seconds since hz_server_create */
   size_t bytes;          /* admission estimate */
   char message[128];     /* failure message, empty otherwise */
+  int group_size;        /* requests solved together with this one, itself
+                            included (1 = alone) */
 } hz_ticket_info;
 
 typedef struct {
@@ -263,6 +282,8 @@ typedef struct {
   int max_active;
   double elapsed_s;          /* since hz_server_create */
   int64_t kernel_launches;   /* kernels launched for the requests finished so far */
+  int groups;                /* solves that served two or more requests together */
+  int grouped;               /* requests served in those solves */
 } hz_server_counters;
 
 /* Starts the server's host threads on the device.  opts may be NULL. */
@@ -324,10 +345,11 @@ hz_status hz_profile_read(const hz_ctx* ctx, double* total_ms, int64_t* launches
  * roofline fraction of the FP64 Krylov passes.  No counterpart in the paper:
  * a measurement hook.  kind 0: FP64 fused multiply-add (DFMA); kind 1: FP32
  * (FFMA).  Every thread of a whole number of waves (SMs x resident blocks of
- * 256 threads) runs 8 independent multiply-add chains with no memory traffic;
- * the best of five launches, timed with CUDA events after two warm-up
- * launches, gives *tflops (2 flops per FMA) and *ms (that launch's time; may
- * be NULL).  Allocates and frees a small device buffer on a private stream
+ * 256 threads) runs independent multiply-add chains with no memory traffic,
+ * in two forms (8 chains sharing their operands; 16 chains with their own);
+ * the best of five launches of either form (about 20 ms each), timed with
+ * CUDA events after two warm-up launches, gives *tflops (2 flops per FMA) and
+ * *ms (that launch's time; may be NULL).  Allocates and frees a small device buffer on a private stream
  * and synchronizes it.  HZ_ERR_INVALID_ARG for another kind or a NULL
  * tflops; HZ_ERR_NO_DEVICE without a device. */
 hz_status hz_measure_peak(int kind, double* tflops, double* ms);

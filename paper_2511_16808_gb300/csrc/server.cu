@@ -18,6 +18,13 @@
 //           budget, which lets the setup thread admit the next request.
 // Requests are independent: a request that fails (bad medium, out of memory,
 // no convergence) records its status and releases its slot; the others go on.
+//
+// Grouping (group_max >= 2): when a request is admitted, the queued requests
+// of the same problem (same grid, medium, frequency, shift and options; only
+// the source differs) join it up to a power of two; the group shares one
+// hierarchy and is solved as one multi-RHS solve (one batched V-cycle per
+// FGMRES iteration for all of them) in the setup thread, and the retire
+// thread hands every member its solution.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -82,7 +89,69 @@ struct Request {
   double t_submit = 0, t_admit = 0, t_start = 0, t_done = 0;
   hz_ctx* ctx = nullptr;
   cudaStream_t stream = nullptr;
+  // grouping of requests of the same problem
+  uint64_t key = 0;                 // identity of the problem without its source (0: never grouped)
+  Request* lead = nullptr;          // a grouped request: the request whose solve serves it
+  std::vector<Request*> members;    // the lead of a group: every member, itself first
+  int group_size = 1;
+  size_t held = 0;                  // bytes held in the admission (a lead: the group's)
+  bool solved = false;              // solved in the setup thread (a group): no hz_solve_end
 };
+
+long long grid_nodes(const hz_grid& g) {
+  return (long long)g.n[0] * g.n[1] * (g.dim == 3 ? g.n[2] : 1);
+}
+
+bool opts_equal(const hz_opts& a, const hz_opts& b) {
+  if (a.levels != b.levels || a.nu1 != b.nu1 || a.nu2 != b.nu2 || a.intergrid != b.intergrid ||
+      a.precision != b.precision || a.restart_m != b.restart_m || a.tol != b.tol || a.max_iter != b.max_iter ||
+      a.cycle_visits != b.cycle_visits || a.stencil != b.stencil)
+    return false;
+  for (int l = 0; l < HZ_MAX_LEVELS; ++l)
+    if (a.patch[l] != b.patch[l] || a.damping[l] != b.damping[l]) return false;
+  return true;
+}
+
+// Identity of a request's problem apart from its source: grid, frequency,
+// shift, solver options and every value of the medium (a multiply-xor hash;
+// equal keys are confirmed value by value before two requests share a solve).
+uint64_t problem_key(const Request& r) {
+  uint64_t h = 0x243f6a8885a308d3ull;
+  auto word = [&](uint64_t w) {
+    h = (h ^ w) * 0x9e3779b97f4a7c15ull;
+    h ^= h >> 31;
+  };
+  auto real = [&](double d) {
+    uint64_t w;
+    std::memcpy(&w, &d, sizeof w);
+    word(w);
+  };
+  word((uint64_t)r.grid.dim);
+  for (int a = 0; a < 3; ++a) word((uint64_t)r.grid.n[a]);
+  real(r.grid.h);
+  real(r.omega);
+  real(r.alpha);
+  real(r.gamma0);
+  const hz_opts& o = r.opts;
+  for (int v : {o.levels, o.nu1, o.nu2, (int)o.intergrid, (int)o.precision, o.restart_m, o.max_iter, o.cycle_visits,
+                o.stencil})
+    word((uint64_t)(uint32_t)v);
+  real(o.tol);
+  for (int l = 0; l < HZ_MAX_LEVELS; ++l) {
+    word((uint64_t)o.patch[l]);
+    real(o.damping[l]);
+  }
+  for (double v : r.kappa) real(v);
+  word(r.gamma.size());
+  for (double v : r.gamma) real(v);
+  return h ? h : 1;
+}
+
+bool same_problem(const Request& a, const Request& b) {
+  return a.key == b.key && a.grid.dim == b.grid.dim && a.grid.n[0] == b.grid.n[0] && a.grid.n[1] == b.grid.n[1] &&
+         a.grid.n[2] == b.grid.n[2] && a.grid.h == b.grid.h && a.omega == b.omega && a.alpha == b.alpha &&
+         a.gamma0 == b.gamma0 && opts_equal(a.opts, b.opts) && a.kappa == b.kappa && a.gamma == b.gamma;
+}
 
 }  // namespace
 }  // namespace hz
@@ -106,6 +175,8 @@ struct hz_server {
   int setting_up = 0;
   bool stop = false;
   std::atomic<int64_t> launches{0};        // kernels launched by finished requests
+  int group_max = 0;                       // >= 2: requests of the same problem solved together
+  int groups = 0, grouped = 0;             // solves serving several requests, and those requests
   std::vector<std::thread> t_setup;
   std::thread t_step, t_retire;
 
@@ -118,6 +189,102 @@ hz_status record(Request* r, hz_status st) {
   r->status = st;
   if (st != HZ_OK && st != HZ_ERR_NOT_CONVERGED) r->message = hz_last_error();
   return st;
+}
+
+// Device bytes of a request's context for nrhs_max right-hand sides: the
+// hierarchy and Krylov workspace, the staged medium, the staged sources and
+// slack for graphs.
+size_t request_bytes(const hz_grid& g, const hz_opts& o, int nrhs_max) {
+  hz_opts oo = o;
+  oo.nrhs_max = nrhs_max;
+  size_t bytes = 0;
+  const hz_status sb = hz_setup_bytes(&g, &oo, &bytes);
+  if (sb != HZ_OK) throw Error(sb, hz_last_error());
+  const long long N = grid_nodes(g);
+  return bytes + (size_t)N * (2 * sizeof(double) + sizeof(double2) * nrhs_max) + (8u << 20);
+}
+
+// Called with the server's lock held, for the request r just admitted: the
+// queued requests of the same problem (arrival order) join it, as many as
+// make a power of two with r, at most group_max, whose host staging (N x size
+// c128 sources and solutions) stays within 1 GiB and whose bytes fit the
+// budget.  They leave the queue, hold no slot and no bytes of their own; r
+// holds the group's bytes.
+void form_group(hz_server* S, Request* r) {
+  if (S->group_max < 2 || r->key == 0) return;
+  const long long N = grid_nodes(r->grid);
+  int cap = S->group_max;
+  while (cap > 1 && (double)N * cap * sizeof(double2) > (double)(1u << 30)) cap >>= 1;
+  std::vector<Request*> cand;
+  for (const auto& e : S->adm.queue) {
+    if ((int)cand.size() + 1 >= cap) break;
+    Request* m = S->reqs[e.first].get();
+    if (m->key == r->key && same_problem(*r, *m)) cand.push_back(m);
+  }
+  int k = 1;
+  while (2 * k <= (int)cand.size() + 1) k *= 2;
+  size_t bytes = 0;
+  for (; k >= 2; k /= 2) {
+    try {
+      bytes = request_bytes(r->grid, r->opts, k);
+    } catch (const Error&) {
+      return;                                       // kept alone
+    }
+    if (S->adm.in_use - r->held + bytes <= S->adm.budget) break;
+  }
+  if (k < 2) return;
+  cand.resize(k - 1);
+  r->members.assign(1, r);
+  for (Request* m : cand) {
+    for (auto it = S->adm.queue.begin(); it != S->adm.queue.end(); ++it)
+      if (it->first == m->ticket) {
+        S->adm.queue.erase(it);
+        break;
+      }
+    m->lead = r;
+    m->state = HZ_REQ_SETUP;
+    m->t_admit = S->now();
+    m->held = 0;
+    r->members.push_back(m);
+  }
+  S->adm.in_use = S->adm.in_use - r->held + bytes;
+  S->adm.peak = std::max(S->adm.peak, S->adm.in_use);
+  r->held = bytes;
+  for (Request* m : r->members) m->group_size = k;
+  ++S->groups;
+  S->grouped += k;
+}
+
+// The group of r as one multi-RHS solve on the context r->ctx (set up for
+// r->members.size() right-hand sides): sources interleaved RHS-innermost,
+// solutions and infos handed back to each member.
+hz_status solve_group(hz_server* S, Request* r) {
+  const int R = (int)r->members.size();
+  const long long N = grid_nodes(r->grid);
+  std::vector<double2> Q((size_t)N * R), P((size_t)N * R);
+  for (int k = 0; k < R; ++k) {
+    const double2* q = r->members[k]->q.data();
+    for (long long p = 0; p < N; ++p) Q[(size_t)p * R + k] = q[p];
+  }
+  std::vector<hz_info> info(R);
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    const double t = S->now();
+    for (Request* m : r->members) {
+      m->state = HZ_REQ_SOLVING;
+      m->t_start = t;
+    }
+  }
+  const hz_status st = hz_solve(r->ctx, Q.data(), P.data(), R, info.data(), r->stream);
+  if (st != HZ_OK && st != HZ_ERR_NOT_CONVERGED) return st;
+  for (int k = 0; k < R; ++k) {
+    Request* m = r->members[k];
+    double2* out = (double2*)m->p_out;
+    for (long long p = 0; p < N; ++p) out[p] = P[(size_t)p * R + k];
+    m->info = info[k];
+    m->status = info[k].converged ? HZ_OK : HZ_ERR_NOT_CONVERGED;
+  }
+  return HZ_OK;
 }
 
 void setup_loop(hz_server* S) {
@@ -139,8 +306,13 @@ void setup_loop(hz_server* S) {
       r = S->reqs[t].get();
       r->state = HZ_REQ_SETUP;
       r->t_admit = S->now();
+      r->held = r->bytes;
+      form_group(S, r);
       ++S->setting_up;
     }
+    const bool group = r->members.size() > 1;
+    hz_opts o = r->opts;
+    if (group) o.nrhs_max = (int)r->members.size();
     hz_status st = HZ_OK;
     if (cudaStreamCreateWithFlags(&r->stream, cudaStreamNonBlocking) != cudaSuccess) {
       (void)cudaGetLastError();
@@ -150,7 +322,19 @@ void setup_loop(hz_server* S) {
     }
     if (st == HZ_OK)
       st = record(r, hz_setup(&r->grid, r->kappa.data(), r->omega, r->gamma.empty() ? nullptr : r->gamma.data(),
-                              r->gamma0, r->alpha, &r->opts, r->stream, &r->ctx));
+                              r->gamma0, r->alpha, &o, r->stream, &r->ctx));
+    if (st == HZ_OK && group) {
+      // the whole group is solved here; the retire thread hands it out
+      const hz_status gs = solve_group(S, r);      // sets each member's own status
+      if (gs != HZ_OK) record(r, gs);
+      std::lock_guard<std::mutex> lk(S->mu);
+      --S->setting_up;
+      r->solved = true;
+      if (gs != HZ_OK) r->state = HZ_REQ_FAILED;
+      S->retiring.push_back(r);
+      S->cv_retire.notify_one();
+      continue;
+    }
     if (st == HZ_OK) st = record(r, hz_solve_begin(r->ctx, r->q.data(), r->stream));
     std::lock_guard<std::mutex> lk(S->mu);
     --S->setting_up;
@@ -225,7 +409,7 @@ void retire_loop(hz_server* S) {
       r = S->retiring.front();
       S->retiring.pop_front();
     }
-    if (r->state == HZ_REQ_SOLVING) {
+    if (r->state == HZ_REQ_SOLVING && !r->solved) {
       const hz_status st = hz_solve_end(r->ctx, r->p_out, &r->info, r->stream);
       if (st != HZ_OK && st != HZ_ERR_NOT_CONVERGED) record(r, st);
       else r->status = st;
@@ -236,13 +420,31 @@ void retire_loop(hz_server* S) {
     r->ctx = nullptr;
     if (r->stream) cudaStreamDestroy(r->stream);
     r->stream = nullptr;
+    // a group's members share the lead's outcome (a failure) or carry their
+    // own status from the batched solve
+    for (Request* m : r->members) {
+      if (m == r) continue;
+      if (r->state == HZ_REQ_FAILED) {
+        m->status = r->status;
+        m->message = r->message;
+        m->state = HZ_REQ_FAILED;
+      }
+      std::vector<double>().swap(m->kappa);
+      std::vector<double>().swap(m->gamma);
+      std::vector<double2>().swap(m->q);
+    }
     std::vector<double>().swap(r->kappa);
     std::vector<double>().swap(r->gamma);
     std::vector<double2>().swap(r->q);
     std::lock_guard<std::mutex> lk(S->mu);
     r->t_done = S->now();
     if (r->state != HZ_REQ_FAILED) r->state = HZ_REQ_DONE;
-    S->adm.release(r->bytes);
+    for (Request* m : r->members) {
+      if (m == r) continue;
+      m->t_done = r->t_done;
+      if (m->state != HZ_REQ_FAILED) m->state = HZ_REQ_DONE;
+    }
+    S->adm.release(r->held);
     S->cv_setup.notify_one();
     S->cv_step.notify_one();
     S->cv_retire.notify_one();
@@ -261,6 +463,7 @@ void fill(const Request& r, hz_ticket_info* out) {
   out->bytes = r.bytes;
   std::memset(out->message, 0, sizeof(out->message));
   std::strncpy(out->message, r.message.c_str(), sizeof(out->message) - 1);
+  out->group_size = r.group_size;
 }
 
 bool finished(int state) { return state == HZ_REQ_DONE || state == HZ_REQ_FAILED; }
@@ -333,6 +536,9 @@ hz_status hz_server_create(const hz_server_opts* opts, hz_server** out) {
     HZ_CUDA(cudaMemGetInfo(&fr, &tot));
     S->adm.budget = (opts && opts->hbm_budget) ? opts->hbm_budget : (size_t)(0.8 * (double)fr);
     S->adm.max_active = (opts && opts->max_active > 0) ? opts->max_active : 32;
+    const int gm = opts ? opts->group_max : 0;
+    require(gm <= 1 || (gm <= 64 && (gm & (gm - 1)) == 0), "group_max must be 0, 1 or a power of two <= 64");
+    S->group_max = gm >= 2 ? gm : 0;
     const int nsetup = (opts && opts->setup_threads > 0) ? std::min(opts->setup_threads, 8) : 2;
     for (int i = 0; i < nsetup; ++i) S->t_setup.emplace_back(setup_loop, S);
     S->t_step = std::thread(step_loop, S);
@@ -369,6 +575,9 @@ hz_status hz_server_submit(hz_server* S, const hz_request* req, uint64_t* ticket
     r->q.assign(q, q + N);
     r->p_out = req->p;
     r->bytes = bytes;
+    // grouped solves run batched: one right-hand side stencils and restarts
+    // longer than 16 stay alone
+    if (S->group_max >= 2 && req->opts.stencil != 1 && req->opts.restart_m <= 16) r->key = problem_key(*r);
     std::lock_guard<std::mutex> lk(S->mu);
     require(!S->stop, "server is shutting down");
     r->ticket = S->next_ticket++;
@@ -426,6 +635,8 @@ hz_status hz_server_stats(hz_server* S, hz_server_counters* out) {
     out->max_active = S->adm.max_active;
     out->elapsed_s = S->now();
     out->kernel_launches = S->launches.load();
+    out->groups = S->groups;
+    out->grouped = S->grouped;
   });
 }
 

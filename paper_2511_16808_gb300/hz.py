@@ -61,7 +61,7 @@ class hz_level_desc(C.Structure):
 
 class hz_server_opts(C.Structure):
     _fields_ = [("hbm_budget", C.c_size_t), ("max_active", C.c_int), ("device", C.c_int),
-                ("setup_threads", C.c_int)]
+                ("setup_threads", C.c_int), ("group_max", C.c_int)]
 
 
 class hz_request(C.Structure):
@@ -76,14 +76,14 @@ REQ_STATE = {0: "queued", 1: "setup", 2: "solving", 3: "done", 4: "failed"}
 class hz_ticket_info(C.Structure):
     _fields_ = [("state", C.c_int), ("status", C.c_int), ("info", hz_info), ("t_submit", C.c_double),
                 ("t_admit", C.c_double), ("t_start", C.c_double), ("t_done", C.c_double),
-                ("bytes", C.c_size_t), ("message", C.c_char * 128)]
+                ("bytes", C.c_size_t), ("message", C.c_char * 128), ("group_size", C.c_int)]
 
 
 class hz_server_counters(C.Structure):
     _fields_ = [("queued", C.c_int), ("setting_up", C.c_int), ("solving", C.c_int), ("done", C.c_int),
                 ("failed", C.c_int), ("bytes_in_use", C.c_size_t), ("peak_bytes", C.c_size_t),
                 ("budget", C.c_size_t), ("max_active", C.c_int), ("elapsed_s", C.c_double),
-                ("kernel_launches", C.c_int64)]
+                ("kernel_launches", C.c_int64), ("groups", C.c_int), ("grouped", C.c_int)]
 
 
 class hz_tune_entry(C.Structure):
@@ -500,8 +500,9 @@ def hz_lfa_factors(dim: int, stencil, patch: str, w, rk: str = "cubic", pk: str 
 
 # ------------------------------------------------------------------ serving
 
-def hz_server_create(hbm_budget: int = 0, max_active: int = 0, device: int = -1, setup_threads: int = 0):
-    o = hz_server_opts(int(hbm_budget), int(max_active), int(device), int(setup_threads))
+def hz_server_create(hbm_budget: int = 0, max_active: int = 0, device: int = -1, setup_threads: int = 0,
+                     group_max: int = 0):
+    o = hz_server_opts(int(hbm_budget), int(max_active), int(device), int(setup_threads), int(group_max))
     out = C.c_void_p()
     _check(lib.hz_server_create(C.byref(o), C.byref(out)), "hz_server_create")
     return out.value

@@ -16,14 +16,16 @@ from .solver import JsonLines, make_opts
 class Server:
     """hbm_budget: device bytes the admitted requests may hold (0: 80% of free
     memory); max_active: requests set up or solving at once (0: 32);
-    setup_threads: hierarchies built concurrently (0: 2); log: a path or text
-    file receiving one JSON line per finished request (latency, queue delay,
-    setup and solve spans, iterations, bytes) and one with the server's
-    counters when it closes."""
+    setup_threads: hierarchies built concurrently (0: 2); group_max: requests
+    of the same problem (only the source differs) waiting together are solved
+    together as one multi-RHS solve of up to this many right-hand sides (0:
+    every request alone); log: a path or text file receiving one JSON line per
+    finished request (latency, queue delay, setup and solve spans, iterations,
+    bytes, group size) and one with the server's counters when it closes."""
 
     def __init__(self, hbm_budget: int = 0, max_active: int = 0, device: int = -1, setup_threads: int = 0,
-                 log=None):
-        self.srv = hz.hz_server_create(hbm_budget, max_active, device, setup_threads)
+                 log=None, group_max: int = 0):
+        self.srv = hz.hz_server_create(hbm_budget, max_active, device, setup_threads, group_max)
         self._keep = {}
         self.log = JsonLines(log) if log is not None else None
 
@@ -101,7 +103,7 @@ def _info(t: hz.hz_ticket_info) -> dict:
     return {"state": hz.REQ_STATE.get(t.state, t.state), "status": hz.STATUS.get(t.status, t.status),
             "iters": t.info.iters, "converged": bool(t.info.converged), "relres_true": t.info.relres_true,
             "t_submit": t.t_submit, "t_admit": t.t_admit, "t_start": t.t_start, "t_done": t.t_done,
-            "bytes": t.bytes, "message": t.message.decode(errors="replace")}
+            "bytes": t.bytes, "message": t.message.decode(errors="replace"), "group_size": t.group_size}
 
 
 def request_record(ticket, d: dict) -> dict:
@@ -110,7 +112,7 @@ def request_record(ticket, d: dict) -> dict:
     solve span, iterations, status and device bytes held."""
     rec = {"event": "request", "t": time.time(), "ticket": int(ticket), "state": d["state"], "status": d["status"],
            "iters": d["iters"], "converged": d["converged"], "relres_true": d["relres_true"], "bytes": d["bytes"],
-           "latency_s": d["t_done"] - d["t_submit"]}
+           "group_size": d["group_size"], "latency_s": d["t_done"] - d["t_submit"]}
 
     def span(a, b):                  # a stage the request never reached has no span
         return d[b] - d[a] if d[b] >= d[a] > 0 or (a == "t_submit" and d[b] >= d[a]) else None

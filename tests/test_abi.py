@@ -18,7 +18,7 @@ def test_exports_every_declared_symbol():
 
 
 def test_abi_version_and_status_strings():
-    assert hz.hz_abi_version() == 3
+    assert hz.hz_abi_version() == 4
     for code in hz.STATUS:
         assert hz.hz_status_string(code)
 

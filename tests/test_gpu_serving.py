@@ -10,6 +10,11 @@
 - A request that runs out of iterations reports HZ_ERR_NOT_CONVERGED with its
   last iterate, equal to the solo one.
 - The asynchronous single-solve calls give the blocking solve's result.
+- Grouping: queued requests of one problem (only the source differs) are
+  solved together as one multi-RHS solve, in groups of a power of two; each
+  member's iteration count is the oracle's +-1 and its solution agrees with
+  the oracle's at the same tolerance (1e-5 mixed); a request of another
+  problem in between stays alone and equals its solo solve bit for bit.
 """
 import numpy as np
 import pytest
@@ -172,3 +177,51 @@ def test_many_small_requests():
         p, d = res[i]
         p1, info1 = _solo(reqs[i])
         assert d["status"] == "HZ_OK" and d["iters"] == info1.iters and np.array_equal(p, p1)
+
+
+def test_grouped_requests_share_one_solve():
+    from oracle import solver as osolver
+    from pairs import check_agreement
+    from paper_2511_16808_gb300 import hz
+    from paper_2511_16808_gb300.serve import Server
+    import workloads
+    g = dict(dim=2, n=129, seed=7, kind="layered", levels=4, patch="rb", intergrid="leveldep", alpha=0.1, layer=6)
+    kappa, gamma, omega, _, opts = _problem(g)
+    n = g["n"]
+    h = 1.0 / (n - 1)
+    rng = np.random.default_rng(21)
+    srcs = [tuple(int(v) for v in rng.integers(10, n - 10, size=2)) for _ in range(6)]
+    qs = [workloads.point_source((n, n), sd, h).ravel() for sd in srcs]
+    with pytest.raises(hz.HzError):
+        Server(group_max=3)
+    # one slot: the first (unrelated) request holds it while the rest queue up
+    with Server(max_active=1, setup_threads=1, group_max=8) as srv:
+        t_block = _submit(srv, REQS[0])
+        tickets = []
+        for k, q in enumerate(qs):
+            tickets.append(srv.submit(2, n, kappa, omega, q, gamma=gamma, alpha=g["alpha"], levels=g["levels"],
+                                      **opts))
+            if k == 2:
+                t_other = _submit(srv, REQS[1])          # another problem, in between
+        res = [srv.wait(t, timeout=600) for t in tickets]
+        p_other, d_other = srv.wait(t_other, timeout=600)
+        p_block, d_block = srv.wait(t_block, timeout=600)
+        st = srv.stats()
+    assert st["done"] == len(qs) + 2 and st["failed"] == 0 and st["bytes_in_use"] == 0
+    # six requests of one problem: a group of four, then one of two
+    assert st["groups"] == 2 and st["grouped"] == 6, st
+    assert sorted(d["group_size"] for _, d in res) == [2, 2, 4, 4, 4, 4]
+    assert d_other["group_size"] == 1 and d_block["group_size"] == 1
+    p1, info1 = _solo(REQS[1])
+    assert d_other["iters"] == info1.iters and np.array_equal(p_other, p1)
+    orc = osolver.Problem((n, n), h, kappa, omega, gamma, g["alpha"], g["levels"], g["patch"], g["intergrid"])
+    for q, (p, d) in zip(qs, res):
+        assert d["state"] == "done" and d["status"] == "HZ_OK", d
+        p_o, info_o = orc.solve(q.copy(), tol=1e-7)
+        assert abs(d["iters"] - info_o.iters) <= 1, (d["iters"], info_o.iters)
+        check_agreement(p, p_o, None, "mixed", f"grouped request, group of {d['group_size']}")
+    # members of a group start and finish together
+    by_size = {}
+    for _, d in res:
+        by_size.setdefault(d["group_size"], set()).add((d["t_start"], d["t_done"]))
+    assert all(len(v) == 1 for v in by_size.values()), by_size

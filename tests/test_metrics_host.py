@@ -39,9 +39,10 @@ def test_json_lines_sink():
 
 def test_request_record_spans():
     d = {"state": "done", "status": "HZ_OK", "iters": 40, "converged": True, "relres_true": 9e-7, "bytes": 1 << 20,
-         "t_submit": 1.0, "t_admit": 1.5, "t_start": 1.75, "t_done": 3.0, "message": ""}
+         "t_submit": 1.0, "t_admit": 1.5, "t_start": 1.75, "t_done": 3.0, "message": "", "group_size": 3}
     r = request_record(7, d)
     assert r["latency_s"] == 2.0 and r["queue_s"] == 0.5 and r["setup_s"] == 0.25 and r["solve_s"] == 1.25
+    assert r["group_size"] == 3
     assert "message" not in r and r["ticket"] == 7
     failed = dict(d, state="failed", status="HZ_ERR_INVALID_ARG", t_start=0.0, t_done=1.6, message="kappa")
     r = request_record(8, failed)

@@ -187,24 +187,41 @@ class ServeRequest:
 
 
 def config5(n_requests: int = 2000, rate: float = 40.0, seed: int = 5, sizes2d=(257, 513, 1025, 2049),
-            sizes3d=(65, 129, 193), p3d: float = 0.5) -> list:
+            sizes3d=(65, 129, 193), p3d: float = 0.5, problems: int = 0) -> list:
     """Serving stream: Poisson arrivals at `rate` per second; each request is
     2D (side uniform over sizes2d) or 3D (side uniform over sizes3d) with
     probability p3d, a homogeneous (config 1's generator) or layered (config
     2's in 2D, config 3's in 3D) medium with seed 1000 + id, 8-12 points per
-    wavelength and a source uniform inside the absorbing layer."""
+    wavelength and a source uniform inside the absorbing layer.
+
+    problems > 0: a many-sources variant (several shots on the same media and
+    frequencies): `problems` problems (dimension, side, medium, frequency)
+    are drawn the same way first, with medium seeds 1000 + problem index, and
+    each request takes one of them uniformly at random with its own source."""
     rng = np.random.default_rng(seed)
-    t = 0.0
-    out = []
-    for i in range(n_requests):
-        t += rng.exponential(1.0 / rate)
+
+    def draw():
         dim = 3 if rng.random() < p3d else 2
         sizes = sizes3d if dim == 3 else sizes2d
         n = int(sizes[rng.integers(len(sizes))])
         gen = "layered" if rng.random() < 0.5 else "homogeneous"
         ppw = float(rng.uniform(8.0, 12.0))
+        return dim, n, gen, ppw
+
+    table = [draw() for _ in range(problems)]
+    t = 0.0
+    out = []
+    for i in range(n_requests):
+        t += rng.exponential(1.0 / rate)
+        if problems > 0:
+            j = int(rng.integers(problems))
+            dim, n, gen, ppw = table[j]
+            mseed = 1000 + j
+        else:
+            dim, n, gen, ppw = draw()
+            mseed = 1000 + i
         u = tuple(float(v) for v in rng.random(dim))
-        out.append(ServeRequest(i, t, dim, n, gen, ppw, 1000 + i, u))
+        out.append(ServeRequest(i, t, dim, n, gen, ppw, mseed, u))
     return out
 
 
