@@ -221,7 +221,7 @@ def tune(solver, nrhs, args):
     if args.no_autotune:
         return None
     from paper_2511_16808_gb300 import tuning
-    entries, _ = tuning.autotune(solver, nrhs, reps=5, cache=None, log=None)
+    entries, _ = tuning.autotune(solver, nrhs, reps=5, cache=args.tune_cache, log=None)
     return [{"level": e["level"], "knob": e["knob"], "candidate": e["candidate"], "us": round(e["us"], 2),
              "others_us": [round(o["us"], 2) for o in entries
                            if (o["kind"], o["level"]) == (e["kind"], e["level"]) and not o["chosen"]]}
@@ -1026,6 +1026,9 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the fixed kernel-choice rules")
+    ap.add_argument("--tune-cache", default=None,
+                    help="JSON file of kernel choices: read when it holds the workload's level shapes, else written "
+                         "(a profiler run then replays the choices of the plain run)")
     ap.add_argument("--no-extra", action="store_true", help="skip the second (3D) workload of the default run")
     ap.add_argument("--cpu-iters", type=int, default=25)
     ap.add_argument("--ref-iters-per-step", type=int, default=5)

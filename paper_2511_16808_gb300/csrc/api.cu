@@ -101,7 +101,8 @@ void ctx_free_all(Ctx& c) {
   if (c.ev_in) cudaEventDestroy(c.ev_in);
   if (c.ev_out) cudaEventDestroy(c.ev_out);
   if (c.ev_status) cudaEventDestroy(c.ev_status);
-  c.ev_in = c.ev_out = c.ev_status = nullptr;
+  if (c.ev_status_b) cudaEventDestroy(c.ev_status_b);
+  c.ev_in = c.ev_out = c.ev_status = c.ev_status_b = nullptr;
   // frees are ordered after the context's own stream; the caller has
   // synchronized every stream that used the context
   cudaStream_t fs = c.graph_stream ? c.graph_stream : c.alloc_stream;

@@ -486,9 +486,14 @@ struct Ctx {
   int cycle_graph_nrhs = 0;
   cudaStream_t graph_stream = nullptr;   // library stream the solve runs on (graph capture needs one)
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-  cudaEvent_t ev_status = nullptr;         // status copy of the last queued restart cycle
+  // status copies of the queued restart cycles: two slots (event, pinned
+  // host copy) used in turn, so the next cycle can be queued before the
+  // status of the one before it has been read
+  cudaEvent_t ev_status = nullptr, ev_status_b = nullptr;
   int as_state = 0;                        // asynchronous solve: 0 idle, 1 in flight, 2 finished
-  int as_before = 0;                       // iterations before the last queued cycle
+  int as_before = 0;                       // iterations before the oldest queued cycle (profiling)
+  int as_head = 0, as_pending = 0;         // slot of the oldest unread status; statuses queued
+  int as_done_slot = 0;                    // slot whose status ended the solve
   bool as_replayed = false;
   int graph_kernels = 0;        // kernel nodes in the captured restart cycle
   // measurement hooks (hz_profile_select / hz_profile_read): CUDA events around

@@ -504,6 +504,24 @@ void ensure_graph(Ctx& c) {
 // reads the status of the last restart cycle (once its event has completed)
 // and queues the next cycle, end hands out the solution.  The blocking solve
 // and the serving loop are both built from these.
+// Queues one restart cycle (the captured graph) and the copy of its status
+// into the next free slot.  A cycle queued after the solve has stopped does
+// nothing: every kernel of the cycle returns at once once the device state
+// says done (the V-cycle and the passes test `active`, the per-restart
+// kernels `done`).
+void queue_cycle(Ctx& c) {
+  const int slot = (c.as_head + c.as_pending) & 1;
+  cudaStream_t s = c.graph_stream;
+  NvtxRange range("hz restart cycle");
+  HZ_CUDA(cudaGraphLaunch(c.cycle_graph, s));
+  c.as_replayed = true;
+  c.launches += c.graph_kernels;
+  HZ_CUDA(cudaMemcpyAsync((KrylovStatus*)c.ks_host + slot, &c.ks->st, sizeof(KrylovStatus), cudaMemcpyDeviceToHost,
+                          s));
+  HZ_CUDA(cudaEventRecord(slot ? c.ev_status_b : c.ev_status, s));
+  ++c.as_pending;
+}
+
 template <typename TZ>
 void solve_begin_t(Ctx& c, const double2* q, cudaStream_t user) {
   Level& L0 = c.L[0];
@@ -537,38 +555,45 @@ void solve_begin_t(Ctx& c, const double2* q, cudaStream_t user) {
   }
   c.as_before = 0;
   c.as_replayed = false;
+  c.as_head = 0;
+  c.as_pending = 1;
   c.as_state = 1;
+  if (!c.prof_class) queue_cycle(c);   // the first cycle, before the initial status is read
 }
 
 }  // namespace
 
+// Reads the oldest queued status; unless the solve has stopped, keeps two
+// restart cycles queued (one while profiling, whose events are rewritten by
+// every replay), so the device goes on with the next cycle while the host
+// reads the status of the previous one.
 int solve_step(Ctx& c, bool block) {
   if (c.as_state != 1) return 1;
+  const int k = c.as_head;
+  cudaEvent_t ev = k ? c.ev_status_b : c.ev_status;
   if (block) {
-    HZ_CUDA(cudaEventSynchronize(c.ev_status));
+    HZ_CUDA(cudaEventSynchronize(ev));
   } else {
-    const cudaError_t e = cudaEventQuery(c.ev_status);
+    const cudaError_t e = cudaEventQuery(ev);
     if (e == cudaErrorNotReady) return 0;
     HZ_CUDA(e);
   }
-  KrylovStatus* hs = (KrylovStatus*)c.ks_host;
+  const KrylovStatus* hs = (const KrylovStatus*)c.ks_host + k;
   if (c.as_replayed && c.prof_class) prof_collect(c, hs->iters - c.as_before, nullptr, 1);
   {
     std::lock_guard<std::mutex> lk(c.history_mu);
     c.history.push_back({(double)hs->iters, hs->relres_true, hs->relres_est});
   }
+  c.as_head ^= 1;
+  --c.as_pending;
   if (hs->done) {
+    c.as_done_slot = k;
     c.as_state = 2;
     return 1;
   }
   c.as_before = hs->iters;
-  cudaStream_t s = c.graph_stream;
-  NvtxRange range("hz restart cycle");
-  HZ_CUDA(cudaGraphLaunch(c.cycle_graph, s));
-  c.as_replayed = true;
-  c.launches += c.graph_kernels;
-  HZ_CUDA(cudaMemcpyAsync(hs, &c.ks->st, sizeof(KrylovStatus), cudaMemcpyDeviceToHost, s));
-  HZ_CUDA(cudaEventRecord(c.ev_status, s));
+  const int depth = c.prof_class ? 1 : 2;
+  while (c.as_pending < depth) queue_cycle(c);
   return 0;
 }
 
@@ -585,7 +610,7 @@ void solve_end(Ctx& c, double2* p, hz_info* info, cudaStream_t user) {
   if (p != c.p) HZ_CUDA(cudaMemcpyAsync(p, c.p, sizeof(double2) * N, cudaMemcpyDeviceToDevice, s));
   HZ_CUDA(cudaEventRecord(c.ev_out, s));
   HZ_CUDA(cudaStreamWaitEvent(user, c.ev_out, 0));
-  const KrylovStatus* hs = (const KrylovStatus*)c.ks_host;
+  const KrylovStatus* hs = (const KrylovStatus*)c.ks_host + c.as_done_slot;
   info->iters = hs->iters;
   info->converged = hs->converged;
   info->relres_est = hs->relres_est;
@@ -748,11 +773,12 @@ void krylov_alloc(Ctx& c) {
   HZ_CUDA(cudaMemsetAsync(c.ks, 0, sizeof(KrylovState) * R, c.alloc_stream));
   c.n_active = (int*)ctx_alloc(c, sizeof(int));
   coarse_tc_alloc(c);
-  c.ks_host = pinned_small_alloc(sizeof(KrylovStatus) * R);
+  c.ks_host = pinned_small_alloc(sizeof(KrylovStatus) * std::max<long long>(R, 2));   // >= 2 status slots
   HZ_CUDA(cudaStreamCreateWithFlags(&c.graph_stream, cudaStreamNonBlocking));
   HZ_CUDA(cudaEventCreateWithFlags(&c.ev_in, cudaEventDisableTiming));
   HZ_CUDA(cudaEventCreateWithFlags(&c.ev_out, cudaEventDisableTiming));
   HZ_CUDA(cudaEventCreateWithFlags(&c.ev_status, cudaEventDisableTiming));
+  HZ_CUDA(cudaEventCreateWithFlags(&c.ev_status_b, cudaEventDisableTiming));
 }
 
 void profile_select(Ctx& c, int cls) {
