@@ -623,12 +623,12 @@ def run_batched(args):
     Ps = [torch.empty_like(Q) for Q in Qs]
     torch.cuda.synchronize()
 
-    def step(Qsrc=None, Pdst=None):
+    def step(Qsrc=None, Pdst=None, sequential=False):
         """One batched solve per frequency (sources Qsrc[k], solutions Pdst[k];
         device tensors by default, pinned host tensors for the e2e leg)."""
         Qsrc = Qs if Qsrc is None else Qsrc
         Pdst = Ps if Pdst is None else Pdst
-        if not conc:
+        if not conc or sequential:
             out = []
             for sv, Q, P in zip(solvers, Qsrc, Pdst):
                 ok, inf = hz.hz_solve(sv.ctx, Q, P, R, stream)
@@ -691,7 +691,10 @@ def run_batched(args):
 
     out = None
     if rank == 0:
-        run = lambda: step()  # noqa: E731
+        # kernel rooflines with the frequencies one after another: events
+        # around a kernel that shares the device with other streams would
+        # time the sharing, not the kernel
+        run = lambda: step(sequential=True)  # noqa: E731
         prof = _profile_class(torch, hz, solvers, run, "gs_update")
         first = _profile_class(torch, hz, solvers, run, "gs_apply")
         vprof = _profile_class(torch, hz, solvers, run, "vcycle")
