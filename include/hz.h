@@ -341,6 +341,19 @@ hz_status hz_kernel_launches(const hz_ctx* ctx, int64_t* count);
 hz_status hz_profile_select(hz_ctx* ctx, int kernel_class);
 hz_status hz_profile_read(const hz_ctx* ctx, double* total_ms, int64_t* launches, double* bytes, double* flops);
 
+/* Checked-index debug build (no counterpart in the paper; the stand-in for
+ * a memory checker, which this library's test machines do not offer).
+ * libhz_checked.so is the same library compiled with every instrumented
+ * global access of the solve's kernels testing its element index against
+ * the array's extent; an index outside the array is counted, the first one
+ * recorded (source line << 40 | low 40 bits of the index in *first), and the
+ * access moved to element 0 of the array, so a kernel never traps.
+ * hz_check_status: *enabled = 1 in that build (0 in the normal one, where
+ * the counts stay 0), *failures the out-of-extent accesses since the last
+ * clear, summed over the library's translation units; clear != 0 resets
+ * them.  Call it with no kernel of the library in flight. */
+hz_status hz_check_status(int* enabled, uint64_t* failures, uint64_t* first, int clear);
+
 /* Measured arithmetic peak of the current device, the denominator of the
  * roofline fraction of the FP64 Krylov passes.  No counterpart in the paper:
  * a measurement hook.  kind 0: FP64 fused multiply-add (DFMA); kind 1: FP32

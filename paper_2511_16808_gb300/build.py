@@ -2,7 +2,10 @@
 
 Each .cu translation unit is compiled in parallel with nvcc, then linked into
 paper_2511_16808_gb300/_build/libhz.so.  Run as `python -m
-paper_2511_16808_gb300.build` or call build().
+paper_2511_16808_gb300.build` or call build().  build(checked=True) (`--checked`)
+builds the checked-index debug variant _build/checked/libhz_checked.so
+(-DHZ_CHECKED: every instrumented global access tests its index, see
+hz_check_status); the binding loads it when HZ_LIB names it.
 """
 from __future__ import annotations
 
@@ -42,17 +45,24 @@ def _newer(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(verbose: bool = False, force: bool = False, extra_flags=None) -> str:
-    """Compile every translation unit and link libhz.so; returns its path."""
-    os.makedirs(OUT, exist_ok=True)
+CHECKED_OUT = os.path.join(OUT, "checked")
+CHECKED_LIB = os.path.join(CHECKED_OUT, "libhz_checked.so")
+
+
+def build(verbose: bool = False, force: bool = False, extra_flags=None, checked: bool = False) -> str:
+    """Compile every translation unit and link libhz.so (checked: the
+    checked-index variant libhz_checked.so); returns its path."""
+    out = CHECKED_OUT if checked else OUT
+    lib = CHECKED_LIB if checked else LIB
+    os.makedirs(out, exist_ok=True)
     nvcc = _nvcc()
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")]
     headers.append(os.path.join(INCLUDE, "hz.h"))
-    flags = FLAGS + list(extra_flags or [])
+    flags = FLAGS + list(extra_flags or []) + (["-DHZ_CHECKED"] if checked else [])
     jobs = []
     objs = []
     for src in sources():
-        obj = os.path.join(OUT, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(out, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
         if force or _newer(obj, [src] + headers):
             jobs.append([nvcc, *ARCH, *flags, "-c", src, "-o", obj])
@@ -67,15 +77,15 @@ def build(verbose: bool = False, force: bool = False, extra_flags=None) -> str:
                 sys.stderr.write(" ".join(cmd) + "\n" + r.stdout + r.stderr)
             if r.returncode != 0:
                 raise RuntimeError(f"nvcc failed for {cmd[-3]}")
-    if force or jobs or _newer(LIB, objs):
-        cmd = [nvcc, *ARCH, "-shared", "-o", LIB, *objs, "-lcudart"]
+    if force or jobs or _newer(lib, objs):
+        cmd = [nvcc, *ARCH, "-shared", "-o", lib, *objs, "-lcudart"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if verbose or r.returncode != 0:
             sys.stderr.write(" ".join(cmd) + "\n" + r.stdout + r.stderr)
         if r.returncode != 0:
-            raise RuntimeError("link of libhz.so failed")
-    return LIB
+            raise RuntimeError(f"link of {os.path.basename(lib)} failed")
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(verbose="-v" in sys.argv, force="-f" in sys.argv))
+    print(build(verbose="-v" in sys.argv, force="-f" in sys.argv, checked="--checked" in sys.argv))

@@ -23,6 +23,14 @@ void set_last_error(const char* msg) {
   else g_last_error.clear();
 }
 
+// readers of the checked-index words, one per translation unit of the
+// checked build (registered during static initialisation)
+std::vector<int (*)(unsigned long long*, int)>& check_readers() {
+  static std::vector<int (*)(unsigned long long*, int)> v;
+  return v;
+}
+void check_register(int (*read)(unsigned long long* words, int clear)) { check_readers().push_back(read); }
+
 // Scratch of the allocation-free sweep (hz_level_smooth_noalloc): the
 // residual of one level, c64 or c128, at most HZ_NOALLOC_MAX_NODES nodes.
 // It lives in the module's static device memory, so every GPU that loads the
@@ -252,6 +260,25 @@ const char* hz_status_string(hz_status s) {
 }
 
 const char* hz_last_error(void) { return g_last_error.c_str(); }
+
+hz_status hz_check_status(int* enabled, uint64_t* failures, uint64_t* first, int clear) {
+  return guarded([&] {
+    require(enabled && failures && first, "null output");
+#ifdef HZ_CHECKED
+    *enabled = 1;
+#else
+    *enabled = 0;
+#endif
+    *failures = 0;
+    *first = 0;
+    for (auto read : check_readers()) {
+      unsigned long long w[2] = {0ull, 0ull};
+      if (read(w, clear) != 0) throw Error(HZ_ERR_CUDA, "reading the checked-index words failed");
+      if (w[0] && !*failures) *first = w[1];
+      *failures += w[0];
+    }
+  });
+}
 
 hz_status hz_opts_default(int dim, hz_opts* out) {
   return guarded([&] {

@@ -56,6 +56,40 @@ inline void require(bool ok, const std::string& what) {
   if (!ok) throw Error(HZ_ERR_INVALID_ARG, what);
 }
 
+// ---------------------------------------------------------------- checked build
+// Built with -DHZ_CHECKED (build.py --checked: libhz_checked.so), every
+// instrumented global access of the solve's kernels tests its element index
+// against the extent of the array it reads or writes.  An index outside
+// [0, n) is counted in a device word of the translation unit, the first one
+// is recorded (source line, index), and the access is moved to element 0, so
+// it stays inside the array: the kernel runs on and never traps.
+// hz_check_status reads (and may clear) the words of every translation unit.
+// Without HZ_CHECKED, HZ_AT(i, n) is i and HZ_EXT(n) is empty: no cost.
+void check_register(int (*read)(unsigned long long* words, int clear));
+#ifdef HZ_CHECKED
+static __device__ unsigned long long hz_chk_words[2];   // failures; first (line << 40 | index bits)
+__device__ __forceinline__ long long hz_chk(long long i, long long n, unsigned line) {
+  if (i >= 0 && i < n) return i;
+  if (atomicAdd(&hz_chk_words[0], 1ull) == 0ull)
+    hz_chk_words[1] = ((unsigned long long)line << 40) | ((unsigned long long)i & 0xffffffffffull);
+  return 0;
+}
+#define HZ_AT(i, n) ::hz::hz_chk((long long)(i), (long long)(n), __LINE__)
+#define HZ_EXT(n) , hz_ext = (long long)(n)
+static int hz_chk_read(unsigned long long* w, int clear) {
+  if (cudaMemcpyFromSymbol(w, hz_chk_words, sizeof(hz_chk_words)) != cudaSuccess) return -1;
+  if (clear) {
+    const unsigned long long z[2] = {0ull, 0ull};
+    if (cudaMemcpyToSymbol(hz_chk_words, z, sizeof(z)) != cudaSuccess) return -1;
+  }
+  return 0;
+}
+static const int hz_chk_registered = (check_register(hz_chk_read), 0);
+#else
+#define HZ_AT(i, n) (i)
+#define HZ_EXT(n)
+#endif
+
 // ---------------------------------------------------------------- complex
 template <typename T> struct cplx;
 template <> struct cplx<float> { using t = float2; };
@@ -299,6 +333,47 @@ std::vector<std::array<int, 3>> patch_difference_offsets(int dim, hz_patch kind)
 __device__ __forceinline__ void pdl_enter() {
   asm volatile("griddepcontrol.wait;" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// L2 prefetch of elements [e0, e1] of a (one request per 128-byte line, every
+// address inside the run).  Kernels issue it before pdl_enter() for operands
+// written at setup (stencil planes, the coarsest inverse): with programmatic
+// dependent launch the block is often resident while its predecessor still
+// runs, so those lines travel from HBM to L2 during the predecessor instead
+// of after it.
+template <typename V>
+__device__ __forceinline__ void prefetch_l2_run(const V* a, long long e0, long long e1) {
+  const char* p0 = reinterpret_cast<const char*>(a + e0);
+  const char* p1 = reinterpret_cast<const char*>(a + e1);
+  const char* q = p0;
+  for (; q <= p1; q += 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(q));
+  if (((uintptr_t)(q - 128) >> 7) != ((uintptr_t)p1 >> 7)) asm volatile("prefetch.global.L2 [%0];" ::"l"(p1));
+}
+
+// elements [e0, e1] of a, the lines spread over nth threads
+template <typename V>
+__device__ __forceinline__ void prefetch_l2_span(const V* a, long long e0, long long e1, int tid, int nth) {
+  const char* p0 = reinterpret_cast<const char*>(a + e0);
+  const char* p1 = reinterpret_cast<const char*>(a + e1);
+  const long long lines = ((long long)(p1 - p0) >> 7) + 1;
+  for (long long k = tid; k < lines; k += nth) asm volatile("prefetch.global.L2 [%0];" ::"l"(p0 + (k << 7)));
+  if (tid == 0) asm volatile("prefetch.global.L2 [%0];" ::"l"(p1));
+}
+
+// The rows [y0, y0 + ny) x columns [x0, x0 + nx) of np planes of an nxg x nyg
+// grid (plane stride N elements), clipped to the grid, one (plane, row) per
+// thread step.
+template <typename V>
+__device__ __forceinline__ void prefetch_l2_planes(const V* P, int np, long long N, int nxg, int nyg, int x0, int nx,
+                                                   int y0, int ny, int tid, int nth) {
+  const int xa = x0 > 0 ? x0 : 0, xb = (x0 + nx < nxg ? x0 + nx : nxg) - 1;
+  if (xb < xa) return;
+  for (int task = tid; task < np * ny; task += nth) {
+    const int s = task / ny, y = y0 + (task - s * ny);
+    if (y < 0 || y >= nyg) continue;
+    const long long row = (long long)s * N + (long long)y * nxg;
+    prefetch_l2_run(P, row + xa, row + xb);
+  }
 }
 
 template <typename... KArgs, typename... Args>

@@ -276,7 +276,7 @@ __device__ __forceinline__ auto box_Au(const Geo& g, const c_t<T>* __restrict__ 
                           (DIM == 2 || (z + dz >= 0 && z + dz < g.nz));
           qq = ok ? qq : q;
         }
-        acc = cfma(P[s * g.N + p], ld(qq), acc);
+        acc = cfma(P[HZ_AT(s * g.N + p, (long long)W * W * (DIM == 3 ? W : 1) * g.N)], ld(qq), acc);
       }
   return acc;
 }
@@ -312,18 +312,19 @@ __device__ __forceinline__ auto box_Au_half(const Geo& g, const c_t<T>* __restri
                           (DIM == 2 || (z + dz >= 0 && z + dz < g.nz));
           qp = ok ? qp : q;
         }
-        acc = cfma(P[k * g.N + p], ld(qp), acc);
+        constexpr long long NH = (long long)(2 * RZ + 1) * W * W - C;   // half planes stored
+        acc = cfma(P[HZ_AT(k * g.N + p, NH * g.N)], ld(qp), acc);
         if (s == C) continue;
         if (CHECK) {
           // the mirrored entry lives at node p - s: outside the grid the address
           // is replaced by p and the coefficient by 0
           const bool ok = x - dx >= 0 && x - dx < g.nx && y - dy >= 0 && y - dy < g.ny &&
                           (DIM == 2 || (z - dz >= 0 && z - dz < g.nz));
-          c_t<T> cm = P[k * g.N + (ok ? p - no : p)];
+          c_t<T> cm = P[HZ_AT(k * g.N + (ok ? p - no : p), NH * g.N)];
           cm = ok ? cm : cmk<c_t<T>>(0, 0);
           acc = cfma(cm, ld(ok ? q - fo : q), acc);
         } else {
-          acc = cfma(P[k * g.N + p - no], ld(q - fo), acc);
+          acc = cfma(P[HZ_AT(k * g.N + p - no, NH * g.N)], ld(q - fo), acc);
         }
       }
   return acc;
@@ -335,7 +336,7 @@ template <typename T, int DIM, int AK, bool CHECK, typename LD>
 __device__ __forceinline__ auto apply_A(const Geo& g, T invh2, const c_t<T>* __restrict__ A, const LD& ld, int p, int q,
                                         int x, int y, int z) {
   if constexpr (AK == 0)
-    return fine_Au<T, DIM, CHECK>(g, invh2, A[p], ld, q, x, y, z);
+    return fine_Au<T, DIM, CHECK>(g, invh2, A[HZ_AT(p, g.N)], ld, q, x, y, z);
   else if constexpr (AK > 10)
     return box_Au_half<T, DIM, AK - 10, CHECK>(g, A, ld, p, q, x, y, z);
   else
@@ -355,7 +356,7 @@ __device__ __forceinline__ auto list_Au(const Geo& g, const MList& m, const c_t<
       const bool ok = xx >= 0 && xx < g.nx && yy >= 0 && yy < g.ny && (DIM == 2 || (zz >= 0 && zz < g.nz));
       qq = ok ? qq : q;
     }
-    acc = cfma(P[s * g.N + p], ld(qq), acc);
+    acc = cfma(P[HZ_AT(s * g.N + p, (long long)m.n * g.N)], ld(qq), acc);
   }
   return acc;
 }
@@ -375,17 +376,18 @@ __device__ __forceinline__ auto sym_Au(const Geo& g, const LST& m, const c_t<T>*
       const int dx = m.d[s][0], dy = m.d[s][1], dz = m.d[s][2];
       const bool okp = x + dx >= 0 && x + dx < g.nx && y + dy >= 0 && y + dy < g.ny &&
                        (DIM == 2 || (z + dz >= 0 && z + dz < g.nz));
-      acc = cfma(P[s * g.N + p], ld(okp ? q + m.flat[s] : q), acc);
+      acc = cfma(P[HZ_AT(s * g.N + p, (long long)m.n * g.N)], ld(okp ? q + m.flat[s] : q), acc);
       if constexpr (SYM) {
         const bool okm = m.mirror[s] && x - dx >= 0 && x - dx < g.nx && y - dy >= 0 && y - dy < g.ny &&
                          (DIM == 2 || (z - dz >= 0 && z - dz < g.nz));
-        const c_t<T> cm = P[s * g.N + (okm ? p - m.nflat[s] : p)];
+        const c_t<T> cm = P[HZ_AT(s * g.N + (okm ? p - m.nflat[s] : p), (long long)m.n * g.N)];
         acc = cfma(okm ? cm : cmk<c_t<T>>(0, 0), ld(okm ? q - m.flat[s] : q), acc);
       }
     } else {
-      acc = cfma(P[s * g.N + p], ld(q + m.flat[s]), acc);
+      acc = cfma(P[HZ_AT(s * g.N + p, (long long)m.n * g.N)], ld(q + m.flat[s]), acc);
       if constexpr (SYM)
-        if (m.mirror[s]) acc = cfma(P[s * g.N + p - m.nflat[s]], ld(q - m.flat[s]), acc);
+        if (m.mirror[s])
+          acc = cfma(P[HZ_AT(s * g.N + p - m.nflat[s], (long long)m.n * g.N)], ld(q - m.flat[s]), acc);
     }
   }
   if constexpr (SYM) return wc[p] * acc;
@@ -405,7 +407,7 @@ __global__ void __launch_bounds__(BX* BY, MB) k_resid(Geo g, T invh2, const c_t<
   const bool in = interior_block<DIM>(g, RA);
   int x, y, z, p, q;
   if (!node_xyz(g, x, y, z, p, q)) return;
-  auto ld = [u](int i) { return ldp<T, VR>(u, i); };
+  auto ld = [u HZ_EXT((long long)g.N * g.R)](int i) { return ldp<T, VR>(u, HZ_AT(i, hz_ext)); };
   const pk_t<T, VR> a = in ? apply_A<T, DIM, AK, false>(g, invh2, A, ld, p, q, x, y, z)
                            : apply_A<T, DIM, AK, true>(g, invh2, A, ld, p, q, x, y, z);
   stp<T, VR>(r, q, ldp<T, VR>(f, q) - a);
@@ -421,7 +423,7 @@ __global__ void __launch_bounds__(BX* BY, MB) k_sweep0(Geo g, MList m, const c_t
   const bool in = interior_block<DIM>(g, m.rho);
   int x, y, z, p, q;
   if (!node_xyz(g, x, y, z, p, q)) return;
-  auto ld = [f](int i) { return ldp<T, VR>(f, i); };
+  auto ld = [f HZ_EXT((long long)g.N * g.R)](int i) { return ldp<T, VR>(f, HZ_AT(i, hz_ext)); };
   const pk_t<T, VR> v = in ? list_Au<T, DIM, false>(g, m, M, ld, p, q, x, y, z)
                            : list_Au<T, DIM, true>(g, m, M, ld, p, q, x, y, z);
   stp<T, VR>(u, q, w * v);
@@ -437,7 +439,7 @@ __global__ void __launch_bounds__(BX* BY, MB) k_sweep0_sym(Geo g, SList m, const
   const bool in = interior_block<DIM>(g, m.rho);
   int x, y, z, p, q;
   if (!node_xyz(g, x, y, z, p, q)) return;
-  auto ld = [f](int i) { return ldp<T, VR>(f, i); };
+  auto ld = [f HZ_EXT((long long)g.N * g.R)](int i) { return ldp<T, VR>(f, HZ_AT(i, hz_ext)); };
   const pk_t<T, VR> v = in ? sym_Au<T, DIM, false, true>(g, m, M, wc, ld, p, q, x, y, z)
                            : sym_Au<T, DIM, true, true>(g, m, M, wc, ld, p, q, x, y, z);
   stp<T, VR>(u, q, w * v);
@@ -456,7 +458,10 @@ __global__ void __launch_bounds__(BX* BY, MB) k_sweep0_resid_diag(Geo g, T invh2
   int x, y, z, p, q;
   if (!node_xyz(g, x, y, z, p, q)) return;
   const int lr = g.lr;
-  auto ld = [m0, f, w, lr](int i) { return w * cmul(m0[i >> lr], ldp<T, VR>(f, i)); };
+  auto ld = [m0, f, w, lr HZ_EXT((long long)g.N * g.R)](int i) {
+    const int j = (int)HZ_AT(i, hz_ext);
+    return w * cmul(m0[j >> lr], ldp<T, VR>(f, j));
+  };
   const pk_t<T, VR> a = in ? apply_A<T, DIM, AK, false>(g, invh2, A, ld, p, q, x, y, z)
                            : apply_A<T, DIM, AK, true>(g, invh2, A, ld, p, q, x, y, z);
   const pk_t<T, VR> fp = ldp<T, VR>(f, q);
@@ -474,7 +479,7 @@ __global__ void __launch_bounds__(BX* BY, MB) k_sweep_out(Geo g, MList m, const 
   const bool inb = interior_block<DIM>(g, m.rho);
   int x, y, z, p, q;
   if (!node_xyz(g, x, y, z, p, q)) return;
-  auto ld = [r](int i) { return ldp<T, VR>(r, i); };
+  auto ld = [r HZ_EXT((long long)g.N * g.R)](int i) { return ldp<T, VR>(r, HZ_AT(i, hz_ext)); };
   const pk_t<T, VR> v = inb ? list_Au<T, DIM, false>(g, m, M, ld, p, q, x, y, z)
                             : list_Au<T, DIM, true>(g, m, M, ld, p, q, x, y, z);
   stp<T, VR>(out, q, ldp<T, VR>(in, q) + w * v);
@@ -490,7 +495,7 @@ __global__ void __launch_bounds__(BX* BY, MB) k_sweep_out_sym(Geo g, SList m, co
   const bool inb = interior_block<DIM>(g, m.rho);
   int x, y, z, p, q;
   if (!node_xyz(g, x, y, z, p, q)) return;
-  auto ld = [r](int i) { return ldp<T, VR>(r, i); };
+  auto ld = [r HZ_EXT((long long)g.N * g.R)](int i) { return ldp<T, VR>(r, HZ_AT(i, hz_ext)); };
   const pk_t<T, VR> v = inb ? sym_Au<T, DIM, false, true>(g, m, M, wc, ld, p, q, x, y, z)
                             : sym_Au<T, DIM, true, true>(g, m, M, wc, ld, p, q, x, y, z);
   stp<T, VR>(out, q, ldp<T, VR>(in, q) + w * v);
@@ -508,7 +513,7 @@ __global__ void __launch_bounds__(BX* BY, MB) k_resid_sweep_diag(Geo g, T invh2,
   const bool inb = interior_block<DIM>(g, RA);
   int x, y, z, p, q;
   if (!node_xyz(g, x, y, z, p, q)) return;
-  auto ld = [in](int i) { return ldp<T, VR>(in, i); };
+  auto ld = [in HZ_EXT((long long)g.N * g.R)](int i) { return ldp<T, VR>(in, HZ_AT(i, hz_ext)); };
   const pk_t<T, VR> a = inb ? apply_A<T, DIM, AK, false>(g, invh2, A, ld, p, q, x, y, z)
                             : apply_A<T, DIM, AK, true>(g, invh2, A, ld, p, q, x, y, z);
   stp<T, VR>(out, q, ldp<T, VR>(in, q) + w * cmul(m0[p], ldp<T, VR>(f, q) - a));
@@ -567,10 +572,10 @@ __global__ void __launch_bounds__(BX* BY, MB) k_restrict(Geo gf, Geo gc, const c
       const int row = (iz[kz] * gf.ny + iy[ky]) * gf.nx;
 #pragma unroll
       for (int kx = 0; kx <= 2 * RAD; ++kx)
-        acc = acc + (wyz * wx[kx]) * ldp<T, VR>(r, (row + ix[kx]) * gf.R + rr);
+        acc = acc + (wyz * wx[kx]) * ldp<T, VR>(r, (int)HZ_AT((row + ix[kx]) * gf.R + rr, (long long)gf.N * gf.R));
     }
   }
-  stp<T, VR>(fc, qc, acc);
+  stp<T, VR>(fc, (int)HZ_AT(qc, (long long)gc.N * gc.R), acc);
 }
 
 // 1D prolongation stencil of fine index j: coarse nodes J0, J0+1, J0+2 with
@@ -620,7 +625,7 @@ __device__ __forceinline__ pk_t<T, VR> prolong_at(const Geo& gf, const Geo& gc, 
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         if (wx[a] == 0.0f) continue;
-        acc = acc + (T)(wyz * wx[a]) * ldp<T, VR>(ec, row + a * gc.R);
+        acc = acc + (T)(wyz * wx[a]) * ldp<T, VR>(ec, (int)HZ_AT(row + a * gc.R, (long long)gc.N * gc.R));
       }
     }
   }
@@ -659,7 +664,7 @@ __global__ void __launch_bounds__(BX* BY, MB) k_prolong_fused_2d(Geo gf, Geo gc,
     const int gx = x0 + tx, gy = y0 + ty;
     c_t<T> v = cmk<c_t<T>>(0, 0);
     if (gx >= 0 && gx < gf.nx && gy >= 0 && gy < gf.ny)
-      v = t[gy * gf.nx + gx] + prolong_at<T, 2, KIND>(gf, gc, ec, gx, gy, 0);
+      v = t[HZ_AT(gy * gf.nx + gx, gf.N)] + prolong_at<T, 2, KIND>(gf, gc, ec, gx, gy, 0);
     sm[ty][tx] = v;
   }
   __syncthreads();
@@ -688,10 +693,11 @@ __global__ void __launch_bounds__(BX* BY, MB) k_prolong_fused_2d(Geo gf, Geo gc,
       for (int dx = -R0; dx <= R0; ++dx) {
         const int s = (dy + R0) * W + (dx + R0);
         if (s < C) continue;
-        a = cfma(A[(s - C) * gf.N + p], sm[ly + dy][lx + dx], a);
+        a = cfma(A[HZ_AT((s - C) * gf.N + p, (long long)(C + 1) * gf.N)], sm[ly + dy][lx + dx], a);
         if (s == C) continue;
         const bool ok = x - dx >= 0 && x - dx < gf.nx && y - dy >= 0 && y - dy < gf.ny;
-        a = cfma(A[(s - C) * gf.N + (ok ? p - dx - dy * gf.nx : p)], sm[ly - dy][lx - dx], a);
+        a = cfma(A[HZ_AT((s - C) * gf.N + (ok ? p - dx - dy * gf.nx : p), (long long)(C + 1) * gf.N)],
+                 sm[ly - dy][lx - dx], a);
       }
   } else {
     // coefficients reaching outside the grid are stored as zeros
@@ -701,7 +707,7 @@ __global__ void __launch_bounds__(BX* BY, MB) k_prolong_fused_2d(Geo gf, Geo gc,
     for (int dy = -AK; dy <= AK; ++dy)
 #pragma unroll
       for (int dx = -AK; dx <= AK; ++dx)
-        a = cfma(A[((dy + AK) * W + (dx + AK)) * gf.N + p], sm[ly + dy][lx + dx], a);
+        a = cfma(A[HZ_AT(((dy + AK) * W + (dx + AK)) * gf.N + p, (long long)W * W * gf.N)], sm[ly + dy][lx + dx], a);
   }
   const c_t<T> res = f[p] - a;
   if (DIAG) {
@@ -756,11 +762,14 @@ __global__ void __launch_bounds__(BX* BY, MB ? MB : 4) k_fine_down_diag_2d(Geo g
   __shared__ c_t<T> st[TY][TX];
   __shared__ c_t<T> sr[RY][RX];
   __shared__ c_t<T> sh[RY][CX];                       // residual rows restricted along x
-  pdl_enter();
-  if (active && !*active) return;
   const int tid = threadIdx.y * BX + threadIdx.x;
   const int X0 = blockIdx.x * CX, Y0 = blockIdx.y * CY;
   const int rx0 = 2 * X0 - RR, ry0 = 2 * Y0 - RR;
+  // the diagonals of the smoother and the operator (setup data) over the t region
+  prefetch_l2_planes(m0, 1, gf.N, gf.nx, gf.ny, rx0 - 1, TX, ry0 - 1, TY, tid, NTH);
+  prefetch_l2_planes(A, 1, gf.N, gf.nx, gf.ny, rx0, RX, ry0, RY, tid, NTH);
+  pdl_enter();
+  if (active && !*active) return;
   // every entry's loads of a phase are issued before any is used (fixed,
   // unrolled trip counts): one memory round trip per phase
   constexpr int NT = (TX * TY + NTH - 1) / NTH, NR = (RX * RY + NTH - 1) / NTH;
@@ -771,7 +780,7 @@ __global__ void __launch_bounds__(BX* BY, MB ? MB : 4) k_fine_down_diag_2d(Geo g
       const int i = tid + k * NTH, ty = i / TX, tx = i - ty * TX;
       const int gx = rx0 - 1 + tx, gy = ry0 - 1 + ty;
       const bool in = i < TX * TY && gx >= 0 && gx < gf.nx && gy >= 0 && gy < gf.ny;
-      const int p = in ? gy * gf.nx + gx : 0;
+      const int p = (int)HZ_AT(in ? gy * gf.nx + gx : 0, gf.N);
       mv[k] = in ? m0[p] : cmk<c_t<T>>(0, 0);
       fv[k] = in ? f[p] : cmk<c_t<T>>(0, 0);
     }
@@ -789,7 +798,7 @@ __global__ void __launch_bounds__(BX* BY, MB ? MB : 4) k_fine_down_diag_2d(Geo g
       const int i = tid + k * NTH, ry = i / RX, rx = i - ry * RX;
       const int gx = rx0 + rx, gy = ry0 + ry;
       const bool in = i < RX * RY && gx >= 0 && gx < gf.nx && gy >= 0 && gy < gf.ny;
-      const int p = in ? gy * gf.nx + gx : 0;
+      const int p = (int)HZ_AT(in ? gy * gf.nx + gx : 0, gf.N);
       av[k] = in ? A[p] : cmk<c_t<T>>(0, 0);
       fv[k] = in ? f[p] : cmk<c_t<T>>(0, 0);
     }
@@ -830,7 +839,7 @@ __global__ void __launch_bounds__(BX* BY, MB ? MB : 4) k_fine_down_diag_2d(Geo g
     const T wy = (jy >= 0 && jy < gf.ny) ? (T)(0.5f * p1f(RK, gf.ny, gc.ny, jy, Y)) : T(0);
     acc = acc + wy * sh[2 * cy + k][cx];
   }
-  fc[Y * gc.nx + X] = acc;
+  fc[HZ_AT(Y * gc.nx + X, gc.N)] = acc;
 }
 
 // up pass, 2D: one block = 64 x FY fine nodes (2 x FY/8 per thread).  The
@@ -854,10 +863,13 @@ __global__ void __launch_bounds__(BX* BY, MB ? MB : 4) k_fine_up_diag_2d(Geo gf,
   __shared__ c_t<T> sh[EY][UX];                      // coarse rows prolongated along x
   __shared__ float wcx[UX][3], wcy[UY][3];
   __shared__ int icx[UX], icy[UY];
-  pdl_enter();
-  if (active && !*active) return;
   const int tid = threadIdx.y * BX + threadIdx.x;
   const int x0 = blockIdx.x * FX, y0 = blockIdx.y * FY;
+  // the diagonals of the smoother and the operator (setup data) over the tile
+  prefetch_l2_planes(m0, 1, gf.N, gf.nx, gf.ny, x0 - 1, UX, y0 - 1, UY, tid, NTH);
+  prefetch_l2_planes(A, 1, gf.N, gf.nx, gf.ny, x0, FX, y0, FY, tid, NTH);
+  pdl_enter();
+  if (active && !*active) return;
   const int ex0 = ((x0 - 1) >> 1) - 1, ey0 = ((y0 - 1) >> 1) - 1;   // coarse origin (floor division)
   constexpr int NE = (EX * EY + NTH - 1) / NTH, NU = (UX * UY + NTH - 1) / NTH;
   c_t<T> fvs[NU], mvs[NU];
@@ -868,14 +880,14 @@ __global__ void __launch_bounds__(BX* BY, MB ? MB : 4) k_fine_up_diag_2d(Geo gf,
       const int i = tid + k * NTH, ey = i / EX, exx = i - ey * EX;
       const int gx = ex0 + exx, gy = ey0 + ey;
       const bool in = i < EX * EY && gx >= 0 && gx < gc.nx && gy >= 0 && gy < gc.ny;
-      ev[k] = in ? ec[gy * gc.nx + gx] : cmk<c_t<T>>(0, 0);
+      ev[k] = in ? ec[HZ_AT(gy * gc.nx + gx, gc.N)] : cmk<c_t<T>>(0, 0);
     }
 #pragma unroll
     for (int k = 0; k < NU; ++k) {
       const int i = tid + k * NTH, uy = i / UX, ux = i - uy * UX;
       const int gx = x0 - 1 + ux, gy = y0 - 1 + uy;
       const bool in = i < UX * UY && gx >= 0 && gx < gf.nx && gy >= 0 && gy < gf.ny;
-      const int p = in ? gy * gf.nx + gx : 0;
+      const int p = (int)HZ_AT(in ? gy * gf.nx + gx : 0, gf.N);
       fvs[k] = in ? f[p] : cmk<c_t<T>>(0, 0);
       mvs[k] = in ? m0[p] : cmk<c_t<T>>(0, 0);
     }
@@ -931,7 +943,7 @@ __global__ void __launch_bounds__(BX* BY, MB ? MB : 4) k_fine_up_diag_2d(Geo gf,
     const int lx = threadIdx.x + (k % (FX / BX)) * BX, ly = threadIdx.y + (k / (FX / BX)) * BY;
     const int x = x0 + lx, y = y0 + ly;
     const bool in = x < gf.nx && y < gf.ny;
-    dv[k] = in ? A[y * gf.nx + x] : cmk<c_t<T>>(0, 0);
+    dv[k] = in ? A[HZ_AT(y * gf.nx + x, gf.N)] : cmk<c_t<T>>(0, 0);
   }
 #pragma unroll
   for (int k = 0; k < NO; ++k) {
@@ -939,7 +951,7 @@ __global__ void __launch_bounds__(BX* BY, MB ? MB : 4) k_fine_up_diag_2d(Geo gf,
     const int x = x0 + lx, y = y0 + ly;
     if (x >= gf.nx || y >= gf.ny) continue;
     const c_t<T> a = fine_tile_Au_2d<T, UX>(su, ly + 1, lx + 1, dv[k], invh2, x, y, gf);
-    out[y * gf.nx + x] = su[ly + 1][lx + 1] + w * cmul(sm[ly + 1][lx + 1], sf[ly + 1][lx + 1] - a);
+    out[HZ_AT(y * gf.nx + x, gf.N)] = su[ly + 1][lx + 1] + w * cmul(sm[ly + 1][lx + 1], sf[ly + 1][lx + 1] - a);
   }
 }
 
@@ -976,11 +988,11 @@ __device__ __forceinline__ c_t<T> tile_Mv(const Geo& g, const LST& m, const c_t<
 #pragma unroll 8
   for (int s = 0; s < m.n; ++s) {
     const int dx = m.d[s][0], dy = m.d[s][1];
-    acc = cfma(P[s * g.N + p], tile[(ly + dy) * W + lx + dx], acc);
+    acc = cfma(P[HZ_AT(s * g.N + p, (long long)m.n * g.N)], tile[(ly + dy) * W + lx + dx], acc);
     if constexpr (SYM) {
       if (m.mirror[s]) {
         const bool okm = x - dx >= 0 && x - dx < g.nx && y - dy >= 0 && y - dy < g.ny;
-        const c_t<T> cm = okm ? P[s * g.N + p - m.nflat[s]] : cmk<c_t<T>>(0, 0);
+        const c_t<T> cm = okm ? P[HZ_AT(s * g.N + p - m.nflat[s], (long long)m.n * g.N)] : cmk<c_t<T>>(0, 0);
         acc = cfma(cm, tile[(ly - dy) * W + lx - dx], acc);
       }
     }
@@ -1003,13 +1015,13 @@ __device__ __forceinline__ c_t<T> tile_Av(const Geo& g, const c_t<T>* __restrict
       const int s = (dy + RHO) * WB + (dx + RHO);
       if constexpr (AK > 10) {
         if (s < C) continue;
-        acc = cfma(A[(s - C) * g.N + p], tile[(ly + dy) * W + lx + dx], acc);
+        acc = cfma(A[HZ_AT((s - C) * g.N + p, (long long)(C + 1) * g.N)], tile[(ly + dy) * W + lx + dx], acc);
         if (s == C) continue;
         const bool ok = x - dx >= 0 && x - dx < g.nx && y - dy >= 0 && y - dy < g.ny;
-        const c_t<T> cm = ok ? A[(s - C) * g.N + p - dx - dy * g.nx] : cmk<c_t<T>>(0, 0);
+        const c_t<T> cm = ok ? A[HZ_AT((s - C) * g.N + p - dx - dy * g.nx, (long long)(C + 1) * g.N)] : cmk<c_t<T>>(0, 0);
         acc = cfma(cm, tile[(ly - dy) * W + lx - dx], acc);
       } else {
-        acc = cfma(A[s * g.N + p], tile[(ly + dy) * W + lx + dx], acc);
+        acc = cfma(A[HZ_AT(s * g.N + p, (long long)WB * WB * g.N)], tile[(ly + dy) * W + lx + dx], acc);
       }
     }
   return acc;
@@ -1031,12 +1043,17 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_level_down_2d(Geo gf, Geo g
   __shared__ c_t<T> st[TY * TX];
   __shared__ c_t<T> sr[RY * RX];
   __shared__ c_t<T> sh[RY * CX];
-  pdl_enter();
-  if (active && !*active) return;
   const int tid = threadIdx.x;
   const int X0 = blockIdx.x * CX, Y0 = blockIdx.y * CY;
   const int rx0 = 2 * X0 - RR, ry0 = 2 * Y0 - RR;
   const int tx0 = rx0 - RA, ty0 = ry0 - RA, fx0 = tx0 - RM, fy0 = ty0 - RM;
+  // the smoother's planes over the t region (mirrored entries up to RM
+  // further) and the operator's over the residual region (mirrored up to RA)
+  prefetch_l2_planes(M, m.n, gf.N, gf.nx, gf.ny, fx0, FX, fy0, FY, tid, NTH);
+  prefetch_l2_planes(A, AK > 10 ? (2 * RA + 1) * (2 * RA + 1) / 2 + 1 : (2 * RA + 1) * (2 * RA + 1), gf.N, gf.nx,
+                     gf.ny, tx0, TX, ty0, TY, tid, NTH);
+  pdl_enter();
+  if (active && !*active) return;
   constexpr int NF = (FX * FY + NTH - 1) / NTH;
   {
     c_t<T> v[NF];
@@ -1045,7 +1062,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_level_down_2d(Geo gf, Geo g
       const int i = tid + k * NTH, ly = i / FX, lx = i - ly * FX;
       const int gx = fx0 + lx, gy = fy0 + ly;
       const bool in = i < FX * FY && gx >= 0 && gx < gf.nx && gy >= 0 && gy < gf.ny;
-      v[k] = in ? f[gy * gf.nx + gx] : cmk<c_t<T>>(0, 0);
+      v[k] = in ? f[HZ_AT(gy * gf.nx + gx, gf.N)] : cmk<c_t<T>>(0, 0);
     }
 #pragma unroll
     for (int k = 0; k < NF; ++k) {
@@ -1060,7 +1077,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_level_down_2d(Geo gf, Geo g
     const int gx = tx0 + lx, gy = ty0 + ly;
     c_t<T> v = cmk<c_t<T>>(0, 0);
     if (gx >= 0 && gx < gf.nx && gy >= 0 && gy < gf.ny) {
-      const int p = gy * gf.nx + gx;
+      const int p = (int)HZ_AT(gy * gf.nx + gx, gf.N);
       v = w * tile_Mv<T, SYM>(gf, m, M, wc, sf, FX, lx + RM, ly + RM, p, gx, gy);
       if (gx >= 2 * X0 && gx < 2 * X0 + 2 * CX && gy >= 2 * Y0 && gy < 2 * Y0 + 2 * CY) t[p] = v;
     }
@@ -1072,7 +1089,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_level_down_2d(Geo gf, Geo g
     const int gx = rx0 + lx, gy = ry0 + ly;
     c_t<T> v = cmk<c_t<T>>(0, 0);
     if (gx >= 0 && gx < gf.nx && gy >= 0 && gy < gf.ny) {
-      const int p = gy * gf.nx + gx;
+      const int p = (int)HZ_AT(gy * gf.nx + gx, gf.N);
       v = sf[(ly + RA + RM) * FX + lx + RA + RM] - tile_Av<T, AK>(gf, A, st, TX, lx + RA, ly + RA, p, gx, gy);
     }
     sr[i] = v;
@@ -1103,7 +1120,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_level_down_2d(Geo gf, Geo g
       const T wy = (jy >= 0 && jy < gf.ny) ? (T)(0.5f * p1f(RK, gf.ny, gc.ny, jy, Y)) : T(0);
       acc = acc + wy * sh[(2 * cy + k) * CX + cx];
     }
-    fc[Y * gc.nx + X] = acc;
+    fc[HZ_AT(Y * gc.nx + X, gc.N)] = acc;
   }
 }
 
@@ -1126,11 +1143,16 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_level_up_2d(Geo gf, Geo gc,
   __shared__ c_t<T> sh[EY * UX];
   __shared__ float wcx[UX][3], wcy[UY][3];
   __shared__ int icx[UX], icy[UY];
-  pdl_enter();
-  if (active && !*active) return;
   const int tid = threadIdx.x;
   const int x0 = blockIdx.x * OX, y0 = blockIdx.y * OY;
   const int ux0 = x0 - RM - RA, uy0 = y0 - RM - RA;
+  // the operator's planes over the u' region, the smoother's over the
+  // residual region (each with its mirrored reach)
+  prefetch_l2_planes(A, AK > 10 ? (2 * RA + 1) * (2 * RA + 1) / 2 + 1 : (2 * RA + 1) * (2 * RA + 1), gf.N, gf.nx,
+                     gf.ny, ux0, UX, uy0, UY, tid, NTH);
+  prefetch_l2_planes(M, m.n, gf.N, gf.nx, gf.ny, ux0, UX, uy0, UY, tid, NTH);
+  pdl_enter();
+  if (active && !*active) return;
   const int ex0 = (ux0 >> 1) - 1, ey0 = (uy0 >> 1) - 1;             // floor division
   constexpr int NE = (EX * EY + NTH - 1) / NTH, NU = (UX * UY + NTH - 1) / NTH;
   c_t<T> tv[NU];
@@ -1141,14 +1163,14 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_level_up_2d(Geo gf, Geo gc,
       const int i = tid + k * NTH, ly = i / EX, lx = i - ly * EX;
       const int gx = ex0 + lx, gy = ey0 + ly;
       const bool in = i < EX * EY && gx >= 0 && gx < gc.nx && gy >= 0 && gy < gc.ny;
-      ev[k] = in ? ec[gy * gc.nx + gx] : cmk<c_t<T>>(0, 0);
+      ev[k] = in ? ec[HZ_AT(gy * gc.nx + gx, gc.N)] : cmk<c_t<T>>(0, 0);
     }
 #pragma unroll
     for (int k = 0; k < NU; ++k) {
       const int i = tid + k * NTH, ly = i / UX, lx = i - ly * UX;
       const int gx = ux0 + lx, gy = uy0 + ly;
       const bool in = i < UX * UY && gx >= 0 && gx < gf.nx && gy >= 0 && gy < gf.ny;
-      tv[k] = in ? t[gy * gf.nx + gx] : cmk<c_t<T>>(0, 0);
+      tv[k] = in ? t[HZ_AT(gy * gf.nx + gx, gf.N)] : cmk<c_t<T>>(0, 0);
     }
 #pragma unroll
     for (int k = 0; k < NE; ++k) {
@@ -1198,7 +1220,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_level_up_2d(Geo gf, Geo gc,
     const int gx = x0 - RM + lx, gy = y0 - RM + ly;
     c_t<T> v = cmk<c_t<T>>(0, 0);
     if (gx >= 0 && gx < gf.nx && gy >= 0 && gy < gf.ny) {
-      const int p = gy * gf.nx + gx;
+      const int p = (int)HZ_AT(gy * gf.nx + gx, gf.N);
       v = f[p] - tile_Av<T, AK>(gf, A, su, UX, lx + RA, ly + RA, p, gx, gy);
     }
     sr[i] = v;
@@ -1208,7 +1230,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_level_up_2d(Geo gf, Geo gc,
     const int ly = i / OX, lx = i - ly * OX;
     const int gx = x0 + lx, gy = y0 + ly;
     if (gx >= gf.nx || gy >= gf.ny) continue;
-    const int p = gy * gf.nx + gx;
+    const int p = (int)HZ_AT(gy * gf.nx + gx, gf.N);
     out[p] = su[(ly + RM + RA) * UX + lx + RM + RA] + w * tile_Mv<T, SYM>(gf, m, M, wc, sr, RX, lx + RM, ly + RM, p, gx, gy);
   }
 }
@@ -1220,6 +1242,13 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_level_up_2d(Geo gf, Geo gc,
 template <typename T, int TPR>
 __global__ void __launch_bounds__(256) k_dense_gemv(int n, const c_t<T>* __restrict__ A, const c_t<T>* __restrict__ f,
                                                     c_t<T>* __restrict__ u, const int* active) {
+  {
+    // this block's rows of the inverse (setup data) into L2 while the
+    // previous kernel runs
+    constexpr int RPB = 256 / TPR;
+    const int r0 = blockIdx.x * RPB, r1 = (r0 + RPB < n ? r0 + RPB : n) - 1;
+    if (r0 <= r1) prefetch_l2_span(A, (long long)r0 * n, (long long)r1 * n + n - 1, threadIdx.x, 256);
+  }
   pdl_enter();
   if (active && !*active) return;
   using V = c_t<T>;
@@ -1233,9 +1262,10 @@ __global__ void __launch_bounds__(256) k_dense_gemv(int n, const c_t<T>* __restr
     int j = tr;
     for (; j + 3 * TPR < n; j += 4 * TPR) {
 #pragma unroll
-      for (int k = 0; k < 4; ++k) acc[k] = cfma(a[j + k * TPR], f[j + k * TPR], acc[k]);
+      for (int k = 0; k < 4; ++k)
+        acc[k] = cfma(a[HZ_AT(j + k * TPR, n)], f[HZ_AT(j + k * TPR, n)], acc[k]);
     }
-    for (int k = 0; j < n; j += TPR, ++k) acc[k] = cfma(a[j], f[j], acc[k]);
+    for (int k = 0; j < n; j += TPR, ++k) acc[k] = cfma(a[HZ_AT(j, n)], f[HZ_AT(j, n)], acc[k]);
   }
   V t = (acc[0] + acc[1]) + (acc[2] + acc[3]);
   for (int o = 16; o > 0; o >>= 1) {

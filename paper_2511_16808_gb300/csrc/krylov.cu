@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(kRedBlock) k_gs_dots(Geo g, double invh2, cons
     const double2 a = apply_A(g, invh2, diag, z, p, x, y, zz);
     w[p] = a;
 #pragma unroll
-    for (int i = 0; i < NV; ++i) acc[i] = dot_acc(acc[i], V[(long long)i * g.N + p], a);
+    for (int i = 0; i < NV; ++i) acc[i] = dot_acc(acc[i], V[HZ_AT((long long)i * g.N + p, (long long)NV * g.N)], a);
   });
   reduce_last_multi<NV>(acc, partials, gridDim.x, blockIdx.x, &st->counter, st->h1);
 }
@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(kRedBlock) k_gs_dots_more(int N, const double2
   for (int p = b0 + threadIdx.x; p < b1; p += kRedBlock) {
     const double2 a = w[p];
 #pragma unroll
-    for (int i = 0; i < NV; ++i) acc[i] = dot_acc(acc[i], Vb[(long long)i * N + p], a);
+    for (int i = 0; i < NV; ++i) acc[i] = dot_acc(acc[i], Vb[HZ_AT((long long)i * N + p, (long long)NV * N)], a);
   }
   reduce_last_multi<NV>(acc, partials, gridDim.x, blockIdx.x, &st->counter, st->h1 + base);
 }
@@ -267,8 +267,8 @@ __global__ void __launch_bounds__(kRedBlock) k_gs_update(int N, const double2* _
   for (int p = b0 + threadIdx.x; p < b1; p += kRedBlock) {
     double2 ww = w[p];
 #pragma unroll
-    for (int i = 0; i < NV; ++i) ww = axmy(ww, c[i], Vb[(long long)i * N + p]);
-    w[p] = ww;
+    for (int i = 0; i < NV; ++i) ww = axmy(ww, c[i], Vb[HZ_AT((long long)i * N + p, (long long)NV * N)]);
+    w[HZ_AT(p, N)] = ww;
     if constexpr (LAST) {
       if constexpr (std::is_same<TF, float2>::value) f[p] = make_float2(d2f_rn(ww.x), d2f_rn(ww.y));
       else f[p] = ww;

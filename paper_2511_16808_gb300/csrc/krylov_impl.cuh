@@ -201,17 +201,20 @@ __device__ __forceinline__ double2 apply_A(const Geo& g, double invh2, const dou
     double2 s;
     if constexpr (std::is_same<U, float2>::value) {
       if (g.dim == 3) {
-        const float2 n[6] = {v[p - 1], v[p + 1], v[p - g.nx], v[p + g.nx], v[p - g.sxy], v[p + g.sxy]};
+        const float2 n[6] = {v[HZ_AT(p - 1, g.N)], v[HZ_AT(p + 1, g.N)], v[HZ_AT(p - g.nx, g.N)],
+                             v[HZ_AT(p + g.nx, g.N)], v[HZ_AT(p - g.sxy, g.N)], v[HZ_AT(p + g.sxy, g.N)]};
         if (g.p2 >= 0) return diag_minus(d, vp, nbr_sum_pow2<6>(n, g.p2));
         s = nbr_sum<6>(n);
       } else {
-        const float2 n[4] = {v[p - 1], v[p + 1], v[p - g.nx], v[p + g.nx]};
+        const float2 n[4] = {v[HZ_AT(p - 1, g.N)], v[HZ_AT(p + 1, g.N)], v[HZ_AT(p - g.nx, g.N)],
+                             v[HZ_AT(p + g.nx, g.N)]};
         if (g.p2 >= 0) return diag_minus(d, vp, nbr_sum_pow2<4>(n, g.p2));
         s = nbr_sum<4>(n);
       }
     } else {
-      s = ld64(v, p - 1) + ld64(v, p + 1) + ld64(v, p - g.nx) + ld64(v, p + g.nx);
-      if (g.dim == 3) s = s + ld64(v, p - g.sxy) + ld64(v, p + g.sxy);
+      s = ld64(v, (int)HZ_AT(p - 1, g.N)) + ld64(v, (int)HZ_AT(p + 1, g.N)) + ld64(v, (int)HZ_AT(p - g.nx, g.N)) +
+          ld64(v, (int)HZ_AT(p + g.nx, g.N));
+      if (g.dim == 3) s = s + ld64(v, (int)HZ_AT(p - g.sxy, g.N)) + ld64(v, (int)HZ_AT(p + g.sxy, g.N));
     }
     // d v - invh2 s, with FMAs
     return make_double2(fma(d.x, vp.x, fma(-d.y, vp.y, -invh2 * s.x)), fma(d.x, vp.y, fma(d.y, vp.x, -invh2 * s.y)));

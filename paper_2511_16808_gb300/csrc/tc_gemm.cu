@@ -123,8 +123,9 @@ __global__ void __launch_bounds__(kTcThreads) k_coarse_gemm_tc(int n, int R, int
       const int st = L % kStages, c = c0 + L;
       unsigned char* dst = sm + st * SB;
       tc::mbar_expect_tx(&full[st], SB);
-      tc::bulk_g2s(dst, aimg + ((long long)tile * nch + c) * 2 * kTileFloats, 2 * kTileFloats * 4, &full[st]);
-      tc::bulk_g2s(dst + 2 * kTileFloats * 4, fimg + (long long)c * (FB / 4), FB, &full[st]);
+      const long long ab = HZ_AT((long long)tile * nch + c, (long long)tc_tiles(n) * nch);   // image block
+      tc::bulk_g2s(dst, aimg + ab * 2 * kTileFloats, 2 * kTileFloats * 4, &full[st]);
+      tc::bulk_g2s(dst + 2 * kTileFloats * 4, fimg + (long long)HZ_AT(c, nch) * (FB / 4), FB, &full[st]);
     };
     int loaded = 0;                                   // chunks whose copies were issued
     for (; loaded < kStages && loaded < nl; ++loaded) load(loaded);
@@ -196,9 +197,9 @@ __global__ void __launch_bounds__(kTcThreads) k_coarse_gemm_tc(int n, int R, int
       if (!rowok) continue;
       if (split == 1) {
 #pragma unroll
-        for (int q = 0; q < 16; ++q) U[(long long)i * R + c + q] = make_float2(re[q], im[q]);
+        for (int q = 0; q < 16; ++q) U[HZ_AT((long long)i * R + c + q, (long long)n * R)] = make_float2(re[q], im[q]);
       } else {
-        float* pp = part + ((long long)sidx * n + i) * 2 * R;
+        float* pp = part + HZ_AT(((long long)sidx * n + i) * 2 * R, (long long)split * n * 2 * R);
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
           pp[c + q] = re[q];

@@ -117,6 +117,7 @@ _SIGS = {
     "hz_profile_read": ([_P, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_double),
                          C.POINTER(C.c_double)], C.c_int),
     "hz_measure_peak": ([C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)], C.c_int),
+    "hz_check_status": ([C.POINTER(C.c_int), C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), C.c_int], C.c_int),
     "hz_memory_stats": ([C.c_int, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)], C.c_int),
     "hz_context_info": ([_P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
     "hz_level_count": ([_P, C.POINTER(C.c_int)], C.c_int),
@@ -204,6 +205,15 @@ def _stream(s):
 
 def hz_abi_version() -> int:
     return lib.hz_abi_version()
+
+
+def hz_check_status(clear: bool = False) -> dict:
+    """Checked-index build: {'enabled', 'failures', 'line', 'index'} of the
+    out-of-extent accesses since the last clear (line and index of the first)."""
+    en, fails, first = C.c_int(), C.c_uint64(), C.c_uint64()
+    _check(lib.hz_check_status(C.byref(en), C.byref(fails), C.byref(first), int(bool(clear))), "hz_check_status")
+    return {"enabled": bool(en.value), "failures": fails.value, "line": first.value >> 40,
+            "index": first.value & ((1 << 40) - 1)}
 
 
 def hz_status_string(s: int) -> str:

@@ -81,3 +81,10 @@ def test_long_restart_needs_one_rhs():
     with pytest.raises(hz.HzError) as e:
         hz.hz_setup_bytes(g, o)
     assert e.value.status == 1
+
+
+def test_check_status_in_normal_build():
+    """The normal library is not the checked-index build: the check reports
+    itself disabled with no failures (no device needed)."""
+    st = hz.hz_check_status()
+    assert st == {"enabled": False, "failures": 0, "line": 0, "index": 0}
