@@ -394,6 +394,25 @@ __device__ __forceinline__ auto sym_Au(const Geo& g, const LST& m, const c_t<T>*
   else return acc;                           // the planes hold M itself
 }
 
+// planes of the operator's stored form: the fine diagonal (AK = 0), a full
+// box of radius rho (AK = rho) or its symmetric half (AK = 10 + rho)
+template <int DIM, int AK>
+constexpr int a_planes() {
+  constexpr int W = 2 * (AK % 10) + 1, BOX = DIM == 3 ? W * W * W : W * W;
+  return AK == 0 ? 1 : (AK > 10 ? (BOX + 1) / 2 : BOX);
+}
+
+// L2 prefetch of the stencil planes a block of the one-RHS node kernels reads
+// (its 32 x 8 nodes of one z plane and their reach rho in x and y), issued
+// before pdl_enter() like the tile passes do: the planes are setup data
+template <typename T>
+__device__ __forceinline__ void prefetch_block_planes(const Geo& g, const c_t<T>* P, int np, int rho) {
+  if (g.R != 1) return;
+  const int x0 = (int)blockIdx.x * BX - rho, y0 = (int)blockIdx.y * BY - rho;
+  prefetch_l2_planes(P + (long long)blockIdx.z * g.sxy, np, g.N, g.nx, g.ny, x0, BX + 2 * rho, y0, BY + 2 * rho,
+                     (int)(threadIdx.y * BX + threadIdx.x), BX * BY);
+}
+
 // ------------------------------------------------------------------ kernels
 
 // r = f - A u
@@ -401,6 +420,7 @@ template <typename T, int DIM, int AK, int VR, int MB>
 __global__ void __launch_bounds__(BX* BY, MB) k_resid(Geo g, T invh2, const c_t<T>* __restrict__ A,
                                                   const c_t<T>* __restrict__ u, const c_t<T>* __restrict__ f,
                                                   c_t<T>* __restrict__ r, const int* active) {
+  prefetch_block_planes<T>(g, A, a_planes<DIM, AK>(), AK == 0 ? 0 : AK % 10);
   pdl_enter();
   if (active && !*active) return;
   constexpr int RA = AK == 0 ? 1 : AK % 10;
@@ -418,6 +438,7 @@ template <typename T, int DIM, int VR, int MB>
 __global__ void __launch_bounds__(BX* BY, MB) k_sweep0(Geo g, MList m, const c_t<T>* __restrict__ M, T w,
                                                    const c_t<T>* __restrict__ f, c_t<T>* __restrict__ u,
                                                    const int* active) {
+  prefetch_block_planes<T>(g, M, m.n, 0);
   pdl_enter();
   if (active && !*active) return;
   const bool in = interior_block<DIM>(g, m.rho);
@@ -434,6 +455,7 @@ template <typename T, int DIM, int VR, int MB>
 __global__ void __launch_bounds__(BX* BY, MB) k_sweep0_sym(Geo g, SList m, const c_t<T>* __restrict__ M,
                                                    const T* __restrict__ wc, T w, const c_t<T>* __restrict__ f,
                                                    c_t<T>* __restrict__ u, const int* active) {
+  prefetch_block_planes<T>(g, M, m.n, m.rho);
   pdl_enter();
   if (active && !*active) return;
   const bool in = interior_block<DIM>(g, m.rho);
@@ -451,6 +473,8 @@ __global__ void __launch_bounds__(BX* BY, MB) k_sweep0_resid_diag(Geo g, T invh2
                                                               const c_t<T>* __restrict__ m0, T w,
                                                               const c_t<T>* __restrict__ f, c_t<T>* __restrict__ u,
                                                               c_t<T>* __restrict__ r, const int* active) {
+  prefetch_block_planes<T>(g, m0, 1, 0);
+  prefetch_block_planes<T>(g, A, a_planes<DIM, AK>(), AK == 0 ? 0 : AK % 10);
   pdl_enter();
   if (active && !*active) return;
   constexpr int RA = AK == 0 ? 1 : AK % 10;
@@ -474,6 +498,7 @@ template <typename T, int DIM, int VR, int MB>
 __global__ void __launch_bounds__(BX* BY, MB) k_sweep_out(Geo g, MList m, const c_t<T>* __restrict__ M, T w,
                                                       const c_t<T>* __restrict__ r, const c_t<T>* in, c_t<T>* out,
                                                       const int* active) {
+  prefetch_block_planes<T>(g, M, m.n, 0);
   pdl_enter();
   if (active && !*active) return;
   const bool inb = interior_block<DIM>(g, m.rho);
@@ -490,6 +515,7 @@ template <typename T, int DIM, int VR, int MB>
 __global__ void __launch_bounds__(BX* BY, MB) k_sweep_out_sym(Geo g, SList m, const c_t<T>* __restrict__ M,
                                                       const T* __restrict__ wc, T w, const c_t<T>* __restrict__ r,
                                                       const c_t<T>* in, c_t<T>* out, const int* active) {
+  prefetch_block_planes<T>(g, M, m.n, m.rho);
   pdl_enter();
   if (active && !*active) return;
   const bool inb = interior_block<DIM>(g, m.rho);
@@ -507,6 +533,8 @@ __global__ void __launch_bounds__(BX* BY, MB) k_resid_sweep_diag(Geo g, T invh2,
                                                              const c_t<T>* __restrict__ m0, T w,
                                                              const c_t<T>* __restrict__ f, const c_t<T>* __restrict__ in,
                                                              c_t<T>* __restrict__ out, const int* active) {
+  prefetch_block_planes<T>(g, m0, 1, 0);
+  prefetch_block_planes<T>(g, A, a_planes<DIM, AK>(), AK == 0 ? 0 : AK % 10);
   pdl_enter();
   if (active && !*active) return;
   constexpr int RA = AK == 0 ? 1 : AK % 10;
@@ -652,6 +680,8 @@ __global__ void __launch_bounds__(BX* BY, MB) k_prolong_fused_2d(Geo gf, Geo gc,
                                                              const c_t<T>* __restrict__ f, const c_t<T>* __restrict__ m0,
                                                              T w, c_t<T>* __restrict__ out, c_t<T>* __restrict__ r,
                                                              const int* active) {
+  prefetch_block_planes<T>(gf, A, a_planes<2, AK>(), AK == 0 ? 0 : AK % 10);
+  if (DIAG) prefetch_block_planes<T>(gf, m0, 1, 0);
   pdl_enter();
   if (active && !*active) return;
   constexpr int RA = AK == 0 ? 1 : AK % 10;
