@@ -277,20 +277,50 @@ __global__ void __launch_bounds__(kRedBlock) k_gs_update(int N, const double2* _
   }
   if constexpr (LAST) {
     const bool last = reduce_last(make_double2(acc, 0.0), partials, gridDim.x, blockIdx.x, &st->counter, &st->nrm2);
-    if (last && threadIdx.x == 0) arnoldi_update(st, j, nullptr, st->scale[j]);
+    if (last) arnoldi_update_staged(st, j, st->scale[j]);
   }
 }
 
 
-__global__ void k_solve_y(KrylovState* __restrict__ st) {
+// y = H^{-1} g (upper triangular, k columns of the cycle) and the update
+// coefficients c_i = scale_i y_i.  For cycles of up to kSolveYStage columns
+// the block stages H, g and the scales in shared memory first, so the one
+// thread that runs the back substitution reads on-chip values; longer cycles
+// read them from global memory.  The same operations in the same order.
+constexpr int kSolveYThreads = 128, kSolveYStage = 32;
+__global__ void __launch_bounds__(kSolveYThreads) k_solve_y(KrylovState* __restrict__ st) {
+  __shared__ double2 hs[kSolveYStage][kSolveYStage + 1];
+  __shared__ double2 gs[kSolveYStage], ys[kSolveYStage];
+  __shared__ double sc[kSolveYStage];
   pdl_enter();
   if (st->st.done) return;
   const int k = st->kcyc;
+  if (k > kSolveYStage) {
+    if (threadIdx.x != 0) return;
+    for (int i = k - 1; i >= 0; --i) {
+      double2 acc = st->g[i];
+      for (int l = i + 1; l < k; ++l) acc = acc - cmul(st->H[i][l], st->y[l]);
+      st->y[i] = cdiv(acc, st->H[i][i]);
+      st->c[i] = st->scale[i] * st->y[i];
+    }
+    return;
+  }
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+    const int i = e / k, l = e - i * k;
+    if (l >= i) hs[i][l] = st->H[i][l];
+  }
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    gs[i] = st->g[i];
+    sc[i] = st->scale[i];
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
   for (int i = k - 1; i >= 0; --i) {
-    double2 acc = st->g[i];
-    for (int l = i + 1; l < k; ++l) acc = acc - cmul(st->H[i][l], st->y[l]);
-    st->y[i] = cdiv(acc, st->H[i][i]);
-    st->c[i] = st->scale[i] * st->y[i];          // once here instead of at every node
+    double2 acc = gs[i];
+    for (int l = i + 1; l < k; ++l) acc = acc - cmul(hs[i][l], ys[l]);
+    ys[i] = cdiv(acc, hs[i][i]);
+    st->y[i] = ys[i];
+    st->c[i] = sc[i] * ys[i];                     // once here instead of at every node
   }
 }
 
@@ -454,7 +484,7 @@ void run_cycle(Ctx& c, cudaStream_t s) {
     prof_end(c, pk, s);
   }
   HZ_LAUNCHED();
-  launch_pdl(k_solve_y, 1, 1, s, st);
+  launch_pdl(k_solve_y, 1, kSolveYThreads, s, st);
   launch_pdl(k_update_p<TZ>, nblk(N, 256), 256, s, N, Z, st, c.p);
   {
     auto kern = k_true_residual<TZ>;

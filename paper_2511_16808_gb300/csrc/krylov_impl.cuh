@@ -301,6 +301,57 @@ __device__ inline void arnoldi_update(KrylovState* st, int j, int* n_active = nu
   }
 }
 
+// arnoldi_update for one right-hand side, called by every thread of the last
+// block of a reduction: the block first stages the column's inputs (scales
+// and raw inner products, the previous rotations) in shared memory, then one
+// thread runs the same sequential chain on the staged values, so its steps
+// wait on shared memory instead of a global-memory round trip each.  Same
+// operations in the same order as arnoldi_update: bit-identical state.
+__device__ inline void arnoldi_update_staged(KrylovState* st, int j, double sj) {
+  __shared__ double2 hc[kMaxM + 1];
+  __shared__ double2 sn[kMaxM];
+  __shared__ double cs[kMaxM];
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
+  for (int i = tid; i <= j; i += nt) hc[i] = (sj * st->scale[i]) * st->h1[i];
+  for (int i = tid; i < j; i += nt) {
+    cs[i] = st->cs[i];
+    sn[i] = st->sn[i];
+  }
+  __syncthreads();
+  if (tid != 0) return;
+  const double hn = sqrt(st->nrm2.x);
+  double2 below = make_double2(sj * hn, 0.0);               // H[j+1][j]
+  for (int i = 0; i < j; ++i) {
+    const double2 a = hc[i], b = hc[i + 1];
+    const double c = cs[i];
+    const double2 sv = sn[i];
+    hc[i] = c * a + cmul(sv, b);
+    hc[i + 1] = cmul(make_double2(-sv.x, sv.y), a) + c * b;  // -conj(s) a + c b
+  }
+  double c;
+  double2 sv;
+  givens(hc[j], below, c, sv);
+  st->cs[j] = c;
+  st->sn[j] = sv;
+  hc[j] = c * hc[j] + cmul(sv, below);
+  for (int i = 0; i <= j; ++i) st->H[i][j] = hc[i];
+  st->H[j + 1][j] = make_double2(0, 0);
+  const double2 gj = st->g[j];
+  st->g[j + 1] = cmul(make_double2(-sv.x, sv.y), gj);
+  st->g[j] = c * gj;
+  st->st.iters += 1;
+  st->kcyc = j + 1;
+  st->st.relres_est = sqrt(cabs2(st->g[j + 1])) / st->bnorm;
+  if (!(hn > 0.0)) {
+    st->st.breakdown = 1;
+    st->scale[j + 1] = 0.0;
+  } else {
+    st->scale[j + 1] = 1.0 / hn;
+  }
+  if (st->st.relres_est < st->tol || st->st.iters >= st->max_iter || st->st.breakdown || st->kcyc >= st->m)
+    st->active = 0;
+}
+
 __device__ inline void restart_update(KrylovState* st, int* n_active = nullptr) {
   const double beta = sqrt(st->nrm2.x);
   st->st.relres_true = beta / st->bnorm;
