@@ -422,6 +422,20 @@ def extra_workload(name, args, stream):
     return out
 
 
+def extra_batched(args):
+    """The batched workload (config 4) in the same run, as extra keys: its
+    solves/s (device-timed), e2e, iterations, the one-at-a-time comparison and
+    the rooflines of its batched V-cycle and FP64 passes."""
+    import copy
+    a = copy.copy(args)
+    a.config, a.steps, a.warmup, a.no_cpu_baseline = "config4", max(1, min(args.steps, 2)), 1, True
+    d = run_batched(a)
+    keep = ("value", "unit", "ms_per_step", "steps", "solves_per_step", "converged", "relres_true_max", "iters",
+            "e2e", "one_at_a_time_mixed", "plain_fp64", "roofline", "roofline_second", "vcycle_roofline",
+            "autotune", "config")
+    return {k: d[k] for k in keep if k in d} if d else None
+
+
 def run_ours(args):
     import torch
     import workloads
@@ -567,6 +581,9 @@ def run_ours(args):
         }
         if args.config == "config2" and not args.no_extra:
             out["config3"] = extra_workload("config3", args, stream)
+            out["config1"] = extra_workload("config1", args, stream)
+            if world == 1:                       # the batched run is a one-process run of its own
+                out["config4"] = extra_batched(args)
     solver.close()
     if dist:
         dist.destroy_process_group()
