@@ -312,7 +312,7 @@ __device__ __forceinline__ auto box_Au_half(const Geo& g, const c_t<T>* __restri
                           (DIM == 2 || (z + dz >= 0 && z + dz < g.nz));
           qp = ok ? qp : q;
         }
-        constexpr long long NH = (long long)(2 * RZ + 1) * W * W - C;   // half planes stored
+        [[maybe_unused]] constexpr long long NH = (long long)(2 * RZ + 1) * W * W - C;   // half planes stored
         acc = cfma(P[HZ_AT(k * g.N + p, NH * g.N)], ld(qp), acc);
         if (s == C) continue;
         if (CHECK) {

@@ -110,7 +110,6 @@ __device__ __forceinline__ bool reduce_last(double2 acc, double2* __restrict__ p
   return true;
 }
 
-__device__ __forceinline__ int block_linear() { return (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x; }
 
 
 // Per-block partials of NV complex accumulators (block_sums, up to 4 vectors
