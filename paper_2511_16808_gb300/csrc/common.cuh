@@ -363,16 +363,26 @@ __device__ __forceinline__ void prefetch_l2_span(const V* a, long long e0, long 
 // The rows [y0, y0 + ny) x columns [x0, x0 + nx) of np planes of an nxg x nyg
 // grid (plane stride N elements), clipped to the grid, one (plane, row) per
 // thread step.
+// Element run [e0, e1] (from P) of task `task` = (plane s, row y0 + r) of a
+// plane-row prefetch, clipped to the grid; false when the row or the columns
+// lie outside it.  Host-callable so the clipping can be checked on the CPU.
+__host__ __device__ inline bool plane_row_run(int task, long long N, int nxg, int nyg, int x0, int nx, int y0, int ny,
+                                              long long& e0, long long& e1) {
+  const int xa = x0 > 0 ? x0 : 0, xb = (x0 + nx < nxg ? x0 + nx : nxg) - 1;
+  const int s = task / ny, y = y0 + (task - s * ny);
+  if (xb < xa || y < 0 || y >= nyg) return false;
+  const long long row = (long long)s * N + (long long)y * nxg;
+  e0 = row + xa;
+  e1 = row + xb;
+  return true;
+}
+
 template <typename V>
 __device__ __forceinline__ void prefetch_l2_planes(const V* P, int np, long long N, int nxg, int nyg, int x0, int nx,
                                                    int y0, int ny, int tid, int nth) {
-  const int xa = x0 > 0 ? x0 : 0, xb = (x0 + nx < nxg ? x0 + nx : nxg) - 1;
-  if (xb < xa) return;
   for (int task = tid; task < np * ny; task += nth) {
-    const int s = task / ny, y = y0 + (task - s * ny);
-    if (y < 0 || y >= nyg) continue;
-    const long long row = (long long)s * N + (long long)y * nxg;
-    prefetch_l2_run(P, row + xa, row + xb);
+    long long e0, e1;
+    if (plane_row_run(task, N, nxg, nyg, x0, nx, y0, ny, e0, e1)) prefetch_l2_run(P, e0, e1);
   }
 }
 
