@@ -198,11 +198,15 @@ hz_status hz_solve(hz_ctx* ctx, const void* q, void* p, int nrhs, hz_info* info,
  *                   cuda_stream.  q: unscaled source, c128, host (copied before
  *                   the call returns) or device (read by the queued work: keep it
  *                   unchanged until the solve has finished).
- *   hz_solve_step   looks at the status of the last queued restart cycle; if it
- *                   has not completed yet (block = 0) or the solve goes on, it
- *                   sets *done = 0 (queuing the next cycle in the second case);
- *                   *done = 1 once converged or out of iterations.  block = 1
- *                   waits for the status first.
+ *   hz_solve_step   looks at the status of the oldest queued restart cycle;
+ *                   if it has not completed yet (block = 0) or the solve goes
+ *                   on, it sets *done = 0 (in the second case queuing cycles so
+ *                   that two stay in flight: the device runs the next cycle
+ *                   while the host reads a status; a cycle queued after the
+ *                   solve has stopped does no work); *done = 1 once converged
+ *                   or out of iterations.  block = 1 waits for the status first.
+ *                   (While a kernel class is profiled, hz_profile_select, one
+ *                   cycle is queued at a time.)
  *   hz_solve_end    after *done = 1: p (c128, host or device) receives the
  *                   solution, ordered before later work on cuda_stream; info as
  *                   for hz_solve, HZ_ERR_NOT_CONVERGED likewise.
