@@ -358,6 +358,16 @@ hz_status hz_profile_read(const hz_ctx* ctx, double* total_ms, int64_t* launches
  * them.  Call it with no kernel of the library in flight. */
 hz_status hz_check_status(int* enabled, uint64_t* failures, uint64_t* first, int clear);
 
+/* The bounded device wait on its own (no counterpart in the paper; the test
+ * of the failure path that every spin-wait of the tensor-core kernels
+ * takes).  One thread waits up to `polls` (1..2^24) times for a phase of a
+ * fresh mbarrier; with arrive = 0 nothing arrives, so the wait gives up:
+ * *timed_out = 1 and HZ_ERR_TIMEOUT, the status the coarsest product returns
+ * when its copies or MMAs do not complete.  arrive != 0: the thread arrives
+ * first, *timed_out = 0, HZ_OK.  Synchronizes a private stream; the device
+ * stays usable either way. */
+hz_status hz_check_wait_timeout(long long polls, int arrive, int* timed_out);
+
 /* Measured arithmetic peak of the current device, the denominator of the
  * roofline fraction of the FP64 Krylov passes.  No counterpart in the paper:
  * a measurement hook.  kind 0: FP64 fused multiply-add (DFMA); kind 1: FP32

@@ -249,6 +249,22 @@ size_t tc_smem(int R) { return 1024 + (size_t)kStages * tc_stage_bytes(R); }
 
 }  // namespace
 
+// The bounded wait of the tensor-core kernels on its own: one thread waits
+// `polls` times for phase 0 of a fresh mbarrier (count 1) and records in
+// *err whether it gave up; with arrive != 0 it first arrives itself, so the
+// phase completes and the wait succeeds at once.
+__global__ void k_wait_probe(long long polls, int arrive, int* err) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x != 0) return;
+  tc::mbar_init(&bar, 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  if (arrive) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(tc::smem_u32(&bar))
+                 : "memory");
+  }
+  *err = tc::mbar_wait(&bar, 0, polls) ? 0 : 1;
+}
+
 bool coarse_tc_supported(const Ctx& c, int nrhs) {
   return c.mixed && (nrhs == 16 || nrhs == 32 || nrhs == 64) && c.tc_err != nullptr && c.tc_image != nullptr &&
          nrhs <= c.opts.nrhs_max;
@@ -300,3 +316,28 @@ void coarse_gemm_tc(Ctx& c, const void* f, void* u, const int* active, cudaStrea
 }
 
 }  // namespace hz
+
+using namespace hz;
+
+extern "C" hz_status hz_check_wait_timeout(long long polls, int arrive, int* timed_out) {
+  return guarded([&] {
+    require(timed_out != nullptr, "null output");
+    require(polls >= 1 && polls <= (1ll << 24), "polls must be in 1..2^24");
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) throw Error(HZ_ERR_NO_DEVICE, "no CUDA device");
+    cudaStream_t s;
+    HZ_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    int* err = nullptr;
+    HZ_CUDA(counted_malloc_async(&err, sizeof(int), s));
+    HZ_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+    k_wait_probe<<<1, 32, 0, s>>>(polls, arrive, err);
+    HZ_CUDA(cudaGetLastError());
+    int h = 0;
+    HZ_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    HZ_CUDA(cudaFreeAsync(err, s));
+    HZ_CUDA(cudaStreamSynchronize(s));
+    cudaStreamDestroy(s);
+    *timed_out = h;
+    if (h) throw Error(HZ_ERR_TIMEOUT, "the bounded device wait gave up (no arrival on the barrier)");
+  });
+}

@@ -32,7 +32,7 @@ PRECISION = {"fp64": 0, "mixed": 1}
 STATUS = {0: "HZ_OK", 1: "HZ_ERR_INVALID_ARG", 2: "HZ_ERR_OOM", 3: "HZ_ERR_CUDA",
           4: "HZ_ERR_NOT_CONVERGED", 5: "HZ_ERR_BREAKDOWN", 6: "HZ_ERR_TIMEOUT",
           7: "HZ_ERR_BUSY", 8: "HZ_ERR_NO_DEVICE"}
-HZ_OK, HZ_ERR_NOT_CONVERGED = 0, 4
+HZ_OK, HZ_ERR_NOT_CONVERGED, HZ_ERR_TIMEOUT = 0, 4, 6
 
 
 class hz_grid(C.Structure):
@@ -118,6 +118,7 @@ _SIGS = {
                          C.POINTER(C.c_double)], C.c_int),
     "hz_measure_peak": ([C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)], C.c_int),
     "hz_check_status": ([C.POINTER(C.c_int), C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), C.c_int], C.c_int),
+    "hz_check_wait_timeout": ([C.c_longlong, C.c_int, C.POINTER(C.c_int)], C.c_int),
     "hz_memory_stats": ([C.c_int, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)], C.c_int),
     "hz_context_info": ([_P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
     "hz_level_count": ([_P, C.POINTER(C.c_int)], C.c_int),
@@ -205,6 +206,14 @@ def _stream(s):
 
 def hz_abi_version() -> int:
     return lib.hz_abi_version()
+
+
+def hz_check_wait_timeout(polls: int, arrive: bool):
+    """(status, timed_out) of one bounded device wait (see hz.h)."""
+    t = C.c_int()
+    st = lib.hz_check_wait_timeout(int(polls), int(bool(arrive)), C.byref(t))
+    _check(st, "hz_check_wait_timeout", ok=(HZ_OK, HZ_ERR_TIMEOUT))
+    return st, bool(t.value)
 
 
 def hz_check_status(clear: bool = False) -> dict:

@@ -86,3 +86,28 @@ def test_tensor_core_variant_refused_where_not_supported():
     with pytest.raises(hz.HzError):
         hz.hz_coarse_solve_batch(gpu.ctx, f16, torch.empty_like(f16), 16, 1)
     gpu.close()
+
+
+def test_bounded_wait_gives_up_and_device_stays_usable():
+    """The spin-wait every bulk copy and MMA of the tensor-core kernel takes,
+    on its own: with nothing arriving on its barrier it gives up after the
+    poll limit and reports HZ_ERR_TIMEOUT (no hang, no trap); with the arrival
+    it succeeds at once; the device then runs the tensor-core product as
+    before."""
+    from paper_2511_16808_gb300 import hz
+    st, timed_out = hz.hz_check_wait_timeout(1000, False)
+    assert st == hz.HZ_ERR_TIMEOUT and timed_out
+    st, timed_out = hz.hz_check_wait_timeout(1000, True)
+    assert st == hz.HZ_OK and not timed_out
+    with pytest.raises(hz.HzError):
+        hz.hz_check_wait_timeout(0, False)               # poll limit out of range
+    orc, gpu = _pair(CASES[0])
+    nc = orc.hier[-1].A.shape[0]
+    rng = np.random.default_rng(9)
+    F = (rng.standard_normal((nc, 16)) + 1j * rng.standard_normal((nc, 16))).astype(np.complex64)
+    Fd = torch.tensor(F.ravel(), device="cuda")
+    U = torch.empty_like(Fd)
+    hz.hz_coarse_solve_batch(gpu.ctx, Fd, U, 16, 2)
+    ref = orc.hier[-1].lu.solve(F.astype(np.complex128))
+    assert np.max(np.abs(U.cpu().numpy().reshape(nc, 16) - ref)) <= 1e-4 * np.max(np.abs(ref))
+    gpu.close()
