@@ -56,7 +56,7 @@ def build(verbose: bool = False, force: bool = False, extra_flags=None, checked:
     lib = CHECKED_LIB if checked else LIB
     os.makedirs(out, exist_ok=True)
     nvcc = _nvcc()
-    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")]
+    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     headers.append(os.path.join(INCLUDE, "hz.h"))
     flags = FLAGS + list(extra_flags or []) + (["-DHZ_CHECKED"] if checked else [])
     jobs = []

@@ -39,6 +39,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "server_policy.h"
 
 namespace hz {
 namespace {
@@ -212,27 +213,17 @@ size_t request_bytes(const hz_grid& g, const hz_opts& o, int nrhs_max) {
 // holds the group's bytes.
 void form_group(hz_server* S, Request* r) {
   if (S->group_max < 2 || r->key == 0) return;
-  const long long N = grid_nodes(r->grid);
-  int cap = S->group_max;
-  while (cap > 1 && (double)N * cap * sizeof(double2) > (double)(1u << 30)) cap >>= 1;
+  const int cap = group_cap(S->group_max, grid_nodes(r->grid));
   std::vector<Request*> cand;
   for (const auto& e : S->adm.queue) {
     if ((int)cand.size() + 1 >= cap) break;
     Request* m = S->reqs[e.first].get();
     if (m->key == r->key && same_problem(*r, *m)) cand.push_back(m);
   }
-  int k = 1;
-  while (2 * k <= (int)cand.size() + 1) k *= 2;
   size_t bytes = 0;
-  for (; k >= 2; k /= 2) {
-    try {
-      bytes = request_bytes(r->grid, r->opts, k);
-    } catch (const Error&) {
-      return;                                       // kept alone
-    }
-    if (S->adm.in_use - r->held + bytes <= S->adm.budget) break;
-  }
-  if (k < 2) return;
+  const int k = group_size_for((int)cand.size(), S->adm.in_use, r->held, S->adm.budget,
+                               [&](int kk) { return request_bytes(r->grid, r->opts, kk); }, &bytes);
+  if (k < 2) return;                                // kept alone
   cand.resize(k - 1);
   r->members.assign(1, r);
   for (Request* m : cand) {
