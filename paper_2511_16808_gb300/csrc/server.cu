@@ -269,9 +269,13 @@ hz_status solve_group(hz_server* S, Request* r) {
   const hz_status st = hz_solve(r->ctx, Q.data(), P.data(), R, info.data(), r->stream);
   if (st != HZ_OK && st != HZ_ERR_NOT_CONVERGED) return st;
   for (int k = 0; k < R; ++k) {
-    Request* m = r->members[k];
-    double2* out = (double2*)m->p_out;
+    double2* out = (double2*)r->members[k]->p_out;
     for (long long p = 0; p < N; ++p) out[p] = P[(size_t)p * R + k];
+  }
+  // statuses under the lock, as hz_server_poll reads them
+  std::lock_guard<std::mutex> lk(S->mu);
+  for (int k = 0; k < R; ++k) {
+    Request* m = r->members[k];
     m->info = info[k];
     m->status = info[k].converged ? HZ_OK : HZ_ERR_NOT_CONVERGED;
   }
